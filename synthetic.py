@@ -1,0 +1,83 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module holds no arithmetic of the method: it only produces meshes (node
+coordinates), random coefficient vectors and random face states from seeds,
+with the shapes and value ranges of the workloads. The Taylor-Green field and
+every operator are computed separately by each implementation.
+
+Workloads (they stand in for the paper's cylinder / sphere / T3L1 / landing-gear
+meshes, which are not available): Taylor-Green vortex at Re = 1600 on the
+triply periodic cube [0, 2 pi]^3 with uniform hexahedra, modal P^k, k <= 4.
+"""
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+RE_TGV = 1600.0
+NU_TGV = 1.0 / RE_TGV
+AC_C = 1.0        # artificial-compressibility constant
+ETA = 7.0         # BR2 penalty, greater than the 6 faces of a hexahedron
+SEED_V = 1809     # Jacobian-action direction
+
+
+def nb(k):
+    """Number of modes of the total-degree-k space in 3D, C(k+3, 3)."""
+    return (k + 1) * (k + 2) * (k + 3) // 6
+
+
+def mode_degrees(k):
+    """Total degree of every mode in the hierarchical ordering (degree 0, then 1, ...)."""
+    out = []
+    for t in range(k + 1):
+        out += [t] * ((t + 1) * (t + 2) // 2)
+    return np.array(out)
+
+
+def uniform_nodes(n, length=TWO_PI):
+    return np.linspace(0.0, length, n + 1)
+
+
+def perturbed_nodes(n, length=TWO_PI, amp=0.25, seed=0):
+    """Node coordinates with each cell size scaled by a seeded factor in [1-amp, 1+amp]."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 + amp * (2.0 * rng.random(n) - 1.0)
+    h *= length / h.sum()
+    return np.concatenate([[0.0], np.cumsum(h)])
+
+
+def direction(ne, k, seed=SEED_V):
+    """Seeded Jacobian-action direction: N(0,1) modal coefficients scaled by 1/(1+degree)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((ne, 4, nb(k)))
+    return v / (1.0 + mode_degrees(k))[None, None, :]
+
+
+def perturbation(ne, k, amp, seed):
+    """Seeded state perturbation amp * N(0,1)/(1+degree) on every coefficient."""
+    return amp * direction(ne, k, seed)
+
+
+def face_states(n, seed, umax=0.9, pmax=1.0):
+    """Random left/right states (u[3], p) for Riemann-solver tests."""
+    rng = np.random.default_rng(seed)
+    uL = rng.uniform(-umax, umax, (n, 3))
+    uR = rng.uniform(-umax, umax, (n, 3))
+    pL = rng.uniform(-pmax, pmax, n)
+    pR = rng.uniform(-pmax, pmax, n)
+    return uL, pL, uR, pR
+
+
+# Benchmark / parity workloads: name -> (cells per axis, fine degree, p-levels)
+CONFIGS = {
+    "tgv4_p2": dict(n=4, k=2, levels=(2, 1)),
+    "tgv16_p4": dict(n=16, k=4, levels=(4, 2, 1)),
+    "tgv32_p4": dict(n=32, k=4, levels=(4, 2, 1)),
+    "tgv24_p4": dict(n=24, k=4, levels=(4, 2, 1)),
+}
+
+
+def acoustic_dt(n, k, cfl=50.0, c=AC_C, umax=1.0, length=TWO_PI):
+    """Time step for an acoustic CFL: cfl * h / ((2k+1) * (|u| + sqrt(|u|^2 + c^2)))."""
+    h = length / n
+    return cfl * h / ((2 * k + 1) * (umax + math.sqrt(umax * umax + c * c)))
