@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: implicit stages of the Taylor-Green vortex, 16^3 hexahedra, P4, 3-level p-multigrid.
+
+One step = one linearly implicit stage from the current state w (Sec. 2.2 with
+gamma = 1): the stage right-hand side g = -f_h(w), the linearisation of G at w
+(cached Riemann-flux Jacobian and velocities at the Gauss points), assembly of
+the preconditioner (element diagonal blocks + inverses on every level,
+inherited block-sparse coarse operators), FGMRES(30) on G dw = g with one
+P4 -> P2 -> P1 V-cycle (2 block-Jacobi sweeps per level, matrix-free fine
+level) per iteration to a true relative residual of 1e-8, and w <- w + dw.
+
+Prints one JSON line: value = seconds per implicit stage (device time, inputs
+resident in HBM, L2 flushed before every timed stage), plus the exact Jacobian
+action throughput (Jv GDOF/s), the roofline of the dominant kernel, the
+end-to-end time through the C ABI with host buffers, the SM clocks seen during
+the timed region, and the oracle timed on the host cores.
+
+--impl reference times the FP64 CPU oracle on the same workload and metric.
+Under torchrun every rank solves its own copy of the problem (replicas: the
+path has no exchange step on one GPU); the reported time is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "Jv GDOF/s and s per implicit stage to rel-res 1e-8: chosen form vs plain FP64"
+CONFIG = "tgv16_p4"
+RTOL = 1e-8
+# Algorithmic FP64 work of the exact Jacobian action at P4 per element (FLOP):
+# faces (3 per element) 241,500, volume terms (interpolation, corrected gradients,
+# pointwise fluxes, integration) 278,500; 0.52 MFLOP in total.
+FLOP_FACE_P4 = 241_500.0
+FLOP_VOL_P4 = 278_500.0
+# FP64 peak of a GB300 (no FP64 entry in the measured-peaks file): nominal 1.25 TFLOP/s
+# (152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz ~ 1.26 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+# Fine-level operator applications (residual or Jacobian action) of one stage on this
+# workload, as counted by the library on the GPU (dg_counters); used to scale the
+# oracle's measured cost of one application to seconds per stage.
+ORACLE_APPS_PER_STAGE_DEFAULT = 900
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def mesh_nodes(cfg):
+    n = cfg["n"]
+    return S.uniform_nodes(n), S.uniform_nodes(n), S.uniform_nodes(n)
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(cfg, max_seconds=30.0):
+    """Oracle cost of one exact Jacobian action on the full mesh (seconds), host cores."""
+    import oracle as O
+    xn, yn, zn = mesh_nodes(cfg)
+    m = O.Mesh(xn, yn, zn, cfg["k"], S.NU_TGV, S.AC_C, S.ETA)
+    w = O.project_tgv(m)
+    v = S.direction(m.ne, cfg["k"], S.SEED_V)
+    t0 = time.perf_counter()
+    O.jvp(m, w, v, 1.0)
+    t = time.perf_counter() - t0
+    return t, m.n
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    cfg = S.CONFIGS[args.config]
+    apps = args.oracle_apps
+    for _ in range(args.warmup):
+        oracle_sample(cfg)
+    times = []
+    for _ in range(args.steps):
+        t, ndof = oracle_sample(cfg)
+        times.append(t)
+    t_app = statistics.mean(times)
+    value = t_app * apps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/stage", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
+                                   "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
+                       "dofs": ndof, "l2": "oracle on host cores"},
+            "jv": {"value": ndof / t_app / 1e9, "unit": "GDOF/s", "mode": "exact"},
+            "cpu_baseline": {"value": value, "unit": "s/stage", "cores": 1, "kind": "oracle",
+                             "sample": "one exact Jacobian action of the FP64 oracle on the full 16^3 P4 state "
+                                       "per step (%.2f s), times the %d fine-operator applications of one stage"
+                                       % (t_app, apps)},
+            "e2e": {"value": value, "unit": "s/stage", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1809_00866_gb300 as P
+    if rank == 0:
+        P.build()
+    if world > 1:
+        dist.barrier()
+    P.build()
+    cfg = S.CONFIGS[args.config]
+    k, levels = cfg["k"], list(cfg["levels"])
+    xn, yn, zn = mesh_nodes(cfg)
+    dg = P.DG(xn, yn, zn, levels, S.NU_TGV, S.AC_C, S.ETA)
+    n0 = dg.n[0]
+    dt = S.acoustic_dt(cfg["n"], k)
+    inv = 1.0 / dt
+    opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=2, post_sweeps=2,
+                        coarse_sweeps=2, omega=1.0)
+    st = torch.cuda.current_stream()
+    w = dg.empty()
+    dg.dg_project_tgv(w)
+    f = dg.empty()
+    dw = dg.empty()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")  # 512 MB > L2
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    its_log = []
+    relres_log = []
+
+    def stage(w, phases=None):
+        e = [ev() for _ in range(5)] if phases is not None else None
+        if e: e[0].record(st)
+        dg.dg_residual(w, f)
+        f.neg_()
+        if e: e[1].record(st)
+        dg.dg_set_linearization(w, inv)
+        if e: e[2].record(st)
+        dg.dg_assemble()
+        if e: e[3].record(st)
+        info, rc = dg.fgmres_solve(f, dw, opts)
+        if rc != P.DG_OK:
+            raise RuntimeError("stage did not converge: rc %d relres %.3e" % (rc, info.true_relres))
+        w.add_(dw)
+        if e:
+            e[4].record(st)
+            phases.append(e)
+        its_log.append(info.its)
+        relres_log.append(info.true_relres)
+
+    for _ in range(args.warmup):
+        stage(w)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    clk.start()
+    l0, a0 = dg.dg_counters()
+    times = []
+    phases = []
+    its_log.clear()
+    relres_log.clear()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        stage(w, phases)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    l1, a1 = dg.dg_counters()
+    clocks = clk.stop()
+    t_total = sum(times)
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    stages_all = args.steps * world
+    s_per_stage = t_total / stages_all
+    names = ["residual", "linearize", "assemble", "solve"]
+    breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
+                 for i, nm in enumerate(names)}
+
+    # --- exact Jacobian action throughput and the roofline of its kernels (L2 flushed each time)
+    v = torch.from_numpy(S.direction(dg.ne, k, S.SEED_V)).cuda()
+    out = dg.empty()
+    dg.dg_set_linearization(w, inv)
+    for _ in range(5):
+        dg.dg_jvp(v, out)
+    jv_times = []
+    dg.dg_profile(True)
+    dg.dg_profile_read()
+    for _ in range(args.jv_reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        dg.dg_jvp(v, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        jv_times.append(e0.elapsed_time(e1) / 1e3)
+    prof = dg.dg_profile_read()
+    dg.dg_profile(False)
+    t_jv = statistics.median(jv_times)
+    jv_gdofs = n0 / t_jv / 1e9
+    face_ms = prof["face_tan"][0] / max(1, prof["face_tan"][1])
+    vol_ms = prof["vol_tan"][0] / max(1, prof["vol_tan"][1])
+    if face_ms >= vol_ms:
+        kname, kms, kflop = "face_kernel<4,tangent>", face_ms, FLOP_FACE_P4 * dg.ne
+    else:
+        kname, kms, kflop = "vol_kernel<4,tangent>", vol_ms, FLOP_VOL_P4 * dg.ne
+    achieved = kflop / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (not in the measured-peaks file)",
+                "kernel_ms": {"face_tan": face_ms, "vol_tan": vol_ms}}
+
+    # --- end to end through the C ABI: state from pinned host memory, result back to the host
+    host_w = w.detach().cpu().pin_memory()
+    host_out = torch.empty_like(host_w).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        wd = host_w.to("cuda", non_blocking=True)
+        stage(wd)
+        host_out.copy_(wd, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    e2e = {"value": statistics.mean(e2e_times), "unit": "s/stage", "h2d_bytes_per_step": n0 * 8,
+           "d2h_bytes_per_step": n0 * 8}
+
+    apps_per_stage = (a1 - a0) / max(1, args.steps)
+    line = {"metric": METRIC, "value": s_per_stage, "unit": "s/stage", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
+                                   "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
+                       "dofs": n0, "dt": dt, "solver": "FGMRES(30) + MG_V, 2 block-Jacobi sweeps per level",
+                       "l2": "flushed (512 MB write) before every timed stage and Jacobian action",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "jv": {"value": jv_gdofs, "unit": "GDOF/s", "mode": "exact (tangent)", "ms": 1e3 * t_jv},
+            "stage": {"breakdown_s": breakdown, "fgmres_its": its_log, "true_relres": relres_log,
+                      "operator_applications": apps_per_stage},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": (l1 - l0) // max(1, args.steps)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_app, _ = oracle_sample(cfg)
+        line["cpu_baseline"] = {"value": t_app * apps_per_stage, "unit": "s/stage", "cores": 1, "kind": "oracle",
+                                "sample": "one exact Jacobian action of the FP64 oracle on the full 16^3 P4 state "
+                                          "(%.2f s) times the %d fine-operator applications of one GPU stage"
+                                          % (t_app, apps_per_stage)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    dg.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default=CONFIG, choices=sorted(S.CONFIGS))
+    ap.add_argument("--jv-reps", type=int, default=30)
+    ap.add_argument("--oracle-apps", type=int, default=ORACLE_APPS_PER_STAGE_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

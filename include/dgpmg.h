@@ -1,0 +1,212 @@
+/*
+ * dgpmg.h - C ABI of the GB300 (sm_103a) implementation of the matrix-free
+ * p-multigrid discontinuous Galerkin hot path of
+ *   Franciolini, Botti, Colombo, Crivellini, "p-Multigrid matrix-free
+ *   discontinuous Galerkin solution strategies for the under-resolved
+ *   simulation of incompressible turbulent flows", arXiv 1809.00866.
+ *
+ * The library applies the implicit-stage operator G = M/(gamma dt) + dR/dw
+ * (Eq. (rosSysOp)) of the DG discretisation of the incompressible
+ * Navier-Stokes equations (Eq. (NSdiscr), residual Eq. (NSdiscrRes)) on a
+ * periodic box of hexahedra with an orthonormal modal P^k basis, and the
+ * p-multigrid preconditioned FGMRES that solves G dw = g (Sec. 2.3-2.4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All vector arguments are DEVICE pointers owned by the caller: contiguous
+ *    FP64 arrays laid out [element][variable u, v, w, p][mode] with
+ *    element e = i + nx*(j + ny*k) and N_b(k) = (k+1)(k+2)(k+3)/6 modes per
+ *    variable, ordered by total degree, then by the x exponent descending,
+ *    then by the y exponent descending. A level-l vector has N_e*4*N_b(k_l)
+ *    entries. Pointers must be 8-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is enqueued on it; a call returns before the GPU finishes
+ *    unless its description says it synchronises.
+ *  - The handle owns all internal workspaces (basis tables, linearisation
+ *    caches, element block inverses, block-sparse coarse operators, Krylov
+ *    bases) and frees them in dg_destroy. Calls on one handle must not
+ *    overlap in time (one host thread, one stream at a time).
+ *  - Every call returns DG_OK (0) or an error code; nothing aborts, throws
+ *    or traps. dg_last_error() gives a text. Device-side conditions (a
+ *    Riemann iteration that did not converge, a non-finite value) are
+ *    recorded in a status word that dg_get_status() reads.
+ */
+#ifndef DGPMG_H
+#define DGPMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_ARG 1            /* invalid argument (size, level, pointer, option) */
+#define DG_ERR_CUDA 2           /* a CUDA runtime call failed */
+#define DG_ERR_NOT_CONVERGED 3  /* FGMRES did not reach the tolerance within maxit */
+#define DG_ERR_RIEMANN 4        /* the star-state iteration did not converge somewhere */
+#define DG_ERR_NONFINITE 5      /* a non-finite value was produced */
+#define DG_ERR_BOUNDS 6         /* an index check failed */
+#define DG_ERR_STATE 7          /* a call was made before what it needs (linearisation, assembly) */
+
+/* Status bits reported by dg_get_status. */
+#define DG_STATUS_RIEMANN 1u
+#define DG_STATUS_NONFINITE 2u
+
+#define DG_JVP_TANGENT 0 /* exact Jacobian action, Eqs. (jacTrilFnotNU), (jacTrilnu) */
+#define DG_JVP_FD 1      /* finite-difference action, Eqs. (matrix-free), (epsdef) */
+
+#define DG_MAX_LEVELS 4
+
+typedef struct dg_params {
+  int nx, ny, nz;        /* cells per axis of the periodic box, each >= 2 */
+  const double* xn;      /* HOST arrays of nx+1, ny+1, nz+1 increasing node coordinates; copied */
+  const double* yn;
+  const double* zn;
+  int nlevels;           /* p-multigrid levels, 1..DG_MAX_LEVELS */
+  int k[DG_MAX_LEVELS];  /* polynomial degree per level: 1 <= k[l] <= 4, strictly decreasing */
+  double nu;             /* kinematic viscosity (> 0) */
+  double ac_c;           /* artificial-compressibility constant c of the Riemann flux (> 0) */
+  double eta;            /* BR2 penalty eta_sigma (> 6 for hexahedra, Sec. 2.1) */
+} dg_params;
+
+typedef struct dg_handle dg_handle;
+
+/* Solver options of fgmres_solve. */
+#define DG_PREC_NONE 0
+#define DG_PREC_VCYCLE 1  /* one MG_V cycle (Algorithm 2) per outer iteration */
+#define DG_PREC_FULLV 2   /* one MG_full cycle (Algorithm 3) per outer iteration */
+
+typedef struct dg_solve_opts {
+  int restart;       /* Krylov subspace size m before a restart (1..64) */
+  int maxit;         /* maximum number of outer iterations */
+  double rtol;       /* stop when ||g - G x||_2 <= rtol * ||g - G x0||_2 (recurrence estimate, then checked) */
+  int fixed_its;     /* > 0: run exactly this many iterations, no early exit */
+  int precond;       /* DG_PREC_* */
+  int pre_sweeps;    /* block-Jacobi sweeps before the coarse correction on every non-coarsest level */
+  int post_sweeps;   /* ... after it */
+  int coarse_sweeps; /* block-Jacobi sweeps from zero that make the coarsest-level SOLVE */
+  double omega;      /* block-Jacobi damping (0, 1] */
+  int jvp_mode;      /* DG_JVP_TANGENT or DG_JVP_FD for the fine-level G products of the outer solve */
+  int x0_is_zero;    /* 1: x holds no initial guess (treated as 0, not read) */
+} dg_solve_opts;
+
+typedef struct dg_solve_info {
+  int its;              /* outer iterations performed */
+  int status;           /* DG_OK or DG_ERR_NOT_CONVERGED */
+  double r0;            /* ||g - G x0||_2 */
+  double relres_est;    /* recurrence estimate at exit / r0 */
+  double true_relres;   /* ||g - G x||_2 / r0 recomputed with the exact G at exit */
+  double rho;           /* convergence factor exp(ln(true_relres)/its), Appendix B */
+} dg_solve_info;
+
+/* ---------------------------------------------------------------- handle */
+
+/* Create a handle: copies the mesh, builds the basis/quadrature tables of every
+ * level (Gauss-Legendre with k+1 points per direction, Sec. 2.1), and
+ * allocates all workspaces on the current device. Synchronises. */
+int dg_create(const dg_params* p, dg_handle** out);
+
+/* Free everything the handle owns. Synchronises the device. h may be NULL. */
+int dg_destroy(dg_handle* h);
+
+/* Text of the last error on h (or of the last failed dg_create when h is NULL). */
+const char* dg_last_error(const dg_handle* h);
+
+/* Size of level lvl: modes per variable and vector length N_e*4*N_b. */
+int dg_level_size(const dg_handle* h, int lvl, int* nb, long long* n);
+
+/* Read and clear the device status word (DG_STATUS_* bits). Synchronises `stream`. */
+int dg_get_status(dg_handle* h, unsigned* status, void* stream);
+
+/* ------------------------------------------------------------- operators */
+
+/* w <- L2 projection (Gauss rule) of the Taylor-Green vortex
+ * u = sin x cos y cos z, v = -cos x sin y cos z, w = 0,
+ * p = (cos 2x + cos 2y)(cos 2z + 2)/16 onto the fine level. */
+int dg_project_tgv(dg_handle* h, double* w, void* stream);
+
+/* f <- f_h(w; phi_m e_i) for every test function (Eq. (NSdiscrRes)): volume
+ * terms with the BR2 corrected gradient grad u - R^K(u), face terms with the
+ * exact artificial-compressibility Riemann flux and the BR2 viscous flux
+ * F^nu({grad u - eta r^s([u])}) (Eq. (vflux), Sec. 2.1). Fine level. w and f
+ * must not alias. */
+int dg_residual(dg_handle* h, const double* w, double* f, void* stream);
+
+/* Fix the linearisation state of G: caches w, f_h(w), ||w||_2, the velocity
+ * at the volume quadrature points and the Jacobian of the Riemann flux at the
+ * face points, and sets 1/(gamma dt) (>= 0). Synchronises (reads ||w||). */
+int dg_set_linearization(dg_handle* h, const double* w, double inv_gamma_dt, void* stream);
+
+/* out <- G v = J(w) v + (1/(gamma dt)) M v on the fine level, M the
+ * velocity-only mass form (Eq. (massBil)). mode DG_JVP_TANGENT: exact
+ * linearisation (Eqs. (jacTrilFnotNU), (jacTrilnu)); DG_JVP_FD:
+ * (f(w + D v) - f(w))/D with D = 1e-9 sqrt(1 + ||w||)/||v|| (Eqs.
+ * (matrix-free), (epsdef)). Needs dg_set_linearization. v and out must not alias. */
+int dg_jvp(dg_handle* h, const double* v, double* out, int mode, void* stream);
+
+/* Assemble the preconditioner at the current linearisation: the element
+ * diagonal blocks of G on every level and their inverses (element-wise block
+ * Jacobi, Sec. 2.3), and the inherited block-sparse coarse operators of levels
+ * >= 1 (Galerkin projection = sub-block extraction with a hierarchical
+ * orthonormal basis, Eq. (GalProj)); off-diagonal blocks are built at the
+ * degree of level 1 only (Sec. 2.4.3). Synchronises. */
+int dg_assemble(dg_handle* h, void* stream);
+
+/* ------------------------------------------------------------ p-multigrid */
+
+/* xc <- restriction of level-lvl vector xf to level lvl+1 (L2 projection =
+ * keep the leading modes, Sec. 2.4.1). */
+int pmg_restrict(dg_handle* h, int lvl, const double* xf, double* xc, void* stream);
+
+/* xf <- xf + prolongation of level-(lvl+1) vector xc (injection = zero-pad, Sec. 2.4.1). */
+int pmg_prolong(dg_handle* h, int lvl, const double* xc, double* xf, void* stream);
+
+/* `sweeps` damped element-block-Jacobi iterations x <- x + omega D^{-1}(g - G x)
+ * on level lvl (lvl 0: G v matrix-free, exact mode; lvl >= 1: block-sparse G).
+ * Needs dg_assemble. x is read and updated in place. */
+int block_jacobi_smooth(dg_handle* h, int lvl, const double* g, double* x, int sweeps, double omega,
+                        void* stream);
+
+/* y <- alpha G_lvl x + beta y with the assembled block-sparse coarse operator
+ * of level lvl >= 1 (diagonal + one block per face). */
+int bsr_spmv(dg_handle* h, int lvl, double alpha, const double* x, double beta, double* y, void* stream);
+
+/* x <- MG_V(0, g, 0) (Algorithm 2) with the smoothing options of opts; the
+ * coarsest-level SOLVE is opts->coarse_sweeps block-Jacobi sweeps from zero. */
+int pmg_vcycle(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, void* stream);
+
+/* Solve G x = g with right-preconditioned flexible GMRES(restart) (Sec.
+ * 2.4.3, Saad 1993), classical Gram-Schmidt with one re-orthogonalisation,
+ * FP64 throughout. x holds the initial guess unless opts->x0_is_zero.
+ * Synchronises. info may be NULL. Returns DG_ERR_NOT_CONVERGED (with x the
+ * last iterate) if the tolerance was not met. */
+int fgmres_solve(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,
+                 void* stream);
+
+/* --------------------------------------------------------- instrumentation
+ * The paper profiles its solver per linear system (Sec. 3.1: code profiling
+ * over 10 time steps); these calls expose the same information per kernel. */
+
+/* Kernel classes timed by the profiler. */
+#define DG_PROF_FACE_RES 0  /* face pass of f_h (and of the linearisation) */
+#define DG_PROF_VOL_RES 1   /* volume pass of f_h */
+#define DG_PROF_FACE_TAN 2  /* face pass of the exact Jacobian action */
+#define DG_PROF_VOL_TAN 3   /* volume pass of the exact Jacobian action */
+#define DG_PROF_N 4
+
+/* Counters since dg_create: kernels launched by the library, and applications
+ * of the fine-level operator (residual or Jacobian action). Host-only, no sync. */
+int dg_counters(const dg_handle* h, long long* kernel_launches, long long* operator_applications);
+
+/* enable != 0: bracket every launch of the timed kernel classes with CUDA
+ * events recorded on the launching stream. Costs two event records per launch. */
+int dg_profile(dg_handle* h, int enable);
+
+/* Accumulated device time (ms) and launch count per kernel class since the
+ * last read (arrays of DG_PROF_N entries); resets them. Synchronises the
+ * device. */
+int dg_profile_read(dg_handle* h, double* ms, long long* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGPMG_H */

@@ -1,0 +1,239 @@
+"""GB300 (sm_103a) implementation of the matrix-free p-multigrid DG hot path of arXiv 1809.00866.
+
+The compute path is the C-ABI CUDA library ``libdgpmg.so`` (``include/dgpmg.h``);
+this package only builds it, loads it with ctypes and marshals torch tensors
+(device memory) and CUDA streams into its plain-pointer calls. Every step of
+the path runs in the library's kernels. There is no CPU fallback: loading
+fails loudly when the library is missing or no GPU is present.
+"""
+import ctypes
+import os
+
+from ._build_lib import LIB, build  # noqa: F401
+
+DG_OK = 0
+DG_ERR_ARG = 1
+DG_ERR_CUDA = 2
+DG_ERR_NOT_CONVERGED = 3
+DG_ERR_RIEMANN = 4
+DG_ERR_NONFINITE = 5
+DG_ERR_BOUNDS = 6
+DG_ERR_STATE = 7
+DG_STATUS_RIEMANN = 1
+DG_STATUS_NONFINITE = 2
+DG_JVP_TANGENT = 0
+DG_JVP_FD = 1
+DG_PREC_NONE = 0
+DG_PREC_VCYCLE = 1
+DG_PREC_FULLV = 2
+DG_MAX_LEVELS = 4
+
+# Every exported symbol of include/dgpmg.h
+EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_status", "dg_project_tgv",
+           "dg_residual", "dg_set_linearization", "dg_jvp", "dg_assemble", "pmg_restrict", "pmg_prolong",
+           "block_jacobi_smooth", "bsr_spmv", "pmg_vcycle", "fgmres_solve", "dg_counters", "dg_profile",
+           "dg_profile_read")
+DG_PROF_N = 4
+PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan")
+
+
+class DgParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("xn", ctypes.POINTER(ctypes.c_double)), ("yn", ctypes.POINTER(ctypes.c_double)),
+                ("zn", ctypes.POINTER(ctypes.c_double)), ("nlevels", ctypes.c_int),
+                ("k", ctypes.c_int * DG_MAX_LEVELS), ("nu", ctypes.c_double), ("ac_c", ctypes.c_double),
+                ("eta", ctypes.c_double)]
+
+
+class DgSolveOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("fixed_its", ctypes.c_int), ("precond", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
+                ("post_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("omega", ctypes.c_double),
+                ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int)]
+
+
+class DgSolveInfo(ctypes.Structure):
+    _fields_ = [("its", ctypes.c_int), ("status", ctypes.c_int), ("r0", ctypes.c_double),
+                ("relres_est", ctypes.c_double), ("true_relres", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libdgpmg.so (build it first with ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError("dgpmg CUDA library not built (%s); run paper_1809_00866_gb300.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.dg_create.argtypes = [ctypes.POINTER(DgParams), ctypes.POINTER(vp)]
+    L.dg_destroy.argtypes = [vp]
+    L.dg_last_error.argtypes = [vp]
+    L.dg_last_error.restype = ctypes.c_char_p
+    L.dg_level_size.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+    L.dg_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint), vp]
+    L.dg_project_tgv.argtypes = [vp, vp, vp]
+    L.dg_residual.argtypes = [vp, vp, vp, vp]
+    L.dg_set_linearization.argtypes = [vp, vp, d, vp]
+    L.dg_jvp.argtypes = [vp, vp, vp, i, vp]
+    L.dg_assemble.argtypes = [vp, vp]
+    L.pmg_restrict.argtypes = [vp, i, vp, vp, vp]
+    L.pmg_prolong.argtypes = [vp, i, vp, vp, vp]
+    L.block_jacobi_smooth.argtypes = [vp, i, vp, vp, i, d, vp]
+    L.bsr_spmv.argtypes = [vp, i, d, vp, d, vp, vp]
+    L.pmg_vcycle.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), vp]
+    L.fgmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), ctypes.POINTER(DgSolveInfo), vp]
+    L.dg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.dg_profile.argtypes = [vp, i]
+    L.dg_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    for name in EXPORTS:
+        if name != "dg_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dgpmg error %d: %s" % (code, msg))
+        self.code = code
+
+
+def solve_opts(restart=30, maxit=200, rtol=1e-8, fixed_its=0, precond=DG_PREC_VCYCLE, pre_sweeps=2,
+               post_sweeps=2, coarse_sweeps=2, omega=1.0, jvp_mode=DG_JVP_TANGENT, x0_is_zero=1):
+    return DgSolveOpts(restart, maxit, rtol, fixed_its, precond, pre_sweeps, post_sweeps, coarse_sweeps, omega,
+                       jvp_mode, x0_is_zero)
+
+
+class DG:
+    """One solver handle (mesh, levels, workspaces) on the current CUDA device.
+
+    Methods mirror the C ABI (same names, same order of arguments) and take
+    contiguous float64 CUDA tensors laid out [element][u, v, w, p][mode].
+    """
+
+    def __init__(self, xn, yn, zn, levels, nu, ac_c=1.0, eta=7.0):
+        import numpy as np
+        self._L = load()
+        self._nodes = [np.ascontiguousarray(a, dtype=np.float64) for a in (xn, yn, zn)]
+        P = ctypes.POINTER(ctypes.c_double)
+        ks = (ctypes.c_int * DG_MAX_LEVELS)(*(list(levels) + [0] * (DG_MAX_LEVELS - len(levels))))
+        self.params = DgParams(len(xn) - 1, len(yn) - 1, len(zn) - 1,
+                               self._nodes[0].ctypes.data_as(P), self._nodes[1].ctypes.data_as(P),
+                               self._nodes[2].ctypes.data_as(P), len(levels), ks, nu, ac_c, eta)
+        h = ctypes.c_void_p()
+        rc = self._L.dg_create(ctypes.byref(self.params), ctypes.byref(h))
+        if rc != DG_OK:
+            raise DgError(rc, self._L.dg_last_error(None).decode())
+        self.h = h
+        self.levels = list(levels)
+        self.ne = self.params.nx * self.params.ny * self.params.nz
+        self.nb = []
+        self.n = []
+        for lvl in range(len(levels)):
+            nb = ctypes.c_int()
+            n = ctypes.c_longlong()
+            self._chk(self._L.dg_level_size(self.h, lvl, ctypes.byref(nb), ctypes.byref(n)))
+            self.nb.append(nb.value)
+            self.n.append(n.value)
+
+    # -- helpers
+    def _chk(self, rc):
+        if rc != DG_OK:
+            raise DgError(rc, self._L.dg_last_error(self.h).decode())
+        return rc
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _ptr(self, t, lvl=0):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        if t.numel() != self.n[lvl]:
+            raise ValueError("expected %d entries on level %d, got %d" % (self.n[lvl], lvl, t.numel()))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty(self, lvl=0):
+        import torch
+        return torch.empty((self.ne, 4, self.nb[lvl]), dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI, one method per entry point
+    def dg_get_status(self, stream=None):
+        s = ctypes.c_uint()
+        self._chk(self._L.dg_get_status(self.h, ctypes.byref(s), self._stream(stream)))
+        return s.value
+
+    def dg_project_tgv(self, w, stream=None):
+        self._chk(self._L.dg_project_tgv(self.h, self._ptr(w), self._stream(stream)))
+
+    def dg_residual(self, w, f, stream=None):
+        self._chk(self._L.dg_residual(self.h, self._ptr(w), self._ptr(f), self._stream(stream)))
+
+    def dg_set_linearization(self, w, inv_gamma_dt, stream=None):
+        self._chk(self._L.dg_set_linearization(self.h, self._ptr(w), float(inv_gamma_dt), self._stream(stream)))
+
+    def dg_jvp(self, v, out, mode=DG_JVP_TANGENT, stream=None):
+        self._chk(self._L.dg_jvp(self.h, self._ptr(v), self._ptr(out), int(mode), self._stream(stream)))
+
+    def dg_assemble(self, stream=None):
+        self._chk(self._L.dg_assemble(self.h, self._stream(stream)))
+
+    def pmg_restrict(self, lvl, xf, xc, stream=None):
+        self._chk(self._L.pmg_restrict(self.h, lvl, self._ptr(xf, lvl), self._ptr(xc, lvl + 1), self._stream(stream)))
+
+    def pmg_prolong(self, lvl, xc, xf, stream=None):
+        self._chk(self._L.pmg_prolong(self.h, lvl, self._ptr(xc, lvl + 1), self._ptr(xf, lvl), self._stream(stream)))
+
+    def block_jacobi_smooth(self, lvl, g, x, sweeps, omega=1.0, stream=None):
+        self._chk(self._L.block_jacobi_smooth(self.h, lvl, self._ptr(g, lvl), self._ptr(x, lvl), int(sweeps),
+                                              float(omega), self._stream(stream)))
+
+    def bsr_spmv(self, lvl, alpha, x, beta, y, stream=None):
+        self._chk(self._L.bsr_spmv(self.h, lvl, float(alpha), self._ptr(x, lvl), float(beta), self._ptr(y, lvl),
+                                   self._stream(stream)))
+
+    def pmg_vcycle(self, g, x, opts=None, stream=None):
+        o = opts or solve_opts()
+        self._chk(self._L.pmg_vcycle(self.h, self._ptr(g), self._ptr(x), ctypes.byref(o), self._stream(stream)))
+
+    def dg_counters(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        self._chk(self._L.dg_counters(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def dg_profile(self, enable=True):
+        self._chk(self._L.dg_profile(self.h, 1 if enable else 0))
+
+    def dg_profile_read(self):
+        ms = (ctypes.c_double * DG_PROF_N)()
+        cnt = (ctypes.c_longlong * DG_PROF_N)()
+        self._chk(self._L.dg_profile_read(self.h, ms, cnt))
+        return {PROF_NAMES[i]: (ms[i], cnt[i]) for i in range(DG_PROF_N)}
+
+    def fgmres_solve(self, g, x, opts=None, stream=None, check=True):
+        o = opts or solve_opts()
+        info = DgSolveInfo()
+        rc = self._L.fgmres_solve(self.h, self._ptr(g), self._ptr(x), ctypes.byref(o), ctypes.byref(info),
+                                  self._stream(stream))
+        if check and rc not in (DG_OK, DG_ERR_NOT_CONVERGED):
+            self._chk(rc)
+        return info, rc

@@ -1,0 +1,405 @@
+// Handle management, basis/quadrature tables and the operator entry points of the C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+static thread_local std::string g_create_error;
+
+int fail(Handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+// ----------------------------------------------------- host basis tables
+// Legendre polynomial P_n(x) and derivative via P'_n = n (x P_n - P_{n-1}) / (x^2 - 1)
+// (interior points only; the face tables evaluate values only).
+static void legendre_pair(int n, double x, double* p, double* dp) {
+  double pm1 = 1.0, pn = x;
+  if (n == 0) { *p = 1.0; if (dp) *dp = 0.0; return; }
+  for (int j = 2; j <= n; ++j) {
+    const double pj = ((2 * j - 1) * x * pn - (j - 1) * pm1) / j;
+    pm1 = pn;
+    pn = pj;
+  }
+  *p = pn;
+  if (dp) *dp = n * (x * pn - pm1) / (x * x - 1.0);
+}
+
+// Gauss-Legendre rule on [-1,1] (ascending nodes): Newton from Chebyshev-like guesses.
+static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double t = -std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+    double p, dp;
+    for (int it = 0; it < 60; ++it) {
+      legendre_pair(n, t, &p, &dp);
+      const double step = p / dp;
+      t -= step;
+      if (std::fabs(step) < 1e-17) break;
+    }
+    legendre_pair(n, t, &p, &dp);
+    x[i] = t;
+    w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+static double phat1(int n, double x) {
+  double p;
+  legendre_pair(n, x, &p, nullptr);
+  return std::sqrt((2.0 * n + 1.0) * 0.5) * p;
+}
+
+// Hierarchical ordering of the total-degree modes: degree 0, 1, ..., k; within a
+// degree the x exponent descending, then the y exponent descending.
+static std::vector<int> mode_list(int k) {
+  std::vector<int> m;
+  for (int t = 0; t <= k; ++t)
+    for (int a = t; a >= 0; --a)
+      for (int b = t - a; b >= 0; --b) {
+        m.push_back(a);
+        m.push_back(b);
+        m.push_back(t - a - b);
+      }
+  return m;
+}
+
+template <class T>
+static int upload(Handle* h, T** dst, const std::vector<T>& src) {
+  DG_CUDA(h, cudaMalloc((void**)dst, sizeof(T) * (src.empty() ? 1 : src.size())));
+  if (!src.empty()) DG_CUDA(h, cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+static int build_tables(Handle* h, int k) {
+  Tables& T = h->tab;
+  T.k = k;
+  T.nb = nb_of(k);
+  T.n1 = k + 1;
+  T.nq = T.n1 * T.n1 * T.n1;
+  T.nqf = T.n1 * T.n1;
+  const int nb = T.nb, n1 = T.n1;
+  std::vector<double> xg, wg;
+  gauss_rule(n1, xg, wg);
+  const std::vector<int> md = mode_list(k);
+  std::vector<double> Bv((size_t)T.nq * nb), wv(T.nq), Bf((size_t)6 * T.nqf * nb), wf(T.nqf);
+  for (int q0 = 0; q0 < n1; ++q0)
+    for (int q1 = 0; q1 < n1; ++q1)
+      for (int q2 = 0; q2 < n1; ++q2) {
+        const int q = (q0 * n1 + q1) * n1 + q2;
+        wv[q] = wg[q0] * wg[q1] * wg[q2];
+        const double xi[3] = {xg[q0], xg[q1], xg[q2]};
+        for (int m = 0; m < nb; ++m)
+          Bv[(size_t)q * nb + m] = phat1(md[3 * m], xi[0]) * phat1(md[3 * m + 1], xi[1]) * phat1(md[3 * m + 2], xi[2]);
+      }
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      for (int q1 = 0; q1 < n1; ++q1)
+        for (int q2 = 0; q2 < n1; ++q2) {
+          const int q = q1 * n1 + q2;
+          wf[q] = wg[q1] * wg[q2];
+          double xi[3];
+          xi[d] = side == 0 ? 1.0 : -1.0;
+          xi[(d + 1) % 3] = xg[q1];
+          xi[(d + 2) % 3] = xg[q2];
+          for (int m = 0; m < nb; ++m)
+            Bf[(((size_t)d * 2 + side) * T.nqf + q) * nb + m] =
+                phat1(md[3 * m], xi[0]) * phat1(md[3 * m + 1], xi[1]) * phat1(md[3 * m + 2], xi[2]);
+        }
+  // d/dxi P_hat_a = sum_{a' < a, a - a' odd} sqrt((2a+1)(2a'+1)) P_hat_a'
+  const int W = Tables::kDw;
+  std::vector<int> ri((size_t)3 * nb * W, 0), ci((size_t)3 * nb * W, 0);
+  std::vector<double> rv((size_t)3 * nb * W, 0.0), cv((size_t)3 * nb * W, 0.0);
+  std::vector<int> rc((size_t)3 * nb, 0), cc((size_t)3 * nb, 0);
+  for (int b = 0; b < 3; ++b)
+    for (int n = 0; n < nb; ++n)
+      for (int m = 0; m < nb; ++m) {
+        bool same = true;
+        for (int t = 0; t < 3; ++t)
+          if (t != b && md[3 * m + t] != md[3 * n + t]) same = false;
+        const int an = md[3 * n + b], am = md[3 * m + b];
+        if (!same || am >= an || ((an - am) & 1) == 0) continue;
+        const double val = std::sqrt((2.0 * an + 1.0) * (2.0 * am + 1.0));
+        int& r = rc[b * nb + m];
+        int& c = cc[b * nb + n];
+        if (r >= W || c >= W) return fail(h, DG_ERR_ARG, "derivative table width exceeded");
+        ri[((size_t)b * nb + m) * W + r] = n;
+        rv[((size_t)b * nb + m) * W + r] = val;
+        ++r;
+        ci[((size_t)b * nb + n) * W + c] = m;
+        cv[((size_t)b * nb + n) * W + c] = val;
+        ++c;
+      }
+  int rcode;
+  if ((rcode = upload(h, &T.Bvol, Bv)) || (rcode = upload(h, &T.wvol, wv)) || (rcode = upload(h, &T.xg, xg)) ||
+      (rcode = upload(h, &T.Bface, Bf)) || (rcode = upload(h, &T.wface, wf)) || (rcode = upload(h, &T.Drow_idx, ri)) ||
+      (rcode = upload(h, &T.Drow_val, rv)) || (rcode = upload(h, &T.Dcol_idx, ci)) || (rcode = upload(h, &T.Dcol_val, cv)))
+    return rcode;
+  return DG_OK;
+}
+
+template <class T>
+static int dalloc(Handle* h, T** p, size_t count) {
+  DG_CUDA(h, cudaMalloc((void**)p, sizeof(T) * (count ? count : 1)));
+  DG_CUDA(h, cudaMemset(*p, 0, sizeof(T) * (count ? count : 1)));
+  return DG_OK;
+}
+
+cudaEvent_t prof_event(Handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int prof_begin(Handle* h, cudaStream_t st, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!h->prof) return DG_OK;
+  *a = prof_event(h);
+  if (!*a) return fail(h, DG_ERR_CUDA, "cudaEventCreate failed");
+  DG_CUDA(h, cudaEventRecord(*a, st));
+  return DG_OK;
+}
+
+int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a) {
+  if (!h->prof || !a) return DG_OK;
+  cudaEvent_t b = prof_event(h);
+  if (!b) return fail(h, DG_ERR_CUDA, "cudaEventCreate failed");
+  DG_CUDA(h, cudaEventRecord(b, st));
+  h->prof_pending.push_back(Handle::ProfEv{cls, a, b});
+  return DG_OK;
+}
+
+static void free_all(Handle* h) {
+  for (auto& p : h->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  h->prof_pending.clear();
+  h->ev_pool.clear();
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  Tables& T = h->tab;
+  F(T.Bvol); F(T.wvol); F(T.xg); F(T.Bface); F(T.wface); F(T.Drow_idx); F(T.Drow_val); F(T.Dcol_idx); F(T.Dcol_val);
+  for (int d = 0; d < 3; ++d) F(h->dnode[d]);
+  F(h->nbr);
+  F(h->colour);
+  for (int l = 0; l < DG_MAX_LEVELS; ++l) {
+    F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
+  }
+  F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
+  F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);
+  if (h->hcol_host) cudaFreeHost(h->hcol_host);
+}
+
+static int create(const dg_params* p, Handle* h) {
+  if (!p) return fail(h, DG_ERR_ARG, "null params");
+  const int nn[3] = {p->nx, p->ny, p->nz};
+  const double* nodes[3] = {p->xn, p->yn, p->zn};
+  for (int d = 0; d < 3; ++d) {
+    if (nn[d] < 2) return fail(h, DG_ERR_ARG, "every axis needs at least 2 cells");
+    if (!nodes[d]) return fail(h, DG_ERR_ARG, "null node array");
+    for (int i = 0; i < nn[d]; ++i)
+      if (!(nodes[d][i + 1] > nodes[d][i])) return fail(h, DG_ERR_ARG, "node coordinates must increase");
+  }
+  if (p->nlevels < 1 || p->nlevels > DG_MAX_LEVELS) return fail(h, DG_ERR_ARG, "nlevels out of range");
+  for (int l = 0; l < p->nlevels; ++l) {
+    if (p->k[l] < 1 || p->k[l] > kMaxK) return fail(h, DG_ERR_ARG, "degree out of range 1..4");
+    if (l > 0 && p->k[l] >= p->k[l - 1]) return fail(h, DG_ERR_ARG, "degrees must decrease with the level");
+  }
+  if (!(p->nu > 0.0) || !(p->ac_c > 0.0) || !(p->eta > 0.0)) return fail(h, DG_ERR_ARG, "nu, ac_c, eta must be > 0");
+  const long long ne = (long long)nn[0] * nn[1] * nn[2];
+  if (ne > (1LL << 28)) return fail(h, DG_ERR_ARG, "mesh too large");
+  h->p = *p;
+  h->p.xn = h->p.yn = h->p.zn = nullptr;
+  for (int d = 0; d < 3; ++d) h->n[d] = nn[d];
+  h->ne = (int)ne;
+  h->nlev = p->nlevels;
+  int dev = 0;
+  DG_CUDA(h, cudaGetDevice(&dev));
+  DG_CUDA(h, cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  int rc;
+  for (int d = 0; d < 3; ++d) {
+    h->node[d].assign(nodes[d], nodes[d] + nn[d] + 1);
+    if ((rc = upload(h, &h->dnode[d], h->node[d]))) return rc;
+  }
+  std::vector<int> nbr((size_t)ne * 6);
+  for (long long e = 0; e < ne; ++e) {
+    const int i = (int)(e % nn[0]), j = (int)((e / nn[0]) % nn[1]), k = (int)(e / ((long long)nn[0] * nn[1]));
+    auto id = [&](int a, int b, int c) {
+      a = (a + nn[0]) % nn[0]; b = (b + nn[1]) % nn[1]; c = (c + nn[2]) % nn[2];
+      return a + nn[0] * (b + nn[1] * c);
+    };
+    nbr[e * 6 + 0] = id(i - 1, j, k); nbr[e * 6 + 1] = id(i + 1, j, k);
+    nbr[e * 6 + 2] = id(i, j - 1, k); nbr[e * 6 + 3] = id(i, j + 1, k);
+    nbr[e * 6 + 4] = id(i, j, k - 1); nbr[e * 6 + 5] = id(i, j, k + 1);
+  }
+  if ((rc = upload(h, &h->nbr, nbr))) return rc;
+  if ((rc = build_tables(h, p->k[0]))) return rc;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->lev[l];
+    L.k = p->k[l];
+    L.nb = nb_of(L.k);
+    L.b = 4 * L.nb;
+    L.n = ne * L.b;
+    if ((rc = dalloc(h, &L.t0, L.n)) || (rc = dalloc(h, &L.t1, L.n)) || (rc = dalloc(h, &L.t2, L.n))) return rc;
+  }
+  const int nb0 = h->lev[0].nb;
+  const long long n0 = h->lev[0].n;
+  if ((rc = dalloc(h, &h->face_out, (size_t)ne * 6 * 4 * nb0)) || (rc = dalloc(h, &h->face_lift, (size_t)ne * 6 * 3 * nb0)) ||
+      (rc = dalloc(h, &h->wlin, n0)) || (rc = dalloc(h, &h->flin, n0)) || (rc = dalloc(h, &h->fd_w, n0)) ||
+      (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
+      (rc = dalloc(h, &h->dFlux, (size_t)3 * ne * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
+      (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 1)))
+    return rc;
+  DG_CUDA(h, cudaDeviceSynchronize());
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+int dg_create(const dg_params* p, dg_handle** out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "null output handle pointer");
+  *out = nullptr;
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return fail(nullptr, DG_ERR_ARG, "out of host memory");
+  const int rc = create(p, h);
+  if (rc != DG_OK) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = reinterpret_cast<dg_handle*>(h);
+  return DG_OK;
+}
+
+int dg_destroy(dg_handle* hh) {
+  if (!hh) return DG_OK;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_handle* hh) {
+  if (!hh) return g_create_error.c_str();
+  return reinterpret_cast<const Handle*>(hh)->err.c_str();
+}
+
+int dg_level_size(const dg_handle* hh, int lvl, int* nb, long long* n) {
+  const Handle* h = reinterpret_cast<const Handle*>(hh);
+  if (!h || lvl < 0 || lvl >= h->nlev) return DG_ERR_ARG;
+  if (nb) *nb = h->lev[lvl].nb;
+  if (n) *n = h->lev[lvl].n;
+  return DG_OK;
+}
+
+int dg_get_status(dg_handle* hh, unsigned* status, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !status) return DG_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  DG_CUDA(h, cudaMemcpyAsync(status, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+  DG_CUDA(h, cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+int dg_project_tgv(dg_handle* hh, double* w, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !w) return h ? fail(h, DG_ERR_ARG, "null pointer") : DG_ERR_ARG;
+  return op_project_tgv(h, w, as_stream(stream));
+}
+
+int dg_residual(dg_handle* hh, const double* w, double* f, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!w || !f || w == f) return fail(h, DG_ERR_ARG, "w and f must be distinct non-null device pointers");
+  return op_residual(h, w, f, false, as_stream(stream));
+}
+
+int dg_set_linearization(dg_handle* hh, const double* w, double inv_gamma_dt, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!w || !(inv_gamma_dt >= 0.0)) return fail(h, DG_ERR_ARG, "null state or negative 1/(gamma dt)");
+  cudaStream_t st = as_stream(stream);
+  const long long n0 = h->lev[0].n;
+  DG_CUDA(h, cudaMemcpyAsync(h->wlin, w, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  h->inv_gdt = inv_gamma_dt;
+  int rc = op_residual(h, h->wlin, h->flin, true, st);
+  if (rc) return rc;
+  if ((rc = vec_norm2(h, h->wlin, n0, h->wnorm2, st))) return rc;
+  DG_CUDA(h, cudaStreamSynchronize(st));
+  h->linearized = true;
+  h->assembled = false;
+  return DG_OK;
+}
+
+int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!v || !out || v == out) return fail(h, DG_ERR_ARG, "v and out must be distinct non-null device pointers");
+  if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_jvp needs dg_set_linearization first");
+  if (mode == DG_JVP_TANGENT) return op_tangent(h, v, out, as_stream(stream));
+  if (mode == DG_JVP_FD) return op_fd(h, v, out, as_stream(stream));
+  return fail(h, DG_ERR_ARG, "unknown jvp mode");
+}
+
+int dg_assemble(dg_handle* hh, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");
+  const int rc = assemble_all(h, as_stream(stream));
+  if (rc == DG_OK) h->assembled = true;
+  return rc;
+}
+
+int dg_counters(const dg_handle* hh, long long* kernel_launches, long long* operator_applications) {
+  const Handle* h = reinterpret_cast<const Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (kernel_launches) *kernel_launches = h->launches;
+  if (operator_applications) *operator_applications = h->op_apps;
+  return DG_OK;
+}
+
+int dg_profile(dg_handle* hh, int enable) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  h->prof = enable != 0;
+  return DG_OK;
+}
+
+int dg_profile_read(dg_handle* hh, double* ms, long long* counts) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !ms || !counts) return h ? fail(h, DG_ERR_ARG, "null output") : DG_ERR_ARG;
+  DG_CUDA(h, cudaDeviceSynchronize());
+  for (auto& p : h->prof_pending) {
+    float t = 0.f;
+    DG_CUDA(h, cudaEventElapsedTime(&t, p.a, p.b));
+    h->prof_ms[p.cls] += t;
+    h->prof_cnt[p.cls] += 1;
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->prof_pending.clear();
+  for (int i = 0; i < DG_PROF_N; ++i) {
+    ms[i] = h->prof_ms[i];
+    counts[i] = h->prof_cnt[i];
+    h->prof_ms[i] = 0.0;
+    h->prof_cnt[i] = 0;
+  }
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Internal declarations of the dgpmg CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dgpmg.h"
+
+namespace dg {
+
+constexpr int kMaxK = 4;
+
+__host__ __device__ constexpr int nb_of(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
+
+// Per-level tables of the reference basis phi_hat_m(xi) = prod_d sqrt((2n_d+1)/2) L_{n_d}(xi_d)
+// on [-1,1]^3 (orthonormal), at the Gauss points of the level's own rule (k+1 points per axis).
+struct Tables {
+  int k = 0, nb = 0, n1 = 0, nq = 0, nqf = 0;
+  double* Bvol = nullptr;   // [nq][nb]          phi_hat at volume points, q = (q0*n1 + q1)*n1 + q2
+  double* wvol = nullptr;   // [nq]              reference volume weights
+  double* xg = nullptr;     // [n1]              Gauss nodes on [-1,1]
+  double* Bface = nullptr;  // [3][2][nqf][nb]   phi_hat on the face normal to d at xi_d = +1 (side 0) / -1 (side 1)
+  double* wface = nullptr;  // [nqf]             reference face weights
+  // Sparse reference derivative operator: d/dxi_b phi_hat_n = sum_m D_b[m][n] phi_hat_m.
+  // Drow[b][m][j] / Dcol[b][n][j] hold at most kDw entries (index, value) of row m / column n.
+  int* Drow_idx = nullptr;     // [3][nb][kDw]
+  double* Drow_val = nullptr;  // [3][nb][kDw]
+  int* Dcol_idx = nullptr;     // [3][nb][kDw]
+  double* Dcol_val = nullptr;  // [3][nb][kDw]
+  static constexpr int kDw = 3;
+};
+
+struct Level {
+  int k = 0, nb = 0, b = 0;  // degree, modes per variable, block size 4*nb
+  long long n = 0;           // vector length ne*4*nb
+  double* Dblk = nullptr;    // [ne][b][b] diagonal blocks, column-major per block
+  double* Dinv = nullptr;    // [ne][b][b] inverses, column-major per block
+  double* Bsr = nullptr;     // [ne][7][b][b] level >= 1: slot 0 diagonal, slots 1..6 faces -x,+x,-y,+y,-z,+z
+  double* t0 = nullptr;      // work vectors of length n
+  double* t1 = nullptr;
+  double* t2 = nullptr;
+};
+
+struct Handle {
+  dg_params p{};
+  int n[3] = {0, 0, 0};
+  int ne = 0;
+  int nlev = 0;
+  std::vector<double> node[3];  // host node coordinates
+  double* dnode[3] = {nullptr, nullptr, nullptr};
+  int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z
+  int* colour = nullptr;        // [ne] element colouring used by the assembly probes
+  Tables tab;                   // fine-level tables (the matrix-free level)
+  Level lev[DG_MAX_LEVELS];
+  int nsm = 0;
+
+  // scratch of the matrix-free operator
+  double* face_out = nullptr;  // [ne][6][4][nb0] face-term contributions per element face slot
+  double* face_lift = nullptr; // [ne][6][3][nb0] BR2 local lifting coefficients per element face slot
+  // linearisation cache
+  bool linearized = false;
+  bool assembled = false;
+  double inv_gdt = 0.0;
+  double* wlin = nullptr;   // [n0]
+  double* flin = nullptr;   // [n0] f_h(wlin)
+  double* ubar = nullptr;   // [ne][3][nq] velocity at the volume points
+  double* dFlux = nullptr;  // [3*ne][nqf][4][8] Jacobian of the Riemann flux at the face points
+  double* wnorm2 = nullptr; // device scalar ||wlin||^2
+  // finite-difference scratch
+  double* fd_w = nullptr;
+  double* fd_f = nullptr;
+  double* red = nullptr;    // reduction partials
+  double* red_out = nullptr;
+  unsigned* status = nullptr;  // device status word
+  // Krylov workspace
+  int kry_m = 0;
+  double* V = nullptr;  // [(m+1)][n0]
+  double* Z = nullptr;  // [m][n0]
+  double* hcol = nullptr;     // device [m+2]
+  double* hcol_host = nullptr;  // pinned [m+2]
+  std::string err;
+  // instrumentation
+  long long launches = 0;
+  long long op_apps = 0;
+  bool prof = false;
+  struct ProfEv { int cls; cudaEvent_t a, b; };
+  std::vector<ProfEv> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[DG_PROF_N] = {0, 0, 0, 0};
+  long long prof_cnt[DG_PROF_N] = {0, 0, 0, 0};
+};
+
+// error helpers
+int fail(Handle* h, int code, const std::string& msg);
+#define DG_CUDA(h, call)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return ::dg::fail((h), DG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+#define DG_LAUNCH_CHECK(h)    \
+  do {                        \
+    ++(h)->launches;          \
+    DG_CUDA(h, cudaGetLastError()); \
+  } while (0)
+
+// CUDA events around the launches of one kernel class (when profiling is on)
+cudaEvent_t prof_event(Handle* h);
+int prof_begin(Handle* h, cudaStream_t st, cudaEvent_t* a);
+int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// mesh geometry on the device
+struct MeshDev {
+  int nx, ny, nz, ne;
+  const double* xn;
+  const double* yn;
+  const double* zn;
+  const int* nbr;
+};
+inline MeshDev mesh_dev(const Handle* h) {
+  return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->dnode[0], h->dnode[1], h->dnode[2], h->nbr};
+}
+
+struct ElemGeom {
+  double h[3];   // box sizes
+  double lo[3];  // lower corner
+  double s;      // sqrt(|K|/8): phi = phi_hat / s
+};
+__device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
+  ElemGeom g;
+  int i = e % M.nx, j = (e / M.nx) % M.ny, k = e / (M.nx * M.ny);
+  g.lo[0] = M.xn[i];
+  g.lo[1] = M.yn[j];
+  g.lo[2] = M.zn[k];
+  g.h[0] = M.xn[i + 1] - g.lo[0];
+  g.h[1] = M.yn[j + 1] - g.lo[1];
+  g.h[2] = M.zn[k + 1] - g.lo[2];
+  g.s = sqrt(g.h[0] * g.h[1] * g.h[2] * 0.125);
+  return g;
+}
+
+// operator entry points (dg_operator.cu)
+int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStream_t st);
+int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st);
+int op_fd(Handle* h, const double* v, double* out, cudaStream_t st);
+int op_project_tgv(Handle* h, double* w, cudaStream_t st);
+
+// vector helpers (dg_solvers.cu)
+int vec_norm2(Handle* h, const double* x, long long n, double* dev_out, cudaStream_t st);
+int launch_axpby(Handle* h, long long n, double a, const double* x, double b, double* y, cudaStream_t st);
+
+// assembly (dg_assemble.cu)
+int assemble_all(Handle* h, cudaStream_t st);
+int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st);  // y = G_lvl x
+
+}  // namespace dg

@@ -1,0 +1,492 @@
+// p-multigrid and Krylov parts of the hot path (Sec. 2.3-2.4, Algorithms 2-3):
+// restriction / prolongation, block-sparse coarse products, element-block-Jacobi
+// smoothing, MG_V / MG_full cycles and right-preconditioned flexible GMRES, with
+// deterministic (fixed-order) FP64 reductions.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+constexpr int kRedBlocks = 512;  // fixed partial count: reductions are bitwise reproducible
+
+// ------------------------------------------------------------ reductions
+__global__ void __launch_bounds__(256) norm2_partial_kernel(long long n, const double* x, double* part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) acc += x[i] * x[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// out[j] = sum_b part[b * stride + j] for j < nvec, in a fixed order.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(int nblk, int nvec, int stride, const double* part,
+                                                              double* out) {
+  __shared__ double s[256];
+  for (int j = 0; j < nvec; ++j) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 256) acc += part[(size_t)b * stride + j];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = s[0];
+    __syncthreads();
+  }
+}
+
+int vec_norm2(Handle* h, const double* x, long long n, double* dev_out, cudaStream_t st) {
+  norm2_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, x, h->red);
+  DG_LAUNCH_CHECK(h);
+  reduce_partials_kernel<<<1, 256, 0, st>>>(kRedBlocks, 1, 1, h->red, dev_out);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+// part[b][j] = sum over this block's slice of V[j][i] * w[i], j < nv (nv <= 8 per launch)
+__global__ void __launch_bounds__(256) multidot_partial_kernel(long long n, int nv, const double* V, long long ldv,
+                                                               const double* w, double* part, int stride) {
+  __shared__ double s[8][256];
+  double acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const double wi = w[i];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < nv) acc[j] += V[j * ldv + i] * wi;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int j = 0; j < nv; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < nv) part[(size_t)blockIdx.x * stride + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// w -= sum_j hcoef[j] * V[j], j < nv; also w is scaled by nothing
+__global__ void multi_axpy_kernel(long long n, int nv, const double* V, long long ldv, const double* hcoef, double* w) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < nv; ++j) acc -= hcoef[j] * V[j * ldv + i];
+    w[i] = acc;
+  }
+}
+
+__global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+__global__ void scale_by_dev_kernel(long long n, const double* x, const double* dnorm2, double* y) {
+  const double inv = 1.0 / sqrt(*dnorm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * inv;
+}
+
+int launch_axpby(Handle* h, long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  axpby_kernel<<<h->nsm * 8, 256, 0, st>>>(n, a, x, b, y);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+// ------------------------------------------------------ transfer operators
+__global__ void restrict_kernel(int ne, int nbf, int nbc, const double* xf, double* xc) {
+  const long long n = (long long)ne * 4 * nbc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long ev = i / nbc;
+    const int m = (int)(i - ev * nbc);
+    xc[i] = xf[ev * nbf + m];
+  }
+}
+__global__ void prolong_add_kernel(int ne, int nbf, int nbc, const double* xc, double* xf) {
+  const long long n = (long long)ne * 4 * nbc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long ev = i / nbc;
+    const int m = (int)(i - ev * nbc);
+    xf[ev * nbf + m] += xc[i];
+  }
+}
+
+// ------------------------------------------------------- block operations
+// y[e] = alpha * sum_s B[e][s] x[nbr(e,s)] + beta * y[e]; slot 0 is the element itself.
+__global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr, const double* B, double alpha,
+                                                  const double* x, double beta, double* y) {
+  extern __shared__ double sx[];  // [7][b]
+  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int t = threadIdx.x; t < 7 * b; t += blockDim.x) {
+      const int s = t / b, c = t - s * b;
+      const int col = s == 0 ? e : nbr[e * 6 + s - 1];
+      sx[t] = x[(size_t)col * b + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < b; r += blockDim.x) {
+      double acc = 0.0;
+      const double* Be = B + (size_t)e * 7 * b * b;
+      for (int s = 0; s < 7; ++s)
+        for (int c = 0; c < b; ++c) acc += Be[((size_t)s * b + c) * b + r] * sx[s * b + c];
+      y[(size_t)e * b + r] = alpha * acc + (beta == 0.0 ? 0.0 : beta * y[(size_t)e * b + r]);
+    }
+    __syncthreads();
+  }
+}
+
+// x[e] += omega * Dinv[e] (g[e] - Gx[e]) (Gx == nullptr: Gx = 0; x_zero: x treated as 0)
+__global__ void __launch_bounds__(128) bj_update_kernel(int ne, int b, const double* Dinv, const double* g,
+                                                        const double* Gx, double omega, int x_zero, double* x) {
+  extern __shared__ double sr[];  // [b]
+  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int c = threadIdx.x; c < b; c += blockDim.x)
+      sr[c] = g[(size_t)e * b + c] - (Gx ? Gx[(size_t)e * b + c] : 0.0);
+    __syncthreads();
+    const double* De = Dinv + (size_t)e * b * b;
+    for (int r = threadIdx.x; r < b; r += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < b; ++c) acc += De[(size_t)c * b + r] * sr[c];
+      const double old = x_zero ? 0.0 : x[(size_t)e * b + r];
+      x[(size_t)e * b + r] = old + omega * acc;
+    }
+    __syncthreads();
+  }
+}
+
+static int grid_for(const Handle* h, long long work) {
+  long long g = (long long)h->nsm * 8;
+  if (g > work) g = work;
+  return g < 1 ? 1 : (int)g;
+}
+
+static int run_bsr(Handle* h, int lvl, double alpha, const double* x, double beta, double* y, cudaStream_t st) {
+  const Level& L = h->lev[lvl];
+  bsr_kernel<<<grid_for(h, h->ne), 128, sizeof(double) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsr, alpha, x, beta, y);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st) {
+  if (lvl == 0) return op_tangent(h, x, y, st);
+  return run_bsr(h, lvl, 1.0, x, 0.0, y, st);
+}
+
+// sweeps of x <- x + omega D^-1 (g - G x) on level lvl; x_zero: the initial x is 0
+static int smooth(Handle* h, int lvl, const double* g, double* x, int sweeps, double omega, bool x_zero,
+                  cudaStream_t st) {
+  Level& L = h->lev[lvl];
+  const size_t smem = sizeof(double) * L.b;
+  for (int s = 0; s < sweeps; ++s) {
+    const bool zero = x_zero && s == 0;
+    if (!zero) {
+      int rc = level_matvec(h, lvl, x, L.t2, st);
+      if (rc) return rc;
+    }
+    bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, g, zero ? nullptr : L.t2, omega,
+                                                            zero ? 1 : 0, x);
+    DG_LAUNCH_CHECK(h);
+  }
+  if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
+  return DG_OK;
+}
+
+static int restrict_to(Handle* h, int lvl, const double* xf, double* xc, cudaStream_t st) {
+  const Level &F = h->lev[lvl], &C = h->lev[lvl + 1];
+  restrict_kernel<<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xf, xc);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+static int prolong_add(Handle* h, int lvl, const double* xc, double* xf, cudaStream_t st) {
+  const Level &F = h->lev[lvl], &C = h->lev[lvl + 1];
+  prolong_add_kernel<<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xc, xf);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+// MG_V(l, g, x) of Algorithm 2 (x in/out; x_zero: the incoming x is 0).
+// Level l >= 1 keeps its right-hand side in t0 and its iterate in t1; t2 is scratch.
+static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const dg_solve_opts& o, cudaStream_t st) {
+  int rc;
+  const int Lc = h->nlev - 1;
+  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, st);
+  if ((rc = smooth(h, l, g, x, o.pre_sweeps, o.omega, x_zero, st))) return rc;
+  Level& L = h->lev[l];
+  Level& C = h->lev[l + 1];
+  const bool xz = x_zero && o.pre_sweeps == 0;
+  if (xz) {
+    if ((rc = restrict_to(h, l, g, C.t0, st))) return rc;
+  } else {
+    if ((rc = level_matvec(h, l, x, L.t2, st))) return rc;
+    axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);  // t2 = g - G x
+    DG_LAUNCH_CHECK(h);
+    if ((rc = restrict_to(h, l, L.t2, C.t0, st))) return rc;
+  }
+  if ((rc = mg_v(h, l + 1, C.t0, C.t1, true, o, st))) return rc;
+  if (xz) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
+  if ((rc = prolong_add(h, l, C.t1, x, st))) return rc;
+  return smooth(h, l, g, x, o.post_sweeps, o.omega, false, st);
+}
+
+// MG_full(l, g, 0) of Algorithm 3 (x output).
+static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_opts& o, cudaStream_t st) {
+  int rc;
+  const int Lc = h->nlev - 1;
+  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, st);
+  Level& L = h->lev[l];
+  Level& C = h->lev[l + 1];
+  // g_{l+1} = I g_l; w_{l+1} = MG_full(l+1, g_{l+1}); keep them in the coarse level's t0/t1
+  if ((rc = restrict_to(h, l, g, C.t0, st))) return rc;
+  if ((rc = mg_full(h, l + 1, C.t0, C.t1, o, st))) return rc;
+  DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
+  if ((rc = prolong_add(h, l, C.t1, x, st))) return rc;  // w_hat_l = I w_{l+1}
+  // d_l = g - G w_hat_l ; e_l = MG_V(l, d_l, 0) ; x = w_hat + e
+  if ((rc = level_matvec(h, l, x, L.t2, st))) return rc;
+  axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);
+  DG_LAUNCH_CHECK(h);
+  // The V-cycle below uses t2 as scratch on this level, so d_l moves out of it. On the fine
+  // level t0/t1 are free here; on coarse levels they hold this level's (g, x), so the fine
+  // finite-difference scratch of the handle (not in use during a preconditioner cycle) serves.
+  double* d = l == 0 ? L.t1 : h->fd_w;
+  double* e = l == 0 ? L.t0 : h->fd_f;
+  DG_CUDA(h, cudaMemcpyAsync(d, L.t2, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, st));
+  if ((rc = mg_v(h, l, d, e, true, o, st))) return rc;
+  axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, e, 1.0, x);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+static int check_opts(Handle* h, const dg_solve_opts* o) {
+  if (!o) return fail(h, DG_ERR_ARG, "null options");
+  if (o->pre_sweeps < 0 || o->post_sweeps < 0 || o->coarse_sweeps < 0) return fail(h, DG_ERR_ARG, "negative sweeps");
+  if (!(o->omega > 0.0 && o->omega <= 1.0)) return fail(h, DG_ERR_ARG, "omega must be in (0, 1]");
+  return DG_OK;
+}
+
+static int apply_prec(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st) {
+  if (o.precond == DG_PREC_NONE) {
+    DG_CUDA(h, cudaMemcpyAsync(z, v, sizeof(double) * h->lev[0].n, cudaMemcpyDeviceToDevice, st));
+    return DG_OK;
+  }
+  if (o.precond == DG_PREC_VCYCLE) return mg_v(h, 0, v, z, true, o, st);
+  if (o.precond == DG_PREC_FULLV) {
+    if (h->nlev > 1 && h->lev[1].n > h->lev[0].n) return fail(h, DG_ERR_ARG, "bad level sizes");
+    return mg_full(h, 0, v, z, o, st);
+  }
+  return fail(h, DG_ERR_ARG, "unknown preconditioner");
+}
+
+static int outer_matvec(Handle* h, const dg_solve_opts& o, const double* x, double* y, cudaStream_t st) {
+  return o.jvp_mode == DG_JVP_FD ? op_fd(h, x, y, st) : op_tangent(h, x, y, st);
+}
+
+// hcol[0..nv) = V[0..nv)^T w (device), in chunks of 8 vectors
+static int multidot(Handle* h, long long n, int nv, const double* V, const double* w, double* hout, cudaStream_t st) {
+  for (int j0 = 0; j0 < nv; j0 += 8) {
+    const int c = nv - j0 < 8 ? nv - j0 : 8;
+    multidot_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, c, V + (size_t)j0 * n, n, w, h->red, 8);
+    DG_LAUNCH_CHECK(h);
+    reduce_partials_kernel<<<1, 256, 0, st>>>(kRedBlocks, c, 8, h->red, hout + j0);
+    DG_LAUNCH_CHECK(h);
+  }
+  return DG_OK;
+}
+
+static int ensure_krylov(Handle* h, int m) {
+  if (h->kry_m >= m) return DG_OK;
+  if (h->V) cudaFree(h->V);
+  if (h->Z) cudaFree(h->Z);
+  if (h->hcol) cudaFree(h->hcol);
+  if (h->hcol_host) cudaFreeHost(h->hcol_host);
+  h->V = h->Z = h->hcol = h->hcol_host = nullptr;
+  h->kry_m = 0;
+  const long long n0 = h->lev[0].n;
+  DG_CUDA(h, cudaMalloc((void**)&h->V, sizeof(double) * (size_t)(m + 1) * n0));
+  DG_CUDA(h, cudaMalloc((void**)&h->Z, sizeof(double) * (size_t)m * n0));
+  DG_CUDA(h, cudaMalloc((void**)&h->hcol, sizeof(double) * (m + 8)));
+  DG_CUDA(h, cudaMallocHost((void**)&h->hcol_host, sizeof(double) * (m + 8)));
+  h->kry_m = m;
+  return DG_OK;
+}
+
+static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o, dg_solve_info* info, cudaStream_t st) {
+  const long long n = h->lev[0].n;
+  const int m = o.restart;
+  int rc;
+  if ((rc = ensure_krylov(h, m))) return rc;
+  double* V = h->V;
+  double* Z = h->Z;
+  double* r = h->lev[0].t0;  // t0/t1 of level 0 are free during the solve (the smoothers use t2)
+  double* tmp = h->lev[0].t1;
+  auto norm = [&](const double* v, double* out) -> int {
+    int c = vec_norm2(h, v, n, h->red_out, st);
+    if (c) return c;
+    DG_CUDA(h, cudaMemcpyAsync(h->hcol_host, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(h, cudaStreamSynchronize(st));
+    *out = std::sqrt(h->hcol_host[0]);
+    return DG_OK;
+  };
+  // r = g - G x0
+  if (o.x0_is_zero) {
+    DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    DG_CUDA(h, cudaMemcpyAsync(r, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  } else {
+    if ((rc = outer_matvec(h, o, x, tmp, st))) return rc;
+    DG_CUDA(h, cudaMemcpyAsync(r, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_axpby(h, n, -1.0, tmp, 1.0, r, st))) return rc;
+  }
+  double beta0;
+  if ((rc = norm(r, &beta0))) return rc;
+  int its = 0;
+  const int limit = o.fixed_its > 0 ? o.fixed_its : o.maxit;
+  double est = beta0;
+  bool converged = beta0 == 0.0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), s(m + 1), y(m);
+  while (!converged && its < limit) {
+    double beta;
+    if ((rc = norm(r, &beta))) return rc;
+    if (beta == 0.0) { converged = true; break; }
+    if ((rc = launch_axpby(h, n, 1.0 / beta, r, 0.0, V, st))) return rc;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(s.begin(), s.end(), 0.0);
+    s[0] = beta;
+    const int mm = std::min(m, limit - its);
+    int jdone = 0;
+    for (int j = 0; j < mm; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      if ((rc = apply_prec(h, o, vj, zj, st))) return rc;
+      if ((rc = outer_matvec(h, o, zj, w, st))) return rc;
+      // classical Gram-Schmidt, twice
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((rc = multidot(h, n, j + 1, V, w, h->hcol, st))) return rc;
+        multi_axpy_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, j + 1, V, n, h->hcol, w);
+        DG_LAUNCH_CHECK(h);
+        DG_CUDA(h, cudaMemcpyAsync(h->hcol_host, h->hcol, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+        DG_CUDA(h, cudaStreamSynchronize(st));
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h->hcol_host[i];
+      }
+      double hn;
+      if ((rc = norm(w, &hn))) return rc;
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0 && (rc = launch_axpby(h, n, 1.0 / hn, w, 0.0, w, st))) return rc;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      cs[j] = H[(size_t)j * m + j] / den;
+      sn[j] = H[(size_t)(j + 1) * m + j] / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      s[j + 1] = -sn[j] * s[j];
+      s[j] = cs[j] * s[j];
+      ++its;
+      jdone = j + 1;
+      est = std::fabs(s[j + 1]);
+      if (o.fixed_its <= 0 && est <= o.rtol * beta0) break;
+      if (hn == 0.0) break;
+    }
+    // y = H^-1 s (upper triangular), x += Z y
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = s[i];
+      for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < jdone; ++i)
+      if ((rc = launch_axpby(h, n, y[i], Z + (size_t)i * n, 1.0, x, st))) return rc;
+    // true residual
+    if ((rc = outer_matvec(h, o, x, tmp, st))) return rc;
+    DG_CUDA(h, cudaMemcpyAsync(r, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_axpby(h, n, -1.0, tmp, 1.0, r, st))) return rc;
+    double rn;
+    if ((rc = norm(r, &rn))) return rc;
+    if (o.fixed_its <= 0 && rn <= o.rtol * beta0) converged = true;
+    if (info) info->true_relres = beta0 > 0 ? rn / beta0 : 0.0;
+  }
+  if (info) {
+    info->its = its;
+    info->r0 = beta0;
+    info->relres_est = beta0 > 0 ? est / beta0 : 0.0;
+    if (beta0 == 0.0) info->true_relres = 0.0;
+    info->rho = (its > 0 && info->true_relres > 0) ? std::exp(std::log(info->true_relres) / its) : 0.0;
+    info->status = (converged || o.fixed_its > 0) ? DG_OK : DG_ERR_NOT_CONVERGED;
+  }
+  if (!converged && o.fixed_its <= 0) return fail(h, DG_ERR_NOT_CONVERGED, "FGMRES did not reach the tolerance");
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+int pmg_restrict(dg_handle* hh, int lvl, const double* xf, double* xc, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 0 || lvl + 1 >= h->nlev || !xf || !xc) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  return restrict_to(h, lvl, xf, xc, as_stream(stream));
+}
+
+int pmg_prolong(dg_handle* hh, int lvl, const double* xc, double* xf, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 0 || lvl + 1 >= h->nlev || !xf || !xc) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  return prolong_add(h, lvl, xc, xf, as_stream(stream));
+}
+
+int block_jacobi_smooth(dg_handle* hh, int lvl, const double* g, double* x, int sweeps, double omega, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 0 || lvl >= h->nlev || !g || !x || g == x) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0)) return fail(h, DG_ERR_ARG, "bad sweeps or omega");
+  if (!h->assembled) return fail(h, DG_ERR_STATE, "block_jacobi_smooth needs dg_assemble first");
+  return smooth(h, lvl, g, x, sweeps, omega, false, as_stream(stream));
+}
+
+int bsr_spmv(dg_handle* hh, int lvl, double alpha, const double* x, double beta, double* y, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 1 || lvl >= h->nlev || !x || !y || x == y) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (!h->assembled) return fail(h, DG_ERR_STATE, "bsr_spmv needs dg_assemble first");
+  return run_bsr(h, lvl, alpha, x, beta, y, as_stream(stream));
+}
+
+int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  int rc = check_opts(h, opts);
+  if (rc) return rc;
+  if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
+  if (!h->assembled) return fail(h, DG_ERR_STATE, "pmg_vcycle needs dg_assemble first");
+  return mg_v(h, 0, g, x, true, *opts, as_stream(stream));
+}
+
+int fgmres_solve(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,
+                 void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  int rc = check_opts(h, opts);
+  if (rc) return rc;
+  if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
+  if (opts->restart < 1 || opts->restart > 64) return fail(h, DG_ERR_ARG, "restart must be in 1..64");
+  if (opts->fixed_its <= 0 && (opts->maxit < 1 || !(opts->rtol > 0.0))) return fail(h, DG_ERR_ARG, "bad maxit/rtol");
+  if (!h->linearized) return fail(h, DG_ERR_STATE, "fgmres_solve needs dg_set_linearization first");
+  if (opts->precond != DG_PREC_NONE && !h->assembled) return fail(h, DG_ERR_STATE, "preconditioner needs dg_assemble");
+  if (opts->jvp_mode != DG_JVP_TANGENT && opts->jvp_mode != DG_JVP_FD) return fail(h, DG_ERR_ARG, "bad jvp mode");
+  if (info) *info = dg_solve_info{};
+  return fgmres(h, g, x, *opts, info, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+"""GPU parity of the p-multigrid and FGMRES parts against the oracle's dense counterparts (through the C ABI).
+
+Operators and one V-cycle application agree to rounding (relative 1e-12).
+Krylov solves are compared at a fixed iteration count (no early exit), where
+rounding differences of two Gram-Schmidt variants are amplified by the
+conditioning, with a 1e-10 bound; converged solves are checked by their true
+residual under the oracle's exact operator.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.solvers as SV
+import synthetic as S
+from _gpu_common import dev, host, meshes, pair, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(name, levels, seed=1, amp=0.2, dt=None):
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()[name], levels)
+    w = O.project_tgv(m) + S.perturbation(m.ne, m.k, amp, seed)
+    inv = 1.0 / (dt if dt else S.acoustic_dt(m.nx, m.k))
+    dg.dg_set_linearization(dev(w), inv)
+    dg.dg_assemble()
+    G0 = O.dense_G(m, w, inv)
+    Gs = [G0]
+    for kl in levels[1:]:
+        Gs.append(SV.inherited_operator(G0, m.ne, m.nb, O.nb(kl)))
+    nbs = [O.nb(k) for k in levels]
+    Ds = [SV.block_inverses(G, m.ne, nb) for G, nb in zip(Gs, nbs)]
+    return P, dg, m, w, inv, Gs, Ds, nbs
+
+
+def test_restrict_prolong():
+    dg, m = pair(*meshes()["box233"], [3, 2, 1])
+    rng = np.random.default_rng(0)
+    xf = rng.standard_normal(m.shape())
+    xc = dg.empty(1)
+    dg.pmg_restrict(0, dev(xf), xc)
+    np.testing.assert_array_equal(host(xc), SV.restrict(xf, m.ne, m.nb, O.nb(2)).reshape(xc.shape))
+    y = rng.standard_normal(m.shape())
+    yd = dev(y)
+    dg.pmg_prolong(0, xc, yd)
+    np.testing.assert_allclose(host(yd), y + SV.prolong(host(xc), m.ne, m.nb, O.nb(2)).reshape(y.shape),
+                               rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("name,levels", [("u2", [3, 2, 1]), ("u3", [2, 1]), ("box233", [3, 1])])
+def test_bsr_and_block_jacobi(name, levels):
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    rng = np.random.default_rng(5)
+    for lvl in range(len(levels)):
+        x = rng.standard_normal(Gs[lvl].shape[0])
+        g = rng.standard_normal(Gs[lvl].shape[0])
+        if lvl >= 1:
+            y0 = rng.standard_normal(Gs[lvl].shape[0])
+            yd = dev(y0.reshape(m.ne, 4, nbs[lvl]))
+            dg.bsr_spmv(lvl, 0.7, dev(x.reshape(m.ne, 4, nbs[lvl])), -0.3, yd)
+            assert rel(host(yd).reshape(-1), 0.7 * Gs[lvl] @ x - 0.3 * y0) < 1e-12
+        xd = dev(x.reshape(m.ne, 4, nbs[lvl]))
+        dg.block_jacobi_smooth(lvl, dev(g.reshape(m.ne, 4, nbs[lvl])), xd, 2, 0.8)
+        ref = SV.block_jacobi(lambda v, G=Gs[lvl]: G @ v, Ds[lvl], g, x, 2, 0.8)
+        assert rel(host(xd).reshape(-1), ref) < 1e-12, lvl
+
+
+@pytest.mark.parametrize("name,levels,sweeps", [("u3", [2, 1], (2, 2, 2)), ("u2", [3, 2, 1], (1, 2, 3)),
+                                                ("box233", [4, 2, 1], (2, 1, 4))])
+def test_vcycle(name, levels, sweeps):
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = np.random.default_rng(9).standard_normal(Gs[0].shape[0])
+    pre, post, cs = sweeps
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g), pre, post, cs, 0.9)
+    opts = P.solve_opts(pre_sweeps=pre, post_sweeps=post, coarse_sweeps=cs, omega=0.9)
+    x = dg.empty()
+    dg.pmg_vcycle(dev(g.reshape(x.shape)), x, opts)
+    assert rel(host(x).reshape(-1), ref) < 1e-12
+    ref_f = SV.mg_full(lv, 0, g, pre, post, cs, 0.9)
+    # MG_full as the preconditioner of one fixed FGMRES iteration equals a scaled MG_full application
+    opts_f = P.solve_opts(restart=1, fixed_its=1, precond=P.DG_PREC_FULLV, pre_sweeps=pre, post_sweeps=post,
+                          coarse_sweeps=cs, omega=0.9)
+    xf = dg.empty()
+    dg.fgmres_solve(dev(g.reshape(x.shape)), xf, opts_f)
+    z = ref_f
+    Gz = Gs[0] @ z
+    alpha = np.dot(Gz, g) / np.dot(Gz, Gz)
+    assert rel(host(xf).reshape(-1), alpha * z) < 1e-11
+
+
+@pytest.mark.parametrize("name,levels", [("u3", [2, 1]), ("u2", [3, 2, 1])])
+def test_fgmres_fixed_iterations(name, levels):
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = -O.residual(m, w).reshape(-1)
+    its = 6
+    xr, _, _ = SV.fgmres(lambda v: Gs[0] @ v, lambda v: SV.mg_v(lv, 0, v, np.zeros_like(v)), g, restart=30,
+                         fixed_its=its)
+    x = dg.empty()
+    info, rc = dg.fgmres_solve(dev(g.reshape(x.shape)), x, P.solve_opts(fixed_its=its))
+    assert info.its == its
+    vol = m.vol()
+    a = SV.remove_mean_pressure(host(x).reshape(-1), m.ne, m.nb, vol)
+    b = SV.remove_mean_pressure(xr, m.ne, m.nb, vol)
+    assert rel(a, b) < 1e-10
+
+
+def test_fgmres_converges_tgv4_p2():
+    # one linearly implicit stage of the 4^3 P2 Taylor-Green workload, 2-level V-cycle, rel-tol 1e-10
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()["u4"], [2, 1])
+    w = O.project_tgv(m)
+    inv = 1.0 / S.acoustic_dt(4, 2)
+    wd = dev(w)
+    f = dg.empty()
+    dg.dg_residual(wd, f)
+    g = -f
+    dg.dg_set_linearization(wd, inv)
+    dg.dg_assemble()
+    x = dg.empty()
+    info, rc = dg.fgmres_solve(g.contiguous(), x, P.solve_opts(rtol=1e-10, maxit=200))
+    assert rc == P.DG_OK and info.true_relres <= 1e-10
+    G0 = O.dense_G(m, w, inv)
+    gr = host(g).reshape(-1)
+    assert np.linalg.norm(gr - G0 @ host(x).reshape(-1)) / np.linalg.norm(gr) < 1e-9
+
+
+def test_fgmres_fd_mode_generic_state():
+    # Finite-difference outer products (Eqs. (matrix-free), (epsdef)). The pure Taylor-Green
+    # state lies on a kink of the upwinded tangential flux (u* = 0 with u_t,L = -u_t,R on faces
+    # where cos z is odd), where a one-sided difference sees only one side; a generic state is
+    # differentiable, and the FD action then serves tolerances above its ~1e-7 noise (Sec. 2.3).
+    # A small time step (acoustic CFL 2) and no preconditioner keep the solve well posed there.
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()["u4"], [2, 1])
+    w = O.project_tgv(m) + S.perturbation(m.ne, 2, 0.01, 21)
+    inv = 1.0 / S.acoustic_dt(4, 2, cfl=2.0)
+    wd = dev(w)
+    f = dg.empty()
+    dg.dg_residual(wd, f)
+    g = (-f).contiguous()
+    dg.dg_set_linearization(wd, inv)
+    dg.dg_assemble()
+    xf = dg.empty()
+    info, rc = dg.fgmres_solve(g, xf, P.solve_opts(rtol=1e-5, maxit=300, jvp_mode=P.DG_JVP_FD,
+                                                   precond=P.DG_PREC_NONE))
+    assert rc == P.DG_OK and info.true_relres <= 1e-5
+    G0 = O.dense_G(m, w, inv)
+    gr = host(g).reshape(-1)
+    assert np.linalg.norm(gr - G0 @ host(xf).reshape(-1)) / np.linalg.norm(gr) < 1e-4
