@@ -182,6 +182,31 @@ int pmg_vcycle(dg_handle* h, const double* g, double* x, const dg_solve_opts* op
 int fgmres_solve(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,
                  void* stream);
 
+/* ------------------------------------------------- residual without allocation
+ * The paper has no counterpart of this call; it serves callers that must not
+ * allocate device memory at the point where they evaluate the residual: a host
+ * application or framework that owns the whole device memory budget and forbids
+ * its plugins to call cudaMalloc, or code running where an allocation would
+ * synchronise the device or fail because the memory is already committed.
+ *
+ * dg_residual_noalloc computes exactly what dg_residual computes (same kernels)
+ * but keeps the face-pass scratch (N_e * 6 * 7 * N_b(k_0) doubles) in a
+ * file-scope device array of DG_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) instead of
+ * the handle's buffers. It calls no cudaMalloc, cudaFree or allocating routine.
+ *  - Meshes needing more scratch than that return DG_ERR_ARG with the sizes in
+ *    the error text (at k = 4: up to 713 elements; at k = 2: up to 2496).
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last call's
+ *    contents (nothing in it needs to start at zero: every entry is written
+ *    before it is read). Calls that overlap on the GPU, from any handle or
+ *    stream, race on it.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ * The handle must come from dg_create as usual; w and f as for dg_residual. */
+#define DG_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
+
 /* --------------------------------------------------------- instrumentation
  * The paper profiles its solver per linear system (Sec. 3.1: code profiling
  * over 10 time steps); these calls expose the same information per kernel. */

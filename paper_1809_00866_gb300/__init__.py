@@ -32,7 +32,7 @@ DG_MAX_LEVELS = 4
 EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_status", "dg_project_tgv",
            "dg_residual", "dg_set_linearization", "dg_jvp", "dg_assemble", "pmg_restrict", "pmg_prolong",
            "block_jacobi_smooth", "bsr_spmv", "pmg_vcycle", "fgmres_solve", "dg_counters", "dg_profile",
-           "dg_profile_read")
+           "dg_profile_read", "dg_residual_noalloc")
 DG_PROF_N = 4
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan")
 
@@ -87,6 +87,7 @@ def load(path=None):
     L.bsr_spmv.argtypes = [vp, i, d, vp, d, vp, vp]
     L.pmg_vcycle.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), vp]
     L.fgmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), ctypes.POINTER(DgSolveInfo), vp]
+    L.dg_residual_noalloc.argtypes = [vp, vp, vp, vp]
     L.dg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.dg_profile.argtypes = [vp, i]
     L.dg_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]

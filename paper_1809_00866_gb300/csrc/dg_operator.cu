@@ -21,6 +21,8 @@
 // axis; the normal of a face points from K (lower index) to K'; [v] = v_K - v_K';
 // the lifting is defined by int r . tau = + int_s [v] {tau} . n so that
 // grad u - R^K is the consistent gradient (Sec. 2.1).
+#include <mutex>
+
 #include "dg_internal.h"
 
 namespace dg {
@@ -633,4 +635,51 @@ int op_project_tgv(Handle* h, double* w, cudaStream_t st) {
   return DG_OK;
 }
 
+// ------------------------------------------------- residual without allocation
+// Scratch of dg_residual_noalloc: the per-face-slot contributions and lifting
+// coefficients of the face pass (N_e * 6 * (4 + 3) * N_b doubles), in a
+// file-scope device array instead of the handle's own buffers. Every GPU that
+// loads the library holds it until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[DG_NOALLOC_SCRATCH_DOUBLES];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device. In host code the array's name is only a host-side stand-in, never a
+// device address, so it must not be passed to a kernel.
+static int noalloc_scratch(Handle* h, double** out) {
+  static std::mutex mu;
+  static double* addr[64] = {};
+  int dev = 0;
+  DG_CUDA(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(h, DG_ERR_ARG, "device index out of range for the static scratch");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    double* p = nullptr;
+    DG_CUDA(h, cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
+    if (!p) return fail(h, DG_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return DG_OK;
+}
+
 }  // namespace dg
+
+extern "C" int dg_residual_noalloc(dg_handle* hh, const double* w, double* f, void* stream) {
+  using namespace dg;
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!w || !f || w == f) return fail(h, DG_ERR_ARG, "w and f must be distinct non-null device pointers");
+  const int nb = h->lev[0].nb;
+  const long long need = (long long)h->ne * 6 * 7 * nb;
+  if (need > (long long)DG_NOALLOC_SCRATCH_DOUBLES)
+    return fail(h, DG_ERR_ARG,
+                "mesh too large for the static scratch of dg_residual_noalloc: it needs N_e*42*N_b = " +
+                    std::to_string(need) + " doubles, the limit is " + std::to_string(DG_NOALLOC_SCRATCH_DOUBLES));
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(h, &scratch);
+  if (rc) return rc;
+  OpArgs a = make_args(h, w, f);
+  a.face_out = scratch;
+  a.face_lift = scratch + (size_t)h->ne * 6 * 4 * nb;
+  return dispatch<MODE_RES>(h, a, as_stream(stream));
+}
