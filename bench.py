@@ -37,11 +37,32 @@ import synthetic as S  # noqa: E402
 METRIC = "Jv GDOF/s and s per implicit stage to rel-res 1e-8: chosen form vs plain FP64"
 CONFIG = "tgv16_p4"
 RTOL = 1e-8
-# Algorithmic FP64 work of the exact Jacobian action at P4 per element (FLOP):
-# faces (3 per element) 241,500, volume terms (interpolation, corrected gradients,
-# pointwise fluxes, integration) 278,500; 0.52 MFLOP in total.
-FLOP_FACE_P4 = 241_500.0
-FLOP_VOL_P4 = 278_500.0
+def jv_flops(k):
+    """Algorithmic FP64 work (FLOP) of the exact Jacobian action per element, as the kernels compute it.
+
+    Counted from the formulation (FMA = 2 FLOP; index arithmetic excluded):
+    face pass, per face (3 per element): 2D traces 2*7*N_b, point values of the
+    4 variables on both sides 8*N_qf*N_2, linearised Riemann flux 32*N_qf,
+    projection 4*N_qf*N_2, 2D viscous flux and lifting ~24*N_2;
+    volume pass: corrected gradients 9*N_b*2, sum-factorised interpolation of 3
+    fields 3*(N_b*n + N_2*n^2 + (k+1)*n^3), 6 products per point, sum-factorised
+    projection of 6 fields 6*((k+1)*n^3 + N_2*n^2 + N_b*n), the viscous flux and
+    the sparse modal derivatives ~30*N_b.
+    Returns (face FLOP per element, volume FLOP per element).
+    """
+    n = k + 1
+    nb = (k + 1) * (k + 2) * (k + 3) // 6
+    n2 = (k + 1) * (k + 2) // 2
+    nqf, nq = n * n, n ** 3
+    face = 3 * 2 * (2 * 7 * nb + 8 * nqf * n2 + 32 * nqf + 4 * nqf * n2 + 24 * n2)
+    vol = 2 * (9 * nb * 2 + 3 * (nb * n + n2 * n * n + (k + 1) * nq) + 6 * nq
+               + 6 * ((k + 1) * nq + n2 * n * n + nb * n) + 30 * nb)
+    return float(face), float(vol)
+
+
+# The dense-quadrature formulation (every contraction with the full N_q x N_b tables) needs
+# about 0.52 MFLOP per element at P4; reported beside the achieved rate for reference.
+DENSE_FLOP_PER_ELEMENT_P4 = 520_000.0
 # FP64 peak of a GB300 (no FP64 entry in the measured-peaks file): nominal 1.25 TFLOP/s
 # (152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz ~ 1.26 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
@@ -266,15 +287,19 @@ def run_ours(args):
     jv_gdofs = n0 / t_jv / 1e9
     face_ms = prof["face_tan"][0] / max(1, prof["face_tan"][1])
     vol_ms = prof["vol_tan"][0] / max(1, prof["vol_tan"][1])
+    ff, fv = jv_flops(k)
     if face_ms >= vol_ms:
-        kname, kms, kflop = "face_kernel<4,tangent>", face_ms, FLOP_FACE_P4 * dg.ne
+        kname, kms, kflop = "face_kernel<%d,tangent>" % k, face_ms, ff * dg.ne
     else:
-        kname, kms, kflop = "vol_kernel<4,tangent>", vol_ms, FLOP_VOL_P4 * dg.ne
+        kname, kms, kflop = "vol_kernel<%d,tangent>" % k, vol_ms, fv * dg.ne
     achieved = kflop / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 rate of GB300 (not in the measured-peaks file)",
-                "kernel_ms": {"face_tan": face_ms, "vol_tan": vol_ms}}
+                "flop_per_element": {"face": ff, "vol": fv},
+                "kernel_ms": {"face_tan": face_ms, "vol_tan": vol_ms},
+                "jv_tflops_of_implemented_work": (ff + fv) * dg.ne / t_jv / 1e12,
+                "jv_dense_equivalent_tflops": DENSE_FLOP_PER_ELEMENT_P4 * dg.ne / t_jv / 1e12}
 
     # --- end to end through the C ABI: state from pinned host memory, result back to the host
     host_w = w.detach().cpu().pin_memory()

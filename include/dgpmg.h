@@ -190,11 +190,11 @@ int fgmres_solve(dg_handle* h, const double* g, double* x, const dg_solve_opts* 
  * synchronise the device or fail because the memory is already committed.
  *
  * dg_residual_noalloc computes exactly what dg_residual computes (same kernels)
- * but keeps the face-pass scratch (N_e * 6 * 7 * N_b(k_0) doubles) in a
+ * but keeps the face-pass scratch (N_e * 6 * 7 * N_2 doubles, N_2 = (k_0+1)(k_0+2)/2) in a
  * file-scope device array of DG_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) instead of
  * the handle's buffers. It calls no cudaMalloc, cudaFree or allocating routine.
  *  - Meshes needing more scratch than that return DG_ERR_ARG with the sizes in
- *    the error text (at k = 4: up to 713 elements; at k = 2: up to 2496).
+ *    the error text (at k = 4: up to 1664 elements; at k = 2: up to 4161).
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.

@@ -87,7 +87,7 @@ static int build_tables(Handle* h, int k) {
   std::vector<double> xg, wg;
   gauss_rule(n1, xg, wg);
   const std::vector<int> md = mode_list(k);
-  std::vector<double> Bv((size_t)T.nq * nb), wv(T.nq), Bf((size_t)6 * T.nqf * nb), wf(T.nqf);
+  std::vector<double> Bv((size_t)T.nq * nb), wv(T.nq);
   for (int q0 = 0; q0 < n1; ++q0)
     for (int q1 = 0; q1 < n1; ++q1)
       for (int q2 = 0; q2 < n1; ++q2) {
@@ -97,20 +97,6 @@ static int build_tables(Handle* h, int k) {
         for (int m = 0; m < nb; ++m)
           Bv[(size_t)q * nb + m] = phat1(md[3 * m], xi[0]) * phat1(md[3 * m + 1], xi[1]) * phat1(md[3 * m + 2], xi[2]);
       }
-  for (int d = 0; d < 3; ++d)
-    for (int side = 0; side < 2; ++side)
-      for (int q1 = 0; q1 < n1; ++q1)
-        for (int q2 = 0; q2 < n1; ++q2) {
-          const int q = q1 * n1 + q2;
-          wf[q] = wg[q1] * wg[q2];
-          double xi[3];
-          xi[d] = side == 0 ? 1.0 : -1.0;
-          xi[(d + 1) % 3] = xg[q1];
-          xi[(d + 2) % 3] = xg[q2];
-          for (int m = 0; m < nb; ++m)
-            Bf[(((size_t)d * 2 + side) * T.nqf + q) * nb + m] =
-                phat1(md[3 * m], xi[0]) * phat1(md[3 * m + 1], xi[1]) * phat1(md[3 * m + 2], xi[2]);
-        }
   // d/dxi P_hat_a = sum_{a' < a, a - a' odd} sqrt((2a+1)(2a'+1)) P_hat_a'
   const int W = Tables::kDw;
   std::vector<int> ri((size_t)3 * nb * W, 0), ci((size_t)3 * nb * W, 0);
@@ -135,10 +121,68 @@ static int build_tables(Handle* h, int k) {
         cv[((size_t)b * nb + n) * W + c] = val;
         ++c;
       }
+  // 1D values, 2D trace modes and the maps between 3D and face modes
+  const int k1 = k + 1;
+  T.n2 = k1 * (k + 2) / 2;
+  const int n2 = T.n2;
+  std::vector<double> L1((size_t)k1 * n1), pvv(2 * k1), pdv(2 * k1);
+  for (int a = 0; a <= k; ++a) {
+    for (int q = 0; q < n1; ++q) L1[(size_t)a * n1 + q] = phat1(a, xg[q]);
+    const double na = std::sqrt((2.0 * a + 1.0) * 0.5);
+    const double der = na * a * (a + 1) * 0.5;  // P_a'(1) = a(a+1)/2
+    pvv[a] = na;
+    pvv[k1 + a] = (a & 1) ? -na : na;
+    pdv[a] = der;
+    pdv[k1 + a] = (a & 1) ? der : -der;  // P_a'(-1) = (-1)^(a+1) a(a+1)/2
+  }
+  std::vector<int> pab, pidx((size_t)k1 * k1, -1);
+  for (int t = 0; t <= k; ++t)
+    for (int a = t; a >= 0; --a) {
+      pidx[a * k1 + (t - a)] = (int)(pab.size() / 2);
+      pab.push_back(a);
+      pab.push_back(t - a);
+    }
+  std::vector<double> B2((size_t)T.nqf * n2), W2(T.nqf);
+  for (int q1 = 0; q1 < n1; ++q1)
+    for (int q2 = 0; q2 < n1; ++q2) {
+      const int q = q1 * n1 + q2;
+      W2[q] = wg[q1] * wg[q2];
+      for (int j = 0; j < n2; ++j) B2[(size_t)q * n2 + j] = phat1(pab[2 * j], xg[q1]) * phat1(pab[2 * j + 1], xg[q2]);
+    }
+  std::vector<int> M3((size_t)3 * n2 * k1, -1), fmap((size_t)3 * nb), fa((size_t)3 * nb), md3((size_t)nb * 3);
+  for (int m = 0; m < nb; ++m)
+    for (int t = 0; t < 3; ++t) md3[3 * m + t] = md[3 * m + t];
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < nb; ++m) {
+      const int a = md[3 * m + d], b = md[3 * m + (d + 1) % 3], c = md[3 * m + (d + 2) % 3];
+      const int j = pidx[b * k1 + c];
+      fmap[(size_t)d * nb + m] = j;
+      fa[(size_t)d * nb + m] = a;
+      M3[((size_t)d * n2 + j) * k1 + a] = m;
+    }
+  std::vector<int> d2i((size_t)2 * n2 * W, 0), d2c((size_t)2 * n2, 0);
+  std::vector<double> d2v((size_t)2 * n2 * W, 0.0);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int jo = 0; jo < n2; ++jo)
+      for (int ji = 0; ji < n2; ++ji) {
+        const int bo = pab[2 * jo + dir], co = pab[2 * jo + 1 - dir];
+        const int bi = pab[2 * ji + dir], ci2 = pab[2 * ji + 1 - dir];
+        if (co != ci2 || bo >= bi || ((bi - bo) & 1) == 0) continue;
+        int& r = d2c[dir * n2 + jo];
+        if (r >= W) return fail(h, DG_ERR_ARG, "2D derivative table width exceeded");
+        d2i[((size_t)dir * n2 + jo) * W + r] = ji;
+        d2v[((size_t)dir * n2 + jo) * W + r] = std::sqrt((2.0 * bi + 1.0) * (2.0 * bo + 1.0));
+        ++r;
+      }
   int rcode;
   if ((rcode = upload(h, &T.Bvol, Bv)) || (rcode = upload(h, &T.wvol, wv)) || (rcode = upload(h, &T.xg, xg)) ||
-      (rcode = upload(h, &T.Bface, Bf)) || (rcode = upload(h, &T.wface, wf)) || (rcode = upload(h, &T.Drow_idx, ri)) ||
-      (rcode = upload(h, &T.Drow_val, rv)) || (rcode = upload(h, &T.Dcol_idx, ci)) || (rcode = upload(h, &T.Dcol_val, cv)))
+      (rcode = upload(h, &T.Drow_idx, ri)) || (rcode = upload(h, &T.Drow_val, rv)) ||
+      (rcode = upload(h, &T.Dcol_idx, ci)) || (rcode = upload(h, &T.Dcol_val, cv)) ||
+      (rcode = upload(h, &T.L1, L1)) || (rcode = upload(h, &T.B2, B2)) || (rcode = upload(h, &T.W2, W2)) ||
+      (rcode = upload(h, &T.pv, pvv)) || (rcode = upload(h, &T.pd, pdv)) || (rcode = upload(h, &T.M3, M3)) ||
+      (rcode = upload(h, &T.fmap, fmap)) || (rcode = upload(h, &T.fa, fa)) || (rcode = upload(h, &T.md3, md3)) ||
+      (rcode = upload(h, &T.pidx, pidx)) || (rcode = upload(h, &T.pab, pab)) || (rcode = upload(h, &T.D2_idx, d2i)) ||
+      (rcode = upload(h, &T.D2_val, d2v)))
     return rcode;
   return DG_OK;
 }
@@ -186,7 +230,9 @@ static void free_all(Handle* h) {
   h->ev_pool.clear();
   auto F = [](void* p) { if (p) cudaFree(p); };
   Tables& T = h->tab;
-  F(T.Bvol); F(T.wvol); F(T.xg); F(T.Bface); F(T.wface); F(T.Drow_idx); F(T.Drow_val); F(T.Dcol_idx); F(T.Dcol_val);
+  F(T.Bvol); F(T.wvol); F(T.xg); F(T.Drow_idx); F(T.Drow_val); F(T.Dcol_idx); F(T.Dcol_val);
+  F(T.L1); F(T.B2); F(T.W2); F(T.pv); F(T.pd); F(T.M3); F(T.fmap); F(T.fa); F(T.md3); F(T.pidx); F(T.pab);
+  F(T.D2_idx); F(T.D2_val);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->nbr);
   F(h->colour);
@@ -252,7 +298,8 @@ static int create(const dg_params* p, Handle* h) {
   }
   const int nb0 = h->lev[0].nb;
   const long long n0 = h->lev[0].n;
-  if ((rc = dalloc(h, &h->face_out, (size_t)ne * 6 * 4 * nb0)) || (rc = dalloc(h, &h->face_lift, (size_t)ne * 6 * 3 * nb0)) ||
+  const int n2f = h->tab.n2;
+  if ((rc = dalloc(h, &h->face_out, (size_t)ne * 6 * 4 * n2f)) || (rc = dalloc(h, &h->face_lift, (size_t)ne * 6 * 3 * n2f)) ||
       (rc = dalloc(h, &h->wlin, n0)) || (rc = dalloc(h, &h->flin, n0)) || (rc = dalloc(h, &h->fd_w, n0)) ||
       (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
       (rc = dalloc(h, &h->dFlux, (size_t)3 * ne * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||

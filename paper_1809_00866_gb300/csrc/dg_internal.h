@@ -15,21 +15,35 @@ constexpr int kMaxK = 4;
 
 __host__ __device__ constexpr int nb_of(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
 
-// Per-level tables of the reference basis phi_hat_m(xi) = prod_d sqrt((2n_d+1)/2) L_{n_d}(xi_d)
-// on [-1,1]^3 (orthonormal), at the Gauss points of the level's own rule (k+1 points per axis).
+// Tables of the fine level's reference basis phi_hat_m(xi) = prod_d sqrt((2n_d+1)/2) L_{n_d}(xi_d)
+// on [-1,1]^3 (orthonormal), at the Gauss points of the level's rule (k+1 points per axis).
 struct Tables {
-  int k = 0, nb = 0, n1 = 0, nq = 0, nqf = 0;
+  int k = 0, nb = 0, n1 = 0, nq = 0, nqf = 0, n2 = 0;
   double* Bvol = nullptr;   // [nq][nb]          phi_hat at volume points, q = (q0*n1 + q1)*n1 + q2
   double* wvol = nullptr;   // [nq]              reference volume weights
   double* xg = nullptr;     // [n1]              Gauss nodes on [-1,1]
-  double* Bface = nullptr;  // [3][2][nqf][nb]   phi_hat on the face normal to d at xi_d = +1 (side 0) / -1 (side 1)
-  double* wface = nullptr;  // [nqf]             reference face weights
+  double* L1 = nullptr;     // [k+1][n1]         normalised Legendre P_hat_a(x_q)
+  // 2D trace modes on a face: pairs (b, c), b + c <= k, b the exponent along the first
+  // tangential axis t1 = (d+1)%3 and c along t2 = (d+2)%3; n2 = (k+1)(k+2)/2 of them.
+  double* B2 = nullptr;     // [nqf][n2]         P_hat_b P_hat_c at the face points, q = q1*n1 + q2
+  double* W2 = nullptr;     // [nqf]             reference face weights
+  double* pv = nullptr;     // [2][k+1]          P_hat_a(+1), P_hat_a(-1)
+  double* pd = nullptr;     // [2][k+1]          P_hat_a'(+1), P_hat_a'(-1)
+  int* M3 = nullptr;        // [3][n2][k+1]      3D mode of (exponent a along d, 2D mode n2) or -1
+  int* fmap = nullptr;      // [3][nb]           2D mode of 3D mode m seen from a face normal to d
+  int* fa = nullptr;        // [3][nb]           exponent of m along d
+  int* md3 = nullptr;       // [nb][3]           exponents of 3D mode m
+  int* pidx = nullptr;      // [(k+1)][(k+1)]    index of the pair (a, b), a + b <= k (the 2D ordering)
+  int* pab = nullptr;       // [n2][2]           the pair (a, b) of a pair index
   // Sparse reference derivative operator: d/dxi_b phi_hat_n = sum_m D_b[m][n] phi_hat_m.
   // Drow[b][m][j] / Dcol[b][n][j] hold at most kDw entries (index, value) of row m / column n.
   int* Drow_idx = nullptr;     // [3][nb][kDw]
   double* Drow_val = nullptr;  // [3][nb][kDw]
   int* Dcol_idx = nullptr;     // [3][nb][kDw]
   double* Dcol_val = nullptr;  // [3][nb][kDw]
+  // the same for the 2D trace modes along t1 (dir 0) and t2 (dir 1), by rows
+  int* D2_idx = nullptr;       // [2][n2][kDw]
+  double* D2_val = nullptr;    // [2][n2][kDw]
   static constexpr int kDw = 3;
 };
 
@@ -58,8 +72,8 @@ struct Handle {
   int nsm = 0;
 
   // scratch of the matrix-free operator
-  double* face_out = nullptr;  // [ne][6][4][nb0] face-term contributions per element face slot
-  double* face_lift = nullptr; // [ne][6][3][nb0] BR2 local lifting coefficients per element face slot
+  double* face_out = nullptr;  // [ne][6][4][n2] face-term contributions per element face slot (2D modes)
+  double* face_lift = nullptr; // [ne][6][3][n2] BR2 local lifting (scaled 2D jump) per element face slot
   // linearisation cache
   bool linearized = false;
   bool assembled = false;

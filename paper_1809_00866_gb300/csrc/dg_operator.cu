@@ -2,25 +2,33 @@
 // exact linearisation (Eqs. (jacTrilFnotNU), (jacTrilnu)) and the
 // finite-difference action (Eqs. (matrix-free), (epsdef)).
 //
-// Two kernels per application:
-//  * face_kernel: one face s = (K, K') at a time. Traces of the four
-//    variables and of the nine velocity gradients on both sides, the BR2 local
-//    liftings r^s([u]) (coefficients on K and K'), the artificial-compressibility
-//    Riemann flux (exact star state by safeguarded Newton; in tangent mode its
-//    cached Jacobian), the BR2 face viscous flux F^nu({grad u - eta r^s}), and
-//    the integration against the test functions of both sides. Writes per
-//    element face slot: the face-term contribution and the lifting coefficients.
-//  * vol_kernel: one element at a time. Corrected-gradient coefficients
-//    grad u - R^K(u) (exact modal derivative + the six liftings), values at the
-//    Gauss points, pointwise flux F~, its projection onto the basis, and the
-//    exact modal derivative of that projection (= integration against grad phi),
-//    plus the six face contributions and the mass shift.
+// GB300 has a narrow FP64 pipe (2 DFMA/clk/SM), so the kernels spend FP64
+// operations only where the method needs quadrature and do everything that is
+// polynomial exactly in modal space:
+//  * face_kernel (one warp per face s = (K, K')): traces of both sides as 2D
+//    modal coefficients on the face (collapse over the normal exponent, exact),
+//    point values only of the four fields the nonlinear artificial-compressibility
+//    Riemann flux needs, the flux (exact star state by safeguarded Newton; in
+//    tangent mode its cached Jacobian) projected back onto the 2D modes, the BR2
+//    lifting r^s([u]) = a diagonal scaling of the 2D jump coefficients, and the
+//    BR2 viscous face flux F^nu({grad u - eta r^s}) built exactly in 2D modal
+//    space. Writes per element face slot the 2D-modal face contribution and the
+//    scaled jump from which the volume pass expands the lifting.
+//  * vol_kernel (one CTA per element): corrected-gradient coefficients
+//    grad u - R^K(u) (sparse exact modal derivative minus the six liftings), the
+//    viscous and pressure terms and the continuity equation as exact modal
+//    derivatives (F^nu is linear, p and u are polynomials of degree k), the
+//    convective term u (x) u by sum-factorised interpolation to and projection
+//    from the Gauss points, plus the six face contributions and the mass shift.
+// All of this equals the quadrature form of the paper's weak form up to
+// rounding, because the Gauss rule with k+1 points integrates every
+// polynomial product that is done exactly here.
 //
 // Conventions (also in the C ABI header): orthonormal modal basis
-// phi_m = phi_hat_m(xi)/s, s = sqrt(|K|/8), Gauss rule with k+1 points per
-// axis; the normal of a face points from K (lower index) to K'; [v] = v_K - v_K';
-// the lifting is defined by int r . tau = + int_s [v] {tau} . n so that
-// grad u - R^K is the consistent gradient (Sec. 2.1).
+// phi_m = phi_hat_m(xi)/s, s = sqrt(|K|/8); the normal of a face points from K
+// (lower index) to K'; [v] = v_K - v_K'; the lifting is defined by
+// int r . tau = + int_s [v] {tau} . n so that grad u - R^K is the consistent
+// gradient (Sec. 2.1).
 #include <mutex>
 
 #include "dg_internal.h"
@@ -34,16 +42,14 @@ struct Sz {
 
 enum { MODE_RES = 0, MODE_RES_LIN = 1, MODE_TAN = 2 };
 
+template <int K>
+struct Sz2 {
+  static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
+};
+
 struct OpArgs {
   MeshDev M;
-  const double* Bvol;
-  const double* wvol;
-  const double* Bface;
-  const double* wface;
-  const int* Drow_idx;
-  const double* Drow_val;
-  const int* Dcol_idx;
-  const double* Dcol_val;
+  Tables T;
   const double* in;
   double* out;
   double* face_out;
@@ -216,86 +222,113 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
 }
 
 // ---------------------------------------------------------------- face pass
+constexpr int kFaceWarps = 4;  // faces per CTA, one warp each
+
+template <int K>
+struct FaceSmem {
+  using S = Sz2<K>;
+  // per warp
+  static constexpr int C = 0;                           // [2][4][NB] coefficients of K and K'
+  static constexpr int T = C + 8 * S::NB;               // [2][4][N2] value traces
+  static constexpr int N = T + 8 * S::N2;               // [2][3][N2] normal-derivative traces of velocity
+  static constexpr int V = N + 6 * S::N2;               // [2][4][NQF] point values
+  static constexpr int F = V + 8 * S::NQF;              // [4][NQF] weighted Riemann flux
+  static constexpr int P = F + 4 * S::NQF;              // [4][N2] its projection
+  static constexpr int WARP = P + 4 * S::N2;
+  // per CTA tables (after the warps)
+  static constexpr int B2 = kFaceWarps * WARP;          // [NQF][N2]
+  static constexpr int W2 = B2 + S::NQF * S::N2;        // [NQF]
+  static constexpr int PV = W2 + S::NQF;                // [2][K+1]
+  static constexpr int PD = PV + 2 * (K + 1);           // [2][K+1]
+  static constexpr int D2V = PD + 2 * (K + 1);          // [2][N2][kDw]
+  static constexpr int DOUBLES = D2V + 2 * S::N2 * Tables::kDw;
+  // ints after the doubles
+  static constexpr int M3 = 0;                          // [3][N2][K+1]
+  static constexpr int D2I = M3 + 3 * S::N2 * (K + 1);  // [2][N2][kDw]
+  static constexpr int DEG = D2I + 2 * S::N2 * Tables::kDw;  // [N2] total degree of each 2D mode
+  static constexpr int INTS = DEG + S::N2;
+  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+};
+
 template <int K, int MODE>
-__global__ void __launch_bounds__(128) face_kernel(OpArgs a) {
-  using S = Sz<K>;
-  constexpr int NB = S::NB, NQF = S::NQF;
+__global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
+  using S = Sz2<K>;
+  using L = FaceSmem<K>;
+  constexpr int NB = S::NB, NQF = S::NQF, N2 = S::N2, K1 = K + 1, DW = Tables::kDw;
   extern __shared__ double sm[];
-  double* sBf = sm;                 // [3][2][NQF][NB]
-  double* sC = sBf + 6 * NQF * NB;  // [2][4][NB]
-  double* sG = sC + 8 * NB;         // [2][9][NB] velocity-gradient coefficients, index a*3+b
-  double* sT = sG + 18 * NB;        // [2][13][NQF] traces: 0..3 values, 4 + a*3+b gradients
-  double* sR = sT + 26 * NQF;       // [2][3][NB] lifting coefficients
-  double* sRq = sR + 6 * NB;        // [2][3][NQF] liftings at the face points
-  double* sFn = sRq + 6 * NQF;      // [4][NQF] weighted normal flux
-  double* sW = sFn + 4 * NQF;       // [NQF] reference face weights
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < 6 * NQF * NB; t += nt) sBf[t] = a.Bface[t];
-  for (int t = tid; t < NQF; t += nt) sW[t] = a.wface[t];
+  double* B2 = sm + L::B2;
+  double* W2 = sm + L::W2;
+  double* PV = sm + L::PV;
+  double* PD = sm + L::PD;
+  double* D2V = sm + L::D2V;
+  int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
+  int* M3 = ism + L::M3;
+  int* D2I = ism + L::D2I;
+  int* DEG = ism + L::DEG;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < N2; t += blockDim.x) DEG[t] = a.T.pab[2 * t] + a.T.pab[2 * t + 1];
+  for (int t = tid; t < NQF * N2; t += blockDim.x) B2[t] = a.T.B2[t];
+  for (int t = tid; t < NQF; t += blockDim.x) W2[t] = a.T.W2[t];
+  for (int t = tid; t < 2 * K1; t += blockDim.x) { PV[t] = a.T.pv[t]; PD[t] = a.T.pd[t]; }
+  for (int t = tid; t < 2 * N2 * DW; t += blockDim.x) { D2V[t] = a.T.D2_val[t]; D2I[t] = a.T.D2_idx[t]; }
+  for (int t = tid; t < 3 * N2 * K1; t += blockDim.x) M3[t] = a.T.M3[t];
   __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  double* W = sm + warp * L::WARP;
+  double* sC = W + L::C;
+  double* sT = W + L::T;
+  double* sN = W + L::N;
+  double* sV = W + L::V;
+  double* sF = W + L::F;
+  double* sP = W + L::P;
   const int nfaces = 3 * a.M.ne;
-  for (int f = blockIdx.x; f < nfaces; f += gridDim.x) {
+  for (int f = blockIdx.x * kFaceWarps + warp; f < nfaces; f += gridDim.x * kFaceWarps) {
     const int e0 = f / 3, d = f - 3 * e0;
     const int e1 = a.M.nbr[e0 * 6 + 2 * d + 1];
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const double A4 = 0.25 * g0.h[t1] * g0.h[t2];
     const double is0 = 1.0 / g0.s, is1 = 1.0 / g1.s;
-    for (int t = tid; t < 8 * NB; t += nt) {
+    for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
       sC[t] = a.in[(size_t)(side ? e1 : e0) * 4 * NB + r];
     }
-    __syncthreads();
-    for (int t = tid; t < 18 * NB; t += nt) {
-      const int side = t / (9 * NB), r = t - side * 9 * NB, ab = r / NB, m = r - ab * NB;
-      const int av = ab / 3, b = ab - 3 * av;
-      const double* cv = sC + side * 4 * NB + av * NB;
+    __syncwarp();
+    // 2D trace coefficients: values of u, v, w, p and normal derivatives of u, v, w
+    for (int t = lane; t < 14 * N2; t += 32) {
+      const int side = t / (7 * N2), r = t - side * 7 * N2, fl = r / N2, j = r - fl * N2;
+      const int var = fl < 4 ? fl : fl - 4;
+      const double* c = sC + side * 4 * NB + var * NB;
+      const double* pw = fl < 4 ? PV + side * K1 : PD + side * K1;
+      const int* mm = M3 + (d * N2 + j) * K1;
       double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < Tables::kDw; ++j) {
-        const int o = (b * NB + m) * Tables::kDw + j;
-        acc += a.Drow_val[o] * cv[a.Drow_idx[o]];
+      for (int e = 0; e < K1; ++e) {
+        const int m = mm[e];
+        if (m >= 0) acc += pw[e] * c[m];
       }
-      sG[t] = acc * (2.0 / (side ? g1.h[b] : g0.h[b]));
+      const double is = side ? is1 : is0;
+      if (fl < 4) sT[side * 4 * N2 + fl * N2 + j] = acc * is;
+      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * (2.0 / (side ? g1.h[d] : g0.h[d]));
     }
-    __syncthreads();
-    const double* B0 = sBf + (2 * d + 0) * NQF * NB;
-    const double* B1 = sBf + (2 * d + 1) * NQF * NB;
-    for (int t = tid; t < 26 * NQF; t += nt) {
-      const int side = t / (13 * NQF), r = t - side * 13 * NQF, fld = r / NQF, q = r - fld * NQF;
-      const double* cf = fld < 4 ? sC + side * 4 * NB + fld * NB : sG + side * 9 * NB + (fld - 4) * NB;
-      const double* B = (side ? B1 : B0) + q * NB;
+    __syncwarp();
+    // point values of the four variables on both sides
+    for (int t = lane; t < 8 * NQF; t += 32) {
+      const int sv = t / NQF, q = t - sv * NQF;
+      const double* Tc = sT + sv * N2;
+      const double* b = B2 + q * N2;
       double acc = 0.0;
 #pragma unroll
-      for (int m = 0; m < NB; ++m) acc += B[m] * cf[m];
-      sT[t] = acc * (side ? is1 : is0);
+      for (int j = 0; j < N2; ++j) acc += b[j] * Tc[j];
+      sV[t] = acc;
     }
-    __syncthreads();
-    for (int t = tid; t < 6 * NB; t += nt) {
-      const int side = t / (3 * NB), r = t - side * 3 * NB, av = r / NB, m = r - av * NB;
-      const double* B = side ? B1 : B0;
-      double acc = 0.0;
-#pragma unroll
-      for (int q = 0; q < NQF; ++q) acc += sW[q] * (sT[av * NQF + q] - sT[13 * NQF + av * NQF + q]) * B[q * NB + m];
-      sR[t] = 0.5 * A4 * (side ? is1 : is0) * acc;
-    }
-    __syncthreads();
-    for (int t = tid; t < 6 * NQF; t += nt) {
-      const int side = t / (3 * NQF), r = t - side * 3 * NQF, av = r / NQF, q = r - av * NQF;
-      const double* B = (side ? B1 : B0) + q * NB;
-      const double* rc = sR + side * 3 * NB + av * NB;
-      double acc = 0.0;
-#pragma unroll
-      for (int m = 0; m < NB; ++m) acc += B[m] * rc[m];
-      sRq[t] = acc * (side ? is1 : is0);
-    }
-    __syncthreads();
-    for (int q = tid; q < NQF; q += nt) {
-      const double* T0 = sT;
-      const double* T1 = sT + 13 * NQF;
-      double uL[3] = {T0[0 * NQF + q], T0[1 * NQF + q], T0[2 * NQF + q]};
-      double uR[3] = {T1[0 * NQF + q], T1[1 * NQF + q], T1[2 * NQF + q]};
-      const double pL = T0[3 * NQF + q], pR = T1[3 * NQF + q];
+    __syncwarp();
+    for (int q = lane; q < NQF; q += 32) {
+      const double* V0 = sV;
+      const double* V1 = sV + 4 * NQF;
+      double uL[3] = {V0[q], V0[NQF + q], V0[2 * NQF + q]};
+      double uR[3] = {V1[q], V1[NQF + q], V1[2 * NQF + q]};
+      const double pL = V0[3 * NQF + q], pR = V1[3 * NQF + q];
       double Fc[4];
       if (MODE == MODE_TAN) {
         const double* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
@@ -318,58 +351,143 @@ __global__ void __launch_bounds__(128) face_kernel(OpArgs a) {
       } else {
         ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status);
       }
-      double Gh[3][3];
 #pragma unroll
-      for (int av = 0; av < 3; ++av)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          Gh[av][b] = 0.5 * (T0[(4 + av * 3 + b) * NQF + q] + T1[(4 + av * 3 + b) * NQF + q]);
-          if (b == d) Gh[av][b] -= a.eta * 0.5 * (sRq[av * NQF + q] + sRq[3 * NQF + av * NQF + q]);
-        }
-      const double trG = Gh[0][0] + Gh[1][1] + Gh[2][2];
-      const double wq = sW[q] * A4;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double fv = a.nu * (Gh[i][d] + Gh[d][i]) - (i == d ? (2.0 / 3.0) * a.nu * trG : 0.0);
-        sFn[i * NQF + q] = (Fc[i] - fv) * wq;
-      }
-      sFn[3 * NQF + q] = Fc[3] * wq;
+      for (int i = 0; i < 4; ++i) sF[i * NQF + q] = Fc[i] * W2[q];
     }
-    __syncthreads();
-    for (int t = tid; t < 8 * NB; t += nt) {
-      const int side = t / (4 * NB), r = t - side * 4 * NB, i = r / NB, m = r - i * NB;
-      const double* B = side ? B1 : B0;
+    __syncwarp();
+    for (int t = lane; t < 4 * N2; t += 32) {
+      const int i = t / N2, j = t - i * N2;
+      const double* Fi = sF + i * NQF;
       double acc = 0.0;
 #pragma unroll
-      for (int q = 0; q < NQF; ++q) acc += B[q * NB + m] * sFn[i * NQF + q];
-      const int el = side ? e1 : e0, slot = side ? 2 * d : 2 * d + 1;
-      a.face_out[((size_t)el * 6 + slot) * 4 * NB + r] = side ? -acc * is1 : acc * is0;
+      for (int q = 0; q < NQF; ++q) acc += B2[q * N2 + j] * Fi[q];
+      sP[t] = acc;
     }
-    for (int t = tid; t < 6 * NB; t += nt) {
-      const int side = t / (3 * NB), r = t - side * 3 * NB;
-      const int el = side ? e1 : e0, slot = side ? 2 * d : 2 * d + 1;
-      a.face_lift[((size_t)el * 6 + slot) * 3 * NB + r] = sR[t];
+    __syncwarp();
+    // viscous face flux in 2D modal space, total flux, lifting; one lane per 2D mode
+    for (int j = lane; j < N2; j += 32) {
+      const double* T0 = sT;
+      const double* T1 = sT + 4 * N2;
+      // {r^s} of the normal gradient component, 2D mode j of total degree bj:
+      // (k - bj + 1)^2 / 4 * (1/h_K + 1/h_K') * [u]
+      const int bj = DEG[j];
+      const double lr = 0.25 * (double)((K - bj + 1) * (K - bj + 1)) * (1.0 / g0.h[d] + 1.0 / g1.h[d]);
+      double jump[3], Gd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        jump[c] = T0[c * N2 + j] - T1[c * N2 + j];
+        Gd[c] = 0.5 * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - a.eta * lr * jump[c];  // Ghat[c][d]
+      }
+      // tangential derivatives (2D modal) of the normal component and of the tangential ones
+      auto tder = [&](const double* Tc, int dir) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < DW; ++q) {
+          const int o = (dir * N2 + j) * DW + q;
+          acc += D2V[o] * Tc[D2I[o]];
+        }
+        return acc;
+      };
+      const double it1 = 2.0 / g0.h[t1], it2 = 2.0 / g0.h[t2];
+      const double Gdt1 = 0.5 * (tder(T0 + d * N2, 0) + tder(T1 + d * N2, 0)) * it1;    // Ghat[d][t1]
+      const double Gdt2 = 0.5 * (tder(T0 + d * N2, 1) + tder(T1 + d * N2, 1)) * it2;    // Ghat[d][t2]
+      const double Gt1 = 0.5 * (tder(T0 + t1 * N2, 0) + tder(T1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
+      const double Gt2 = 0.5 * (tder(T0 + t2 * N2, 1) + tder(T1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
+      const double trG = Gd[d] + Gt1 + Gt2;
+      double Fv[3];
+      Fv[d] = a.nu * (2.0 * Gd[d] - (2.0 / 3.0) * trG);
+      Fv[t1] = a.nu * (Gd[t1] + Gdt1);
+      Fv[t2] = a.nu * (Gd[t2] + Gdt2);
+      double Fn[4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fn[i] = A4 * (sP[i * N2 + j] - Fv[i]);
+      Fn[3] = A4 * sP[3 * N2 + j];
+      double* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
+      double* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o0[i * N2 + j] = Fn[i] * is0;
+        o1[i * N2 + j] = -Fn[i] * is1;
+      }
+      double* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
+      double* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        l0[c * N2 + j] = 0.5 * A4 * is0 * jump[c];
+        l1[c * N2 + j] = 0.5 * A4 * is1 * jump[c];
+      }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
 // -------------------------------------------------------------- volume pass
+template <int K>
+struct VolSmem {
+  using S = Sz2<K>;
+  static constexpr int NB = S::NB, N1 = S::N1, NQ = S::NQ, N2 = S::N2, K1 = K + 1;
+  static constexpr int L1 = 0;                        // [K+1][N1]
+  static constexpr int W3 = L1 + K1 * N1;             // [NQ]
+  static constexpr int PV = W3 + NQ;                  // [2][K+1]
+  static constexpr int C = PV + 2 * K1;               // [4][NB]
+  static constexpr int G = C + 4 * NB;                // [9][NB] corrected gradient
+  static constexpr int FV = G + 9 * NB;               // [6][NB] viscous flux (symmetric pairs)
+  static constexpr int U = FV + 6 * NB;               // [3][NQ] velocity (or its variation) at the points
+  static constexpr int T1 = U + 3 * NQ;               // [3][N2][N1] interpolation step 1
+  static constexpr int T2 = T1 + 3 * N2 * N1;         // [3][K+1][N1*N1] interpolation step 2
+  static constexpr int PR = T2 + 3 * K1 * N1 * N1;    // [6][NQ] weighted products
+  static constexpr int S1 = PR + 6 * NQ;              // [6][K+1][N1*N1] projection step 1
+  static constexpr int S2 = S1 + 6 * K1 * N1 * N1;    // [6][N2][N1] projection step 2
+  static constexpr int CV = S2 + 6 * N2 * N1;         // [6][NB] projections of the products
+  static constexpr int DOUBLES = CV + 6 * NB;
+  static constexpr int MD3 = 0;                       // [NB][3]
+  static constexpr int PIDX = MD3 + 3 * NB;           // [K+1][K+1]
+  static constexpr int PAB = PIDX + K1 * K1;          // [N2][2]
+  static constexpr int FMAP = PAB + 2 * N2;           // [3][NB]
+  static constexpr int FA = FMAP + 3 * NB;            // [3][NB]
+  static constexpr int IDX3 = FA + 3 * NB;            // [K+1]^3 3D mode of exponents (a, b, c) or -1
+  static constexpr int INTS = IDX3 + K1 * K1 * K1;
+  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+};
+
+__device__ __forceinline__ int sym_index(int p, int i) { return p == i ? p : (p + i + 2); }  // 01->3 02->4 12->5
+
 template <int K, int MODE>
 __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
-  using S = Sz<K>;
-  constexpr int NB = S::NB, NQ = S::NQ;
+  using L = VolSmem<K>;
+  constexpr int NB = L::NB, N1 = L::N1, NQ = L::NQ, N2 = L::N2, K1 = L::K1, DW = Tables::kDw;
   extern __shared__ double sm[];
-  double* sB = sm;              // [NQ][NB]
-  double* sW = sB + NQ * NB;    // [NQ]
-  double* sC = sW + NQ;         // [4][NB]
-  double* sG = sC + 4 * NB;     // [9][NB]
-  double* sV = sG + 9 * NB;     // [13][NQ]
-  double* sF = sV + 13 * NQ;    // [12][NQ] weighted flux, index p*4+i
-  double* sP = sF + 12 * NQ;    // [12][NB]
+  double* L1 = sm + L::L1;
+  double* W3 = sm + L::W3;
+  double* PV = sm + L::PV;
+  double* sC = sm + L::C;
+  double* sG = sm + L::G;
+  double* sFv = sm + L::FV;
+  double* sU = sm + L::U;
+  double* sT1 = sm + L::T1;
+  double* sT2 = sm + L::T2;
+  double* sPr = sm + L::PR;
+  double* sS1 = sm + L::S1;
+  double* sS2 = sm + L::S2;
+  double* sCv = sm + L::CV;
+  int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
+  int* MD3 = ism + L::MD3;
+  int* PIDX = ism + L::PIDX;
+  int* PAB = ism + L::PAB;
+  int* FMAP = ism + L::FMAP;
+  int* FA = ism + L::FA;
+  int* IDX3 = ism + L::IDX3;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.Bvol[t];
-  for (int t = tid; t < NQ; t += nt) sW[t] = a.wvol[t];
+  for (int t = tid; t < K1 * K1 * K1; t += nt) IDX3[t] = -1;
+  __syncthreads();
+  for (int m = tid; m < NB; m += nt)
+    IDX3[(a.T.md3[3 * m] * K1 + a.T.md3[3 * m + 1]) * K1 + a.T.md3[3 * m + 2]] = m;
+  for (int t = tid; t < K1 * N1; t += nt) L1[t] = a.T.L1[t];
+  for (int t = tid; t < NQ; t += nt) W3[t] = a.T.wvol[t];
+  for (int t = tid; t < 2 * K1; t += nt) PV[t] = a.T.pv[t];
+  for (int t = tid; t < 3 * NB; t += nt) { MD3[t] = a.T.md3[t]; FMAP[t] = a.T.fmap[t]; FA[t] = a.T.fa[t]; }
+  for (int t = tid; t < K1 * K1; t += nt) PIDX[t] = a.T.pidx[t];
+  for (int t = tid; t < 2 * N2; t += nt) PAB[t] = a.T.pab[t];
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
@@ -377,39 +495,60 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     const double Jd[3] = {2.0 / g.h[0], 2.0 / g.h[1], 2.0 / g.h[2]};
     for (int t = tid; t < 4 * NB; t += nt) sC[t] = a.in[(size_t)e * 4 * NB + t];
     __syncthreads();
-    // corrected gradient coefficients (grad u - R^K(u))_{ab}, R^K = liftings of the six faces
+    // (A) corrected gradient coefficients; interpolation step 1 of the velocity
+    const double* Lf = a.face_lift + (size_t)e * 6 * 3 * N2;
     for (int t = tid; t < 9 * NB; t += nt) {
       const int ab = t / NB, m = t - ab * NB, av = ab / 3, b = ab - 3 * av;
       const double* cv = sC + av * NB;
       double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < Tables::kDw; ++j) {
-        const int o = (b * NB + m) * Tables::kDw + j;
-        acc += a.Drow_val[o] * cv[a.Drow_idx[o]];
+      for (int j = 0; j < DW; ++j) {
+        const int o = (b * NB + m) * DW + j;
+        acc += a.T.Drow_val[o] * cv[a.T.Drow_idx[o]];
       }
-      const double* L = a.face_lift + (size_t)e * 6 * 3 * NB;
-      sG[t] = acc * Jd[b] - (L[(2 * b) * 3 * NB + av * NB + m] + L[(2 * b + 1) * 3 * NB + av * NB + m]);
+      // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
+      const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
+      const double r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
+      sG[t] = acc * Jd[b] - r;
+    }
+    for (int t = tid; t < 3 * N2 * N1; t += nt) {
+      const int fl = t / (N2 * N1), r = t - fl * N2 * N1, pi = r / N1, q2 = r - pi * N1;
+      const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+      const double* c = sC + fl * NB;
+      double acc = 0.0;
+      const int* row = IDX3 + (pa * K1 + pb) * K1;
+      for (int cc = 0; cc <= K - pa - pb; ++cc) acc += c[row[cc]] * L1[cc * N1 + q2];
+      sT1[t] = acc;
     }
     __syncthreads();
-    for (int t = tid; t < 13 * NQ; t += nt) {
-      const int fld = t / NQ, q = t - fld * NQ;
-      const double* cf = fld < 4 ? sC + fld * NB : sG + (fld - 4) * NB;
-      const double* B = sB + q * NB;
+    // (B) viscous flux coefficients; interpolation step 2
+    for (int t = tid; t < 6 * NB; t += nt) {
+      const int sp = t / NB, m = t - sp * NB;
+      int p, i;
+      if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
+      const double trG = sG[0 * NB + m] + sG[4 * NB + m] + sG[8 * NB + m];
+      sFv[t] = a.nu * (sG[(i * 3 + p) * NB + m] + sG[(p * 3 + i) * NB + m] - (p == i ? (2.0 / 3.0) * trG : 0.0));
+    }
+    for (int t = tid; t < 3 * K1 * N1 * N1; t += nt) {
+      const int fl = t / (K1 * N1 * N1), r = t - fl * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
+      const int q1 = r2 / N1, q2 = r2 - q1 * N1;
+      double acc = 0.0;
+      for (int pb = 0; pb <= K - pa; ++pb) acc += sT1[fl * N2 * N1 + PIDX[pa * K1 + pb] * N1 + q2] * L1[pb * N1 + q1];
+      sT2[t] = acc;
+    }
+    __syncthreads();
+    // (C) interpolation step 3: velocity (or its variation) at the Gauss points
+    for (int t = tid; t < 3 * NQ; t += nt) {
+      const int fl = t / NQ, q = t - fl * NQ, q0 = q / (N1 * N1), r = q - q0 * N1 * N1;
       double acc = 0.0;
 #pragma unroll
-      for (int m = 0; m < NB; ++m) acc += B[m] * cf[m];
-      sV[t] = acc * is;
+      for (int pa = 0; pa < K1; ++pa) acc += sT2[(fl * K1 + pa) * N1 * N1 + r] * L1[pa * N1 + q0];
+      sU[t] = acc * is;
     }
     __syncthreads();
+    // (D) pointwise convective products, weighted
     for (int q = tid; q < NQ; q += nt) {
-      const double u[3] = {sV[0 * NQ + q], sV[1 * NQ + q], sV[2 * NQ + q]};
-      const double p = sV[3 * NQ + q];
-      double G[3][3];
-#pragma unroll
-      for (int av = 0; av < 3; ++av)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) G[av][b] = sV[(4 + av * 3 + b) * NQ + q];
-      const double trG = G[0][0] + G[1][1] + G[2][2];
+      const double u[3] = {sU[q], sU[NQ + q], sU[2 * NQ + q]};
       double ub[3];
       if (MODE == MODE_TAN) {
 #pragma unroll
@@ -417,34 +556,52 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
       } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = u[c];
-        if (MODE == MODE_RES_LIN) {
+        if (MODE == MODE_RES_LIN)
 #pragma unroll
           for (int c = 0; c < 3; ++c) a.ubar[((size_t)e * 3 + c) * NQ + q] = u[c];
-        }
       }
-      const double wq = sW[q];
+      const double wq = W3[q];
 #pragma unroll
-      for (int pp = 0; pp < 3; ++pp) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const double fv = a.nu * (G[i][pp] + G[pp][i]) - (pp == i ? (2.0 / 3.0) * a.nu * trG : 0.0);
-          // residual: u_p u_i; tangent: du_p ub_i + ub_p du_i
-          const double conv = (MODE == MODE_TAN) ? (u[pp] * ub[i] + ub[pp] * u[i]) : u[pp] * u[i];
-          sF[(pp * 4 + i) * NQ + q] = (conv + (pp == i ? p : 0.0) - fv) * wq;
-        }
-        sF[(pp * 4 + 3) * NQ + q] = u[pp] * wq;
+      for (int sp = 0; sp < 6; ++sp) {
+        int p, i;
+        if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
+        const double v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i]) : u[p] * u[i];
+        sPr[sp * NQ + q] = v * wq;
       }
     }
     __syncthreads();
-    for (int t = tid; t < 12 * NB; t += nt) {
-      const int j = t / NB, n = t - j * NB;
-      const double* F = sF + j * NQ;
+    // (E) projection step 1: S1[sp][a][q1 q2] = sum_q0 L1[a][q0] Pr[sp][q0 q1 q2]
+    for (int t = tid; t < 6 * K1 * N1 * N1; t += nt) {
+      const int sp = t / (K1 * N1 * N1), r = t - sp * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
       double acc = 0.0;
-#pragma unroll 5
-      for (int q = 0; q < NQ; ++q) acc += sB[q * NB + n] * F[q];
-      sP[t] = acc * g.s;
+#pragma unroll
+      for (int q0 = 0; q0 < N1; ++q0) acc += L1[pa * N1 + q0] * sPr[sp * NQ + q0 * N1 * N1 + r2];
+      sS1[t] = acc;
     }
     __syncthreads();
+    // (F) projection step 2: S2[sp][pair(a,b)][q2] = sum_q1 L1[b][q1] S1[sp][a][q1 q2]
+    for (int t = tid; t < 6 * N2 * N1; t += nt) {
+      const int sp = t / (N2 * N1), r = t - sp * N2 * N1, pi = r / N1, q2 = r - pi * N1;
+      const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+      double acc = 0.0;
+#pragma unroll
+      for (int q1 = 0; q1 < N1; ++q1) acc += L1[pb * N1 + q1] * sS1[(sp * K1 + pa) * N1 * N1 + q1 * N1 + q2];
+      sS2[t] = acc;
+    }
+    __syncthreads();
+    // (G) projection step 3: Cv[sp][m] = s * sum_q2 L1[c][q2] S2[sp][pair(a,b)][q2]
+    for (int t = tid; t < 6 * NB; t += nt) {
+      const int sp = t / NB, m = t - sp * NB;
+      const int pa = MD3[3 * m], pb = MD3[3 * m + 1], pc = MD3[3 * m + 2];
+      const double* s2 = sS2 + (sp * N2 + PIDX[pa * K1 + pb]) * N1;
+      double acc = 0.0;
+#pragma unroll
+      for (int q2 = 0; q2 < N1; ++q2) acc += L1[pc * N1 + q2] * s2[q2];
+      sCv[t] = acc * g.s;
+    }
+    __syncthreads();
+    // (H) assemble: modal derivatives of (F^nu - u(x)u) and p, continuity, face terms, mass shift
+    const double* FO = a.face_out + (size_t)e * 6 * 4 * N2;
     for (int t = tid; t < 4 * NB; t += nt) {
       const int i = t / NB, m = t - i * NB;
       double acc = 0.0;
@@ -452,18 +609,27 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
       for (int pp = 0; pp < 3; ++pp) {
         double s2 = 0.0;
 #pragma unroll
-        for (int j = 0; j < Tables::kDw; ++j) {
-          const int o = (pp * NB + m) * Tables::kDw + j;
-          s2 += a.Dcol_val[o] * sP[(pp * 4 + i) * NB + a.Dcol_idx[o]];
+        for (int j = 0; j < DW; ++j) {
+          const int o = (pp * NB + m) * DW + j;
+          const int n = a.T.Dcol_idx[o];
+          double fld;
+          if (i < 3) {
+            const int sp = sym_index(pp, i);
+            fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : 0.0);
+          } else {
+            fld = -sC[pp * NB + n];
+          }
+          s2 += a.T.Dcol_val[o] * fld;
         }
         acc += Jd[pp] * s2;
       }
-      const double* FO = a.face_out + (size_t)e * 6 * 4 * NB + i * NB + m;
-      double v = -acc;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) v += FO[s * 4 * NB];
-      if (MODE == MODE_TAN && i < 3) v += a.inv_gdt * sC[t];
-      a.out[(size_t)e * 4 * NB + t] = v;
+      for (int sl = 0; sl < 6; ++sl) {
+        const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
+        acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
+      }
+      if (MODE == MODE_TAN && i < 3) acc += a.inv_gdt * sC[t];
+      a.out[(size_t)e * 4 * NB + t] = acc;
     }
     __syncthreads();
   }
@@ -520,29 +686,10 @@ __global__ void fd_finish_kernel(long long n, int nb, const double* f1, const do
 }
 
 // ------------------------------------------------------------- launchers
-template <int K>
-static size_t face_smem() {
-  using S = Sz<K>;
-  return sizeof(double) * (6 * S::NQF * S::NB + 8 * S::NB + 18 * S::NB + 26 * S::NQF + 6 * S::NB + 6 * S::NQF +
-                           4 * S::NQF + S::NQF);
-}
-template <int K>
-static size_t vol_smem() {
-  using S = Sz<K>;
-  return sizeof(double) * (S::NQ * S::NB + S::NQ + 4 * S::NB + 9 * S::NB + 13 * S::NQ + 12 * S::NQ + 12 * S::NB);
-}
-
 static OpArgs make_args(Handle* h, const double* in, double* out) {
   OpArgs a;
   a.M = mesh_dev(h);
-  a.Bvol = h->tab.Bvol;
-  a.wvol = h->tab.wvol;
-  a.Bface = h->tab.Bface;
-  a.wface = h->tab.wface;
-  a.Drow_idx = h->tab.Drow_idx;
-  a.Drow_val = h->tab.Drow_val;
-  a.Dcol_idx = h->tab.Dcol_idx;
-  a.Dcol_val = h->tab.Dcol_val;
+  a.T = h->tab;
   a.in = in;
   a.out = out;
   a.face_out = h->face_out;
@@ -559,22 +706,23 @@ static OpArgs make_args(Handle* h, const double* in, double* out) {
 
 template <int K, int MODE>
 static int run_operator(Handle* h, const OpArgs& a, cudaStream_t st) {
-  const size_t fs = face_smem<K>(), vs = vol_smem<K>();
+  const size_t fs = FaceSmem<K>::bytes(), vs = VolSmem<K>::bytes();
   DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
   DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
   const int nfaces = 3 * h->ne;
-  const int per_sm_f = (int)(200 * 1024 / fs) < 8 ? (int)(200 * 1024 / fs) : 8;
-  const int per_sm_v = (int)(200 * 1024 / vs) < 8 ? (int)(200 * 1024 / vs) : 8;
-  int gf = h->nsm * (per_sm_f > 0 ? per_sm_f : 1);
-  int gv = h->nsm * (per_sm_v > 0 ? per_sm_v : 1);
-  if (gf > nfaces) gf = nfaces;
+  int per_sm_f = (int)((200 * 1024) / fs), per_sm_v = (int)((200 * 1024) / vs);
+  per_sm_f = per_sm_f < 1 ? 1 : (per_sm_f > 8 ? 8 : per_sm_f);
+  per_sm_v = per_sm_v < 1 ? 1 : (per_sm_v > 12 ? 12 : per_sm_v);
+  int gf = h->nsm * per_sm_f, gv = h->nsm * per_sm_v;
+  const int fblocks = (nfaces + kFaceWarps - 1) / kFaceWarps;
+  if (gf > fblocks) gf = fblocks;
   if (gv > h->ne) gv = h->ne;
   const int cf = MODE == MODE_TAN ? DG_PROF_FACE_TAN : DG_PROF_FACE_RES;
   const int cv = MODE == MODE_TAN ? DG_PROF_VOL_TAN : DG_PROF_VOL_RES;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if ((rc = prof_begin(h, st, &e0))) return rc;
-  face_kernel<K, MODE><<<gf, 128, fs, st>>>(a);
+  face_kernel<K, MODE><<<gf, 32 * kFaceWarps, fs, st>>>(a);
   DG_LAUNCH_CHECK(h);
   if ((rc = prof_end(h, cf, st, e0))) return rc;
   if ((rc = prof_begin(h, st, &e1))) return rc;
@@ -637,7 +785,7 @@ int op_project_tgv(Handle* h, double* w, cudaStream_t st) {
 
 // ------------------------------------------------- residual without allocation
 // Scratch of dg_residual_noalloc: the per-face-slot contributions and lifting
-// coefficients of the face pass (N_e * 6 * (4 + 3) * N_b doubles), in a
+// coefficients of the face pass (N_e * 6 * (4 + 3) * N_2 doubles, N_2 = (k+1)(k+2)/2), in a
 // file-scope device array instead of the handle's own buffers. Every GPU that
 // loads the library holds it until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[DG_NOALLOC_SCRATCH_DOUBLES];
@@ -669,17 +817,17 @@ extern "C" int dg_residual_noalloc(dg_handle* hh, const double* w, double* f, vo
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!w || !f || w == f) return fail(h, DG_ERR_ARG, "w and f must be distinct non-null device pointers");
-  const int nb = h->lev[0].nb;
-  const long long need = (long long)h->ne * 6 * 7 * nb;
+  const int n2 = h->tab.n2;
+  const long long need = (long long)h->ne * 6 * 7 * n2;
   if (need > (long long)DG_NOALLOC_SCRATCH_DOUBLES)
     return fail(h, DG_ERR_ARG,
-                "mesh too large for the static scratch of dg_residual_noalloc: it needs N_e*42*N_b = " +
+                "mesh too large for the static scratch of dg_residual_noalloc: it needs N_e*42*N_2 = " +
                     std::to_string(need) + " doubles, the limit is " + std::to_string(DG_NOALLOC_SCRATCH_DOUBLES));
   double* scratch = nullptr;
   int rc = noalloc_scratch(h, &scratch);
   if (rc) return rc;
   OpArgs a = make_args(h, w, f);
   a.face_out = scratch;
-  a.face_lift = scratch + (size_t)h->ne * 6 * 4 * nb;
+  a.face_lift = scratch + (size_t)h->ne * 6 * 4 * n2;
   return dispatch<MODE_RES>(h, a, as_stream(stream));
 }
