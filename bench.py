@@ -69,7 +69,7 @@ FP64_PEAK_TFLOPS = 1.25
 # Fine-level operator applications (residual or Jacobian action) of one stage on this
 # workload, as counted by the library on the GPU (dg_counters); used to scale the
 # oracle's measured cost of one application to seconds per stage.
-ORACLE_APPS_PER_STAGE_DEFAULT = 900
+ORACLE_APPS_PER_STAGE_DEFAULT = 105
 
 
 def env_rank():

@@ -238,6 +238,7 @@ static void free_all(Handle* h) {
   F(h->colour);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
+    F(h->lev[l].Dlin); F(h->lev[l].Blin);
   }
   F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
   F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);

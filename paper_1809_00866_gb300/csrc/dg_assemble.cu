@@ -1,11 +1,13 @@
 // Preconditioner assembly at the current linearisation (Sec. 2.3-2.4):
-//  * element diagonal blocks of G on the fine level, by probing the exact
-//    Jacobian action with unit vectors on the elements of one colour of a
-//    distance-1 colouring (no two face neighbours share a colour);
-//  * off-diagonal blocks at the degree of level 1 only (Sec. 2.4.3: coarse
-//    off-diagonal blocks are built at the coarse degree), by probing the coarse
-//    modes on the elements of one colour of a distance-2 colouring (no element
-//    has two face neighbours of one colour);
+//  * the state-independent linear part of J (viscous and BR2 terms, pressure
+//    gradient, continuity) is probed once per handle with unit vectors on the
+//    elements of one colour: a distance-1 colouring (no two face neighbours share
+//    a colour) for the element diagonal blocks, a distance-2 colouring (no element
+//    has two face neighbours of one colour) for the off-diagonal blocks at the
+//    degree of level 1 (Sec. 2.4.3: coarse off-diagonal blocks are built at the
+//    coarse degree);
+//  * the state-dependent part (convective volume term, Riemann face terms) and
+//    the mass shift are assembled directly per element at every call;
 //  * inherited operators of every coarser level by sub-block extraction
 //    (Eq. (GalProj) with a hierarchical orthonormal basis);
 //  * inverses of all diagonal blocks (element-wise block Jacobi) by in-place
@@ -18,6 +20,208 @@
 #include "dg_internal.h"
 
 namespace dg {
+
+// ------------------------------------------------ direct state-dependent assembly
+// J = J_lin + J_state. J_lin (viscous and BR2 terms, pressure gradient, continuity)
+// depends on the mesh only; its blocks are probed once per handle (MODE_LINPART).
+// J_state is assembled here per element from the cached linearisation:
+//  * convective volume term: -int (u_p u_i)' d_p phi_m with weighted mass matrices
+//    U_c[n'][n] = sum_q w_q ubar_c(q) phi_hat_n'(q) phi_hat_n(q) (|K|/8 / s^2 = 1):
+//    A[i,m; j,n] = -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n];
+//  * Riemann face terms: with the cached flux Jacobian dF_i/ds_j at the face points
+//    and phi_m on a face = P_hat_a(+-1) B2[q][n2(m)] / s, each face adds
+//    sign * A4/(s s') P_hat_a(side) P_hat_a'(side') E_ij[n2(m)][n2(n)],
+//    E_ij = sum_q w2_q dF_i/ds_j(q) B2[q][n2] B2[q][n2'].
+// Diagonal blocks use the own side's columns of the Jacobian; the level-1 off-diagonal
+// blocks the other side's, restricted to the coarse modes.
+template <int K>
+struct AsmSmem {
+  static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
+  static constexpr int B = 0;                 // [NQ][NB]
+  static constexpr int W = B + NQ * NB;       // [NQ]
+  static constexpr int UB = W + NQ;           // [3][NQ]
+  static constexpr int U = UB + 3 * NQ;       // [3][NB][NB]
+  static constexpr int E = U + 3 * NB * NB;   // [6][N2][N2]
+  static constexpr int JQ = E + 6 * N2 * N2;  // [6][NQF] Jacobian entry of the current pair at the face points
+  static constexpr int B2 = JQ + 6 * NQF;     // [NQF][N2]
+  static constexpr int W2 = B2 + NQF * N2;    // [NQF]
+  static constexpr int PV = W2 + NQF;         // [2][K+1]
+  static constexpr int DOUBLES = PV + 2 * (K + 1);
+  static constexpr int FMAP = 0;              // [3][NB]
+  static constexpr int FA = FMAP + 3 * NB;    // [3][NB]
+  static constexpr int INTS = FA + 3 * NB;
+  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+};
+
+struct AsmArgs {
+  MeshDev M;
+  Tables T;
+  const double* ubar;
+  const double* dFlux;
+  const double* Dlin;  // level 0 linear-part diagonal blocks
+  double* D;           // level 0 diagonal blocks (output)
+  const double* Blin;  // level 1 linear-part off-diagonal blocks
+  double* Bsr;         // level 1 block rows (output, slots 1..6)
+  int nb1;             // modes per variable on level 1 (0: no coarse level)
+  double inv_gdt;
+};
+
+template <int K>
+__global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
+  using L = AsmSmem<K>;
+  constexpr int NB = L::NB, NQ = L::NQ, NQF = L::NQF, N2 = L::N2, K1 = K + 1, BS = 4 * NB, DW = Tables::kDw;
+  extern __shared__ double sm[];
+  double* sB = sm + L::B;
+  double* sW = sm + L::W;
+  double* sUb = sm + L::UB;
+  double* sU = sm + L::U;
+  double* sE = sm + L::E;
+  double* sJ = sm + L::JQ;
+  double* sB2 = sm + L::B2;
+  double* sW2 = sm + L::W2;
+  double* sPV = sm + L::PV;
+  int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
+  int* FMAP = ism + L::FMAP;
+  int* FA = ism + L::FA;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.T.Bvol[t];
+  for (int t = tid; t < NQ; t += nt) sW[t] = a.T.wvol[t];
+  for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.T.B2[t];
+  for (int t = tid; t < NQF; t += nt) sW2[t] = a.T.W2[t];
+  for (int t = tid; t < 2 * K1; t += nt) sPV[t] = a.T.pv[t];
+  for (int t = tid; t < 3 * NB; t += nt) { FMAP[t] = a.T.fmap[t]; FA[t] = a.T.fa[t]; }
+  __syncthreads();
+  for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
+    const ElemGeom g = elem_geom(a.M, e);
+    const double Jd[3] = {2.0 / g.h[0], 2.0 / g.h[1], 2.0 / g.h[2]};
+    for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
+    __syncthreads();
+    // weighted mass matrices U_c (symmetric)
+    for (int t = tid; t < 3 * NB * NB; t += nt) {
+      const int c = t / (NB * NB), r = t - c * NB * NB, n1 = r / NB, n = r - n1 * NB;
+      if (n1 > n) continue;
+      double acc = 0.0;
+      for (int q = 0; q < NQ; ++q) acc += sW[q] * sUb[c * NQ + q] * sB[q * NB + n1] * sB[q * NB + n];
+      sU[(c * NB + n1) * NB + n] = acc;
+      sU[(c * NB + n) * NB + n1] = acc;
+    }
+    __syncthreads();
+    // face geometry of the six slots: face index, own side, Jacobian column offset, scale
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        // Jacobian entry (i, own j) at the points of the six faces
+        for (int t = tid; t < 6 * NQF; t += nt) {
+          const int sl = t / NQF, q = t - sl * NQF, d = sl >> 1, side = (sl & 1) ? 0 : 1;
+          const int f = side == 0 ? 3 * e + d : 3 * a.M.nbr[e * 6 + 2 * d] + d;
+          sJ[t] = a.dFlux[((size_t)f * NQF + q) * 32 + i * 8 + (side == 0 ? 0 : 4) + j] * sW2[q];
+        }
+        __syncthreads();
+        for (int t = tid; t < 6 * N2 * N2; t += nt) {
+          const int sl = t / (N2 * N2), r = t - sl * N2 * N2, j1 = r / N2, j2 = r - j1 * N2;
+          double acc = 0.0;
+#pragma unroll
+          for (int q = 0; q < NQF; ++q) acc += sJ[sl * NQF + q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
+          sE[t] = acc;
+        }
+        __syncthreads();
+        double* Dout = a.D + (size_t)e * BS * BS;
+        const double* Dl = a.Dlin + (size_t)e * BS * BS;
+        for (int t = tid; t < NB * NB; t += nt) {
+          const int n = t / NB, m = t - n * NB;  // column-major within the pair: consecutive threads, consecutive rows
+          double v = Dl[(size_t)(j * NB + n) * BS + i * NB + m];
+          if (i == j && i < 3 && m == n) v += a.inv_gdt;
+          if (i < 3 && j < 3) {
+            // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
+            double cv = 0.0;
+#pragma unroll
+            for (int q = 0; q < DW; ++q) {
+              const int o = (j * NB + m) * DW + q;
+              cv += a.T.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
+            }
+            v -= Jd[j] * cv;
+            if (i == j) {
+#pragma unroll
+              for (int pp = 0; pp < 3; ++pp) {
+                double c2 = 0.0;
+#pragma unroll
+                for (int q = 0; q < DW; ++q) {
+                  const int o = (pp * NB + m) * DW + q;
+                  c2 += a.T.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
+                }
+                v -= Jd[pp] * c2;
+              }
+            }
+          }
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) {
+            const int d = sl >> 1, side = (sl & 1) ? 0 : 1;
+            const double scale = (side == 0 ? 1.0 : -1.0) * Jd[d];  // A4 / s^2 = 2 / h_d
+            v += scale * sPV[side * K1 + FA[d * NB + m]] * sPV[side * K1 + FA[d * NB + n]] *
+                 sE[(sl * N2 + FMAP[d * NB + m]) * N2 + FMAP[d * NB + n]];
+          }
+          Dout[(size_t)(j * NB + n) * BS + i * NB + m] = v;
+        }
+        __syncthreads();
+      }
+    // level-1 off-diagonal blocks: the other side's Jacobian columns, coarse modes only
+    if (a.nb1 > 0) {
+      const int nb1 = a.nb1, b1 = 4 * nb1;
+      for (int sl = 0; sl < 6; ++sl) {
+        const int d = sl >> 1, side = (sl & 1) ? 0 : 1, other = 1 - side;
+        const int p = a.M.nbr[e * 6 + sl];
+        const int f = side == 0 ? 3 * e + d : 3 * p + d;
+        int tgt = sl;
+        for (int s2 = 0; s2 < sl; ++s2)
+          if (a.M.nbr[e * 6 + s2] == p) { tgt = s2; break; }
+        const ElemGeom gp = elem_geom(a.M, p);
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        const double scale = (side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] / (g.s * gp.s);
+        double* blk = a.Bsr + ((size_t)e * 7 + 1 + tgt) * b1 * b1;
+        const double* lin = a.Blin + ((size_t)e * 7 + 1 + sl) * b1 * b1;
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) {
+            for (int t = tid; t < NQF; t += nt)
+              sJ[t] = a.dFlux[((size_t)f * NQF + t) * 32 + i * 8 + (other == 0 ? 0 : 4) + j] * sW2[t];
+            __syncthreads();
+            for (int t = tid; t < N2 * N2; t += nt) {
+              const int j1 = t / N2, j2 = t - j1 * N2;
+              double acc = 0.0;
+#pragma unroll
+              for (int q = 0; q < NQF; ++q) acc += sJ[q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
+              sE[t] = acc;
+            }
+            __syncthreads();
+            for (int t = tid; t < nb1 * nb1; t += nt) {
+              const int n = t / nb1, m = t - n * nb1;
+              const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
+              const double base = (tgt == sl) ? lin[o] : blk[o];
+              blk[o] = base + scale * sPV[side * K1 + FA[d * NB + m]] * sPV[other * K1 + FA[d * NB + n]] *
+                                  sE[FMAP[d * NB + m] * N2 + FMAP[d * NB + n]];
+            }
+            __syncthreads();
+          }
+        if (tgt != sl) {
+          double* z = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
+          for (int t = tid; t < b1 * b1; t += nt) z[t] = 0.0;
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+template <int K>
+static int launch_assemble_state(Handle* h, const AsmArgs& a, cudaStream_t st) {
+  const size_t smem = AsmSmem<K>::bytes();
+  DG_CUDA(h, cudaFuncSetAttribute(assemble_state_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = (int)((200 * 1024) / smem);
+  per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+  int grid = h->nsm * per_sm;
+  if (grid > h->ne) grid = h->ne;
+  assemble_state_kernel<K><<<grid, 256, smem, st>>>(a);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
 
 static std::vector<int> greedy_colouring(const Handle* h, int dist) {
   const int ne = h->ne;
@@ -33,6 +237,15 @@ static std::vector<int> greedy_colouring(const Handle* h, int dist) {
     nb6[e * 6 + 4] = id(i, j, k - 1); nb6[e * 6 + 5] = id(i, j, k + 1);
   }
   std::vector<int> col(ne, -1);
+  if (dist == 2 && h->n[0] % 8 == 0 && h->n[1] % 8 == 0 && h->n[2] % 8 == 0) {
+    // (i + 2j + 3k) mod 8: the six neighbour offsets +-1, +-2, +-3 are distinct and non-zero mod 8,
+    // so no element shares a colour with a neighbour or with a neighbour's neighbour
+    for (int e = 0; e < ne; ++e) {
+      const int i = e % h->n[0], j = (e / h->n[0]) % h->n[1], k = e / (h->n[0] * h->n[1]);
+      col[e] = (i + 2 * j + 3 * k) % 8;
+    }
+    return col;
+  }
   std::vector<int> mark(64, -1);
   for (int e = 0; e < ne; ++e) {
     std::vector<int> around;
@@ -193,6 +406,50 @@ static int invert_blocks(Handle* h, int nblk, int b, const double* in, double* o
   return DG_OK;
 }
 
+// Blocks of the state-independent linear part of J (viscous and BR2 terms, pressure
+// gradient, continuity), probed once per handle: element diagonal blocks on level 0 and
+// the level-1 off-diagonal blocks.
+static int probe_linear_part(Handle* h, cudaStream_t st) {
+  const int ne = h->ne;
+  Level& L0 = h->lev[0];
+  const int b0 = L0.b;
+  const int grid = h->nsm * 8;
+  int rc;
+  if (!h->colour) DG_CUDA(h, cudaMalloc((void**)&h->colour, sizeof(int) * ne));
+  int* dcol = h->colour;
+  double* probe = L0.t0;
+  double* out = L0.t1;
+  const std::vector<int> c1 = greedy_colouring(h, 1);
+  const int nc1 = *std::max_element(c1.begin(), c1.end()) + 1;
+  DG_CUDA(h, cudaMemcpyAsync(dcol, c1.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+  for (int c = 0; c < nc1; ++c)
+    for (int j = 0; j < b0; ++j) {
+      probe_kernel<<<grid, 256, 0, st>>>(L0.n, b0, dcol, c, j, probe);
+      DG_LAUNCH_CHECK(h);
+      if ((rc = op_linear_part(h, probe, out, st))) return rc;
+      scatter_diag_kernel<<<grid, 256, 0, st>>>(ne, b0, dcol, c, j, out, L0.Dlin);
+      DG_LAUNCH_CHECK(h);
+    }
+  if (h->nlev > 1) {
+    Level& L1 = h->lev[1];
+    const int b1 = L1.b;
+    DG_CUDA(h, cudaMemsetAsync(L1.Blin, 0, sizeof(double) * (size_t)b1 * b1 * 7 * ne, st));
+    const std::vector<int> c2 = greedy_colouring(h, 2);
+    const int nc2 = *std::max_element(c2.begin(), c2.end()) + 1;
+    DG_CUDA(h, cudaMemcpyAsync(dcol, c2.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+    for (int c = 0; c < nc2; ++c)
+      for (int jc = 0; jc < b1; ++jc) {
+        const int jf = (jc / L1.nb) * L0.nb + jc % L1.nb;
+        probe_kernel<<<grid, 256, 0, st>>>(L0.n, b0, dcol, c, jf, probe);
+        DG_LAUNCH_CHECK(h);
+        if ((rc = op_linear_part(h, probe, out, st))) return rc;
+        scatter_offdiag_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L1.nb, h->nbr, dcol, c, jc, out, L1.Blin);
+        DG_LAUNCH_CHECK(h);
+      }
+  }
+  return DG_OK;
+}
+
 int assemble_all(Handle* h, cudaStream_t st) {
   const int ne = h->ne;
   Level& L0 = h->lev[0];
@@ -206,59 +463,51 @@ int assemble_all(Handle* h, cudaStream_t st) {
     if (!L.Dblk) DG_CUDA(h, cudaMalloc((void**)&L.Dblk, sizeof(double) * bb * ne));
     if (!L.Dinv) DG_CUDA(h, cudaMalloc((void**)&L.Dinv, sizeof(double) * bb * ne));
     if (l >= 1 && !L.Bsr) DG_CUDA(h, cudaMalloc((void**)&L.Bsr, sizeof(double) * bb * 7 * ne));
+    if (l == 0 && !L.Dlin) DG_CUDA(h, cudaMalloc((void**)&L.Dlin, sizeof(double) * bb * ne));
+    if (l == 1 && !L.Blin) DG_CUDA(h, cudaMalloc((void**)&L.Blin, sizeof(double) * bb * 7 * ne));
   }
-  // --- fine diagonal blocks
-  const std::vector<int> c1 = greedy_colouring(h, 1);
-  const int nc1 = *std::max_element(c1.begin(), c1.end()) + 1;
-  if (!h->colour) DG_CUDA(h, cudaMalloc((void**)&h->colour, sizeof(int) * ne));
-  int* dcol = h->colour;
-  DG_CUDA(h, cudaMemcpyAsync(dcol, c1.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, st));
-  double* probe = L0.t0;
-  double* out = L0.t1;
-  for (int c = 0; c < nc1; ++c)
-    for (int j = 0; j < b0; ++j) {
-      probe_kernel<<<grid, 256, 0, st>>>(L0.n, b0, dcol, c, j, probe);
-      DG_LAUNCH_CHECK(h);
-      if ((rc = op_tangent(h, probe, out, st))) return rc;
-      scatter_diag_kernel<<<grid, 256, 0, st>>>(ne, b0, dcol, c, j, out, L0.Dblk);
-      DG_LAUNCH_CHECK(h);
-    }
-  // --- coarse levels
-  if (h->nlev > 1) {
-    Level& L1 = h->lev[1];
-    const int b1 = L1.b;
-    DG_CUDA(h, cudaMemsetAsync(L1.Bsr, 0, sizeof(double) * (size_t)b1 * b1 * 7 * ne, st));
-    const std::vector<int> c2 = greedy_colouring(h, 2);
-    const int nc2 = *std::max_element(c2.begin(), c2.end()) + 1;
-    DG_CUDA(h, cudaMemcpyAsync(dcol, c2.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, st));
-    for (int c = 0; c < nc2; ++c)
-      for (int jc = 0; jc < b1; ++jc) {
-        const int jf = (jc / L1.nb) * L0.nb + jc % L1.nb;
-        probe_kernel<<<grid, 256, 0, st>>>(L0.n, b0, dcol, c, jf, probe);
+  if (!h->linpart_ready) {
+    if ((rc = probe_linear_part(h, st))) return rc;
+    h->linpart_ready = true;
+  }
+  // state-dependent part + linear part + mass: level-0 diagonal and level-1 off-diagonal blocks
+  AsmArgs a;
+  a.M = mesh_dev(h);
+  a.T = h->tab;
+  a.ubar = h->ubar;
+  a.dFlux = h->dFlux;
+  a.Dlin = L0.Dlin;
+  a.D = L0.Dblk;
+  a.Blin = h->nlev > 1 ? h->lev[1].Blin : nullptr;
+  a.Bsr = h->nlev > 1 ? h->lev[1].Bsr : nullptr;
+  a.nb1 = h->nlev > 1 ? h->lev[1].nb : 0;
+  a.inv_gdt = h->inv_gdt;
+  switch (h->tab.k) {
+    case 1: rc = launch_assemble_state<1>(h, a, st); break;
+    case 2: rc = launch_assemble_state<2>(h, a, st); break;
+    case 3: rc = launch_assemble_state<3>(h, a, st); break;
+    case 4: rc = launch_assemble_state<4>(h, a, st); break;
+    default: rc = fail(h, DG_ERR_ARG, "unsupported degree");
+  }
+  if (rc) return rc;
+  // coarse levels: inherited sub-blocks
+  for (int l = 1; l < h->nlev; ++l) {
+    Level& L = h->lev[l];
+    const size_t bb = (size_t)L.b * L.b;
+    subblock_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, L0.Dblk, (long long)b0 * b0, L.Dblk, (long long)bb);
+    DG_LAUNCH_CHECK(h);
+    subblock_kernel<<<grid, 256, 0, st>>>(ne, L.nb, L.nb, L.Dblk, (long long)bb, L.Bsr, (long long)bb * 7);
+    DG_LAUNCH_CHECK(h);
+    if (l >= 2) {
+      const Level& P = h->lev[l - 1];
+      for (int s = 1; s < 7; ++s) {
+        subblock_kernel<<<grid, 256, 0, st>>>(ne, P.nb, L.nb, P.Bsr + (size_t)s * P.b * P.b, (long long)P.b * P.b * 7,
+                                              L.Bsr + (size_t)s * bb, (long long)bb * 7);
         DG_LAUNCH_CHECK(h);
-        if ((rc = op_tangent(h, probe, out, st))) return rc;
-        scatter_offdiag_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L1.nb, h->nbr, dcol, c, jc, out, L1.Bsr);
-        DG_LAUNCH_CHECK(h);
-      }
-    for (int l = 1; l < h->nlev; ++l) {
-      Level& L = h->lev[l];
-      const size_t bb = (size_t)L.b * L.b;
-      // diagonal: leading sub-block of the fine diagonal block
-      subblock_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, L0.Dblk, (long long)b0 * b0, L.Dblk, (long long)bb);
-      DG_LAUNCH_CHECK(h);
-      subblock_kernel<<<grid, 256, 0, st>>>(ne, L.nb, L.nb, L.Dblk, (long long)bb, L.Bsr, (long long)bb * 7);
-      DG_LAUNCH_CHECK(h);
-      if (l >= 2) {
-        const Level& P = h->lev[l - 1];
-        for (int s = 1; s < 7; ++s) {
-          subblock_kernel<<<grid, 256, 0, st>>>(ne, P.nb, L.nb, P.Bsr + (size_t)s * P.b * P.b,
-                                                (long long)P.b * P.b * 7, L.Bsr + (size_t)s * bb, (long long)bb * 7);
-          DG_LAUNCH_CHECK(h);
-        }
       }
     }
   }
-  // --- inverses
+  // inverses
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];
     if ((rc = invert_blocks(h, ne, L.b, L.Dblk, L.Dinv, st))) return rc;

@@ -53,6 +53,8 @@ struct Level {
   double* Dblk = nullptr;    // [ne][b][b] diagonal blocks, column-major per block
   double* Dinv = nullptr;    // [ne][b][b] inverses, column-major per block
   double* Bsr = nullptr;     // [ne][7][b][b] level >= 1: slot 0 diagonal, slots 1..6 faces -x,+x,-y,+y,-z,+z
+  double* Dlin = nullptr;    // level 0: [ne][b][b] diagonal blocks of the state-independent linear part
+  double* Blin = nullptr;    // level 1: [ne][7][b][b] off-diagonal blocks of the linear part (slot 0 unused)
   double* t0 = nullptr;      // work vectors of length n
   double* t1 = nullptr;
   double* t2 = nullptr;
@@ -77,6 +79,7 @@ struct Handle {
   // linearisation cache
   bool linearized = false;
   bool assembled = false;
+  bool linpart_ready = false;  // Dlin / Blin probed (they depend on the mesh only)
   double inv_gdt = 0.0;
   double* wlin = nullptr;   // [n0]
   double* flin = nullptr;   // [n0] f_h(wlin)
@@ -161,6 +164,7 @@ __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
 // operator entry points (dg_operator.cu)
 int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStream_t st);
 int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st);
+int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_fd(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_project_tgv(Handle* h, double* w, cudaStream_t st);
 

@@ -40,7 +40,9 @@ struct Sz {
   static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1;
 };
 
-enum { MODE_RES = 0, MODE_RES_LIN = 1, MODE_TAN = 2 };
+// MODE_LINPART: the state-independent linear part of the Jacobian action (viscous and BR2
+// terms, pressure gradient, continuity); no convective product, no Riemann flux, no mass.
+enum { MODE_RES = 0, MODE_RES_LIN = 1, MODE_TAN = 2, MODE_LINPART = 3 };
 
 template <int K>
 struct Sz2 {
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
       double uL[3] = {V0[q], V0[NQF + q], V0[2 * NQF + q]};
       double uR[3] = {V1[q], V1[NQF + q], V1[2 * NQF + q]};
       const double pL = V0[3 * NQF + q], pR = V1[3 * NQF + q];
-      double Fc[4];
+      double Fc[4] = {0.0, 0.0, 0.0, 0.0};
       if (MODE == MODE_TAN) {
         const double* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
         const double ds[8] = {uL[0], uL[1], uL[2], pL, uR[0], uR[1], uR[2], pR};
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) Jq[i * 8 + j] = Jm[i][j];
-      } else {
+      } else if (MODE == MODE_RES) {
         ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status);
       }
 #pragma unroll
@@ -553,6 +555,9 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
       if (MODE == MODE_TAN) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = a.ubar[((size_t)e * 3 + c) * NQ + q];
+      } else if (MODE == MODE_LINPART) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ub[c] = 0.0;
       } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = u[c];
@@ -565,7 +570,8 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
       for (int sp = 0; sp < 6; ++sp) {
         int p, i;
         if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
-        const double v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i]) : u[p] * u[i];
+        const double v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i])
+                         : (MODE == MODE_LINPART) ? 0.0 : u[p] * u[i];
         sPr[sp * NQ + q] = v * wq;
       }
     }
@@ -717,8 +723,8 @@ static int run_operator(Handle* h, const OpArgs& a, cudaStream_t st) {
   const int fblocks = (nfaces + kFaceWarps - 1) / kFaceWarps;
   if (gf > fblocks) gf = fblocks;
   if (gv > h->ne) gv = h->ne;
-  const int cf = MODE == MODE_TAN ? DG_PROF_FACE_TAN : DG_PROF_FACE_RES;
-  const int cv = MODE == MODE_TAN ? DG_PROF_VOL_TAN : DG_PROF_VOL_RES;
+  const int cf = (MODE == MODE_TAN || MODE == MODE_LINPART) ? DG_PROF_FACE_TAN : DG_PROF_FACE_RES;
+  const int cv = (MODE == MODE_TAN || MODE == MODE_LINPART) ? DG_PROF_VOL_TAN : DG_PROF_VOL_RES;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if ((rc = prof_begin(h, st, &e0))) return rc;
@@ -752,6 +758,11 @@ int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStrea
 int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st) {
   OpArgs a = make_args(h, v, out);
   return dispatch<MODE_TAN>(h, a, st);
+}
+
+int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st) {
+  OpArgs a = make_args(h, v, out);
+  return dispatch<MODE_LINPART>(h, a, st);
 }
 
 int op_fd(Handle* h, const double* v, double* out, cudaStream_t st) {
