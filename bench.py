@@ -196,8 +196,10 @@ def run_ours(args):
     n0 = dg.n[0]
     dt = S.acoustic_dt(cfg["n"], k)
     inv = 1.0 / dt
-    opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=2, post_sweeps=2,
-                        coarse_sweeps=2, omega=1.0)
+    pre, post, coarse = (int(x) for x in args.sweeps.split(","))
+    smoother = P.DG_SMOOTH_GMRES if args.smoother == "gmres" else P.DG_SMOOTH_JACOBI
+    opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=pre,
+                        post_sweeps=post, coarse_sweeps=coarse, omega=1.0, smoother=smoother)
     st = torch.cuda.current_stream()
     w = dg.empty()
     dg.dg_project_tgv(w)
@@ -325,7 +327,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
                                    "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
-                       "dofs": n0, "dt": dt, "solver": "FGMRES(30) + MG_V, 2 block-Jacobi sweeps per level",
+                       "dofs": n0, "dt": dt,
+                       "solver": "FGMRES(30) + MG_V, %s smoother, pre/post/coarse %s" % (args.smoother, args.sweeps),
                        "l2": "flushed (512 MB write) before every timed stage and Jacobian action",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "jv": {"value": jv_gdofs, "unit": "GDOF/s", "mode": "exact (tangent)", "ms": 1e3 * t_jv},
@@ -356,6 +359,8 @@ def main():
     ap.add_argument("--jv-reps", type=int, default=30)
     ap.add_argument("--oracle-apps", type=int, default=ORACLE_APPS_PER_STAGE_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi")
+    ap.add_argument("--sweeps", default="2,2,2", help="pre,post,coarse smoothing iterations")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

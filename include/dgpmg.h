@@ -75,6 +75,13 @@ typedef struct dg_handle dg_handle;
 #define DG_PREC_VCYCLE 1  /* one MG_V cycle (Algorithm 2) per outer iteration */
 #define DG_PREC_FULLV 2   /* one MG_full cycle (Algorithm 3) per outer iteration */
 
+/* Smoothers of the p-multigrid cycles (Sec. 2.4.3). */
+#define DG_SMOOTH_JACOBI 0 /* damped element-block-Jacobi sweeps x <- x + omega D^-1 (g - G x) */
+#define DG_SMOOTH_GMRES 1  /* GMRES iterations left-preconditioned by the element block inverses
+                              (EWBJ), restarted at every call, from the current iterate; at most
+                              DG_SMOOTH_MAX_ITS iterations per call */
+#define DG_SMOOTH_MAX_ITS 32
+
 typedef struct dg_solve_opts {
   int restart;       /* Krylov subspace size m before a restart (1..64) */
   int maxit;         /* maximum number of outer iterations */
@@ -87,6 +94,7 @@ typedef struct dg_solve_opts {
   double omega;      /* block-Jacobi damping (0, 1] */
   int jvp_mode;      /* DG_JVP_TANGENT or DG_JVP_FD for the fine-level G products of the outer solve */
   int x0_is_zero;    /* 1: x holds no initial guess (treated as 0, not read) */
+  int smoother;      /* DG_SMOOTH_JACOBI or DG_SMOOTH_GMRES: what the sweep counts above count */
 } dg_solve_opts;
 
 typedef struct dg_solve_info {
@@ -171,7 +179,7 @@ int block_jacobi_smooth(dg_handle* h, int lvl, const double* g, double* x, int s
 int bsr_spmv(dg_handle* h, int lvl, double alpha, const double* x, double beta, double* y, void* stream);
 
 /* x <- MG_V(0, g, 0) (Algorithm 2) with the smoothing options of opts; the
- * coarsest-level SOLVE is opts->coarse_sweeps block-Jacobi sweeps from zero. */
+ * coarsest-level SOLVE is opts->coarse_sweeps iterations of the smoother from zero. */
 int pmg_vcycle(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, void* stream);
 
 /* Solve G x = g with right-preconditioned flexible GMRES(restart) (Sec.

@@ -100,6 +100,58 @@ def block_jacobi(matvec, Dinv, g, x, sweeps, omega=1.0):
     return x
 
 
+def gmres_smooth(matvec, Dinv, g, x, iters):
+    """``iters`` iterations of GMRES left-preconditioned by the element block inverses (EWBJ).
+
+    The smoother of Sec. 2.4.3 ("all the smoothers of the multigrid strategy are
+    GMRES"): from x, minimise ||D^{-1}(g - G y)||_2 over y in x + K_iters(D^{-1}G, D^{-1}(g - G x)),
+    built by modified Gram-Schmidt Arnoldi with Givens rotations; no restart.
+    """
+    x = np.array(x, dtype=np.float64, copy=True)
+    r = apply_block_inverse(Dinv, g - matvec(x))
+    beta = np.linalg.norm(r)
+    if iters <= 0 or beta == 0.0:
+        return x
+    n = g.size
+    V = np.zeros((iters + 1, n))
+    H = np.zeros((iters + 1, iters))
+    V[0] = r / beta
+    cs = np.zeros(iters)
+    sn = np.zeros(iters)
+    s = np.zeros(iters + 1)
+    s[0] = beta
+    k = 0
+    for j in range(iters):
+        w = apply_block_inverse(Dinv, matvec(V[j]))
+        for i in range(j + 1):
+            H[i, j] = np.dot(w, V[i])
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] != 0.0:
+            V[j + 1] = w / H[j + 1, j]
+        for i in range(j):
+            t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+            H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+            H[i, j] = t
+        den = np.hypot(H[j, j], H[j + 1, j])
+        cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+        H[j, j] = den
+        H[j + 1, j] = 0.0
+        s[j + 1] = -sn[j] * s[j]
+        s[j] = cs[j] * s[j]
+        k = j + 1
+        if H[j + 1, j] == 0.0 and den == 0.0:
+            break
+    y = np.linalg.solve(np.triu(H[:k, :k]), s[:k])
+    return x + V[:k].T @ y
+
+
+def smooth(smoother, matvec, Dinv, g, x, iters, omega):
+    if smoother == "gmres":
+        return gmres_smooth(matvec, Dinv, g, x, iters)
+    return block_jacobi(matvec, Dinv, g, x, iters, omega)
+
+
 class Level:
     """One p-multigrid level: operator (callable), block inverses, sizes."""
 
@@ -107,31 +159,36 @@ class Level:
         self.matvec, self.Dinv, self.ne, self.nb = matvec, Dinv, ne, nb
 
 
-def mg_v(levels, l, g, x, pre=2, post=2, coarse_sweeps=2, omega=1.0):
-    """MG_V(l, g_l, w_l) of Algorithm 2; the coarsest SOLVE is ``coarse_sweeps`` block-Jacobi sweeps from 0."""
+def mg_v(levels, l, g, x, pre=2, post=2, coarse_sweeps=2, omega=1.0, smoother="jacobi"):
+    """MG_V(l, g_l, w_l) of Algorithm 2.
+
+    SMOOTH is ``pre`` / ``post`` iterations of the chosen smoother (damped element-block
+    Jacobi sweeps, or GMRES left-preconditioned by the element block inverses); the
+    coarsest SOLVE is ``coarse_sweeps`` iterations of the same smoother from 0.
+    """
     L = len(levels) - 1
     lv = levels[l]
     if l == L:
-        return block_jacobi(lv.matvec, lv.Dinv, g, np.zeros_like(g), coarse_sweeps, omega)
-    xb = block_jacobi(lv.matvec, lv.Dinv, g, x, pre, omega)            # pre-smoothing
+        return smooth(smoother, lv.matvec, lv.Dinv, g, np.zeros_like(g), coarse_sweeps, omega)
+    xb = smooth(smoother, lv.matvec, lv.Dinv, g, x, pre, omega)       # pre-smoothing
     d = g - lv.matvec(xb)                                              # defect
     dc = restrict(d, lv.ne, lv.nb, levels[l + 1].nb)                   # restriction
-    e = mg_v(levels, l + 1, dc, np.zeros_like(dc), pre, post, coarse_sweeps, omega)
+    e = mg_v(levels, l + 1, dc, np.zeros_like(dc), pre, post, coarse_sweeps, omega, smoother)
     xh = xb + prolong(e, lv.ne, lv.nb, levels[l + 1].nb)               # coarse-grid correction
-    return block_jacobi(lv.matvec, lv.Dinv, g, xh, post, omega)        # post-smoothing
+    return smooth(smoother, lv.matvec, lv.Dinv, g, xh, post, omega)   # post-smoothing
 
 
-def mg_full(levels, l, g, pre=2, post=2, coarse_sweeps=2, omega=1.0):
+def mg_full(levels, l, g, pre=2, post=2, coarse_sweeps=2, omega=1.0, smoother="jacobi"):
     """MG_full(l, g_l, 0) of Algorithm 3."""
     L = len(levels) - 1
     lv = levels[l]
     if l == L:
-        return block_jacobi(lv.matvec, lv.Dinv, g, np.zeros_like(g), coarse_sweeps, omega)
+        return smooth(smoother, lv.matvec, lv.Dinv, g, np.zeros_like(g), coarse_sweeps, omega)
     gc = restrict(g, lv.ne, lv.nb, levels[l + 1].nb)
-    wc = mg_full(levels, l + 1, gc, pre, post, coarse_sweeps, omega)
+    wc = mg_full(levels, l + 1, gc, pre, post, coarse_sweeps, omega, smoother)
     wh = prolong(wc, lv.ne, lv.nb, levels[l + 1].nb)
     d = g - lv.matvec(wh)
-    e = mg_v(levels, l, d, np.zeros_like(d), pre, post, coarse_sweeps, omega)
+    e = mg_v(levels, l, d, np.zeros_like(d), pre, post, coarse_sweeps, omega, smoother)
     return wh + e
 
 

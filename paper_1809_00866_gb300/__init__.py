@@ -26,6 +26,8 @@ DG_JVP_FD = 1
 DG_PREC_NONE = 0
 DG_PREC_VCYCLE = 1
 DG_PREC_FULLV = 2
+DG_SMOOTH_JACOBI = 0
+DG_SMOOTH_GMRES = 1
 DG_MAX_LEVELS = 4
 
 # Every exported symbol of include/dgpmg.h
@@ -49,7 +51,7 @@ class DgSolveOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("fixed_its", ctypes.c_int), ("precond", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("omega", ctypes.c_double),
-                ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int)]
+                ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class DgSolveInfo(ctypes.Structure):
@@ -105,9 +107,10 @@ class DgError(RuntimeError):
 
 
 def solve_opts(restart=30, maxit=200, rtol=1e-8, fixed_its=0, precond=DG_PREC_VCYCLE, pre_sweeps=2,
-               post_sweeps=2, coarse_sweeps=2, omega=1.0, jvp_mode=DG_JVP_TANGENT, x0_is_zero=1):
+               post_sweeps=2, coarse_sweeps=2, omega=1.0, jvp_mode=DG_JVP_TANGENT, x0_is_zero=1,
+               smoother=DG_SMOOTH_JACOBI):
     return DgSolveOpts(restart, maxit, rtol, fixed_its, precond, pre_sweeps, post_sweeps, coarse_sweeps, omega,
-                       jvp_mode, x0_is_zero)
+                       jvp_mode, x0_is_zero, smoother)
 
 
 class DG:

@@ -243,6 +243,8 @@ static void free_all(Handle* h) {
   F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
   F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);
   if (h->hcol_host) cudaFreeHost(h->hcol_host);
+  for (int l = 0; l < DG_MAX_LEVELS; ++l) F(h->smV[l]);
+  F(h->smSmall);
 }
 
 static int create(const dg_params* p, Handle* h) {

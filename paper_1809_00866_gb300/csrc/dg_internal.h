@@ -98,6 +98,10 @@ struct Handle {
   double* Z = nullptr;  // [m][n0]
   double* hcol = nullptr;     // device [m+2]
   double* hcol_host = nullptr;  // pinned [m+2]
+  // GMRES smoother workspace: per-level Krylov basis and small device arrays
+  double* smV[DG_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};  // [(its+1)][n_l]
+  int smV_its[DG_MAX_LEVELS] = {0, 0, 0, 0};
+  double* smSmall = nullptr;  // H, dots, squared norms, beta^2, -y
   std::string err;
   // instrumentation
   long long launches = 0;

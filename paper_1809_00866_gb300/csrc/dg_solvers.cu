@@ -91,7 +91,8 @@ __global__ void axpby_kernel(long long n, double a, const double* x, double b, d
 }
 
 __global__ void scale_by_dev_kernel(long long n, const double* x, const double* dnorm2, double* y) {
-  const double inv = 1.0 / sqrt(*dnorm2);
+  const double nv = sqrt(*dnorm2);
+  const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = x[i] * inv;
 }
@@ -181,8 +182,8 @@ int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st
 }
 
 // sweeps of x <- x + omega D^-1 (g - G x) on level lvl; x_zero: the initial x is 0
-static int smooth(Handle* h, int lvl, const double* g, double* x, int sweeps, double omega, bool x_zero,
-                  cudaStream_t st) {
+static int jacobi_sweeps(Handle* h, int lvl, const double* g, double* x, int sweeps, double omega, bool x_zero,
+                         cudaStream_t st) {
   Level& L = h->lev[lvl];
   const size_t smem = sizeof(double) * L.b;
   for (int s = 0; s < sweeps; ++s) {
@@ -197,6 +198,138 @@ static int smooth(Handle* h, int lvl, const double* g, double* x, int sweeps, do
   }
   if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
   return DG_OK;
+}
+
+// small device arrays of the GMRES smoother (offsets into h->smSmall)
+constexpr int kSmH = 0;                                                     // [(its+1) * its] column-major
+constexpr int kSmTmp = kSmH + (DG_SMOOTH_MAX_ITS + 1) * DG_SMOOTH_MAX_ITS;  // [its+1] dot products
+constexpr int kSmHn2 = kSmTmp + DG_SMOOTH_MAX_ITS + 1;                      // [its] squared norms
+constexpr int kSmBeta2 = kSmHn2 + DG_SMOOTH_MAX_ITS;                        // [1]
+constexpr int kSmNy = kSmBeta2 + 1;                                         // [its] -y
+constexpr int kSmTotal = kSmNy + DG_SMOOTH_MAX_ITS;
+
+// H[col j][0..nv) (+)= src[0..nv)
+__global__ void hcol_accumulate_kernel(double* Hcol, const double* src, int nv, int first) {
+  const int i = threadIdx.x;
+  if (i < nv) Hcol[i] = first ? src[i] : Hcol[i] + src[i];
+}
+
+// v <- v / sqrt(n2[0]) (zero when the norm vanishes)
+__global__ void normalize_kernel(long long n, double* v, const double* n2) {
+  const double nv = sqrt(*n2);
+  const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] *= inv;
+}
+
+// Least-squares step of GMRES(its): min || beta e1 - H y || with Givens rotations, H
+// upper Hessenberg with subdiagonal sqrt(hn2); writes -y (for the update x -= (-y) V).
+// Stops at the first breakdown (zero subdiagonal). One thread.
+__global__ void gmres_lsq_kernel(int its, const double* Hc, const double* hn2, const double* beta2, double* ny) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double H[(DG_SMOOTH_MAX_ITS + 1) * DG_SMOOTH_MAX_ITS];
+  double cs[DG_SMOOTH_MAX_ITS], sn[DG_SMOOTH_MAX_ITS], s[DG_SMOOTH_MAX_ITS + 1], y[DG_SMOOTH_MAX_ITS];
+  const int ld = its + 1;
+  const double beta = sqrt(*beta2);
+  for (int j = 0; j < its; ++j) ny[j] = 0.0;
+  if (!(beta > 0.0)) return;
+  int k = its;
+  for (int j = 0; j < its; ++j)
+    if (!(hn2[j] > 0.0)) { k = j + 1; break; }
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i <= j; ++i) H[j * ld + i] = Hc[j * ld + i];
+    H[j * ld + j + 1] = sqrt(hn2[j]);
+  }
+  for (int i = 0; i <= k; ++i) s[i] = 0.0;
+  s[0] = beta;
+  for (int j = 0; j < k; ++j) {
+    double* c = H + j * ld;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * c[i] + sn[i] * c[i + 1];
+      c[i + 1] = -sn[i] * c[i] + cs[i] * c[i + 1];
+      c[i] = t;
+    }
+    const double den = hypot(c[j], c[j + 1]);
+    cs[j] = den > 0.0 ? c[j] / den : 1.0;
+    sn[j] = den > 0.0 ? c[j + 1] / den : 0.0;
+    c[j] = den;
+    c[j + 1] = 0.0;
+    s[j + 1] = -sn[j] * s[j];
+    s[j] = cs[j] * s[j];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = s[i];
+    for (int j = i + 1; j < k; ++j) acc -= H[j * ld + i] * y[j];
+    y[i] = H[i * ld + i] != 0.0 ? acc / H[i * ld + i] : 0.0;
+  }
+  for (int j = 0; j < k; ++j) ny[j] = -y[j];
+}
+
+static int multidot(Handle* h, long long n, int nv, const double* V, const double* w, double* hout, cudaStream_t st);
+
+// GMRES(its) on level lvl left-preconditioned by the element block inverses, from x
+// (x_zero: from 0), no restart: min ||D^-1 (g - G y)|| over y in x + K_its (Sec. 2.4.3).
+static int gmres_smooth(Handle* h, int lvl, const double* g, double* x, int its, bool x_zero, cudaStream_t st) {
+  Level& L = h->lev[lvl];
+  const long long n = L.n;
+  if (its <= 0) {
+    if (x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    return DG_OK;
+  }
+  if (its > DG_SMOOTH_MAX_ITS) return fail(h, DG_ERR_ARG, "too many GMRES smoother iterations");
+  if (h->smV_its[lvl] < its) {
+    if (h->smV[lvl]) cudaFree(h->smV[lvl]);
+    h->smV[lvl] = nullptr;
+    h->smV_its[lvl] = 0;
+    DG_CUDA(h, cudaMalloc((void**)&h->smV[lvl], sizeof(double) * (size_t)(its + 1) * n));
+    h->smV_its[lvl] = its;
+  }
+  if (!h->smSmall) DG_CUDA(h, cudaMalloc((void**)&h->smSmall, sizeof(double) * kSmTotal));
+  double* V = h->smV[lvl];
+  double* Hc = h->smSmall + kSmH;
+  double* tmp = h->smSmall + kSmTmp;
+  double* hn2 = h->smSmall + kSmHn2;
+  double* beta2 = h->smSmall + kSmBeta2;
+  double* ny = h->smSmall + kSmNy;
+  const size_t smem = sizeof(double) * L.b;
+  const int ld = its + 1;
+  int rc;
+  // v0 = D^-1 (g - G x)
+  if (!x_zero && (rc = level_matvec(h, lvl, x, L.t2, st))) return rc;
+  bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, g, x_zero ? nullptr : L.t2, 1.0, 1, V);
+  DG_LAUNCH_CHECK(h);
+  if ((rc = vec_norm2(h, V, n, beta2, st))) return rc;
+  normalize_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, V, beta2);
+  DG_LAUNCH_CHECK(h);
+  for (int j = 0; j < its; ++j) {
+    double* vj = V + (size_t)j * n;
+    double* w = V + (size_t)(j + 1) * n;
+    if ((rc = level_matvec(h, lvl, vj, L.t2, st))) return rc;
+    bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, L.t2, nullptr, 1.0, 1, w);
+    DG_LAUNCH_CHECK(h);
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((rc = multidot(h, n, j + 1, V, w, tmp, st))) return rc;
+      multi_axpy_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, j + 1, V, n, tmp, w);
+      DG_LAUNCH_CHECK(h);
+      hcol_accumulate_kernel<<<1, 64, 0, st>>>(Hc + (size_t)j * ld, tmp, j + 1, pass == 0 ? 1 : 0);
+      DG_LAUNCH_CHECK(h);
+    }
+    if ((rc = vec_norm2(h, w, n, hn2 + j, st))) return rc;
+    normalize_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, w, hn2 + j);
+    DG_LAUNCH_CHECK(h);
+  }
+  gmres_lsq_kernel<<<1, 32, 0, st>>>(its, Hc, hn2, beta2, ny);
+  DG_LAUNCH_CHECK(h);
+  if (x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  multi_axpy_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, its, V, n, ny, x);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+static int smooth(Handle* h, int lvl, const double* g, double* x, int iters, double omega, bool x_zero, int kind,
+                  cudaStream_t st) {
+  if (kind == DG_SMOOTH_GMRES) return gmres_smooth(h, lvl, g, x, iters, x_zero, st);
+  return jacobi_sweeps(h, lvl, g, x, iters, omega, x_zero, st);
 }
 
 static int restrict_to(Handle* h, int lvl, const double* xf, double* xc, cudaStream_t st) {
@@ -217,8 +350,8 @@ static int prolong_add(Handle* h, int lvl, const double* xc, double* xf, cudaStr
 static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const dg_solve_opts& o, cudaStream_t st) {
   int rc;
   const int Lc = h->nlev - 1;
-  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, st);
-  if ((rc = smooth(h, l, g, x, o.pre_sweeps, o.omega, x_zero, st))) return rc;
+  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, o.smoother, st);
+  if ((rc = smooth(h, l, g, x, o.pre_sweeps, o.omega, x_zero, o.smoother, st))) return rc;
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
   const bool xz = x_zero && o.pre_sweeps == 0;
@@ -233,14 +366,14 @@ static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const
   if ((rc = mg_v(h, l + 1, C.t0, C.t1, true, o, st))) return rc;
   if (xz) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
   if ((rc = prolong_add(h, l, C.t1, x, st))) return rc;
-  return smooth(h, l, g, x, o.post_sweeps, o.omega, false, st);
+  return smooth(h, l, g, x, o.post_sweeps, o.omega, false, o.smoother, st);
 }
 
 // MG_full(l, g, 0) of Algorithm 3 (x output).
 static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_opts& o, cudaStream_t st) {
   int rc;
   const int Lc = h->nlev - 1;
-  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, st);
+  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, o.smoother, st);
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
   // g_{l+1} = I g_l; w_{l+1} = MG_full(l+1, g_{l+1}); keep them in the coarse level's t0/t1
@@ -268,6 +401,10 @@ static int check_opts(Handle* h, const dg_solve_opts* o) {
   if (!o) return fail(h, DG_ERR_ARG, "null options");
   if (o->pre_sweeps < 0 || o->post_sweeps < 0 || o->coarse_sweeps < 0) return fail(h, DG_ERR_ARG, "negative sweeps");
   if (!(o->omega > 0.0 && o->omega <= 1.0)) return fail(h, DG_ERR_ARG, "omega must be in (0, 1]");
+  if (o->smoother != DG_SMOOTH_JACOBI && o->smoother != DG_SMOOTH_GMRES) return fail(h, DG_ERR_ARG, "unknown smoother");
+  if (o->smoother == DG_SMOOTH_GMRES &&
+      (o->pre_sweeps > DG_SMOOTH_MAX_ITS || o->post_sweeps > DG_SMOOTH_MAX_ITS || o->coarse_sweeps > DG_SMOOTH_MAX_ITS))
+    return fail(h, DG_ERR_ARG, "GMRES smoother iterations above DG_SMOOTH_MAX_ITS");
   return DG_OK;
 }
 
@@ -452,7 +589,7 @@ int block_jacobi_smooth(dg_handle* hh, int lvl, const double* g, double* x, int 
   if (lvl < 0 || lvl >= h->nlev || !g || !x || g == x) return fail(h, DG_ERR_ARG, "bad level or pointer");
   if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0)) return fail(h, DG_ERR_ARG, "bad sweeps or omega");
   if (!h->assembled) return fail(h, DG_ERR_STATE, "block_jacobi_smooth needs dg_assemble first");
-  return smooth(h, lvl, g, x, sweeps, omega, false, as_stream(stream));
+  return jacobi_sweeps(h, lvl, g, x, sweeps, omega, false, as_stream(stream));
 }
 
 int bsr_spmv(dg_handle* hh, int lvl, double alpha, const double* x, double beta, double* y, void* stream) {

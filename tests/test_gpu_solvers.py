@@ -149,3 +149,31 @@ def test_fgmres_fd_mode_generic_state():
     G0 = O.dense_G(m, w, inv)
     gr = host(g).reshape(-1)
     assert np.linalg.norm(gr - G0 @ host(xf).reshape(-1)) / np.linalg.norm(gr) < 1e-4
+
+
+@pytest.mark.parametrize("name,levels,its", [("u3", [2, 1], (2, 2, 6)), ("u2", [3, 2, 1], (3, 2, 8))])
+def test_vcycle_gmres_smoother(name, levels, its):
+    # GMRES[EWBJ] smoothers (Sec. 2.4.3); the device version orthogonalises with classical
+    # Gram-Schmidt twice, the oracle with modified Gram-Schmidt: equal up to rounding of the
+    # small least-squares problems.
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = np.random.default_rng(17).standard_normal(Gs[0].shape[0])
+    pre, post, cs = its
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g), pre, post, cs, 1.0, "gmres")
+    opts = P.solve_opts(pre_sweeps=pre, post_sweeps=post, coarse_sweeps=cs, smoother=P.DG_SMOOTH_GMRES)
+    x = dg.empty()
+    dg.pmg_vcycle(dev(g.reshape(x.shape)), x, opts)
+    assert rel(host(x).reshape(-1), ref) < 1e-10
+    # FGMRES at a fixed iteration count with this preconditioner
+    gg = -O.residual(m, w).reshape(-1)
+    xr, _, _ = SV.fgmres(lambda v: Gs[0] @ v, lambda v: SV.mg_v(lv, 0, v, np.zeros_like(v), pre, post, cs, 1.0,
+                                                               "gmres"), gg, restart=30, fixed_its=4)
+    xg = dg.empty()
+    info, rc = dg.fgmres_solve(dev(gg.reshape(x.shape)), xg, P.solve_opts(fixed_its=4, pre_sweeps=pre,
+                                                                            post_sweeps=post, coarse_sweeps=cs,
+                                                                            smoother=P.DG_SMOOTH_GMRES))
+    vol = m.vol()
+    a = SV.remove_mean_pressure(host(xg).reshape(-1), m.ne, m.nb, vol)
+    b = SV.remove_mean_pressure(xr, m.ne, m.nb, vol)
+    assert rel(a, b) < 1e-9

@@ -114,3 +114,30 @@ def test_vcycle_is_product_of_iteration_matrices(setup3):
 
 def test_convergence_factor():
     assert abs(SV.convergence_factor(1.0, 1e-8, 4) - 1e-2) < 1e-15
+
+
+@pytest.mark.parametrize("iters", [1, 3, 6])
+def test_gmres_smoother_is_the_krylov_minimiser(setup3, iters):
+    # GMRES(iters) left-preconditioned by EWBJ minimises ||D^-1 (g - G y)|| over
+    # x0 + span{r, (D^-1 G) r, ...}: compare with a least-squares solve on that explicit basis
+    m, w, dt, G0 = setup3
+    D = SV.block_inverses(G0, m.ne, m.nb)
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal(G0.shape[0])
+    x0 = rng.standard_normal(G0.shape[0]) * 0.1
+    got = SV.gmres_smooth(lambda v: G0 @ v, D, g, x0, iters)
+    A = lambda v: SV.apply_block_inverse(D, G0 @ v)
+    r0 = SV.apply_block_inverse(D, g - G0 @ x0)
+    K = [r0]
+    for _ in range(iters - 1):
+        K.append(A(K[-1]))
+    K = np.array(K).T
+    K, _ = np.linalg.qr(K)  # orthonormal basis of the same space
+    AK = np.stack([A(K[:, i]) for i in range(K.shape[1])], 1)
+    c = np.linalg.lstsq(AK, r0, rcond=None)[0]
+    ref = x0 + K @ c
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+    # the preconditioned residual never grows
+    res = lambda y: np.linalg.norm(SV.apply_block_inverse(D, g - G0 @ y))
+    assert res(got) <= res(x0) * (1 + 1e-12)
+
