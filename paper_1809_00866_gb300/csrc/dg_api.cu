@@ -234,11 +234,12 @@ static void free_all(Handle* h) {
   F(T.L1); F(T.B2); F(T.W2); F(T.pv); F(T.pd); F(T.M3); F(T.fmap); F(T.fa); F(T.md3); F(T.pidx); F(T.pab);
   F(T.D2_idx); F(T.D2_val);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
+  F(h->geo);
   F(h->nbr);
   F(h->colour);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
-    F(h->lev[l].Dlin); F(h->lev[l].Blin);
+    F(h->lev[l].Dlin); F(h->lev[l].Blin); F(h->lev[l].perm);
   }
   F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
   F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);
@@ -290,6 +291,19 @@ static int create(const dg_params* p, Handle* h) {
     nbr[e * 6 + 4] = id(i, j, k - 1); nbr[e * 6 + 5] = id(i, j, k + 1);
   }
   if ((rc = upload(h, &h->nbr, nbr))) return rc;
+  std::vector<double> geo((size_t)ne * kGeo, 0.0);
+  for (long long e = 0; e < ne; ++e) {
+    const int I[3] = {(int)(e % nn[0]), (int)((e / nn[0]) % nn[1]), (int)(e / ((long long)nn[0] * nn[1]))};
+    double* G = &geo[(size_t)e * kGeo];
+    for (int d = 0; d < 3; ++d) {
+      G[d] = nodes[d][I[d] + 1] - nodes[d][I[d]];
+      G[5 + d] = 2.0 / G[d];
+      G[8 + d] = nodes[d][I[d]];
+    }
+    G[3] = std::sqrt(G[0] * G[1] * G[2] * 0.125);
+    G[4] = 1.0 / G[3];
+  }
+  if ((rc = upload(h, &h->geo, geo))) return rc;
   if ((rc = build_tables(h, p->k[0]))) return rc;
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];

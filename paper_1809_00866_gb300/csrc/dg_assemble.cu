@@ -10,9 +10,8 @@
 //    the mass shift are assembled directly per element at every call;
 //  * inherited operators of every coarser level by sub-block extraction
 //    (Eq. (GalProj) with a hierarchical orthonormal basis);
-//  * inverses of all diagonal blocks (element-wise block Jacobi) by in-place
-//    Gauss-Jordan elimination with partial pivoting, one block per CTA in
-//    shared memory.
+//  * LU factors with partial pivoting of all diagonal blocks (element-wise block
+//    Jacobi), one block per CTA in shared memory.
 // Blocks are stored column-major: block[c * b + r] = G[row r][col c].
 #include <algorithm>
 #include <vector>
@@ -93,7 +92,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
-    const double Jd[3] = {2.0 / g.h[0], 2.0 / g.h[1], 2.0 / g.h[2]};
+    const double* Jd = g.J;
     for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
     __syncthreads();
     // weighted mass matrices U_c (symmetric)
@@ -175,7 +174,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
           if (a.M.nbr[e * 6 + s2] == p) { tgt = s2; break; }
         const ElemGeom gp = elem_geom(a.M, p);
         const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        const double scale = (side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] / (g.s * gp.s);
+        const double scale = (side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is;
         double* blk = a.Bsr + ((size_t)e * 7 + 1 + tgt) * b1 * b1;
         const double* lin = a.Blin + ((size_t)e * 7 + 1 + sl) * b1 * b1;
         for (int i = 0; i < 4; ++i)
@@ -315,17 +314,18 @@ __global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const doubl
   }
 }
 
-// In-place Gauss-Jordan inversion with partial (row) pivoting of one b x b block per
-// CTA in shared memory (row-major with a padded leading dimension).
-__global__ void __launch_bounds__(256) gj_inverse_kernel(int nblk, int b, const double* in, double* out,
-                                                         unsigned* status) {
+// In-place LU factorisation with partial (row) pivoting of one b x b block per CTA in
+// shared memory (row-major, padded leading dimension). Output, column-major per block:
+// the unit-lower L below the diagonal, U above it, and 1/U_kk on the diagonal; and the
+// row permutation pi (row i of P A is row pi[i] of A).
+__global__ void __launch_bounds__(256) lu_factor_kernel(int nblk, int b, const double* in, double* out, int* perm,
+                                                       unsigned* status) {
   extern __shared__ double sm[];
   const int LD = b + 1;
-  double* A = sm;             // [b][LD]
-  double* col = A + b * LD;   // [b]
-  int* perm = reinterpret_cast<int*>(col + b);  // [b]
+  double* A = sm;                               // [b][LD]
+  int* piv = reinterpret_cast<int*>(A + b * LD);  // [b] row swapped with k at step k
   __shared__ int s_piv;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const double* src = in + (size_t)blk * b * b;
     for (int t = tid; t < b * b; t += nt) {
@@ -334,10 +334,10 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(int nblk, int b, const 
     }
     __syncthreads();
     for (int k = 0; k < b; ++k) {
-      if (tid < 32) {
+      if (warp == 0) {
         double best = -1.0;
         int bi = k;
-        for (int i = k + tid; i < b; i += 32) {
+        for (int i = k + lane; i < b; i += 32) {
           const double v = fabs(A[i * LD + k]);
           if (v > best) { best = v; bi = i; }
         }
@@ -346,9 +346,9 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(int nblk, int b, const 
           const int oi = __shfl_down_sync(0xffffffffu, bi, off);
           if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
-        if (tid == 0) {
+        if (lane == 0) {
           s_piv = bi;
-          perm[k] = bi;
+          piv[k] = bi;
           if (!(best > 0.0) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
         }
       }
@@ -361,27 +361,17 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(int nblk, int b, const 
           A[p * LD + j] = t;
         }
       __syncthreads();
-      for (int i = tid; i < b; i += nt) col[i] = A[i * LD + k];
+      const double rk = 1.0 / A[k * LD + k];
+      for (int i = k + 1 + tid; i < b; i += nt) A[i * LD + k] *= rk;
       __syncthreads();
-      const double ipiv = 1.0 / col[k];
-      for (int j = tid; j < b; j += nt) A[k * LD + j] = (j == k ? 1.0 : A[k * LD + j]) * ipiv;
-      __syncthreads();
-      for (int t = tid; t < b * b; t += nt) {
-        const int i = t / b, j = t - i * b;
-        if (i == k) continue;
-        const double f = col[i];
-        A[i * LD + j] = (j == k) ? -f * A[k * LD + k] : A[i * LD + j] - f * A[k * LD + j];
+      // trailing update: warp w takes rows k+1+w, k+1+w+nw, ...; lanes take the columns
+      for (int i = k + 1 + warp; i < b; i += nw) {
+        const double l = A[i * LD + k];
+        double* Ai = A + i * LD;
+        const double* Ak = A + k * LD;
+        for (int j = k + 1 + lane; j < b; j += 32) Ai[j] = fma(-l, Ak[j], Ai[j]);
       }
-      __syncthreads();
-    }
-    for (int k = b - 1; k >= 0; --k) {
-      const int p = perm[k];
-      if (p != k)
-        for (int i = tid; i < b; i += nt) {
-          const double t = A[i * LD + k];
-          A[i * LD + k] = A[i * LD + p];
-          A[i * LD + p] = t;
-        }
+      if (tid == 0) A[k * LD + k] = rk;
       __syncthreads();
     }
     double* dst = out + (size_t)blk * b * b;
@@ -389,19 +379,30 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(int nblk, int b, const 
       const int c = t / b, r = t - c * b;
       dst[t] = A[r * LD + c];
     }
+    if (tid == 0) {
+      // compose the swaps into pi: apply them in order to the identity
+      int* pi = perm + (size_t)blk * b;
+      for (int i = 0; i < b; ++i) pi[i] = i;
+      for (int kk = 0; kk < b; ++kk) {
+        const int q = piv[kk];
+        const int t = pi[kk];
+        pi[kk] = pi[q];
+        pi[q] = t;
+      }
+    }
     __syncthreads();
   }
 }
 
-static int invert_blocks(Handle* h, int nblk, int b, const double* in, double* out, cudaStream_t st) {
-  const size_t smem = sizeof(double) * ((size_t)b * (b + 1) + b) + sizeof(int) * b;
-  DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static int factor_blocks(Handle* h, int nblk, int b, const double* in, double* out, int* perm, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)b * (b + 1) + sizeof(int) * b;
+  DG_CUDA(h, cudaFuncSetAttribute(lu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = (int)((220 * 1024) / smem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
   int grid = h->nsm * per_sm;
   if (grid > nblk) grid = nblk;
-  gj_inverse_kernel<<<grid, 256, smem, st>>>(nblk, b, in, out, h->status);
+  lu_factor_kernel<<<grid, 256, smem, st>>>(nblk, b, in, out, perm, h->status);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -507,10 +508,11 @@ int assemble_all(Handle* h, cudaStream_t st) {
       }
     }
   }
-  // inverses
+  // LU factors of the diagonal blocks (element-wise block Jacobi)
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];
-    if ((rc = invert_blocks(h, ne, L.b, L.Dblk, L.Dinv, st))) return rc;
+    if (!L.perm) DG_CUDA(h, cudaMalloc((void**)&L.perm, sizeof(int) * (size_t)ne * L.b));
+    if ((rc = factor_blocks(h, ne, L.b, L.Dblk, L.Dinv, L.perm, st))) return rc;
   }
   DG_CUDA(h, cudaStreamSynchronize(st));
   unsigned s = 0;

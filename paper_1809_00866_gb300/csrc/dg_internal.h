@@ -51,7 +51,8 @@ struct Level {
   int k = 0, nb = 0, b = 0;  // degree, modes per variable, block size 4*nb
   long long n = 0;           // vector length ne*4*nb
   double* Dblk = nullptr;    // [ne][b][b] diagonal blocks, column-major per block
-  double* Dinv = nullptr;    // [ne][b][b] inverses, column-major per block
+  double* Dinv = nullptr;    // [ne][b][b] LU factors (unit L, U, 1/U_kk on the diagonal), column-major per block
+  int* perm = nullptr;       // [ne][b] row permutation of the LU factors
   double* Bsr = nullptr;     // [ne][7][b][b] level >= 1: slot 0 diagonal, slots 1..6 faces -x,+x,-y,+y,-z,+z
   double* Dlin = nullptr;    // level 0: [ne][b][b] diagonal blocks of the state-independent linear part
   double* Blin = nullptr;    // level 1: [ne][7][b][b] off-diagonal blocks of the linear part (slot 0 unused)
@@ -67,6 +68,7 @@ struct Handle {
   int nlev = 0;
   std::vector<double> node[3];  // host node coordinates
   double* dnode[3] = {nullptr, nullptr, nullptr};
+  double* geo = nullptr;        // [ne][kGeo] per-element geometry
   int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z
   int* colour = nullptr;        // [ne] element colouring used by the assembly probes
   Tables tab;                   // fine-level tables (the matrix-free level)
@@ -136,32 +138,31 @@ int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a);
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // mesh geometry on the device
+// Per-element geometry, computed once on the host: h[3], s = sqrt(|K|/8) (phi = phi_hat/s),
+// 1/s, J = 2/h[3] (reference-to-physical derivative factors), lower corner lo[3].
+constexpr int kGeo = 12;
 struct MeshDev {
   int nx, ny, nz, ne;
-  const double* xn;
-  const double* yn;
-  const double* zn;
+  const double* geo;  // [ne][kGeo]
   const int* nbr;
 };
-inline MeshDev mesh_dev(const Handle* h) {
-  return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->dnode[0], h->dnode[1], h->dnode[2], h->nbr};
-}
+inline MeshDev mesh_dev(const Handle* h) { return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->geo, h->nbr}; }
 
 struct ElemGeom {
   double h[3];   // box sizes
   double lo[3];  // lower corner
-  double s;      // sqrt(|K|/8): phi = phi_hat / s
+  double s;      // sqrt(|K|/8)
+  double is;     // 1/s
+  double J[3];   // 2/h
 };
 __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
   ElemGeom g;
-  int i = e % M.nx, j = (e / M.nx) % M.ny, k = e / (M.nx * M.ny);
-  g.lo[0] = M.xn[i];
-  g.lo[1] = M.yn[j];
-  g.lo[2] = M.zn[k];
-  g.h[0] = M.xn[i + 1] - g.lo[0];
-  g.h[1] = M.yn[j + 1] - g.lo[1];
-  g.h[2] = M.zn[k + 1] - g.lo[2];
-  g.s = sqrt(g.h[0] * g.h[1] * g.h[2] * 0.125);
+  const double* G = M.geo + (size_t)e * kGeo;
+  g.h[0] = G[0]; g.h[1] = G[1]; g.h[2] = G[2];
+  g.s = G[3];
+  g.is = G[4];
+  g.J[0] = G[5]; g.J[1] = G[6]; g.J[2] = G[7];
+  g.lo[0] = G[8]; g.lo[1] = G[9]; g.lo[2] = G[10];
   return g;
 }
 

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const double A4 = 0.25 * g0.h[t1] * g0.h[t2];
-    const double is0 = 1.0 / g0.s, is1 = 1.0 / g1.s;
+    const double is0 = g0.is, is1 = g1.is;
     for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
       sC[t] = a.in[(size_t)(side ? e1 : e0) * 4 * NB + r];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
       }
       const double is = side ? is1 : is0;
       if (fl < 4) sT[side * 4 * N2 + fl * N2 + j] = acc * is;
-      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * (2.0 / (side ? g1.h[d] : g0.h[d]));
+      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * (side ? g1.J[d] : g0.J[d]);
     }
     __syncwarp();
     // point values of the four variables on both sides
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
       // {r^s} of the normal gradient component, 2D mode j of total degree bj:
       // (k - bj + 1)^2 / 4 * (1/h_K + 1/h_K') * [u]
       const int bj = DEG[j];
-      const double lr = 0.25 * (double)((K - bj + 1) * (K - bj + 1)) * (1.0 / g0.h[d] + 1.0 / g1.h[d]);
+      const double lr = 0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]);
       double jump[3], Gd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
         }
         return acc;
       };
-      const double it1 = 2.0 / g0.h[t1], it2 = 2.0 / g0.h[t2];
+      const double it1 = g0.J[t1], it2 = g0.J[t2];
       const double Gdt1 = 0.5 * (tder(T0 + d * N2, 0) + tder(T1 + d * N2, 0)) * it1;    // Ghat[d][t1]
       const double Gdt2 = 0.5 * (tder(T0 + d * N2, 1) + tder(T1 + d * N2, 1)) * it2;    // Ghat[d][t2]
       const double Gt1 = 0.5 * (tder(T0 + t1 * N2, 0) + tder(T1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
-    const double is = 1.0 / g.s;
-    const double Jd[3] = {2.0 / g.h[0], 2.0 / g.h[1], 2.0 / g.h[2]};
+    const double is = g.is;
+    const double* Jd = g.J;
     for (int t = tid; t < 4 * NB; t += nt) sC[t] = a.in[(size_t)e * 4 * NB + t];
     __syncthreads();
     // (A) corrected gradient coefficients; interpolation step 1 of the velocity

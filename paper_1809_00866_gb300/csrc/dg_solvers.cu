@@ -144,22 +144,45 @@ __global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr,
   }
 }
 
-// x[e] += omega * Dinv[e] (g[e] - Gx[e]) (Gx == nullptr: Gx = 0; x_zero: x treated as 0)
-__global__ void __launch_bounds__(128) bj_update_kernel(int ne, int b, const double* Dinv, const double* g,
-                                                        const double* Gx, double omega, int x_zero, double* x) {
-  extern __shared__ double sr[];  // [b]
-  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
-    for (int c = threadIdx.x; c < b; c += blockDim.x)
-      sr[c] = g[(size_t)e * b + c] - (Gx ? Gx[(size_t)e * b + c] : 0.0);
-    __syncthreads();
-    const double* De = Dinv + (size_t)e * b * b;
-    for (int r = threadIdx.x; r < b; r += blockDim.x) {
-      double acc = 0.0;
-      for (int c = 0; c < b; ++c) acc += De[(size_t)c * b + r] * sr[c];
-      const double old = x_zero ? 0.0 : x[(size_t)e * b + r];
-      x[(size_t)e * b + r] = old + omega * acc;
+// x[e] = x[e] + omega * D[e]^-1 (g[e] - Gx[e]) with the LU factors of D[e]
+// (Gx == nullptr: Gx = 0; x_zero: the old x is 0). One warp per element: the
+// residual is gathered in row order pi into shared memory, then forward substitution
+// with the unit-lower L and backward substitution with U (1/U_kk stored on the
+// diagonal), both along contiguous columns.
+constexpr int kApplyWarps = 4;
+__global__ void __launch_bounds__(32 * kApplyWarps) bj_update_kernel(int ne, int b, const double* LU, const int* perm,
+                                                                    const double* g, const double* Gx, double omega,
+                                                                    int x_zero, double* x) {
+  extern __shared__ double sz[];  // [warps][b]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* z = sz + warp * b;
+  for (int e = blockIdx.x * kApplyWarps + warp; e < ne; e += gridDim.x * kApplyWarps) {
+    const int* pi = perm + (size_t)e * b;
+    const double* ge = g + (size_t)e * b;
+    const double* gx = Gx ? Gx + (size_t)e * b : nullptr;
+    for (int i = lane; i < b; i += 32) {
+      const int r = pi[i];
+      z[i] = ge[r] - (gx ? gx[r] : 0.0);
     }
-    __syncthreads();
+    __syncwarp();
+    const double* M = LU + (size_t)e * b * b;
+    for (int j = 0; j < b; ++j) {  // z <- L^-1 z
+      const double zj = z[j];
+      const double* col = M + (size_t)j * b;
+      for (int i = j + 1 + lane; i < b; i += 32) z[i] = fma(-col[i], zj, z[i]);
+      __syncwarp();
+    }
+    for (int j = b - 1; j >= 0; --j) {  // z <- U^-1 z
+      const double* col = M + (size_t)j * b;
+      const double zj = z[j] * col[j];
+      __syncwarp();
+      if (lane == 0) z[j] = zj;
+      for (int i = lane; i < j; i += 32) z[i] = fma(-col[i], zj, z[i]);
+      __syncwarp();
+    }
+    double* xe = x + (size_t)e * b;
+    for (int i = lane; i < b; i += 32) xe[i] = (x_zero ? 0.0 : xe[i]) + omega * z[i];
+    __syncwarp();
   }
 }
 
@@ -167,6 +190,13 @@ static int grid_for(const Handle* h, long long work) {
   long long g = (long long)h->nsm * 8;
   if (g > work) g = work;
   return g < 1 ? 1 : (int)g;
+}
+
+static int apply_grid(const Handle* h) {
+  long long g = (h->ne + kApplyWarps - 1) / kApplyWarps;
+  const long long cap = (long long)h->nsm * 16;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
 }
 
 static int run_bsr(Handle* h, int lvl, double alpha, const double* x, double beta, double* y, cudaStream_t st) {
@@ -185,15 +215,15 @@ int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st
 static int jacobi_sweeps(Handle* h, int lvl, const double* g, double* x, int sweeps, double omega, bool x_zero,
                          cudaStream_t st) {
   Level& L = h->lev[lvl];
-  const size_t smem = sizeof(double) * L.b;
+  const size_t smem = sizeof(double) * L.b * kApplyWarps;
   for (int s = 0; s < sweeps; ++s) {
     const bool zero = x_zero && s == 0;
     if (!zero) {
       int rc = level_matvec(h, lvl, x, L.t2, st);
       if (rc) return rc;
     }
-    bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, g, zero ? nullptr : L.t2, omega,
-                                                            zero ? 1 : 0, x);
+    bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
+                                                                    zero ? nullptr : L.t2, omega, zero ? 1 : 0, x);
     DG_LAUNCH_CHECK(h);
   }
   if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
@@ -291,12 +321,13 @@ static int gmres_smooth(Handle* h, int lvl, const double* g, double* x, int its,
   double* hn2 = h->smSmall + kSmHn2;
   double* beta2 = h->smSmall + kSmBeta2;
   double* ny = h->smSmall + kSmNy;
-  const size_t smem = sizeof(double) * L.b;
+  const size_t smem = sizeof(double) * L.b * kApplyWarps;
   const int ld = its + 1;
   int rc;
   // v0 = D^-1 (g - G x)
   if (!x_zero && (rc = level_matvec(h, lvl, x, L.t2, st))) return rc;
-  bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, g, x_zero ? nullptr : L.t2, 1.0, 1, V);
+  bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
+                                                                  x_zero ? nullptr : L.t2, 1.0, 1, V);
   DG_LAUNCH_CHECK(h);
   if ((rc = vec_norm2(h, V, n, beta2, st))) return rc;
   normalize_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, V, beta2);
@@ -305,7 +336,8 @@ static int gmres_smooth(Handle* h, int lvl, const double* g, double* x, int its,
     double* vj = V + (size_t)j * n;
     double* w = V + (size_t)(j + 1) * n;
     if ((rc = level_matvec(h, lvl, vj, L.t2, st))) return rc;
-    bj_update_kernel<<<grid_for(h, h->ne), 128, smem, st>>>(h->ne, L.b, L.Dinv, L.t2, nullptr, 1.0, 1, w);
+    bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, L.t2, nullptr, 1.0,
+                                                                    1, w);
     DG_LAUNCH_CHECK(h);
     for (int pass = 0; pass < 2; ++pass) {
       if ((rc = multidot(h, n, j + 1, V, w, tmp, st))) return rc;
