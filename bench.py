@@ -198,20 +198,25 @@ def run_ours(args):
     inv = 1.0 / dt
     pre, post, coarse = (int(x) for x in args.sweeps.split(","))
     smoother = P.DG_SMOOTH_GMRES if args.smoother == "gmres" else P.DG_SMOOTH_JACOBI
-    opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=pre,
-                        post_sweeps=post, coarse_sweeps=coarse, omega=1.0, smoother=smoother)
+
+    def opts_for(precision, omega):
+        return P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=pre,
+                            post_sweeps=post, coarse_sweeps=coarse, omega=omega, smoother=smoother,
+                            precision=precision)
+
+    chosen_prec = P.DG_PRECOND_FP32 if args.form == "fp32" else P.DG_PRECOND_FP64
+    chosen_opts = opts_for(chosen_prec, args.omega)
+    plain_opts = opts_for(P.DG_PRECOND_FP64, 1.0)
+
     st = torch.cuda.current_stream()
     w = dg.empty()
-    dg.dg_project_tgv(w)
     f = dg.empty()
     dw = dg.empty()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")  # 512 MB > L2
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    its_log = []
-    relres_log = []
 
-    def stage(w, phases=None):
+    def stage(w, opts, log, phases=None):
         e = [ev() for _ in range(5)] if phases is not None else None
         if e: e[0].record(st)
         dg.dg_residual(w, f)
@@ -228,42 +233,59 @@ def run_ours(args):
         if e:
             e[4].record(st)
             phases.append(e)
-        its_log.append(info.its)
-        relres_log.append(info.true_relres)
+        log["its"].append(info.its)
+        log["relres"].append(info.true_relres)
 
-    for _ in range(args.warmup):
-        stage(w)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    def run_form(opts):
+        dg.dg_project_tgv(w)
+        log = {"its": [], "relres": []}
+        for _ in range(args.warmup):
+            stage(w, opts, log)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        log = {"its": [], "relres": []}
+        l0, a0 = dg.dg_counters()
+        times, phases = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(st)
+            stage(w, opts, log, phases)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        l1, a1 = dg.dg_counters()
+        t_total = sum(times)
+        if world > 1:
+            tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_total = float(tt.item())
+        names = ["residual", "linearize", "assemble", "solve"]
+        breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
+                     for i, nm in enumerate(names)}
+        return {"s_per_stage": t_total / (args.steps * world), "t_total": t_total, "breakdown_s": breakdown,
+                "fgmres_its": log["its"], "true_relres": log["relres"],
+                "operator_applications": (a1 - a0) / max(1, args.steps),
+                "gpu_launches": (l1 - l0) // max(1, args.steps)}
+
     clk = Clocks(local)
     clk.start()
-    l0, a0 = dg.dg_counters()
-    times = []
-    phases = []
-    its_log.clear()
-    relres_log.clear()
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record(st)
-        stage(w, phases)
-        e1.record(st)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-    l1, a1 = dg.dg_counters()
+    plain = run_form(plain_opts)
+    chosen = run_form(chosen_opts)
     clocks = clk.stop()
-    t_total = sum(times)
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    stages_all = args.steps * world
-    s_per_stage = t_total / stages_all
-    names = ["residual", "linearize", "assemble", "solve"]
-    breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
-                 for i, nm in enumerate(names)}
+
+    # error of the chosen form against the plain FP64 form, first stage from the TGV field
+    dg.dg_project_tgv(w)
+    dg.dg_residual(w, f)
+    f.neg_()
+    dg.dg_set_linearization(w, inv)
+    dg.dg_assemble()
+    d64, d32 = dg.empty(), dg.empty()
+    dg.fgmres_solve(f, d64, plain_opts)
+    dg.fgmres_solve(f, d32, chosen_opts)
+    chosen_err = float((d32 - d64).norm() / d64.norm())
 
     # --- exact Jacobian action throughput and the roofline of its kernels (L2 flushed each time)
     v = torch.from_numpy(S.direction(dg.ne, k, S.SEED_V)).cuda()
@@ -286,6 +308,21 @@ def run_ours(args):
     prof = dg.dg_profile_read()
     dg.dg_profile(False)
     t_jv = statistics.median(jv_times)
+    # FP32 Jacobian action as used inside the chosen form's cycle (timed through one V-cycle's profile)
+    dg.dg_assemble()
+    g32 = torch.from_numpy(S.direction(dg.ne, k, S.SEED_V + 1)).cuda()
+    z32 = dg.empty()
+    opts32 = opts_for(P.DG_PRECOND_FP32, args.omega)
+    dg.pmg_vcycle(g32, z32, opts32)
+    dg.dg_profile(True)
+    dg.dg_profile_read()
+    for _ in range(5):
+        flush.zero_()
+        dg.pmg_vcycle(g32, z32, opts32)
+    prof32 = dg.dg_profile_read()
+    dg.dg_profile(False)
+    n32 = max(1, prof32["face_tan32"][1])
+    t_jv32 = (prof32["face_tan32"][0] + prof32["vol_tan32"][0]) / n32 / 1e3
     jv_gdofs = n0 / t_jv / 1e9
     face_ms = prof["face_tan"][0] / max(1, prof["face_tan"][1])
     vol_ms = prof["vol_tan"][0] / max(1, prof["vol_tan"][1])
@@ -313,7 +350,7 @@ def run_ours(args):
         e0, e1 = ev(), ev()
         e0.record(st)
         wd = host_w.to("cuda", non_blocking=True)
-        stage(wd)
+        stage(wd, chosen_opts, {"its": [], "relres": []})
         host_out.copy_(wd, non_blocking=True)
         e1.record(st)
         torch.cuda.synchronize()
@@ -321,20 +358,26 @@ def run_ours(args):
     e2e = {"value": statistics.mean(e2e_times), "unit": "s/stage", "h2d_bytes_per_step": n0 * 8,
            "d2h_bytes_per_step": n0 * 8}
 
-    apps_per_stage = (a1 - a0) / max(1, args.steps)
-    line = {"metric": METRIC, "value": s_per_stage, "unit": "s/stage", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    apps_per_stage = chosen["operator_applications"]
+    line = {"metric": METRIC, "value": chosen["s_per_stage"], "unit": "s/stage", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * chosen["t_total"] / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.form == "fp64" else "f64 (FGMRES, products with G, stage RHS) + f32 (preconditioner cycle)",
+            "data": "synthetic",
             "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
                                    "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
                        "dofs": n0, "dt": dt,
                        "solver": "FGMRES(30) + MG_V, %s smoother, pre/post/coarse %s" % (args.smoother, args.sweeps),
                        "l2": "flushed (512 MB write) before every timed stage and Jacobian action",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "jv": {"value": jv_gdofs, "unit": "GDOF/s", "mode": "exact (tangent)", "ms": 1e3 * t_jv},
-            "stage": {"breakdown_s": breakdown, "fgmres_its": its_log, "true_relres": relres_log,
-                      "operator_applications": apps_per_stage},
-            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": (l1 - l0) // max(1, args.steps)}
+            "jv": {"value": jv_gdofs, "unit": "GDOF/s", "mode": "exact (tangent), FP64", "ms": 1e3 * t_jv,
+                   "fp32_ms": 1e3 * t_jv32, "fp32_gdofs": n0 / t_jv32 / 1e9},
+            "form": "chosen: %s preconditioner cycle, block-Jacobi omega %.2f, inside FP64 FGMRES; "
+                    "plain: FP64 cycle, omega 1" % (args.form.upper(), args.omega),
+            "stage": chosen, "plain_fp64": plain,
+            "chosen_vs_plain": {"speedup": plain["s_per_stage"] / chosen["s_per_stage"],
+                                "first_stage_solution_rel_diff": chosen_err},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_app, _ = oracle_sample(cfg)
         line["cpu_baseline"] = {"value": t_app * apps_per_stage, "unit": "s/stage", "cores": 1, "kind": "oracle",
@@ -361,6 +404,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi")
     ap.add_argument("--sweeps", default="2,2,2", help="pre,post,coarse smoothing iterations")
+    ap.add_argument("--form", choices=["fp64", "fp32"], default="fp32", help="precision of the chosen form's cycle")
+    ap.add_argument("--omega", type=float, default=0.7, help="block-Jacobi damping of the chosen form")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

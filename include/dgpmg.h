@@ -82,6 +82,10 @@ typedef struct dg_handle dg_handle;
                               DG_SMOOTH_MAX_ITS iterations per call */
 #define DG_SMOOTH_MAX_ITS 32
 
+/* Precision of the preconditioner cycle. */
+#define DG_PRECOND_FP64 0
+#define DG_PRECOND_FP32 1 /* block-Jacobi smoothing only */
+
 typedef struct dg_solve_opts {
   int restart;       /* Krylov subspace size m before a restart (1..64) */
   int maxit;         /* maximum number of outer iterations */
@@ -95,6 +99,9 @@ typedef struct dg_solve_opts {
   int jvp_mode;      /* DG_JVP_TANGENT or DG_JVP_FD for the fine-level G products of the outer solve */
   int x0_is_zero;    /* 1: x holds no initial guess (treated as 0, not read) */
   int smoother;      /* DG_SMOOTH_JACOBI or DG_SMOOTH_GMRES: what the sweep counts above count */
+  int precision;     /* DG_PRECOND_FP64, or DG_PRECOND_FP32: the preconditioner cycle (its operator
+                        products, block-Jacobi factors, block-sparse coarse operators and vectors) in
+                        FP32; FGMRES, its products with G and the true residual stay FP64 */
 } dg_solve_opts;
 
 typedef struct dg_solve_info {
@@ -224,7 +231,9 @@ int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
 #define DG_PROF_VOL_RES 1   /* volume pass of f_h */
 #define DG_PROF_FACE_TAN 2  /* face pass of the exact Jacobian action */
 #define DG_PROF_VOL_TAN 3   /* volume pass of the exact Jacobian action */
-#define DG_PROF_N 4
+#define DG_PROF_FACE_TAN32 4 /* face pass of the FP32 Jacobian action (reduced-precision preconditioner) */
+#define DG_PROF_VOL_TAN32 5  /* volume pass of the FP32 Jacobian action */
+#define DG_PROF_N 6
 
 /* Counters since dg_create: kernels launched by the library, and applications
  * of the fine-level operator (residual or Jacobian action). Host-only, no sync. */

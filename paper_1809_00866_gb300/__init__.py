@@ -28,6 +28,8 @@ DG_PREC_VCYCLE = 1
 DG_PREC_FULLV = 2
 DG_SMOOTH_JACOBI = 0
 DG_SMOOTH_GMRES = 1
+DG_PRECOND_FP64 = 0
+DG_PRECOND_FP32 = 1
 DG_MAX_LEVELS = 4
 
 # Every exported symbol of include/dgpmg.h
@@ -35,8 +37,8 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_residual", "dg_set_linearization", "dg_jvp", "dg_assemble", "pmg_restrict", "pmg_prolong",
            "block_jacobi_smooth", "bsr_spmv", "pmg_vcycle", "fgmres_solve", "dg_counters", "dg_profile",
            "dg_profile_read", "dg_residual_noalloc")
-DG_PROF_N = 4
-PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan")
+DG_PROF_N = 6
+PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32")
 
 
 class DgParams(ctypes.Structure):
@@ -51,7 +53,8 @@ class DgSolveOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("fixed_its", ctypes.c_int), ("precond", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("omega", ctypes.c_double),
-                ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
 
 class DgSolveInfo(ctypes.Structure):
@@ -108,9 +111,9 @@ class DgError(RuntimeError):
 
 def solve_opts(restart=30, maxit=200, rtol=1e-8, fixed_its=0, precond=DG_PREC_VCYCLE, pre_sweeps=2,
                post_sweeps=2, coarse_sweeps=2, omega=1.0, jvp_mode=DG_JVP_TANGENT, x0_is_zero=1,
-               smoother=DG_SMOOTH_JACOBI):
+               smoother=DG_SMOOTH_JACOBI, precision=DG_PRECOND_FP64):
     return DgSolveOpts(restart, maxit, rtol, fixed_its, precond, pre_sweeps, post_sweeps, coarse_sweeps, omega,
-                       jvp_mode, x0_is_zero, smoother)
+                       jvp_mode, x0_is_zero, smoother, precision)
 
 
 class DG:

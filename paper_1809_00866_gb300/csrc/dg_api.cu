@@ -184,6 +184,14 @@ static int build_tables(Handle* h, int k) {
       (rcode = upload(h, &T.pidx, pidx)) || (rcode = upload(h, &T.pab, pab)) || (rcode = upload(h, &T.D2_idx, d2i)) ||
       (rcode = upload(h, &T.D2_val, d2v)))
     return rcode;
+  auto tof = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+  TablesF& TF = h->tabf;
+  if ((rcode = upload(h, &TF.L1, tof(L1))) || (rcode = upload(h, &TF.wvol, tof(wv))) ||
+      (rcode = upload(h, &TF.B2, tof(B2))) || (rcode = upload(h, &TF.W2, tof(W2))) ||
+      (rcode = upload(h, &TF.pv, tof(pvv))) || (rcode = upload(h, &TF.pd, tof(pdv))) ||
+      (rcode = upload(h, &TF.Drow_val, tof(rv))) || (rcode = upload(h, &TF.Dcol_val, tof(cv))) ||
+      (rcode = upload(h, &TF.D2_val, tof(d2v))))
+    return rcode;
   return DG_OK;
 }
 
@@ -233,6 +241,9 @@ static void free_all(Handle* h) {
   F(T.Bvol); F(T.wvol); F(T.xg); F(T.Drow_idx); F(T.Drow_val); F(T.Dcol_idx); F(T.Dcol_val);
   F(T.L1); F(T.B2); F(T.W2); F(T.pv); F(T.pd); F(T.M3); F(T.fmap); F(T.fa); F(T.md3); F(T.pidx); F(T.pab);
   F(T.D2_idx); F(T.D2_val);
+  TablesF& TF = h->tabf;
+  F(TF.L1); F(TF.wvol); F(TF.B2); F(TF.W2); F(TF.pv); F(TF.pd); F(TF.Drow_val); F(TF.Dcol_val); F(TF.D2_val);
+  F(h->face_out_f); F(h->face_lift_f); F(h->ubar_f); F(h->dFlux_f);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
   F(h->nbr);
@@ -240,6 +251,7 @@ static void free_all(Handle* h) {
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
     F(h->lev[l].Dlin); F(h->lev[l].Blin); F(h->lev[l].perm);
+    F(h->lev[l].LUf); F(h->lev[l].Bsrf); F(h->lev[l].t0f); F(h->lev[l].t1f); F(h->lev[l].t2f);
   }
   F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
   F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);
@@ -321,6 +333,11 @@ static int create(const dg_params* p, Handle* h) {
       (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
       (rc = dalloc(h, &h->dFlux, (size_t)3 * ne * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
       (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 1)))
+    return rc;
+  if ((rc = dalloc(h, &h->face_out_f, (size_t)ne * 6 * 4 * n2f)) ||
+      (rc = dalloc(h, &h->face_lift_f, (size_t)ne * 6 * 3 * n2f)) ||
+      (rc = dalloc(h, &h->ubar_f, (size_t)ne * 3 * h->tab.nq)) ||
+      (rc = dalloc(h, &h->dFlux_f, (size_t)3 * ne * h->tab.nqf * 32)))
     return rc;
   DG_CUDA(h, cudaDeviceSynchronize());
   return DG_OK;
@@ -407,6 +424,7 @@ int dg_set_linearization(dg_handle* hh, const double* w, double inv_gamma_dt, vo
   DG_CUDA(h, cudaStreamSynchronize(st));
   h->linearized = true;
   h->assembled = false;
+  h->lin_f_ready = false;
   return DG_OK;
 }
 
@@ -426,6 +444,7 @@ int dg_assemble(dg_handle* hh, void* stream) {
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");
   const int rc = assemble_all(h, as_stream(stream));
   if (rc == DG_OK) h->assembled = true;
+  h->asm_f_ready = false;
   return rc;
 }
 

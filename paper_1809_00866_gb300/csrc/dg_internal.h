@@ -47,6 +47,19 @@ struct Tables {
   static constexpr int kDw = 3;
 };
 
+// FP32 copies of the real-valued tables (reduced-precision preconditioner)
+struct TablesF {
+  float* L1 = nullptr;
+  float* wvol = nullptr;
+  float* B2 = nullptr;
+  float* W2 = nullptr;
+  float* pv = nullptr;
+  float* pd = nullptr;
+  float* Drow_val = nullptr;
+  float* Dcol_val = nullptr;
+  float* D2_val = nullptr;
+};
+
 struct Level {
   int k = 0, nb = 0, b = 0;  // degree, modes per variable, block size 4*nb
   long long n = 0;           // vector length ne*4*nb
@@ -59,6 +72,12 @@ struct Level {
   double* t0 = nullptr;      // work vectors of length n
   double* t1 = nullptr;
   double* t2 = nullptr;
+  // FP32 copies for the reduced-precision preconditioner (allocated on first use)
+  float* LUf = nullptr;      // [ne][b][b]
+  float* Bsrf = nullptr;     // [ne][7][b][b] (level >= 1)
+  float* t0f = nullptr;
+  float* t1f = nullptr;
+  float* t2f = nullptr;
 };
 
 struct Handle {
@@ -72,12 +91,19 @@ struct Handle {
   int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z
   int* colour = nullptr;        // [ne] element colouring used by the assembly probes
   Tables tab;                   // fine-level tables (the matrix-free level)
+  TablesF tabf;                 // their FP32 copies
   Level lev[DG_MAX_LEVELS];
   int nsm = 0;
 
   // scratch of the matrix-free operator
   double* face_out = nullptr;  // [ne][6][4][n2] face-term contributions per element face slot (2D modes)
   double* face_lift = nullptr; // [ne][6][3][n2] BR2 local lifting (scaled 2D jump) per element face slot
+  float* face_out_f = nullptr;   // FP32 scratch of the FP32 operator
+  float* face_lift_f = nullptr;
+  float* ubar_f = nullptr;       // FP32 copies of the linearisation cache
+  float* dFlux_f = nullptr;
+  bool lin_f_ready = false;      // the FP32 copies match the current linearisation
+  bool asm_f_ready = false;      // the FP32 factors / blocks match the current assembly
   // linearisation cache
   bool linearized = false;
   bool assembled = false;
@@ -112,8 +138,8 @@ struct Handle {
   struct ProfEv { int cls; cudaEvent_t a, b; };
   std::vector<ProfEv> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
-  double prof_ms[DG_PROF_N] = {0, 0, 0, 0};
-  long long prof_cnt[DG_PROF_N] = {0, 0, 0, 0};
+  double prof_ms[DG_PROF_N] = {};
+  long long prof_cnt[DG_PROF_N] = {};
 };
 
 // error helpers
@@ -170,6 +196,7 @@ __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
 int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStream_t st);
 int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st);
+int op_tangent_f32(Handle* h, const float* v, float* out, cudaStream_t st);
 int op_fd(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_project_tgv(Handle* h, double* w, cudaStream_t st);
 

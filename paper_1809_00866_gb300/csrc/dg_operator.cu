@@ -49,18 +49,35 @@ struct Sz2 {
   static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
 };
 
-struct OpArgs {
+// Real-valued tables in the kernel's precision (the integer tables stay in Tables).
+template <class R>
+struct RTab {
+  const R* L1;
+  const R* wvol;
+  const R* B2;
+  const R* W2;
+  const R* pv;
+  const R* pd;
+  const R* Drow_val;
+  const R* Dcol_val;
+  const R* D2_val;
+};
+
+template <class R>
+struct OpArgsT {
   MeshDev M;
   Tables T;
-  const double* in;
-  double* out;
-  double* face_out;
-  double* face_lift;
-  double* ubar;
-  double* dFlux;
+  RTab<R> rt;
+  const R* in;
+  R* out;
+  R* face_out;
+  R* face_lift;
+  R* ubar;
+  R* dFlux;
   double nu, c, eta, inv_gdt;
   unsigned* status;
 };
+using OpArgs = OpArgsT<double>;
 
 // ------------------------------------------------------------------ Riemann
 // Pressure on the 1-wave curve through (uL, pL) at star velocity u, and its
@@ -226,7 +243,7 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
 // ---------------------------------------------------------------- face pass
 constexpr int kFaceWarps = 4;  // faces per CTA, one warp each
 
-template <int K>
+template <int K, class R = double>
 struct FaceSmem {
   using S = Sz2<K>;
   // per warp
@@ -249,48 +266,49 @@ struct FaceSmem {
   static constexpr int D2I = M3 + 3 * S::N2 * (K + 1);  // [2][N2][kDw]
   static constexpr int DEG = D2I + 2 * S::N2 * Tables::kDw;  // [N2] total degree of each 2D mode
   static constexpr int INTS = DEG + S::N2;
-  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+  static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
 
-template <int K, int MODE>
-__global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
+template <int K, int MODE, class R>
+__global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgsT<R> a) {
   using S = Sz2<K>;
-  using L = FaceSmem<K>;
+  using L = FaceSmem<K, R>;
   constexpr int NB = S::NB, NQF = S::NQF, N2 = S::N2, K1 = K + 1, DW = Tables::kDw;
-  extern __shared__ double sm[];
-  double* B2 = sm + L::B2;
-  double* W2 = sm + L::W2;
-  double* PV = sm + L::PV;
-  double* PD = sm + L::PD;
-  double* D2V = sm + L::D2V;
+  extern __shared__ __align__(16) unsigned char smraw_[];
+  R* sm = reinterpret_cast<R*>(smraw_);
+  R* B2 = sm + L::B2;
+  R* W2 = sm + L::W2;
+  R* PV = sm + L::PV;
+  R* PD = sm + L::PD;
+  R* D2V = sm + L::D2V;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
   int* M3 = ism + L::M3;
   int* D2I = ism + L::D2I;
   int* DEG = ism + L::DEG;
   const int tid = threadIdx.x;
   for (int t = tid; t < N2; t += blockDim.x) DEG[t] = a.T.pab[2 * t] + a.T.pab[2 * t + 1];
-  for (int t = tid; t < NQF * N2; t += blockDim.x) B2[t] = a.T.B2[t];
-  for (int t = tid; t < NQF; t += blockDim.x) W2[t] = a.T.W2[t];
-  for (int t = tid; t < 2 * K1; t += blockDim.x) { PV[t] = a.T.pv[t]; PD[t] = a.T.pd[t]; }
-  for (int t = tid; t < 2 * N2 * DW; t += blockDim.x) { D2V[t] = a.T.D2_val[t]; D2I[t] = a.T.D2_idx[t]; }
+  for (int t = tid; t < NQF * N2; t += blockDim.x) B2[t] = a.rt.B2[t];
+  for (int t = tid; t < NQF; t += blockDim.x) W2[t] = a.rt.W2[t];
+  for (int t = tid; t < 2 * K1; t += blockDim.x) { PV[t] = a.rt.pv[t]; PD[t] = a.rt.pd[t]; }
+  for (int t = tid; t < 2 * N2 * DW; t += blockDim.x) { D2V[t] = a.rt.D2_val[t]; D2I[t] = a.T.D2_idx[t]; }
   for (int t = tid; t < 3 * N2 * K1; t += blockDim.x) M3[t] = a.T.M3[t];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  double* W = sm + warp * L::WARP;
-  double* sC = W + L::C;
-  double* sT = W + L::T;
-  double* sN = W + L::N;
-  double* sV = W + L::V;
-  double* sF = W + L::F;
-  double* sP = W + L::P;
+  R* W = sm + warp * L::WARP;
+  R* sC = W + L::C;
+  R* sT = W + L::T;
+  R* sN = W + L::N;
+  R* sV = W + L::V;
+  R* sF = W + L::F;
+  R* sP = W + L::P;
   const int nfaces = 3 * a.M.ne;
   for (int f = blockIdx.x * kFaceWarps + warp; f < nfaces; f += gridDim.x * kFaceWarps) {
     const int e0 = f / 3, d = f - 3 * e0;
     const int e1 = a.M.nbr[e0 * 6 + 2 * d + 1];
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    const double A4 = 0.25 * g0.h[t1] * g0.h[t2];
-    const double is0 = g0.is, is1 = g1.is;
+    const R A4 = R(0.25 * g0.h[t1] * g0.h[t2]);
+    const R is0 = R(g0.is), is1 = R(g1.is);
     for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
       sC[t] = a.in[(size_t)(side ? e1 : e0) * 4 * NB + r];
@@ -300,57 +318,57 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
     for (int t = lane; t < 14 * N2; t += 32) {
       const int side = t / (7 * N2), r = t - side * 7 * N2, fl = r / N2, j = r - fl * N2;
       const int var = fl < 4 ? fl : fl - 4;
-      const double* c = sC + side * 4 * NB + var * NB;
-      const double* pw = fl < 4 ? PV + side * K1 : PD + side * K1;
+      const R* c = sC + side * 4 * NB + var * NB;
+      const R* pw = fl < 4 ? PV + side * K1 : PD + side * K1;
       const int* mm = M3 + (d * N2 + j) * K1;
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int e = 0; e < K1; ++e) {
         const int m = mm[e];
         if (m >= 0) acc += pw[e] * c[m];
       }
-      const double is = side ? is1 : is0;
+      const R is = side ? is1 : is0;
       if (fl < 4) sT[side * 4 * N2 + fl * N2 + j] = acc * is;
-      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * (side ? g1.J[d] : g0.J[d]);
+      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * R(side ? g1.J[d] : g0.J[d]);
     }
     __syncwarp();
     // point values of the four variables on both sides
     for (int t = lane; t < 8 * NQF; t += 32) {
       const int sv = t / NQF, q = t - sv * NQF;
-      const double* Tc = sT + sv * N2;
-      const double* b = B2 + q * N2;
-      double acc = 0.0;
+      const R* Tc = sT + sv * N2;
+      const R* b = B2 + q * N2;
+      R acc = R(0);
 #pragma unroll
       for (int j = 0; j < N2; ++j) acc += b[j] * Tc[j];
       sV[t] = acc;
     }
     __syncwarp();
     for (int q = lane; q < NQF; q += 32) {
-      const double* V0 = sV;
-      const double* V1 = sV + 4 * NQF;
-      double uL[3] = {V0[q], V0[NQF + q], V0[2 * NQF + q]};
-      double uR[3] = {V1[q], V1[NQF + q], V1[2 * NQF + q]};
-      const double pL = V0[3 * NQF + q], pR = V1[3 * NQF + q];
-      double Fc[4] = {0.0, 0.0, 0.0, 0.0};
-      if (MODE == MODE_TAN) {
-        const double* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
-        const double ds[8] = {uL[0], uL[1], uL[2], pL, uR[0], uR[1], uR[2], pR};
+      const R* V0 = sV;
+      const R* V1 = sV + 4 * NQF;
+      R uL[3] = {V0[q], V0[NQF + q], V0[2 * NQF + q]};
+      R uR[3] = {V1[q], V1[NQF + q], V1[2 * NQF + q]};
+      const R pL = V0[3 * NQF + q], pR = V1[3 * NQF + q];
+      R Fc[4] = {R(0), R(0), R(0), R(0)};
+      if constexpr (MODE == MODE_TAN) {
+        const R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
+        const R ds[8] = {uL[0], uL[1], uL[2], pL, uR[0], uR[1], uR[2], pR};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          double acc = 0.0;
+          R acc = R(0);
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc += Jq[i * 8 + j] * ds[j];
           Fc[i] = acc;
         }
-      } else if (MODE == MODE_RES_LIN) {
-        double Jm[4][8];
+      } else if constexpr (MODE == MODE_RES_LIN) {
+        double Jm[4][8];  // residual modes run in FP64 only
         ac_riemann(uL, pL, uR, pR, d, a.c, Fc, Jm, a.status);
-        double* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
+        R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) Jq[i * 8 + j] = Jm[i][j];
-      } else if (MODE == MODE_RES) {
+      } else if constexpr (MODE == MODE_RES) {
         ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status);
       }
 #pragma unroll
@@ -359,8 +377,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
     __syncwarp();
     for (int t = lane; t < 4 * N2; t += 32) {
       const int i = t / N2, j = t - i * N2;
-      const double* Fi = sF + i * NQF;
-      double acc = 0.0;
+      const R* Fi = sF + i * NQF;
+      R acc = R(0);
 #pragma unroll
       for (int q = 0; q < NQF; ++q) acc += B2[q * N2 + j] * Fi[q];
       sP[t] = acc;
@@ -368,21 +386,21 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
     __syncwarp();
     // viscous face flux in 2D modal space, total flux, lifting; one lane per 2D mode
     for (int j = lane; j < N2; j += 32) {
-      const double* T0 = sT;
-      const double* T1 = sT + 4 * N2;
+      const R* T0 = sT;
+      const R* T1 = sT + 4 * N2;
       // {r^s} of the normal gradient component, 2D mode j of total degree bj:
       // (k - bj + 1)^2 / 4 * (1/h_K + 1/h_K') * [u]
       const int bj = DEG[j];
-      const double lr = 0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]);
-      double jump[3], Gd[3];
+      const R lr = R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]));
+      R jump[3], Gd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         jump[c] = T0[c * N2 + j] - T1[c * N2 + j];
-        Gd[c] = 0.5 * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - a.eta * lr * jump[c];  // Ghat[c][d]
+        Gd[c] = R(0.5) * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - R(a.eta) * lr * jump[c];  // Ghat[c][d]
       }
       // tangential derivatives (2D modal) of the normal component and of the tangential ones
-      auto tder = [&](const double* Tc, int dir) {
-        double acc = 0.0;
+      auto tder = [&](const R* Tc, int dir) {
+        R acc = R(0);
 #pragma unroll
         for (int q = 0; q < DW; ++q) {
           const int o = (dir * N2 + j) * DW + q;
@@ -390,33 +408,33 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
         }
         return acc;
       };
-      const double it1 = g0.J[t1], it2 = g0.J[t2];
-      const double Gdt1 = 0.5 * (tder(T0 + d * N2, 0) + tder(T1 + d * N2, 0)) * it1;    // Ghat[d][t1]
-      const double Gdt2 = 0.5 * (tder(T0 + d * N2, 1) + tder(T1 + d * N2, 1)) * it2;    // Ghat[d][t2]
-      const double Gt1 = 0.5 * (tder(T0 + t1 * N2, 0) + tder(T1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
-      const double Gt2 = 0.5 * (tder(T0 + t2 * N2, 1) + tder(T1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
-      const double trG = Gd[d] + Gt1 + Gt2;
-      double Fv[3];
-      Fv[d] = a.nu * (2.0 * Gd[d] - (2.0 / 3.0) * trG);
-      Fv[t1] = a.nu * (Gd[t1] + Gdt1);
-      Fv[t2] = a.nu * (Gd[t2] + Gdt2);
-      double Fn[4];
+      const R it1 = R(g0.J[t1]), it2 = R(g0.J[t2]);
+      const R Gdt1 = R(0.5) * (tder(T0 + d * N2, 0) + tder(T1 + d * N2, 0)) * it1;    // Ghat[d][t1]
+      const R Gdt2 = R(0.5) * (tder(T0 + d * N2, 1) + tder(T1 + d * N2, 1)) * it2;    // Ghat[d][t2]
+      const R Gt1 = R(0.5) * (tder(T0 + t1 * N2, 0) + tder(T1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
+      const R Gt2 = R(0.5) * (tder(T0 + t2 * N2, 1) + tder(T1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
+      const R trG = Gd[d] + Gt1 + Gt2;
+      R Fv[3];
+      Fv[d] = R(a.nu) * (2.0 * Gd[d] - R(2.0 / 3.0) * trG);
+      Fv[t1] = R(a.nu) * (Gd[t1] + Gdt1);
+      Fv[t2] = R(a.nu) * (Gd[t2] + Gdt2);
+      R Fn[4];
 #pragma unroll
       for (int i = 0; i < 3; ++i) Fn[i] = A4 * (sP[i * N2 + j] - Fv[i]);
       Fn[3] = A4 * sP[3 * N2 + j];
-      double* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
-      double* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
+      R* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
+      R* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         o0[i * N2 + j] = Fn[i] * is0;
         o1[i * N2 + j] = -Fn[i] * is1;
       }
-      double* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
-      double* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
+      R* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
+      R* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        l0[c * N2 + j] = 0.5 * A4 * is0 * jump[c];
-        l1[c * N2 + j] = 0.5 * A4 * is1 * jump[c];
+        l0[c * N2 + j] = R(0.5) * A4 * is0 * jump[c];
+        l1[c * N2 + j] = R(0.5) * A4 * is1 * jump[c];
       }
     }
     __syncwarp();
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgs a) {
 }
 
 // -------------------------------------------------------------- volume pass
-template <int K>
+template <int K, class R = double>
 struct VolSmem {
   using S = Sz2<K>;
   static constexpr int NB = S::NB, N1 = S::N1, NQ = S::NQ, N2 = S::N2, K1 = K + 1;
@@ -449,29 +467,30 @@ struct VolSmem {
   static constexpr int FA = FMAP + 3 * NB;            // [3][NB]
   static constexpr int IDX3 = FA + 3 * NB;            // [K+1]^3 3D mode of exponents (a, b, c) or -1
   static constexpr int INTS = IDX3 + K1 * K1 * K1;
-  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+  static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
 
 __device__ __forceinline__ int sym_index(int p, int i) { return p == i ? p : (p + i + 2); }  // 01->3 02->4 12->5
 
-template <int K, int MODE>
-__global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
-  using L = VolSmem<K>;
+template <int K, int MODE, class R>
+__global__ void __launch_bounds__(128) vol_kernel(OpArgsT<R> a) {
+  using L = VolSmem<K, R>;
   constexpr int NB = L::NB, N1 = L::N1, NQ = L::NQ, N2 = L::N2, K1 = L::K1, DW = Tables::kDw;
-  extern __shared__ double sm[];
-  double* L1 = sm + L::L1;
-  double* W3 = sm + L::W3;
-  double* PV = sm + L::PV;
-  double* sC = sm + L::C;
-  double* sG = sm + L::G;
-  double* sFv = sm + L::FV;
-  double* sU = sm + L::U;
-  double* sT1 = sm + L::T1;
-  double* sT2 = sm + L::T2;
-  double* sPr = sm + L::PR;
-  double* sS1 = sm + L::S1;
-  double* sS2 = sm + L::S2;
-  double* sCv = sm + L::CV;
+  extern __shared__ __align__(16) unsigned char smraw_[];
+  R* sm = reinterpret_cast<R*>(smraw_);
+  R* L1 = sm + L::L1;
+  R* W3 = sm + L::W3;
+  R* PV = sm + L::PV;
+  R* sC = sm + L::C;
+  R* sG = sm + L::G;
+  R* sFv = sm + L::FV;
+  R* sU = sm + L::U;
+  R* sT1 = sm + L::T1;
+  R* sT2 = sm + L::T2;
+  R* sPr = sm + L::PR;
+  R* sS1 = sm + L::S1;
+  R* sS2 = sm + L::S2;
+  R* sCv = sm + L::CV;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
   int* MD3 = ism + L::MD3;
   int* PIDX = ism + L::PIDX;
@@ -484,40 +503,40 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
   __syncthreads();
   for (int m = tid; m < NB; m += nt)
     IDX3[(a.T.md3[3 * m] * K1 + a.T.md3[3 * m + 1]) * K1 + a.T.md3[3 * m + 2]] = m;
-  for (int t = tid; t < K1 * N1; t += nt) L1[t] = a.T.L1[t];
-  for (int t = tid; t < NQ; t += nt) W3[t] = a.T.wvol[t];
-  for (int t = tid; t < 2 * K1; t += nt) PV[t] = a.T.pv[t];
+  for (int t = tid; t < K1 * N1; t += nt) L1[t] = a.rt.L1[t];
+  for (int t = tid; t < NQ; t += nt) W3[t] = a.rt.wvol[t];
+  for (int t = tid; t < 2 * K1; t += nt) PV[t] = a.rt.pv[t];
   for (int t = tid; t < 3 * NB; t += nt) { MD3[t] = a.T.md3[t]; FMAP[t] = a.T.fmap[t]; FA[t] = a.T.fa[t]; }
   for (int t = tid; t < K1 * K1; t += nt) PIDX[t] = a.T.pidx[t];
   for (int t = tid; t < 2 * N2; t += nt) PAB[t] = a.T.pab[t];
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
-    const double is = g.is;
-    const double* Jd = g.J;
+    const R is = R(g.is);
+    const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
     for (int t = tid; t < 4 * NB; t += nt) sC[t] = a.in[(size_t)e * 4 * NB + t];
     __syncthreads();
     // (A) corrected gradient coefficients; interpolation step 1 of the velocity
-    const double* Lf = a.face_lift + (size_t)e * 6 * 3 * N2;
+    const R* Lf = a.face_lift + (size_t)e * 6 * 3 * N2;
     for (int t = tid; t < 9 * NB; t += nt) {
       const int ab = t / NB, m = t - ab * NB, av = ab / 3, b = ab - 3 * av;
-      const double* cv = sC + av * NB;
-      double acc = 0.0;
+      const R* cv = sC + av * NB;
+      R acc = R(0);
 #pragma unroll
       for (int j = 0; j < DW; ++j) {
         const int o = (b * NB + m) * DW + j;
-        acc += a.T.Drow_val[o] * cv[a.T.Drow_idx[o]];
+        acc += a.rt.Drow_val[o] * cv[a.T.Drow_idx[o]];
       }
       // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
       const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
-      const double r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
+      const R r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
       sG[t] = acc * Jd[b] - r;
     }
     for (int t = tid; t < 3 * N2 * N1; t += nt) {
       const int fl = t / (N2 * N1), r = t - fl * N2 * N1, pi = r / N1, q2 = r - pi * N1;
       const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
-      const double* c = sC + fl * NB;
-      double acc = 0.0;
+      const R* c = sC + fl * NB;
+      R acc = R(0);
       const int* row = IDX3 + (pa * K1 + pb) * K1;
       for (int cc = 0; cc <= K - pa - pb; ++cc) acc += c[row[cc]] * L1[cc * N1 + q2];
       sT1[t] = acc;
@@ -528,13 +547,13 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
       const int sp = t / NB, m = t - sp * NB;
       int p, i;
       if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
-      const double trG = sG[0 * NB + m] + sG[4 * NB + m] + sG[8 * NB + m];
-      sFv[t] = a.nu * (sG[(i * 3 + p) * NB + m] + sG[(p * 3 + i) * NB + m] - (p == i ? (2.0 / 3.0) * trG : 0.0));
+      const R trG = sG[0 * NB + m] + sG[4 * NB + m] + sG[8 * NB + m];
+      sFv[t] = R(a.nu) * (sG[(i * 3 + p) * NB + m] + sG[(p * 3 + i) * NB + m] - (p == i ? R(2.0 / 3.0) * trG : R(0)));
     }
     for (int t = tid; t < 3 * K1 * N1 * N1; t += nt) {
       const int fl = t / (K1 * N1 * N1), r = t - fl * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
       const int q1 = r2 / N1, q2 = r2 - q1 * N1;
-      double acc = 0.0;
+      R acc = R(0);
       for (int pb = 0; pb <= K - pa; ++pb) acc += sT1[fl * N2 * N1 + PIDX[pa * K1 + pb] * N1 + q2] * L1[pb * N1 + q1];
       sT2[t] = acc;
     }
@@ -542,7 +561,7 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     // (C) interpolation step 3: velocity (or its variation) at the Gauss points
     for (int t = tid; t < 3 * NQ; t += nt) {
       const int fl = t / NQ, q = t - fl * NQ, q0 = q / (N1 * N1), r = q - q0 * N1 * N1;
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int pa = 0; pa < K1; ++pa) acc += sT2[(fl * K1 + pa) * N1 * N1 + r] * L1[pa * N1 + q0];
       sU[t] = acc * is;
@@ -550,14 +569,14 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     __syncthreads();
     // (D) pointwise convective products, weighted
     for (int q = tid; q < NQ; q += nt) {
-      const double u[3] = {sU[q], sU[NQ + q], sU[2 * NQ + q]};
-      double ub[3];
+      const R u[3] = {sU[q], sU[NQ + q], sU[2 * NQ + q]};
+      R ub[3];
       if (MODE == MODE_TAN) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = a.ubar[((size_t)e * 3 + c) * NQ + q];
       } else if (MODE == MODE_LINPART) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ub[c] = 0.0;
+        for (int c = 0; c < 3; ++c) ub[c] = R(0);
       } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) ub[c] = u[c];
@@ -565,13 +584,13 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) a.ubar[((size_t)e * 3 + c) * NQ + q] = u[c];
       }
-      const double wq = W3[q];
+      const R wq = W3[q];
 #pragma unroll
       for (int sp = 0; sp < 6; ++sp) {
         int p, i;
         if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
-        const double v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i])
-                         : (MODE == MODE_LINPART) ? 0.0 : u[p] * u[i];
+        const R v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i])
+                         : (MODE == MODE_LINPART) ? R(0) : u[p] * u[i];
         sPr[sp * NQ + q] = v * wq;
       }
     }
@@ -579,7 +598,7 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     // (E) projection step 1: S1[sp][a][q1 q2] = sum_q0 L1[a][q0] Pr[sp][q0 q1 q2]
     for (int t = tid; t < 6 * K1 * N1 * N1; t += nt) {
       const int sp = t / (K1 * N1 * N1), r = t - sp * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int q0 = 0; q0 < N1; ++q0) acc += L1[pa * N1 + q0] * sPr[sp * NQ + q0 * N1 * N1 + r2];
       sS1[t] = acc;
@@ -589,7 +608,7 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     for (int t = tid; t < 6 * N2 * N1; t += nt) {
       const int sp = t / (N2 * N1), r = t - sp * N2 * N1, pi = r / N1, q2 = r - pi * N1;
       const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int q1 = 0; q1 < N1; ++q1) acc += L1[pb * N1 + q1] * sS1[(sp * K1 + pa) * N1 * N1 + q1 * N1 + q2];
       sS2[t] = acc;
@@ -599,33 +618,33 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
     for (int t = tid; t < 6 * NB; t += nt) {
       const int sp = t / NB, m = t - sp * NB;
       const int pa = MD3[3 * m], pb = MD3[3 * m + 1], pc = MD3[3 * m + 2];
-      const double* s2 = sS2 + (sp * N2 + PIDX[pa * K1 + pb]) * N1;
-      double acc = 0.0;
+      const R* s2 = sS2 + (sp * N2 + PIDX[pa * K1 + pb]) * N1;
+      R acc = R(0);
 #pragma unroll
       for (int q2 = 0; q2 < N1; ++q2) acc += L1[pc * N1 + q2] * s2[q2];
-      sCv[t] = acc * g.s;
+      sCv[t] = acc * R(g.s);
     }
     __syncthreads();
     // (H) assemble: modal derivatives of (F^nu - u(x)u) and p, continuity, face terms, mass shift
-    const double* FO = a.face_out + (size_t)e * 6 * 4 * N2;
+    const R* FO = a.face_out + (size_t)e * 6 * 4 * N2;
     for (int t = tid; t < 4 * NB; t += nt) {
       const int i = t / NB, m = t - i * NB;
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int pp = 0; pp < 3; ++pp) {
-        double s2 = 0.0;
+        R s2 = R(0);
 #pragma unroll
         for (int j = 0; j < DW; ++j) {
           const int o = (pp * NB + m) * DW + j;
           const int n = a.T.Dcol_idx[o];
-          double fld;
+          R fld;
           if (i < 3) {
             const int sp = sym_index(pp, i);
-            fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : 0.0);
+            fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0));
           } else {
             fld = -sC[pp * NB + n];
           }
-          s2 += a.T.Dcol_val[o] * fld;
+          s2 += a.rt.Dcol_val[o] * fld;
         }
         acc += Jd[pp] * s2;
       }
@@ -634,7 +653,7 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgs a) {
         const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
         acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
       }
-      if (MODE == MODE_TAN && i < 3) acc += a.inv_gdt * sC[t];
+      if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt) * sC[t];
       a.out[(size_t)e * 4 * NB + t] = acc;
     }
     __syncthreads();
@@ -696,6 +715,8 @@ static OpArgs make_args(Handle* h, const double* in, double* out) {
   OpArgs a;
   a.M = mesh_dev(h);
   a.T = h->tab;
+  a.rt = RTab<double>{h->tab.L1, h->tab.wvol, h->tab.B2, h->tab.W2, h->tab.pv, h->tab.pd, h->tab.Drow_val,
+                     h->tab.Dcol_val, h->tab.D2_val};
   a.in = in;
   a.out = out;
   a.face_out = h->face_out;
@@ -710,11 +731,31 @@ static OpArgs make_args(Handle* h, const double* in, double* out) {
   return a;
 }
 
-template <int K, int MODE>
-static int run_operator(Handle* h, const OpArgs& a, cudaStream_t st) {
-  const size_t fs = FaceSmem<K>::bytes(), vs = VolSmem<K>::bytes();
-  DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
-  DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
+static OpArgsT<float> make_args_f(Handle* h, const float* in, float* out) {
+  OpArgsT<float> a;
+  const TablesF& F = h->tabf;
+  a.M = mesh_dev(h);
+  a.T = h->tab;
+  a.rt = RTab<float>{F.L1, F.wvol, F.B2, F.W2, F.pv, F.pd, F.Drow_val, F.Dcol_val, F.D2_val};
+  a.in = in;
+  a.out = out;
+  a.face_out = h->face_out_f;
+  a.face_lift = h->face_lift_f;
+  a.ubar = h->ubar_f;
+  a.dFlux = h->dFlux_f;
+  a.nu = h->p.nu;
+  a.c = h->p.ac_c;
+  a.eta = h->p.eta;
+  a.inv_gdt = h->inv_gdt;
+  a.status = h->status;
+  return a;
+}
+
+template <int K, int MODE, class R>
+static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
+  const size_t fs = FaceSmem<K, R>::bytes(), vs = VolSmem<K, R>::bytes();
+  DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+  DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
   const int nfaces = 3 * h->ne;
   int per_sm_f = (int)((200 * 1024) / fs), per_sm_v = (int)((200 * 1024) / vs);
   per_sm_f = per_sm_f < 1 ? 1 : (per_sm_f > 8 ? 8 : per_sm_f);
@@ -723,29 +764,30 @@ static int run_operator(Handle* h, const OpArgs& a, cudaStream_t st) {
   const int fblocks = (nfaces + kFaceWarps - 1) / kFaceWarps;
   if (gf > fblocks) gf = fblocks;
   if (gv > h->ne) gv = h->ne;
-  const int cf = (MODE == MODE_TAN || MODE == MODE_LINPART) ? DG_PROF_FACE_TAN : DG_PROF_FACE_RES;
-  const int cv = (MODE == MODE_TAN || MODE == MODE_LINPART) ? DG_PROF_VOL_TAN : DG_PROF_VOL_RES;
+  const bool tan = (MODE == MODE_TAN || MODE == MODE_LINPART);
+  const int cf = tan ? (sizeof(R) == 4 ? DG_PROF_FACE_TAN32 : DG_PROF_FACE_TAN) : DG_PROF_FACE_RES;
+  const int cv = tan ? (sizeof(R) == 4 ? DG_PROF_VOL_TAN32 : DG_PROF_VOL_TAN) : DG_PROF_VOL_RES;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if ((rc = prof_begin(h, st, &e0))) return rc;
-  face_kernel<K, MODE><<<gf, 32 * kFaceWarps, fs, st>>>(a);
+  face_kernel<K, MODE, R><<<gf, 32 * kFaceWarps, fs, st>>>(a);
   DG_LAUNCH_CHECK(h);
   if ((rc = prof_end(h, cf, st, e0))) return rc;
   if ((rc = prof_begin(h, st, &e1))) return rc;
-  vol_kernel<K, MODE><<<gv, 128, vs, st>>>(a);
+  vol_kernel<K, MODE, R><<<gv, 128, vs, st>>>(a);
   DG_LAUNCH_CHECK(h);
   if ((rc = prof_end(h, cv, st, e1))) return rc;
   ++h->op_apps;
   return DG_OK;
 }
 
-template <int MODE>
-static int dispatch(Handle* h, const OpArgs& a, cudaStream_t st) {
+template <int MODE, class R>
+static int dispatch(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
   switch (h->tab.k) {
-    case 1: return run_operator<1, MODE>(h, a, st);
-    case 2: return run_operator<2, MODE>(h, a, st);
-    case 3: return run_operator<3, MODE>(h, a, st);
-    case 4: return run_operator<4, MODE>(h, a, st);
+    case 1: return run_operator<1, MODE, R>(h, a, st);
+    case 2: return run_operator<2, MODE, R>(h, a, st);
+    case 3: return run_operator<3, MODE, R>(h, a, st);
+    case 4: return run_operator<4, MODE, R>(h, a, st);
   }
   return fail(h, DG_ERR_ARG, "unsupported degree");
 }
@@ -757,6 +799,11 @@ int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStrea
 
 int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st) {
   OpArgs a = make_args(h, v, out);
+  return dispatch<MODE_TAN>(h, a, st);
+}
+
+int op_tangent_f32(Handle* h, const float* v, float* out, cudaStream_t st) {
+  OpArgsT<float> a = make_args_f(h, v, out);
   return dispatch<MODE_TAN>(h, a, st);
 }
 
@@ -840,5 +887,5 @@ extern "C" int dg_residual_noalloc(dg_handle* hh, const double* w, double* f, vo
   OpArgs a = make_args(h, w, f);
   a.face_out = scratch;
   a.face_lift = scratch + (size_t)h->ne * 6 * 4 * n2;
-  return dispatch<MODE_RES>(h, a, as_stream(stream));
+  return dispatch<MODE_RES, double>(h, a, as_stream(stream));
 }

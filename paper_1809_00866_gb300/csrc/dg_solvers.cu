@@ -85,9 +85,17 @@ __global__ void multi_axpy_kernel(long long n, int nv, const double* V, long lon
   }
 }
 
-__global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
+template <class R>
+__global__ void axpby_kernel(long long n, R a, const R* x, R b, R* y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+    y[i] = a * x[i] + (b == R(0) ? R(0) : b * y[i]);
+}
+
+// FP64 <-> FP32 copies at the boundary of the reduced-precision preconditioner
+template <class A, class B>
+__global__ void convert_kernel(long long n, const A* x, B* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (B)x[i];
 }
 
 __global__ void scale_by_dev_kernel(long long n, const double* x, const double* dnorm2, double* y) {
@@ -98,13 +106,14 @@ __global__ void scale_by_dev_kernel(long long n, const double* x, const double* 
 }
 
 int launch_axpby(Handle* h, long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
-  axpby_kernel<<<h->nsm * 8, 256, 0, st>>>(n, a, x, b, y);
+  axpby_kernel<double><<<h->nsm * 8, 256, 0, st>>>(n, a, x, b, y);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
 
 // ------------------------------------------------------ transfer operators
-__global__ void restrict_kernel(int ne, int nbf, int nbc, const double* xf, double* xc) {
+template <class R>
+__global__ void restrict_kernel(int ne, int nbf, int nbc, const R* xf, R* xc) {
   const long long n = (long long)ne * 4 * nbc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long ev = i / nbc;
@@ -112,7 +121,8 @@ __global__ void restrict_kernel(int ne, int nbf, int nbc, const double* xf, doub
     xc[i] = xf[ev * nbf + m];
   }
 }
-__global__ void prolong_add_kernel(int ne, int nbf, int nbc, const double* xc, double* xf) {
+template <class R>
+__global__ void prolong_add_kernel(int ne, int nbf, int nbc, const R* xc, R* xf) {
   const long long n = (long long)ne * 4 * nbc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long ev = i / nbc;
@@ -123,9 +133,11 @@ __global__ void prolong_add_kernel(int ne, int nbf, int nbc, const double* xc, d
 
 // ------------------------------------------------------- block operations
 // y[e] = alpha * sum_s B[e][s] x[nbr(e,s)] + beta * y[e]; slot 0 is the element itself.
-__global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr, const double* B, double alpha,
-                                                  const double* x, double beta, double* y) {
-  extern __shared__ double sx[];  // [7][b]
+template <class R>
+__global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr, const R* B, R alpha,
+                                                  const R* x, R beta, R* y) {
+  extern __shared__ __align__(16) unsigned char sraw_[];
+  R* sx = reinterpret_cast<R*>(sraw_);  // [7][b]
   for (int e = blockIdx.x; e < ne; e += gridDim.x) {
     for (int t = threadIdx.x; t < 7 * b; t += blockDim.x) {
       const int s = t / b, c = t - s * b;
@@ -134,11 +146,11 @@ __global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr,
     }
     __syncthreads();
     for (int r = threadIdx.x; r < b; r += blockDim.x) {
-      double acc = 0.0;
-      const double* Be = B + (size_t)e * 7 * b * b;
+      R acc = R(0);
+      const R* Be = B + (size_t)e * 7 * b * b;
       for (int s = 0; s < 7; ++s)
         for (int c = 0; c < b; ++c) acc += Be[((size_t)s * b + c) * b + r] * sx[s * b + c];
-      y[(size_t)e * b + r] = alpha * acc + (beta == 0.0 ? 0.0 : beta * y[(size_t)e * b + r]);
+      y[(size_t)e * b + r] = alpha * acc + (beta == R(0) ? R(0) : beta * y[(size_t)e * b + r]);
     }
     __syncthreads();
   }
@@ -150,38 +162,40 @@ __global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr,
 // with the unit-lower L and backward substitution with U (1/U_kk stored on the
 // diagonal), both along contiguous columns.
 constexpr int kApplyWarps = 4;
-__global__ void __launch_bounds__(32 * kApplyWarps) bj_update_kernel(int ne, int b, const double* LU, const int* perm,
-                                                                    const double* g, const double* Gx, double omega,
-                                                                    int x_zero, double* x) {
-  extern __shared__ double sz[];  // [warps][b]
+template <class R>
+__global__ void __launch_bounds__(32 * kApplyWarps) bj_update_kernel(int ne, int b, const R* LU, const int* perm,
+                                                                    const R* g, const R* Gx, R omega, int x_zero,
+                                                                    R* x) {
+  extern __shared__ __align__(16) unsigned char sraw_[];
+  R* sz = reinterpret_cast<R*>(sraw_);  // [warps][b]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* z = sz + warp * b;
+  R* z = sz + warp * b;
   for (int e = blockIdx.x * kApplyWarps + warp; e < ne; e += gridDim.x * kApplyWarps) {
     const int* pi = perm + (size_t)e * b;
-    const double* ge = g + (size_t)e * b;
-    const double* gx = Gx ? Gx + (size_t)e * b : nullptr;
+    const R* ge = g + (size_t)e * b;
+    const R* gx = Gx ? Gx + (size_t)e * b : nullptr;
     for (int i = lane; i < b; i += 32) {
       const int r = pi[i];
-      z[i] = ge[r] - (gx ? gx[r] : 0.0);
+      z[i] = ge[r] - (gx ? gx[r] : R(0));
     }
     __syncwarp();
-    const double* M = LU + (size_t)e * b * b;
+    const R* M = LU + (size_t)e * b * b;
     for (int j = 0; j < b; ++j) {  // z <- L^-1 z
-      const double zj = z[j];
-      const double* col = M + (size_t)j * b;
+      const R zj = z[j];
+      const R* col = M + (size_t)j * b;
       for (int i = j + 1 + lane; i < b; i += 32) z[i] = fma(-col[i], zj, z[i]);
       __syncwarp();
     }
     for (int j = b - 1; j >= 0; --j) {  // z <- U^-1 z
-      const double* col = M + (size_t)j * b;
-      const double zj = z[j] * col[j];
+      const R* col = M + (size_t)j * b;
+      const R zj = z[j] * col[j];
       __syncwarp();
       if (lane == 0) z[j] = zj;
       for (int i = lane; i < j; i += 32) z[i] = fma(-col[i], zj, z[i]);
       __syncwarp();
     }
-    double* xe = x + (size_t)e * b;
-    for (int i = lane; i < b; i += 32) xe[i] = (x_zero ? 0.0 : xe[i]) + omega * z[i];
+    R* xe = x + (size_t)e * b;
+    for (int i = lane; i < b; i += 32) xe[i] = (x_zero ? R(0) : xe[i]) + omega * z[i];
     __syncwarp();
   }
 }
@@ -201,7 +215,7 @@ static int apply_grid(const Handle* h) {
 
 static int run_bsr(Handle* h, int lvl, double alpha, const double* x, double beta, double* y, cudaStream_t st) {
   const Level& L = h->lev[lvl];
-  bsr_kernel<<<grid_for(h, h->ne), 128, sizeof(double) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsr, alpha, x, beta, y);
+  bsr_kernel<double><<<grid_for(h, h->ne), 128, sizeof(double) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsr, alpha, x, beta, y);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -222,7 +236,7 @@ static int jacobi_sweeps(Handle* h, int lvl, const double* g, double* x, int swe
       int rc = level_matvec(h, lvl, x, L.t2, st);
       if (rc) return rc;
     }
-    bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
+    bj_update_kernel<double><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
                                                                     zero ? nullptr : L.t2, omega, zero ? 1 : 0, x);
     DG_LAUNCH_CHECK(h);
   }
@@ -326,7 +340,7 @@ static int gmres_smooth(Handle* h, int lvl, const double* g, double* x, int its,
   int rc;
   // v0 = D^-1 (g - G x)
   if (!x_zero && (rc = level_matvec(h, lvl, x, L.t2, st))) return rc;
-  bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
+  bj_update_kernel<double><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
                                                                   x_zero ? nullptr : L.t2, 1.0, 1, V);
   DG_LAUNCH_CHECK(h);
   if ((rc = vec_norm2(h, V, n, beta2, st))) return rc;
@@ -336,7 +350,7 @@ static int gmres_smooth(Handle* h, int lvl, const double* g, double* x, int its,
     double* vj = V + (size_t)j * n;
     double* w = V + (size_t)(j + 1) * n;
     if ((rc = level_matvec(h, lvl, vj, L.t2, st))) return rc;
-    bj_update_kernel<<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, L.t2, nullptr, 1.0,
+    bj_update_kernel<double><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, L.t2, nullptr, 1.0,
                                                                     1, w);
     DG_LAUNCH_CHECK(h);
     for (int pass = 0; pass < 2; ++pass) {
@@ -366,13 +380,13 @@ static int smooth(Handle* h, int lvl, const double* g, double* x, int iters, dou
 
 static int restrict_to(Handle* h, int lvl, const double* xf, double* xc, cudaStream_t st) {
   const Level &F = h->lev[lvl], &C = h->lev[lvl + 1];
-  restrict_kernel<<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xf, xc);
+  restrict_kernel<double><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xf, xc);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
 static int prolong_add(Handle* h, int lvl, const double* xc, double* xf, cudaStream_t st) {
   const Level &F = h->lev[lvl], &C = h->lev[lvl + 1];
-  prolong_add_kernel<<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xc, xf);
+  prolong_add_kernel<double><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, F.nb, C.nb, xc, xf);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -391,7 +405,7 @@ static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const
     if ((rc = restrict_to(h, l, g, C.t0, st))) return rc;
   } else {
     if ((rc = level_matvec(h, l, x, L.t2, st))) return rc;
-    axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);  // t2 = g - G x
+    axpby_kernel<double><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);  // t2 = g - G x
     DG_LAUNCH_CHECK(h);
     if ((rc = restrict_to(h, l, L.t2, C.t0, st))) return rc;
   }
@@ -415,7 +429,7 @@ static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_
   if ((rc = prolong_add(h, l, C.t1, x, st))) return rc;  // w_hat_l = I w_{l+1}
   // d_l = g - G w_hat_l ; e_l = MG_V(l, d_l, 0) ; x = w_hat + e
   if ((rc = level_matvec(h, l, x, L.t2, st))) return rc;
-  axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);
+  axpby_kernel<double><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t2);
   DG_LAUNCH_CHECK(h);
   // The V-cycle below uses t2 as scratch on this level, so d_l moves out of it. On the fine
   // level t0/t1 are free here; on coarse levels they hold this level's (g, x), so the fine
@@ -424,7 +438,110 @@ static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_
   double* e = l == 0 ? L.t0 : h->fd_f;
   DG_CUDA(h, cudaMemcpyAsync(d, L.t2, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, st));
   if ((rc = mg_v(h, l, d, e, true, o, st))) return rc;
-  axpby_kernel<<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, e, 1.0, x);
+  axpby_kernel<double><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, e, 1.0, x);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+// ------------------------------------------------------ FP32 preconditioner cycle
+// FP32 copies of the linearisation cache (for the FP32 operator) and of the LU factors
+// and block-sparse coarse operators; refreshed after every linearisation / assembly.
+static int prepare_fp32(Handle* h, cudaStream_t st) {
+  const int ne = h->ne;
+  if (!h->lin_f_ready) {
+    const long long nu = (long long)ne * 3 * h->tab.nq, nf = (long long)3 * ne * h->tab.nqf * 32;
+    convert_kernel<double, float><<<grid_for(h, nu / 256 + 1), 256, 0, st>>>(nu, h->ubar, h->ubar_f);
+    DG_LAUNCH_CHECK(h);
+    convert_kernel<double, float><<<grid_for(h, nf / 256 + 1), 256, 0, st>>>(nf, h->dFlux, h->dFlux_f);
+    DG_LAUNCH_CHECK(h);
+    h->lin_f_ready = true;
+  }
+  if (!h->asm_f_ready) {
+    for (int l = 0; l < h->nlev; ++l) {
+      Level& L = h->lev[l];
+      const long long nbb = (long long)ne * L.b * L.b;
+      if (!L.LUf) DG_CUDA(h, cudaMalloc((void**)&L.LUf, sizeof(float) * nbb));
+      if (!L.t0f) DG_CUDA(h, cudaMalloc((void**)&L.t0f, sizeof(float) * L.n));
+      if (!L.t1f) DG_CUDA(h, cudaMalloc((void**)&L.t1f, sizeof(float) * L.n));
+      if (!L.t2f) DG_CUDA(h, cudaMalloc((void**)&L.t2f, sizeof(float) * L.n));
+      convert_kernel<double, float><<<grid_for(h, nbb / 256 + 1), 256, 0, st>>>(nbb, L.Dinv, L.LUf);
+      DG_LAUNCH_CHECK(h);
+      if (l >= 1) {
+        if (!L.Bsrf) DG_CUDA(h, cudaMalloc((void**)&L.Bsrf, sizeof(float) * nbb * 7));
+        convert_kernel<double, float><<<grid_for(h, 7 * nbb / 256 + 1), 256, 0, st>>>(7 * nbb, L.Bsr, L.Bsrf);
+        DG_LAUNCH_CHECK(h);
+      }
+    }
+    h->asm_f_ready = true;
+  }
+  return DG_OK;
+}
+
+static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, cudaStream_t st) {
+  if (lvl == 0) return op_tangent_f32(h, x, y, st);
+  const Level& L = h->lev[lvl];
+  bsr_kernel<float><<<grid_for(h, h->ne), 128, sizeof(float) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsrf, 1.0f, x,
+                                                                               0.0f, y);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+static int jacobi_sweeps_f(Handle* h, int lvl, const float* g, float* x, int sweeps, float omega, bool x_zero,
+                           cudaStream_t st) {
+  Level& L = h->lev[lvl];
+  const size_t smem = sizeof(float) * L.b * kApplyWarps;
+  for (int s = 0; s < sweeps; ++s) {
+    const bool zero = x_zero && s == 0;
+    if (!zero) {
+      int rc = level_matvec_f(h, lvl, x, L.t2f, st);
+      if (rc) return rc;
+    }
+    bj_update_kernel<float><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.LUf, L.perm, g,
+                                                                           zero ? nullptr : L.t2f, omega,
+                                                                           zero ? 1 : 0, x);
+    DG_LAUNCH_CHECK(h);
+  }
+  if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * L.n, st));
+  return DG_OK;
+}
+
+// MG_V(l, g, x) of Algorithm 2 in FP32 (block-Jacobi smoothing); level l >= 1 keeps its
+// right-hand side in t0f and its iterate in t1f, t2f is scratch.
+static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const dg_solve_opts& o, cudaStream_t st) {
+  int rc;
+  const int Lc = h->nlev - 1;
+  const float om = (float)o.omega;
+  if (l == Lc) return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, true, st);
+  if ((rc = jacobi_sweeps_f(h, l, g, x, o.pre_sweeps, om, x_zero, st))) return rc;
+  Level& L = h->lev[l];
+  Level& C = h->lev[l + 1];
+  const bool xz = x_zero && o.pre_sweeps == 0;
+  if (xz) {
+    restrict_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, g, C.t0f);
+    DG_LAUNCH_CHECK(h);
+  } else {
+    if ((rc = level_matvec_f(h, l, x, L.t2f, st))) return rc;
+    axpby_kernel<float><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0f, g, -1.0f, L.t2f);
+    DG_LAUNCH_CHECK(h);
+    restrict_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, L.t2f, C.t0f);
+    DG_LAUNCH_CHECK(h);
+  }
+  if ((rc = mg_v_f(h, l + 1, C.t0f, C.t1f, true, o, st))) return rc;
+  if (xz) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * L.n, st));
+  prolong_add_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, C.t1f, x);
+  DG_LAUNCH_CHECK(h);
+  return jacobi_sweeps_f(h, l, g, x, o.post_sweeps, om, false, st);
+}
+
+// z = MG_V(v) with the cycle in FP32: v rounded to FP32, the result widened to FP64.
+static int vcycle_fp32(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st) {
+  int rc;
+  if ((rc = prepare_fp32(h, st))) return rc;
+  Level& L0 = h->lev[0];
+  convert_kernel<double, float><<<grid_for(h, L0.n / 256 + 1), 256, 0, st>>>(L0.n, v, L0.t0f);
+  DG_LAUNCH_CHECK(h);
+  if ((rc = mg_v_f(h, 0, L0.t0f, L0.t1f, true, o, st))) return rc;
+  convert_kernel<float, double><<<grid_for(h, L0.n / 256 + 1), 256, 0, st>>>(L0.n, L0.t1f, z);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -434,6 +551,10 @@ static int check_opts(Handle* h, const dg_solve_opts* o) {
   if (o->pre_sweeps < 0 || o->post_sweeps < 0 || o->coarse_sweeps < 0) return fail(h, DG_ERR_ARG, "negative sweeps");
   if (!(o->omega > 0.0 && o->omega <= 1.0)) return fail(h, DG_ERR_ARG, "omega must be in (0, 1]");
   if (o->smoother != DG_SMOOTH_JACOBI && o->smoother != DG_SMOOTH_GMRES) return fail(h, DG_ERR_ARG, "unknown smoother");
+  if (o->precision != DG_PRECOND_FP64 && o->precision != DG_PRECOND_FP32)
+    return fail(h, DG_ERR_ARG, "unknown preconditioner precision");
+  if (o->precision == DG_PRECOND_FP32 && (o->smoother != DG_SMOOTH_JACOBI || o->precond == DG_PREC_FULLV))
+    return fail(h, DG_ERR_ARG, "the FP32 preconditioner supports block-Jacobi smoothing in V-cycles only");
   if (o->smoother == DG_SMOOTH_GMRES &&
       (o->pre_sweeps > DG_SMOOTH_MAX_ITS || o->post_sweeps > DG_SMOOTH_MAX_ITS || o->coarse_sweeps > DG_SMOOTH_MAX_ITS))
     return fail(h, DG_ERR_ARG, "GMRES smoother iterations above DG_SMOOTH_MAX_ITS");
@@ -445,7 +566,10 @@ static int apply_prec(Handle* h, const dg_solve_opts& o, const double* v, double
     DG_CUDA(h, cudaMemcpyAsync(z, v, sizeof(double) * h->lev[0].n, cudaMemcpyDeviceToDevice, st));
     return DG_OK;
   }
-  if (o.precond == DG_PREC_VCYCLE) return mg_v(h, 0, v, z, true, o, st);
+  if (o.precond == DG_PREC_VCYCLE) {
+    if (o.precision == DG_PRECOND_FP32) return vcycle_fp32(h, o, v, z, st);
+    return mg_v(h, 0, v, z, true, o, st);
+  }
   if (o.precond == DG_PREC_FULLV) {
     if (h->nlev > 1 && h->lev[1].n > h->lev[0].n) return fail(h, DG_ERR_ARG, "bad level sizes");
     return mg_full(h, 0, v, z, o, st);
@@ -639,6 +763,7 @@ int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* o
   if (rc) return rc;
   if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
   if (!h->assembled) return fail(h, DG_ERR_STATE, "pmg_vcycle needs dg_assemble first");
+  if (opts->precision == DG_PRECOND_FP32) return vcycle_fp32(h, *opts, g, x, as_stream(stream));
   return mg_v(h, 0, g, x, true, *opts, as_stream(stream));
 }
 

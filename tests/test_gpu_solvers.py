@@ -177,3 +177,49 @@ def test_vcycle_gmres_smoother(name, levels, its):
     a = SV.remove_mean_pressure(host(xg).reshape(-1), m.ne, m.nb, vol)
     b = SV.remove_mean_pressure(xr, m.ne, m.nb, vol)
     assert rel(a, b) < 1e-9
+
+
+@pytest.mark.parametrize("name,levels", [("u3", [2, 1]), ("u2", [3, 2, 1]), ("box233", [4, 2, 1])])
+def test_fp32_preconditioner_cycle(name, levels):
+    # Reduced-precision preconditioner: the same V-cycle with FP32 operator products,
+    # LU factors, coarse blocks and vectors. Its deviation from the FP64 cycle is rounding of
+    # FP32 arithmetic (unit roundoff 6e-8) amplified through the cycle: stated bound 1e-5.
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = -O.residual(m, w).reshape(-1)
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g))
+    x64, x32 = dg.empty(), dg.empty()
+    gd = dev(g.reshape(x64.shape))
+    dg.pmg_vcycle(gd, x64, P.solve_opts())
+    dg.pmg_vcycle(gd, x32, P.solve_opts(precision=P.DG_PRECOND_FP32))
+    assert rel(host(x64).reshape(-1), ref) < 1e-12
+    assert rel(host(x32).reshape(-1), ref) < 1e-5
+
+
+def test_fp32_preconditioner_reaches_fp64_accuracy():
+    # FGMRES and its products with G stay FP64, so the FP32 preconditioner does not limit the
+    # attainable accuracy: one implicit stage of the 4^3 P2 Taylor-Green workload to 1e-10.
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()["u4"], [2, 1])
+    w = O.project_tgv(m)
+    inv = 1.0 / S.acoustic_dt(4, 2)
+    wd = dev(w)
+    f = dg.empty()
+    dg.dg_residual(wd, f)
+    g = (-f).contiguous()
+    dg.dg_set_linearization(wd, inv)
+    dg.dg_assemble()
+    # damped block Jacobi (omega 0.7): the FP32 rounding noise leaves the symmetric subspace of the
+    # Taylor-Green right-hand side, where undamped block Jacobi is not a convergent smoother
+    x64, x32 = dg.empty(), dg.empty()
+    i64, rc64 = dg.fgmres_solve(g, x64, P.solve_opts(rtol=1e-10, maxit=300, omega=0.7))
+    i32, rc32 = dg.fgmres_solve(g, x32, P.solve_opts(rtol=1e-10, maxit=300, omega=0.7,
+                                                     precision=P.DG_PRECOND_FP32))
+    assert rc64 == P.DG_OK and rc32 == P.DG_OK
+    G0 = O.dense_G(m, w, inv)
+    gr = host(g).reshape(-1)
+    assert np.linalg.norm(gr - G0 @ host(x32).reshape(-1)) / np.linalg.norm(gr) < 1e-9
+    vol = m.vol()
+    a = SV.remove_mean_pressure(host(x32).reshape(-1), m.ne, m.nb, vol)
+    b = SV.remove_mean_pressure(host(x64).reshape(-1), m.ne, m.nb, vol)
+    assert rel(a, b) < 1e-8
