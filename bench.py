@@ -224,7 +224,7 @@ def run_ours(args):
         if e: e[1].record(st)
         dg.dg_set_linearization(w, inv)
         if e: e[2].record(st)
-        dg.dg_assemble()
+        dg.dg_assemble(precision=opts.precision)
         if e: e[3].record(st)
         info, rc = dg.fgmres_solve(f, dw, opts)
         if rc != P.DG_OK:
@@ -281,9 +281,10 @@ def run_ours(args):
     dg.dg_residual(w, f)
     f.neg_()
     dg.dg_set_linearization(w, inv)
-    dg.dg_assemble()
+    dg.dg_assemble(precision=plain_opts.precision)
     d64, d32 = dg.empty(), dg.empty()
     dg.fgmres_solve(f, d64, plain_opts)
+    dg.dg_assemble(precision=chosen_opts.precision)
     dg.fgmres_solve(f, d32, chosen_opts)
     chosen_err = float((d32 - d64).norm() / d64.norm())
 
@@ -309,7 +310,7 @@ def run_ours(args):
     dg.dg_profile(False)
     t_jv = statistics.median(jv_times)
     # FP32 Jacobian action as used inside the chosen form's cycle (timed through one V-cycle's profile)
-    dg.dg_assemble()
+    dg.dg_assemble(precision=P.DG_PRECOND_FP32)
     g32 = torch.from_numpy(S.direction(dg.ne, k, S.SEED_V + 1)).cuda()
     z32 = dg.empty()
     opts32 = opts_for(P.DG_PRECOND_FP32, args.omega)

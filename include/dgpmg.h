@@ -82,7 +82,7 @@ typedef struct dg_handle dg_handle;
                               DG_SMOOTH_MAX_ITS iterations per call */
 #define DG_SMOOTH_MAX_ITS 32
 
-/* Precision of the preconditioner cycle. */
+/* Precision of the preconditioner cycle (and of its assembly, dg_assemble_precision). */
 #define DG_PRECOND_FP64 0
 #define DG_PRECOND_FP32 1 /* block-Jacobi smoothing only */
 
@@ -165,6 +165,13 @@ int dg_jvp(dg_handle* h, const double* v, double* out, int mode, void* stream);
  * orthonormal basis, Eq. (GalProj)); off-diagonal blocks are built at the
  * degree of level 1 only (Sec. 2.4.3). Synchronises. */
 int dg_assemble(dg_handle* h, void* stream);
+
+/* dg_assemble in the precision of the preconditioner that will use it:
+ * DG_PRECOND_FP64 (= dg_assemble; also usable by the FP32 cycle after rounding), or
+ * DG_PRECOND_FP32: the state-dependent blocks, the inherited coarse blocks and the LU
+ * factors are computed in FP32 (the mesh-only linear part is probed once in FP64), for
+ * the FP32 preconditioner cycle only. Synchronises. */
+int dg_assemble_precision(dg_handle* h, int precision, void* stream);
 
 /* ------------------------------------------------------------ p-multigrid */
 

@@ -36,7 +36,7 @@ DG_MAX_LEVELS = 4
 EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_status", "dg_project_tgv",
            "dg_residual", "dg_set_linearization", "dg_jvp", "dg_assemble", "pmg_restrict", "pmg_prolong",
            "block_jacobi_smooth", "bsr_spmv", "pmg_vcycle", "fgmres_solve", "dg_counters", "dg_profile",
-           "dg_profile_read", "dg_residual_noalloc")
+           "dg_profile_read", "dg_residual_noalloc", "dg_assemble_precision")
 DG_PROF_N = 6
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32")
 
@@ -93,6 +93,7 @@ def load(path=None):
     L.pmg_vcycle.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), vp]
     L.fgmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), ctypes.POINTER(DgSolveInfo), vp]
     L.dg_residual_noalloc.argtypes = [vp, vp, vp, vp]
+    L.dg_assemble_precision.argtypes = [vp, i, vp]
     L.dg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.dg_profile.argtypes = [vp, i]
     L.dg_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -201,8 +202,11 @@ class DG:
     def dg_jvp(self, v, out, mode=DG_JVP_TANGENT, stream=None):
         self._chk(self._L.dg_jvp(self.h, self._ptr(v), self._ptr(out), int(mode), self._stream(stream)))
 
-    def dg_assemble(self, stream=None):
-        self._chk(self._L.dg_assemble(self.h, self._stream(stream)))
+    def dg_assemble(self, stream=None, precision=None):
+        if precision is None:
+            self._chk(self._L.dg_assemble(self.h, self._stream(stream)))
+        else:
+            self._chk(self._L.dg_assemble_precision(self.h, int(precision), self._stream(stream)))
 
     def pmg_restrict(self, lvl, xf, xc, stream=None):
         self._chk(self._L.pmg_restrict(self.h, lvl, self._ptr(xf, lvl), self._ptr(xc, lvl + 1), self._stream(stream)))

@@ -186,7 +186,7 @@ static int build_tables(Handle* h, int k) {
     return rcode;
   auto tof = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
   TablesF& TF = h->tabf;
-  if ((rcode = upload(h, &TF.L1, tof(L1))) || (rcode = upload(h, &TF.wvol, tof(wv))) ||
+  if ((rcode = upload(h, &TF.Bvol, tof(Bv))) || (rcode = upload(h, &TF.L1, tof(L1))) || (rcode = upload(h, &TF.wvol, tof(wv))) ||
       (rcode = upload(h, &TF.B2, tof(B2))) || (rcode = upload(h, &TF.W2, tof(W2))) ||
       (rcode = upload(h, &TF.pv, tof(pvv))) || (rcode = upload(h, &TF.pd, tof(pdv))) ||
       (rcode = upload(h, &TF.Drow_val, tof(rv))) || (rcode = upload(h, &TF.Dcol_val, tof(cv))) ||
@@ -242,7 +242,7 @@ static void free_all(Handle* h) {
   F(T.L1); F(T.B2); F(T.W2); F(T.pv); F(T.pd); F(T.M3); F(T.fmap); F(T.fa); F(T.md3); F(T.pidx); F(T.pab);
   F(T.D2_idx); F(T.D2_val);
   TablesF& TF = h->tabf;
-  F(TF.L1); F(TF.wvol); F(TF.B2); F(TF.W2); F(TF.pv); F(TF.pd); F(TF.Drow_val); F(TF.Dcol_val); F(TF.D2_val);
+  F(TF.Bvol); F(TF.L1); F(TF.wvol); F(TF.B2); F(TF.W2); F(TF.pv); F(TF.pd); F(TF.Drow_val); F(TF.Dcol_val); F(TF.D2_val);
   F(h->face_out_f); F(h->face_lift_f); F(h->ubar_f); F(h->dFlux_f);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
@@ -438,15 +438,22 @@ int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) 
   return fail(h, DG_ERR_ARG, "unknown jvp mode");
 }
 
-int dg_assemble(dg_handle* hh, void* stream) {
+int dg_assemble_precision(dg_handle* hh, int precision, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");
-  const int rc = assemble_all(h, as_stream(stream));
-  if (rc == DG_OK) h->assembled = true;
-  h->asm_f_ready = false;
+  if (precision != DG_PRECOND_FP64 && precision != DG_PRECOND_FP32) return fail(h, DG_ERR_ARG, "unknown precision");
+  h->assembled = h->asm64_ready = h->asm_f_ready = false;
+  const int rc = assemble_all(h, precision, as_stream(stream));
+  if (rc == DG_OK) {
+    h->assembled = true;
+    h->asm64_ready = precision == DG_PRECOND_FP64;
+    h->asm_f_ready = precision == DG_PRECOND_FP32;
+  }
   return rc;
 }
+
+int dg_assemble(dg_handle* hh, void* stream) { return dg_assemble_precision(hh, DG_PRECOND_FP64, stream); }
 
 int dg_counters(const dg_handle* hh, long long* kernel_launches, long long* operator_applications) {
   const Handle* h = reinterpret_cast<const Handle*>(hh);

@@ -33,7 +33,7 @@ namespace dg {
 //    E_ij = sum_q w2_q dF_i/ds_j(q) B2[q][n2] B2[q][n2'].
 // Diagonal blocks use the own side's columns of the Jacobian; the level-1 off-diagonal
 // blocks the other side's, restricted to the coarse modes.
-template <int K>
+template <int K, class R = double>
 struct AsmSmem {
   static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
   static constexpr int B = 0;                 // [NQ][NB]
@@ -49,57 +49,65 @@ struct AsmSmem {
   static constexpr int FMAP = 0;              // [3][NB]
   static constexpr int FA = FMAP + 3 * NB;    // [3][NB]
   static constexpr int INTS = FA + 3 * NB;
-  static constexpr size_t bytes() { return sizeof(double) * DOUBLES + sizeof(int) * INTS; }
+  static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
 
+template <class R>
 struct AsmArgs {
   MeshDev M;
   Tables T;
-  const double* ubar;
-  const double* dFlux;
-  const double* Dlin;  // level 0 linear-part diagonal blocks
-  double* D;           // level 0 diagonal blocks (output)
-  const double* Blin;  // level 1 linear-part off-diagonal blocks
-  double* Bsr;         // level 1 block rows (output, slots 1..6)
+  const R* Bvol;       // tables in the assembly precision
+  const R* wvol;
+  const R* B2;
+  const R* W2;
+  const R* pv;
+  const R* Dcol_val;
+  const R* ubar;       // linearisation cache in the assembly precision
+  const R* dFlux;
+  const double* Dlin;  // level 0 linear-part diagonal blocks (FP64, probed once)
+  R* D;                // level 0 diagonal blocks (output)
+  const double* Blin;  // level 1 linear-part off-diagonal blocks (FP64)
+  R* Bsr;              // level 1 block rows (output, slots 1..6)
   int nb1;             // modes per variable on level 1 (0: no coarse level)
   double inv_gdt;
 };
 
-template <int K>
-__global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
-  using L = AsmSmem<K>;
+template <int K, class R>
+__global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
+  using L = AsmSmem<K, R>;
   constexpr int NB = L::NB, NQ = L::NQ, NQF = L::NQF, N2 = L::N2, K1 = K + 1, BS = 4 * NB, DW = Tables::kDw;
-  extern __shared__ double sm[];
-  double* sB = sm + L::B;
-  double* sW = sm + L::W;
-  double* sUb = sm + L::UB;
-  double* sU = sm + L::U;
-  double* sE = sm + L::E;
-  double* sJ = sm + L::JQ;
-  double* sB2 = sm + L::B2;
-  double* sW2 = sm + L::W2;
-  double* sPV = sm + L::PV;
+  extern __shared__ __align__(16) unsigned char smraw_[];
+  R* sm = reinterpret_cast<R*>(smraw_);
+  R* sB = sm + L::B;
+  R* sW = sm + L::W;
+  R* sUb = sm + L::UB;
+  R* sU = sm + L::U;
+  R* sE = sm + L::E;
+  R* sJ = sm + L::JQ;
+  R* sB2 = sm + L::B2;
+  R* sW2 = sm + L::W2;
+  R* sPV = sm + L::PV;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
   int* FMAP = ism + L::FMAP;
   int* FA = ism + L::FA;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.T.Bvol[t];
-  for (int t = tid; t < NQ; t += nt) sW[t] = a.T.wvol[t];
-  for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.T.B2[t];
-  for (int t = tid; t < NQF; t += nt) sW2[t] = a.T.W2[t];
-  for (int t = tid; t < 2 * K1; t += nt) sPV[t] = a.T.pv[t];
+  for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.Bvol[t];
+  for (int t = tid; t < NQ; t += nt) sW[t] = a.wvol[t];
+  for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.B2[t];
+  for (int t = tid; t < NQF; t += nt) sW2[t] = a.W2[t];
+  for (int t = tid; t < 2 * K1; t += nt) sPV[t] = a.pv[t];
   for (int t = tid; t < 3 * NB; t += nt) { FMAP[t] = a.T.fmap[t]; FA[t] = a.T.fa[t]; }
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
-    const double* Jd = g.J;
+    const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
     for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
     __syncthreads();
     // weighted mass matrices U_c (symmetric)
     for (int t = tid; t < 3 * NB * NB; t += nt) {
       const int c = t / (NB * NB), r = t - c * NB * NB, n1 = r / NB, n = r - n1 * NB;
       if (n1 > n) continue;
-      double acc = 0.0;
+      R acc = R(0);
       for (int q = 0; q < NQ; ++q) acc += sW[q] * sUb[c * NQ + q] * sB[q * NB + n1] * sB[q * NB + n];
       sU[(c * NB + n1) * NB + n] = acc;
       sU[(c * NB + n) * NB + n1] = acc;
@@ -117,35 +125,35 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
         __syncthreads();
         for (int t = tid; t < 6 * N2 * N2; t += nt) {
           const int sl = t / (N2 * N2), r = t - sl * N2 * N2, j1 = r / N2, j2 = r - j1 * N2;
-          double acc = 0.0;
+          R acc = R(0);
 #pragma unroll
           for (int q = 0; q < NQF; ++q) acc += sJ[sl * NQF + q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
           sE[t] = acc;
         }
         __syncthreads();
-        double* Dout = a.D + (size_t)e * BS * BS;
+        R* Dout = a.D + (size_t)e * BS * BS;
         const double* Dl = a.Dlin + (size_t)e * BS * BS;
         for (int t = tid; t < NB * NB; t += nt) {
           const int n = t / NB, m = t - n * NB;  // column-major within the pair: consecutive threads, consecutive rows
-          double v = Dl[(size_t)(j * NB + n) * BS + i * NB + m];
-          if (i == j && i < 3 && m == n) v += a.inv_gdt;
+          R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
+          if (i == j && i < 3 && m == n) v += R(a.inv_gdt);
           if (i < 3 && j < 3) {
             // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
-            double cv = 0.0;
+            R cv = R(0);
 #pragma unroll
             for (int q = 0; q < DW; ++q) {
               const int o = (j * NB + m) * DW + q;
-              cv += a.T.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
+              cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
             }
             v -= Jd[j] * cv;
             if (i == j) {
 #pragma unroll
               for (int pp = 0; pp < 3; ++pp) {
-                double c2 = 0.0;
+                R c2 = R(0);
 #pragma unroll
                 for (int q = 0; q < DW; ++q) {
                   const int o = (pp * NB + m) * DW + q;
-                  c2 += a.T.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
+                  c2 += a.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
                 }
                 v -= Jd[pp] * c2;
               }
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
 #pragma unroll
           for (int sl = 0; sl < 6; ++sl) {
             const int d = sl >> 1, side = (sl & 1) ? 0 : 1;
-            const double scale = (side == 0 ? 1.0 : -1.0) * Jd[d];  // A4 / s^2 = 2 / h_d
+            const R scale = (side == 0 ? R(1) : -R(1)) * Jd[d];  // A4 / s^2 = 2 / h_d
             v += scale * sPV[side * K1 + FA[d * NB + m]] * sPV[side * K1 + FA[d * NB + n]] *
                  sE[(sl * N2 + FMAP[d * NB + m]) * N2 + FMAP[d * NB + n]];
           }
@@ -174,8 +182,8 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
           if (a.M.nbr[e * 6 + s2] == p) { tgt = s2; break; }
         const ElemGeom gp = elem_geom(a.M, p);
         const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        const double scale = (side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is;
-        double* blk = a.Bsr + ((size_t)e * 7 + 1 + tgt) * b1 * b1;
+        const R scale = R((side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is);
+        R* blk = a.Bsr + ((size_t)e * 7 + 1 + tgt) * b1 * b1;
         const double* lin = a.Blin + ((size_t)e * 7 + 1 + sl) * b1 * b1;
         for (int i = 0; i < 4; ++i)
           for (int j = 0; j < 4; ++j) {
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
             __syncthreads();
             for (int t = tid; t < N2 * N2; t += nt) {
               const int j1 = t / N2, j2 = t - j1 * N2;
-              double acc = 0.0;
+              R acc = R(0);
 #pragma unroll
               for (int q = 0; q < NQF; ++q) acc += sJ[q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
               sE[t] = acc;
@@ -193,15 +201,15 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
             for (int t = tid; t < nb1 * nb1; t += nt) {
               const int n = t / nb1, m = t - n * nb1;
               const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
-              const double base = (tgt == sl) ? lin[o] : blk[o];
+              const R base = (tgt == sl) ? R(lin[o]) : blk[o];
               blk[o] = base + scale * sPV[side * K1 + FA[d * NB + m]] * sPV[other * K1 + FA[d * NB + n]] *
                                   sE[FMAP[d * NB + m] * N2 + FMAP[d * NB + n]];
             }
             __syncthreads();
           }
         if (tgt != sl) {
-          double* z = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
-          for (int t = tid; t < b1 * b1; t += nt) z[t] = 0.0;
+          R* z = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
+          for (int t = tid; t < b1 * b1; t += nt) z[t] = R(0);
         }
         __syncthreads();
       }
@@ -209,15 +217,15 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs a) {
   }
 }
 
-template <int K>
-static int launch_assemble_state(Handle* h, const AsmArgs& a, cudaStream_t st) {
-  const size_t smem = AsmSmem<K>::bytes();
-  DG_CUDA(h, cudaFuncSetAttribute(assemble_state_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <int K, class R>
+static int launch_assemble_state(Handle* h, const AsmArgs<R>& a, cudaStream_t st) {
+  const size_t smem = AsmSmem<K, R>::bytes();
+  DG_CUDA(h, cudaFuncSetAttribute(assemble_state_kernel<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = (int)((200 * 1024) / smem);
   per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
   int grid = h->nsm * per_sm;
   if (grid > h->ne) grid = h->ne;
-  assemble_state_kernel<K><<<grid, 256, smem, st>>>(a);
+  assemble_state_kernel<K, R><<<grid, 256, smem, st>>>(a);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -302,8 +310,9 @@ __global__ void scatter_offdiag_kernel(int ne, int nb0, int nb1, const int* nbr,
 }
 
 // dst block (size bd, nbd modes/variable) = leading sub-block of src block (bs, nbs).
-__global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const double* src, long long src_stride,
-                                double* dst, long long dst_stride) {
+template <class R>
+__global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const R* src, long long src_stride,
+                                R* dst, long long dst_stride) {
   const int bs = 4 * nbs, bd = 4 * nbd;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblocks * bd * bd;
        i += (long long)gridDim.x * blockDim.x) {
@@ -318,16 +327,18 @@ __global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const doubl
 // shared memory (row-major, padded leading dimension). Output, column-major per block:
 // the unit-lower L below the diagonal, U above it, and 1/U_kk on the diagonal; and the
 // row permutation pi (row i of P A is row pi[i] of A).
-__global__ void __launch_bounds__(256) lu_factor_kernel(int nblk, int b, const double* in, double* out, int* perm,
+template <class R>
+__global__ void __launch_bounds__(256) lu_factor_kernel(int nblk, int b, const R* in, R* out, int* perm,
                                                        unsigned* status) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw_[];
+  R* sm = reinterpret_cast<R*>(smraw_);
   const int LD = b + 1;
-  double* A = sm;                               // [b][LD]
+  R* A = sm;                               // [b][LD]
   int* piv = reinterpret_cast<int*>(A + b * LD);  // [b] row swapped with k at step k
   __shared__ int s_piv;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const double* src = in + (size_t)blk * b * b;
+    const R* src = in + (size_t)blk * b * b;
     for (int t = tid; t < b * b; t += nt) {
       const int c = t / b, r = t - c * b;
       A[r * LD + c] = src[t];
@@ -335,46 +346,46 @@ __global__ void __launch_bounds__(256) lu_factor_kernel(int nblk, int b, const d
     __syncthreads();
     for (int k = 0; k < b; ++k) {
       if (warp == 0) {
-        double best = -1.0;
+        R best = R(-1);
         int bi = k;
         for (int i = k + lane; i < b; i += 32) {
-          const double v = fabs(A[i * LD + k]);
+          const R v = fabs(A[i * LD + k]);
           if (v > best) { best = v; bi = i; }
         }
         for (int off = 16; off > 0; off >>= 1) {
-          const double ov = __shfl_down_sync(0xffffffffu, best, off);
+          const R ov = __shfl_down_sync(0xffffffffu, best, off);
           const int oi = __shfl_down_sync(0xffffffffu, bi, off);
           if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
         if (lane == 0) {
           s_piv = bi;
           piv[k] = bi;
-          if (!(best > 0.0) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
+          if (!(best > R(0)) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
         }
       }
       __syncthreads();
       const int p = s_piv;
       if (p != k)
         for (int j = tid; j < b; j += nt) {
-          const double t = A[k * LD + j];
+          const R t = A[k * LD + j];
           A[k * LD + j] = A[p * LD + j];
           A[p * LD + j] = t;
         }
       __syncthreads();
-      const double rk = 1.0 / A[k * LD + k];
+      const R rk = R(1) / A[k * LD + k];
       for (int i = k + 1 + tid; i < b; i += nt) A[i * LD + k] *= rk;
       __syncthreads();
       // trailing update: warp w takes rows k+1+w, k+1+w+nw, ...; lanes take the columns
       for (int i = k + 1 + warp; i < b; i += nw) {
-        const double l = A[i * LD + k];
-        double* Ai = A + i * LD;
-        const double* Ak = A + k * LD;
+        const R l = A[i * LD + k];
+        R* Ai = A + i * LD;
+        const R* Ak = A + k * LD;
         for (int j = k + 1 + lane; j < b; j += 32) Ai[j] = fma(-l, Ak[j], Ai[j]);
       }
       if (tid == 0) A[k * LD + k] = rk;
       __syncthreads();
     }
-    double* dst = out + (size_t)blk * b * b;
+    R* dst = out + (size_t)blk * b * b;
     for (int t = tid; t < b * b; t += nt) {
       const int c = t / b, r = t - c * b;
       dst[t] = A[r * LD + c];
@@ -394,15 +405,16 @@ __global__ void __launch_bounds__(256) lu_factor_kernel(int nblk, int b, const d
   }
 }
 
-static int factor_blocks(Handle* h, int nblk, int b, const double* in, double* out, int* perm, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (size_t)b * (b + 1) + sizeof(int) * b;
-  DG_CUDA(h, cudaFuncSetAttribute(lu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <class R>
+static int factor_blocks(Handle* h, int nblk, int b, const R* in, R* out, int* perm, cudaStream_t st) {
+  const size_t smem = sizeof(R) * (size_t)b * (b + 1) + sizeof(int) * b;
+  DG_CUDA(h, cudaFuncSetAttribute(lu_factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = (int)((220 * 1024) / smem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
   int grid = h->nsm * per_sm;
   if (grid > nblk) grid = nblk;
-  lu_factor_kernel<<<grid, 256, smem, st>>>(nblk, b, in, out, perm, h->status);
+  lu_factor_kernel<R><<<grid, 256, smem, st>>>(nblk, b, in, out, perm, h->status);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -451,68 +463,121 @@ static int probe_linear_part(Handle* h, cudaStream_t st) {
   return DG_OK;
 }
 
-int assemble_all(Handle* h, cudaStream_t st) {
-  const int ne = h->ne;
-  Level& L0 = h->lev[0];
-  const int b0 = L0.b;
-  const int grid = h->nsm * 8;
-  int rc;
-  // allocate on first use
+static int alloc_fp32_levels(Handle* h) {
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];
-    const size_t bb = (size_t)L.b * L.b;
-    if (!L.Dblk) DG_CUDA(h, cudaMalloc((void**)&L.Dblk, sizeof(double) * bb * ne));
-    if (!L.Dinv) DG_CUDA(h, cudaMalloc((void**)&L.Dinv, sizeof(double) * bb * ne));
-    if (l >= 1 && !L.Bsr) DG_CUDA(h, cudaMalloc((void**)&L.Bsr, sizeof(double) * bb * 7 * ne));
-    if (l == 0 && !L.Dlin) DG_CUDA(h, cudaMalloc((void**)&L.Dlin, sizeof(double) * bb * ne));
-    if (l == 1 && !L.Blin) DG_CUDA(h, cudaMalloc((void**)&L.Blin, sizeof(double) * bb * 7 * ne));
+    const size_t nbb = (size_t)h->ne * L.b * L.b;
+    if (!L.LUf) DG_CUDA(h, cudaMalloc((void**)&L.LUf, sizeof(float) * nbb));
+    if (!L.t0f) DG_CUDA(h, cudaMalloc((void**)&L.t0f, sizeof(float) * L.n));
+    if (!L.t1f) DG_CUDA(h, cudaMalloc((void**)&L.t1f, sizeof(float) * L.n));
+    if (!L.t2f) DG_CUDA(h, cudaMalloc((void**)&L.t2f, sizeof(float) * L.n));
+    if (l >= 1 && !L.Bsrf) DG_CUDA(h, cudaMalloc((void**)&L.Bsrf, sizeof(float) * nbb * 7));
+    if (!L.perm) DG_CUDA(h, cudaMalloc((void**)&L.perm, sizeof(int) * (size_t)h->ne * L.b));
   }
-  if (!h->linpart_ready) {
-    if ((rc = probe_linear_part(h, st))) return rc;
-    h->linpart_ready = true;
-  }
-  // state-dependent part + linear part + mass: level-0 diagonal and level-1 off-diagonal blocks
-  AsmArgs a;
-  a.M = mesh_dev(h);
-  a.T = h->tab;
-  a.ubar = h->ubar;
-  a.dFlux = h->dFlux;
-  a.Dlin = L0.Dlin;
-  a.D = L0.Dblk;
-  a.Blin = h->nlev > 1 ? h->lev[1].Blin : nullptr;
-  a.Bsr = h->nlev > 1 ? h->lev[1].Bsr : nullptr;
-  a.nb1 = h->nlev > 1 ? h->lev[1].nb : 0;
-  a.inv_gdt = h->inv_gdt;
+  return DG_OK;
+}
+
+template <class R>
+static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* const* Bsrlev, cudaStream_t st) {
+  const int ne = h->ne;
+  const int grid = h->nsm * 8;
+  int rc;
   switch (h->tab.k) {
-    case 1: rc = launch_assemble_state<1>(h, a, st); break;
-    case 2: rc = launch_assemble_state<2>(h, a, st); break;
-    case 3: rc = launch_assemble_state<3>(h, a, st); break;
-    case 4: rc = launch_assemble_state<4>(h, a, st); break;
+    case 1: rc = launch_assemble_state<1, R>(h, a, st); break;
+    case 2: rc = launch_assemble_state<2, R>(h, a, st); break;
+    case 3: rc = launch_assemble_state<3, R>(h, a, st); break;
+    case 4: rc = launch_assemble_state<4, R>(h, a, st); break;
     default: rc = fail(h, DG_ERR_ARG, "unsupported degree");
   }
   if (rc) return rc;
-  // coarse levels: inherited sub-blocks
+  const Level& L0 = h->lev[0];
+  const int b0 = L0.b;
+  // coarse levels: inherited sub-blocks (taken before the fine blocks are factored in place)
   for (int l = 1; l < h->nlev; ++l) {
     Level& L = h->lev[l];
     const size_t bb = (size_t)L.b * L.b;
-    subblock_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, L0.Dblk, (long long)b0 * b0, L.Dblk, (long long)bb);
+    subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, Dlev[0], (long long)b0 * b0, Dlev[l], (long long)bb);
     DG_LAUNCH_CHECK(h);
-    subblock_kernel<<<grid, 256, 0, st>>>(ne, L.nb, L.nb, L.Dblk, (long long)bb, L.Bsr, (long long)bb * 7);
+    subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L.nb, L.nb, Dlev[l], (long long)bb, Bsrlev[l], (long long)bb * 7);
     DG_LAUNCH_CHECK(h);
     if (l >= 2) {
       const Level& P = h->lev[l - 1];
       for (int s = 1; s < 7; ++s) {
-        subblock_kernel<<<grid, 256, 0, st>>>(ne, P.nb, L.nb, P.Bsr + (size_t)s * P.b * P.b, (long long)P.b * P.b * 7,
-                                              L.Bsr + (size_t)s * bb, (long long)bb * 7);
+        subblock_kernel<R><<<grid, 256, 0, st>>>(ne, P.nb, L.nb, Bsrlev[l - 1] + (size_t)s * P.b * P.b,
+                                                 (long long)P.b * P.b * 7, Bsrlev[l] + (size_t)s * bb, (long long)bb * 7);
         DG_LAUNCH_CHECK(h);
       }
     }
   }
-  // LU factors of the diagonal blocks (element-wise block Jacobi)
-  for (int l = 0; l < h->nlev; ++l) {
-    Level& L = h->lev[l];
-    if (!L.perm) DG_CUDA(h, cudaMalloc((void**)&L.perm, sizeof(int) * (size_t)ne * L.b));
-    if ((rc = factor_blocks(h, ne, L.b, L.Dblk, L.Dinv, L.perm, st))) return rc;
+  return DG_OK;
+}
+
+int assemble_all(Handle* h, int precision, cudaStream_t st) {
+  const int ne = h->ne;
+  Level& L0 = h->lev[0];
+  int rc;
+  // the linear part (FP64, mesh only) and the FP64 fine diagonal-block buffer it lives next to
+  if (!L0.Dlin) DG_CUDA(h, cudaMalloc((void**)&L0.Dlin, sizeof(double) * (size_t)L0.b * L0.b * ne));
+  if (h->nlev > 1 && !h->lev[1].Blin)
+    DG_CUDA(h, cudaMalloc((void**)&h->lev[1].Blin, sizeof(double) * (size_t)h->lev[1].b * h->lev[1].b * 7 * ne));
+  if (!h->linpart_ready) {
+    if ((rc = probe_linear_part(h, st))) return rc;
+    h->linpart_ready = true;
+  }
+  if (precision == DG_PRECOND_FP64) {
+    for (int l = 0; l < h->nlev; ++l) {
+      Level& L = h->lev[l];
+      const size_t bb = (size_t)L.b * L.b;
+      if (!L.Dblk) DG_CUDA(h, cudaMalloc((void**)&L.Dblk, sizeof(double) * bb * ne));
+      if (!L.Dinv) DG_CUDA(h, cudaMalloc((void**)&L.Dinv, sizeof(double) * bb * ne));
+      if (l >= 1 && !L.Bsr) DG_CUDA(h, cudaMalloc((void**)&L.Bsr, sizeof(double) * bb * 7 * ne));
+      if (!L.perm) DG_CUDA(h, cudaMalloc((void**)&L.perm, sizeof(int) * (size_t)ne * L.b));
+    }
+    AsmArgs<double> a;
+    a.M = mesh_dev(h);
+    a.T = h->tab;
+    a.Bvol = h->tab.Bvol; a.wvol = h->tab.wvol; a.B2 = h->tab.B2; a.W2 = h->tab.W2; a.pv = h->tab.pv;
+    a.Dcol_val = h->tab.Dcol_val;
+    a.ubar = h->ubar;
+    a.dFlux = h->dFlux;
+    a.Dlin = L0.Dlin;
+    a.D = L0.Dblk;
+    a.Blin = h->nlev > 1 ? h->lev[1].Blin : nullptr;
+    a.Bsr = h->nlev > 1 ? h->lev[1].Bsr : nullptr;
+    a.nb1 = h->nlev > 1 ? h->lev[1].nb : 0;
+    a.inv_gdt = h->inv_gdt;
+    double* Dl[DG_MAX_LEVELS];
+    double* Bl[DG_MAX_LEVELS];
+    for (int l = 0; l < h->nlev; ++l) { Dl[l] = h->lev[l].Dblk; Bl[l] = h->lev[l].Bsr; }
+    if ((rc = assemble_levels<double>(h, a, Dl, Bl, st))) return rc;
+    for (int l = 0; l < h->nlev; ++l) {
+      Level& L = h->lev[l];
+      if ((rc = factor_blocks<double>(h, ne, L.b, L.Dblk, L.Dinv, L.perm, st))) return rc;
+    }
+  } else {
+    if ((rc = alloc_fp32_levels(h))) return rc;
+    if ((rc = prepare_lin_fp32(h, st))) return rc;
+    AsmArgs<float> a;
+    const TablesF& F = h->tabf;
+    a.M = mesh_dev(h);
+    a.T = h->tab;
+    a.Bvol = F.Bvol; a.wvol = F.wvol; a.B2 = F.B2; a.W2 = F.W2; a.pv = F.pv; a.Dcol_val = F.Dcol_val;
+    a.ubar = h->ubar_f;
+    a.dFlux = h->dFlux_f;
+    a.Dlin = L0.Dlin;
+    a.D = L0.LUf;
+    a.Blin = h->nlev > 1 ? h->lev[1].Blin : nullptr;
+    a.Bsr = h->nlev > 1 ? h->lev[1].Bsrf : nullptr;
+    a.nb1 = h->nlev > 1 ? h->lev[1].nb : 0;
+    a.inv_gdt = h->inv_gdt;
+    float* Dl[DG_MAX_LEVELS];
+    float* Bl[DG_MAX_LEVELS];
+    for (int l = 0; l < h->nlev; ++l) { Dl[l] = h->lev[l].LUf; Bl[l] = h->lev[l].Bsrf; }
+    if ((rc = assemble_levels<float>(h, a, Dl, Bl, st))) return rc;
+    for (int l = 0; l < h->nlev; ++l) {
+      Level& L = h->lev[l];
+      if ((rc = factor_blocks<float>(h, ne, L.b, L.LUf, L.LUf, L.perm, st))) return rc;
+    }
   }
   DG_CUDA(h, cudaStreamSynchronize(st));
   unsigned s = 0;

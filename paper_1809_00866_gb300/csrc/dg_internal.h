@@ -49,6 +49,7 @@ struct Tables {
 
 // FP32 copies of the real-valued tables (reduced-precision preconditioner)
 struct TablesF {
+  float* Bvol = nullptr;
   float* L1 = nullptr;
   float* wvol = nullptr;
   float* B2 = nullptr;
@@ -104,6 +105,7 @@ struct Handle {
   float* dFlux_f = nullptr;
   bool lin_f_ready = false;      // the FP32 copies match the current linearisation
   bool asm_f_ready = false;      // the FP32 factors / blocks match the current assembly
+  bool asm64_ready = false;      // the FP64 factors / blocks match the current assembly
   // linearisation cache
   bool linearized = false;
   bool assembled = false;
@@ -205,7 +207,8 @@ int vec_norm2(Handle* h, const double* x, long long n, double* dev_out, cudaStre
 int launch_axpby(Handle* h, long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 
 // assembly (dg_assemble.cu)
-int assemble_all(Handle* h, cudaStream_t st);
+int assemble_all(Handle* h, int precision, cudaStream_t st);
+int prepare_lin_fp32(Handle* h, cudaStream_t st);
 int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st);  // y = G_lvl x
 
 }  // namespace dg

@@ -446,17 +446,24 @@ static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_
 // ------------------------------------------------------ FP32 preconditioner cycle
 // FP32 copies of the linearisation cache (for the FP32 operator) and of the LU factors
 // and block-sparse coarse operators; refreshed after every linearisation / assembly.
+int prepare_lin_fp32(Handle* h, cudaStream_t st) {
+  if (h->lin_f_ready) return DG_OK;
+  const int ne = h->ne;
+  const long long nu = (long long)ne * 3 * h->tab.nq, nf = (long long)3 * ne * h->tab.nqf * 32;
+  convert_kernel<double, float><<<grid_for(h, nu / 256 + 1), 256, 0, st>>>(nu, h->ubar, h->ubar_f);
+  DG_LAUNCH_CHECK(h);
+  convert_kernel<double, float><<<grid_for(h, nf / 256 + 1), 256, 0, st>>>(nf, h->dFlux, h->dFlux_f);
+  DG_LAUNCH_CHECK(h);
+  h->lin_f_ready = true;
+  return DG_OK;
+}
+
 static int prepare_fp32(Handle* h, cudaStream_t st) {
   const int ne = h->ne;
-  if (!h->lin_f_ready) {
-    const long long nu = (long long)ne * 3 * h->tab.nq, nf = (long long)3 * ne * h->tab.nqf * 32;
-    convert_kernel<double, float><<<grid_for(h, nu / 256 + 1), 256, 0, st>>>(nu, h->ubar, h->ubar_f);
-    DG_LAUNCH_CHECK(h);
-    convert_kernel<double, float><<<grid_for(h, nf / 256 + 1), 256, 0, st>>>(nf, h->dFlux, h->dFlux_f);
-    DG_LAUNCH_CHECK(h);
-    h->lin_f_ready = true;
-  }
+  int rc;
+  if ((rc = prepare_lin_fp32(h, st))) return rc;
   if (!h->asm_f_ready) {
+    if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "no assembled preconditioner");
     for (int l = 0; l < h->nlev; ++l) {
       Level& L = h->lev[l];
       const long long nbb = (long long)ne * L.b * L.b;
@@ -566,6 +573,8 @@ static int apply_prec(Handle* h, const dg_solve_opts& o, const double* v, double
     DG_CUDA(h, cudaMemcpyAsync(z, v, sizeof(double) * h->lev[0].n, cudaMemcpyDeviceToDevice, st));
     return DG_OK;
   }
+  if (o.precision == DG_PRECOND_FP64 && !h->asm64_ready)
+    return fail(h, DG_ERR_STATE, "the FP64 preconditioner needs an FP64 assembly");
   if (o.precond == DG_PREC_VCYCLE) {
     if (o.precision == DG_PRECOND_FP32) return vcycle_fp32(h, o, v, z, st);
     return mg_v(h, 0, v, z, true, o, st);
@@ -744,7 +753,7 @@ int block_jacobi_smooth(dg_handle* hh, int lvl, const double* g, double* x, int 
   if (!h) return DG_ERR_ARG;
   if (lvl < 0 || lvl >= h->nlev || !g || !x || g == x) return fail(h, DG_ERR_ARG, "bad level or pointer");
   if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0)) return fail(h, DG_ERR_ARG, "bad sweeps or omega");
-  if (!h->assembled) return fail(h, DG_ERR_STATE, "block_jacobi_smooth needs dg_assemble first");
+  if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "block_jacobi_smooth needs an FP64 dg_assemble first");
   return jacobi_sweeps(h, lvl, g, x, sweeps, omega, false, as_stream(stream));
 }
 
@@ -752,7 +761,7 @@ int bsr_spmv(dg_handle* hh, int lvl, double alpha, const double* x, double beta,
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (lvl < 1 || lvl >= h->nlev || !x || !y || x == y) return fail(h, DG_ERR_ARG, "bad level or pointer");
-  if (!h->assembled) return fail(h, DG_ERR_STATE, "bsr_spmv needs dg_assemble first");
+  if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "bsr_spmv needs an FP64 dg_assemble first");
   return run_bsr(h, lvl, alpha, x, beta, y, as_stream(stream));
 }
 
@@ -764,6 +773,7 @@ int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* o
   if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
   if (!h->assembled) return fail(h, DG_ERR_STATE, "pmg_vcycle needs dg_assemble first");
   if (opts->precision == DG_PRECOND_FP32) return vcycle_fp32(h, *opts, g, x, as_stream(stream));
+  if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "the FP64 cycle needs an FP64 assembly");
   return mg_v(h, 0, g, x, true, *opts, as_stream(stream));
 }
 

@@ -223,3 +223,21 @@ def test_fp32_preconditioner_reaches_fp64_accuracy():
     a = SV.remove_mean_pressure(host(x32).reshape(-1), m.ne, m.nb, vol)
     b = SV.remove_mean_pressure(host(x64).reshape(-1), m.ne, m.nb, vol)
     assert rel(a, b) < 1e-8
+
+
+@pytest.mark.parametrize("name,levels", [("u3", [2, 1]), ("box233", [4, 2, 1])])
+def test_fp32_assembly(name, levels):
+    # assembly in FP32 (state blocks, inherited coarse blocks, LU factors): the cycle built on it
+    # stays within the FP32 bound of the FP64 cycle; the FP64 cycle then refuses to run
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = -O.residual(m, w).reshape(-1)
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g), 2, 2, 2, 0.7)
+    dg.dg_assemble(precision=P.DG_PRECOND_FP32)
+    x = dg.empty()
+    gd = dev(g.reshape(x.shape))
+    dg.pmg_vcycle(gd, x, P.solve_opts(omega=0.7, precision=P.DG_PRECOND_FP32))
+    assert rel(host(x).reshape(-1), ref) < 1e-5
+    with pytest.raises(P.DgError) as e:
+        dg.pmg_vcycle(gd, x, P.solve_opts(omega=0.7))
+    assert e.value.code == P.DG_ERR_STATE
