@@ -235,6 +235,7 @@ def run_ours(args):
             phases.append(e)
         log["its"].append(info.its)
         log["relres"].append(info.true_relres)
+        log.setdefault("fallback_at", []).append(info.fallback_at)
 
     def run_form(opts):
         dg.dg_project_tgv(w)
@@ -266,14 +267,55 @@ def run_ours(args):
         breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
                      for i, nm in enumerate(names)}
         return {"s_per_stage": t_total / (args.steps * world), "t_total": t_total, "breakdown_s": breakdown,
-                "fgmres_its": log["its"], "true_relres": log["relres"],
+                "fgmres_its": log["its"], "true_relres": log["relres"], "fallback_at": log.get("fallback_at"),
                 "operator_applications": (a1 - a0) / max(1, args.steps),
                 "gpu_launches": (l1 - l0) // max(1, args.steps)}
+
+    # --- learned coarse correction: trained here (untimed setup) by the library's BF16 kernels on
+    # the coarse right-hand sides that the chosen cycle produces in the stages of the first states
+    learned_opts, learned_setup = None, None
+    if args.learned:
+        import paper_1809_00866_gb300.learned as Lrn
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dg.dg_project_tgv(w)
+        states = [w.clone()]
+        for _ in range(3):
+            stage(w, chosen_opts, {"its": [], "relres": []})
+            states.append(w.clone())
+        D = Lrn.collect_rhs(dg, states, inv, chosen_opts, per_state=40)
+        torch.cuda.synchronize()
+        t_collect = time.perf_counter() - t0
+        dg.dg_set_linearization(states[-1], inv)
+        dg.dg_assemble()
+        theta, rep = Lrn.train_residual(dg, D, steps=args.learn_steps, lr=1e-3, seed=0)
+        # coarse-level quality on the last state: the network vs the block-Jacobi sweeps it replaces
+        r_net = Lrn.residual_ratio(dg, D[-8:])
+        lc = len(levels) - 1
+        yj, rj = dg.empty(lc), dg.empty(lc)
+        r_jac = []
+        for d in D[-8:]:
+            yj.zero_()
+            dg.block_jacobi_smooth(lc, d, yj, max(1, coarse), args.omega)
+            rj.copy_(d)
+            dg.bsr_spmv(lc, -1.0, yj, 1.0, rj)
+            r_jac.append(float(rj.norm().item()) / float(d.norm().item()))
+        learned_setup = {"collect_s": t_collect, "train_s": rep["train_s"], "train_steps": rep["steps"],
+                         "coarse_vectors": rep["vectors"],
+                         "coarse_residual_ratio": {"network": r_net,
+                                                   "block_jacobi_%d_sweeps" % max(1, coarse): statistics.mean(r_jac)}}
+        learned_opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=pre,
+                                    post_sweeps=post, coarse_sweeps=coarse, omega=args.omega, smoother=smoother,
+                                    precision=chosen_prec, coarse_solver=P.DG_COARSE_LEARNED, fallback_its=5,
+                                    fallback_rho=0.8)
+        if args.coarse == "learned":
+            chosen_opts = learned_opts
 
     clk = Clocks(local)
     clk.start()
     plain = run_form(plain_opts)
     chosen = run_form(chosen_opts)
+    learned = run_form(learned_opts) if (learned_opts is not None and args.coarse != "learned") else None
     clocks = clk.stop()
 
     # error of the chosen form against the plain FP64 form, first stage from the TGV field
@@ -379,6 +421,17 @@ def run_ours(args):
             "chosen_vs_plain": {"speedup": plain["s_per_stage"] / chosen["s_per_stage"],
                                 "first_stage_solution_rel_diff": chosen_err},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"]}
+    if learned_setup is not None:
+        lf = chosen if args.coarse == "learned" else learned
+        line["learned_form"] = dict(learned_setup, **{
+            "cycle": "the chosen cycle with its coarsest (P1) solve replaced by the BF16 network followed by "
+                     "%d block-Jacobi sweeps; fallback to the plain coarse solve if the residual estimate is "
+                     "above 0.8^its after 5 iterations" % coarse,
+            "s_per_stage": lf["s_per_stage"], "fgmres_its": lf["fgmres_its"], "true_relres": lf["true_relres"],
+            "fallback_at": lf["fallback_at"],
+            "vs_plain_fp64": plain["s_per_stage"] / lf["s_per_stage"],
+            "vs_precision_form_without_network": (chosen["s_per_stage"] / lf["s_per_stage"])
+            if args.coarse != "learned" else None})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_app, _ = oracle_sample(cfg)
         line["cpu_baseline"] = {"value": t_app * apps_per_stage, "unit": "s/stage", "cores": 1, "kind": "oracle",
@@ -407,6 +460,10 @@ def main():
     ap.add_argument("--sweeps", default="2,2,2", help="pre,post,coarse smoothing iterations")
     ap.add_argument("--form", choices=["fp64", "fp32"], default="fp32", help="precision of the chosen form's cycle")
     ap.add_argument("--omega", type=float, default=0.7, help="block-Jacobi damping of the chosen form")
+    ap.add_argument("--coarse", choices=["smoother", "learned"], default="smoother",
+                    help="coarsest-level solve of the chosen form (the learned form is also measured separately)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip training the coarse network")
+    ap.add_argument("--learn-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -50,6 +50,7 @@ extern "C" {
 /* Status bits reported by dg_get_status. */
 #define DG_STATUS_RIEMANN 1u
 #define DG_STATUS_NONFINITE 2u
+#define DG_STATUS_WAIT 4u       /* a bounded wait inside a kernel gave up (its work was skipped) */
 
 #define DG_JVP_TANGENT 0 /* exact Jacobian action, Eqs. (jacTrilFnotNU), (jacTrilnu) */
 #define DG_JVP_FD 1      /* finite-difference action, Eqs. (matrix-free), (epsdef) */
@@ -86,6 +87,16 @@ typedef struct dg_handle dg_handle;
 #define DG_PRECOND_FP64 0
 #define DG_PRECOND_FP32 1 /* block-Jacobi smoothing only */
 
+/* Coarsest-level SOLVE of the cycles (Sec. 2.4.3 uses a preconditioned GMRES there). */
+#define DG_COARSE_SMOOTHER 0 /* coarse_sweeps iterations of the level smoother from zero */
+#define DG_COARSE_GMRES 1    /* coarse_sweeps GMRES iterations left-preconditioned by the element
+                                block inverses (restarted every DG_SMOOTH_MAX_ITS), from zero; FP64 cycle */
+#define DG_COARSE_LEARNED 2  /* the learned per-element correction (dg_set_coarse_network) as the
+                                initial iterate, then coarse_sweeps smoother iterations; needs
+                                k = 1 on the coarsest level */
+#define DG_COARSE_LEARNED_ITER 3 /* x = N(g), then coarse_sweeps iterations x <- x + N(g - G x):
+                                    the network as the approximate inverse of a Richardson iteration */
+
 typedef struct dg_solve_opts {
   int restart;       /* Krylov subspace size m before a restart (1..64) */
   int maxit;         /* maximum number of outer iterations */
@@ -102,6 +113,12 @@ typedef struct dg_solve_opts {
   int precision;     /* DG_PRECOND_FP64, or DG_PRECOND_FP32: the preconditioner cycle (its operator
                         products, block-Jacobi factors, block-sparse coarse operators and vectors) in
                         FP32; FGMRES, its products with G and the true residual stay FP64 */
+  int coarse_solver; /* DG_COARSE_SMOOTHER, DG_COARSE_GMRES or DG_COARSE_LEARNED */
+  int fallback_its;  /* DG_COARSE_LEARNED(_ITER) only, > 0: from this outer iteration on, if the residual
+                        estimate is above fallback_rho^its * r0, the rest of the solve uses
+                        DG_COARSE_SMOOTHER. A non-finite Arnoldi vector under the learned
+                        correction always redoes that iteration with DG_COARSE_SMOOTHER and keeps it */
+  double fallback_rho;
 } dg_solve_opts;
 
 typedef struct dg_solve_info {
@@ -111,6 +128,7 @@ typedef struct dg_solve_info {
   double relres_est;    /* recurrence estimate at exit / r0 */
   double true_relres;   /* ||g - G x||_2 / r0 recomputed with the exact G at exit */
   double rho;           /* convergence factor exp(ln(true_relres)/its), Appendix B */
+  int fallback_at;      /* outer iteration at which the learned coarse correction was dropped, or -1 */
 } dg_solve_info;
 
 /* ---------------------------------------------------------------- handle */
@@ -192,6 +210,10 @@ int block_jacobi_smooth(dg_handle* h, int lvl, const double* g, double* x, int s
  * of level lvl >= 1 (diagonal + one block per face). */
 int bsr_spmv(dg_handle* h, int lvl, double alpha, const double* x, double beta, double* y, void* stream);
 
+/* y <- alpha G_lvl^T x + beta y with the transpose of the assembled block-sparse coarse operator
+ * of level lvl >= 1 (used to train the learned coarse correction on the coarse residual). */
+int bsr_spmv_t(dg_handle* h, int lvl, double alpha, const double* x, double beta, double* y, void* stream);
+
 /* x <- MG_V(0, g, 0) (Algorithm 2) with the smoothing options of opts; the
  * coarsest-level SOLVE is opts->coarse_sweeps iterations of the smoother from zero. */
 int pmg_vcycle(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, void* stream);
@@ -203,6 +225,81 @@ int pmg_vcycle(dg_handle* h, const double* g, double* x, const dg_solve_opts* op
  * last iterate) if the tolerance was not met. */
 int fgmres_solve(dg_handle* h, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,
                  void* stream);
+
+/* Solve G_lvl x = g on a coarse level lvl >= 1 with its assembled block-sparse operator by
+ * GMRES(DG_SMOOTH_MAX_ITS) left-preconditioned by the element block inverses, restarted,
+ * until ||g - G x||_2 <= rtol ||g - G x0||_2 or maxit iterations (the coarse solver of Sec.
+ * 2.4.3 run to a tolerance). x0 = 0 when x0_is_zero. FP64; needs an FP64 dg_assemble.
+ * Synchronises once per restart. info (may be NULL): its, r0, true_relres, status. */
+int pmg_level_solve(dg_handle* h, int lvl, const double* g, double* x, double rtol, int maxit, int x0_is_zero,
+                    dg_solve_info* info, void* stream);
+
+/* x <- x - (c.x / c.c) c on level lvl, with c the constant-pressure vector (coefficient
+ * sqrt|K_e| on the pressure mode 0 of every element, zero elsewhere). On a periodic box c spans
+ * the null space of G (a constant pressure has no gradient and no jump) and, read as test-function
+ * integrals, its left null space (the continuity residuals integrate to zero), so this projection
+ * makes a right-hand side consistent and removes the arbitrary constant from a solution. */
+int pmg_project_pressure(dg_handle* h, int lvl, double* x, void* stream);
+
+/* --------------------------------------------------- learned coarse correction
+ * The paper has no learned component. These calls add a per-element network that
+ * stands in for the coarsest (P1) SOLVE of the cycles:
+ *   x_e = s_e * N(X_e),  X_e = F_e / s_e,  s_e = ||F_e||_2  (x_e = 0 where s_e = 0),
+ * F_e = the coarsest-level right-hand side of element e followed by that of its six face
+ * neighbours (order -x, +x, -y, +y, -z, +z), 7 x 4 variables x 4 modes = 112 values;
+ * N(X) = W3 gelu(W2 gelu(W1 X + b1) + b2) + b3 with gelu(t) = t (1 + erf(t/sqrt 2))/2.
+ * Parameters: one FP32 vector theta of DG_MLP_NPARAM entries, in the order W1 [128][112],
+ * b1 [128], W2 [128][128], b2 [128], W3 [16][128], b3 [16] (row-major, [out][in]).
+ * Every evaluation uses BF16 weights and layer inputs (round to nearest even) on the tensor
+ * cores with FP32 accumulation; biases and activations are FP32. */
+#define DG_MLP_IN 112
+#define DG_MLP_HIDDEN 128
+#define DG_MLP_OUT 16
+#define DG_MLP_NPARAM 33040
+
+/* Bytes of the device workspace that dg_mlp_forward / dg_mlp_grad need for `rows` rows. */
+long long dg_mlp_workspace_bytes(long long rows);
+
+/* Y [n][16] <- N(X [n][112]) (features used as given). theta, X, Y, ws: device pointers, ws of
+ * dg_mlp_workspace_bytes(n) bytes, 16-byte aligned. */
+int dg_mlp_forward(const float* theta, const float* X, long long n, float* Y, void* ws, void* stream);
+
+/* Loss L = (1/B) sum_s ||N(X_r(s)) - T_r(s)||_2^2 over a batch of B rows and its gradient
+ * grad [DG_MLP_NPARAM] = dL/dtheta (BF16 operands, FP32 accumulation, fixed reduction order).
+ * Rows: seed < 0: r(s) = s (B <= npairs); seed >= 0: r(s) drawn uniformly from [0, npairs)
+ * by a counter-based hash of (seed, step, s). X [npairs][112], T [npairs][16]. loss: device
+ * scalar (may be NULL). ws of dg_mlp_workspace_bytes(B) bytes. */
+int dg_mlp_grad(const float* theta, const float* X, const float* T, long long npairs, int batch, long long seed,
+                long long step, float* grad, float* loss, void* ws, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) on theta with moments m, v (all DG_MLP_NPARAM FP32,
+ * device): t >= 1 is the step number used in the bias corrections. */
+int dg_mlp_adam(float* theta, const float* grad, float* m, float* v, long long t, double lr, double beta1,
+                double beta2, double eps, void* stream);
+
+/* Set (copy, rounded to BF16) the network of DG_COARSE_LEARNED from device theta; NULL unsets it. */
+int dg_set_coarse_network(dg_handle* h, const float* theta, void* stream);
+
+/* x <- s_e N(X_e(d)) (accumulate = 0) or x + s_e N(X_e(d)) on the coarsest level (FP64 vectors;
+ * the network of dg_set_coarse_network). */
+int dg_coarse_apply(dg_handle* h, const double* d, double* x, int accumulate, void* stream);
+
+/* Training pairs of the coarsest level from a right-hand side d and a coarsest-level vector x:
+ * X [ne][112] the normalised features of d, s [ne] their norms and T [ne][16] = x_e / s_e +
+ * s_e q_e (FP32, device; q may be NULL = 0; rows with s_e = 0 are zero). Needs k = 1 there.
+ *  - supervised targets: x = the solution of G x = d, q = NULL;
+ *  - residual targets: x = s N(X) (dg_coarse_apply) and q = G^T (d - G x) (bsr_spmv_t): then the
+ *    gradient of the squared error ||N(X) - T||^2 with respect to N(X) is the gradient of the
+ *    coarse residual ||d - G x||^2 (times a constant), so dg_mlp_grad trains N as a local
+ *    approximate inverse of the coarse operator. */
+int dg_coarse_pairs(dg_handle* h, const double* d, const double* x, const double* q, float* X, float* T, float* s,
+                    void* stream);
+
+/* Record the right-hand sides that the cycles pass to the coarsest-level SOLVE: each one
+ * is copied (as FP64) into buf [capacity][n_coarsest] in call order until capacity is
+ * reached; buf = NULL stops recording. dg_recorded reads how many were stored. */
+int dg_record_coarse(dg_handle* h, double* buf, int capacity);
+int dg_recorded(const dg_handle* h, int* count);
 
 /* ------------------------------------------------- residual without allocation
  * The paper has no counterpart of this call; it serves callers that must not

@@ -30,13 +30,26 @@ DG_SMOOTH_JACOBI = 0
 DG_SMOOTH_GMRES = 1
 DG_PRECOND_FP64 = 0
 DG_PRECOND_FP32 = 1
+DG_COARSE_SMOOTHER = 0
+DG_COARSE_GMRES = 1
+DG_COARSE_LEARNED = 2
+DG_COARSE_LEARNED_ITER = 3
+DG_STATUS_WAIT = 4
 DG_MAX_LEVELS = 4
+DG_SMOOTH_MAX_ITS = 32
+DG_MLP_IN = 112
+DG_MLP_HIDDEN = 128
+DG_MLP_OUT = 16
+DG_MLP_NPARAM = 33040
 
 # Every exported symbol of include/dgpmg.h
 EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_status", "dg_project_tgv",
            "dg_residual", "dg_set_linearization", "dg_jvp", "dg_assemble", "pmg_restrict", "pmg_prolong",
            "block_jacobi_smooth", "bsr_spmv", "pmg_vcycle", "fgmres_solve", "dg_counters", "dg_profile",
-           "dg_profile_read", "dg_residual_noalloc", "dg_assemble_precision")
+           "dg_profile_read", "dg_residual_noalloc", "dg_assemble_precision", "pmg_level_solve",
+           "dg_mlp_workspace_bytes", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_adam", "dg_set_coarse_network",
+           "dg_coarse_pairs", "dg_record_coarse", "dg_recorded", "pmg_project_pressure",
+           "bsr_spmv_t", "dg_coarse_apply")
 DG_PROF_N = 6
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32")
 
@@ -54,12 +67,14 @@ class DgSolveOpts(ctypes.Structure):
                 ("fixed_its", ctypes.c_int), ("precond", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("omega", ctypes.c_double),
                 ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("fallback_its", ctypes.c_int),
+                ("fallback_rho", ctypes.c_double)]
 
 
 class DgSolveInfo(ctypes.Structure):
     _fields_ = [("its", ctypes.c_int), ("status", ctypes.c_int), ("r0", ctypes.c_double),
-                ("relres_est", ctypes.c_double), ("true_relres", ctypes.c_double), ("rho", ctypes.c_double)]
+                ("relres_est", ctypes.c_double), ("true_relres", ctypes.c_double), ("rho", ctypes.c_double),
+                ("fallback_at", ctypes.c_int)]
 
 
 _lib = None
@@ -94,12 +109,26 @@ def load(path=None):
     L.fgmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(DgSolveOpts), ctypes.POINTER(DgSolveInfo), vp]
     L.dg_residual_noalloc.argtypes = [vp, vp, vp, vp]
     L.dg_assemble_precision.argtypes = [vp, i, vp]
+    ll, f32p = ctypes.c_longlong, ctypes.c_void_p
+    L.pmg_level_solve.argtypes = [vp, i, vp, vp, d, i, i, ctypes.POINTER(DgSolveInfo), vp]
+    L.dg_mlp_workspace_bytes.argtypes = [ll]
+    L.dg_mlp_forward.argtypes = [vp, vp, ll, vp, vp, vp]
+    L.dg_mlp_grad.argtypes = [vp, vp, vp, ll, i, ll, ll, vp, vp, vp, vp]
+    L.dg_mlp_adam.argtypes = [vp, vp, vp, vp, ll, d, d, d, d, vp]
+    L.dg_set_coarse_network.argtypes = [vp, vp, vp]
+    L.dg_coarse_pairs.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.bsr_spmv_t.argtypes = [vp, i, d, vp, d, vp, vp]
+    L.dg_coarse_apply.argtypes = [vp, vp, vp, i, vp]
+    L.dg_record_coarse.argtypes = [vp, vp, i]
+    L.dg_recorded.argtypes = [vp, ctypes.POINTER(i)]
+    L.pmg_project_pressure.argtypes = [vp, i, vp, vp]
     L.dg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.dg_profile.argtypes = [vp, i]
     L.dg_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTS:
         if name != "dg_last_error":
             getattr(L, name).restype = ctypes.c_int
+    L.dg_mlp_workspace_bytes.restype = ctypes.c_longlong
     _lib = L
     return L
 
@@ -112,9 +141,67 @@ class DgError(RuntimeError):
 
 def solve_opts(restart=30, maxit=200, rtol=1e-8, fixed_its=0, precond=DG_PREC_VCYCLE, pre_sweeps=2,
                post_sweeps=2, coarse_sweeps=2, omega=1.0, jvp_mode=DG_JVP_TANGENT, x0_is_zero=1,
-               smoother=DG_SMOOTH_JACOBI, precision=DG_PRECOND_FP64):
+               smoother=DG_SMOOTH_JACOBI, precision=DG_PRECOND_FP64, coarse_solver=DG_COARSE_SMOOTHER,
+               fallback_its=0, fallback_rho=0.9):
     return DgSolveOpts(restart, maxit, rtol, fixed_its, precond, pre_sweeps, post_sweeps, coarse_sweeps, omega,
-                       jvp_mode, x0_is_zero, smoother, precision)
+                       jvp_mode, x0_is_zero, smoother, precision, coarse_solver, fallback_its, fallback_rho)
+
+
+def _tptr(t, dtype, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous %s CUDA tensor" % dtype)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d entries, got %d" % (numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _mchk(rc):
+    if rc != DG_OK:
+        raise DgError(rc, load().dg_last_error(None).decode())
+
+
+def _cur_stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dg_mlp_workspace_bytes(rows):
+    return int(load().dg_mlp_workspace_bytes(int(rows)))
+
+
+def mlp_workspace(rows):
+    """A device workspace (uint8 tensor) for dg_mlp_forward / dg_mlp_grad on `rows` rows."""
+    import torch
+    return torch.empty(dg_mlp_workspace_bytes(rows), dtype=torch.uint8, device="cuda")
+
+
+def dg_mlp_forward(theta, X, Y, ws=None, stream=None):
+    import torch
+    n = X.shape[0]
+    ws = mlp_workspace(n) if ws is None else ws
+    _mchk(load().dg_mlp_forward(_tptr(theta, torch.float32, DG_MLP_NPARAM), _tptr(X, torch.float32, n * DG_MLP_IN),
+                                n, _tptr(Y, torch.float32, n * DG_MLP_OUT), _tptr(ws, torch.uint8),
+                                _cur_stream(stream)))
+
+
+def dg_mlp_grad(theta, X, T, batch, grad, loss=None, seed=-1, step=0, ws=None, stream=None):
+    import torch
+    npairs = X.shape[0]
+    ws = mlp_workspace(batch) if ws is None else ws
+    lp = _tptr(loss, torch.float32, 1) if loss is not None else None
+    _mchk(load().dg_mlp_grad(_tptr(theta, torch.float32, DG_MLP_NPARAM), _tptr(X, torch.float32, npairs * DG_MLP_IN),
+                             _tptr(T, torch.float32, npairs * DG_MLP_OUT), npairs, int(batch), int(seed), int(step),
+                             _tptr(grad, torch.float32, DG_MLP_NPARAM), lp, _tptr(ws, torch.uint8),
+                             _cur_stream(stream)))
+
+
+def dg_mlp_adam(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    import torch
+    f = lambda a: _tptr(a, torch.float32, DG_MLP_NPARAM)
+    _mchk(load().dg_mlp_adam(f(theta), f(grad), f(m), f(v), int(t), float(lr), float(beta1), float(beta2),
+                             float(eps), _cur_stream(stream)))
 
 
 class DG:
@@ -239,6 +326,58 @@ class DG:
         cnt = (ctypes.c_longlong * DG_PROF_N)()
         self._chk(self._L.dg_profile_read(self.h, ms, cnt))
         return {PROF_NAMES[i]: (ms[i], cnt[i]) for i in range(DG_PROF_N)}
+
+    def pmg_level_solve(self, lvl, g, x, rtol=1e-8, maxit=1000, x0_is_zero=True, stream=None, check=True):
+        info = DgSolveInfo()
+        rc = self._L.pmg_level_solve(self.h, int(lvl), self._ptr(g, lvl), self._ptr(x, lvl), float(rtol), int(maxit),
+                                     1 if x0_is_zero else 0, ctypes.byref(info), self._stream(stream))
+        if check and rc not in (DG_OK, DG_ERR_NOT_CONVERGED):
+            self._chk(rc)
+        return info, rc
+
+    def pmg_project_pressure(self, lvl, x, stream=None):
+        self._chk(self._L.pmg_project_pressure(self.h, int(lvl), self._ptr(x, lvl), self._stream(stream)))
+
+    def dg_set_coarse_network(self, theta, stream=None):
+        import torch
+        p = None if theta is None else _tptr(theta, torch.float32, DG_MLP_NPARAM)
+        self._chk(self._L.dg_set_coarse_network(self.h, p, self._stream(stream)))
+
+    def bsr_spmv_t(self, lvl, alpha, x, beta, y, stream=None):
+        self._chk(self._L.bsr_spmv_t(self.h, lvl, float(alpha), self._ptr(x, lvl), float(beta), self._ptr(y, lvl),
+                                     self._stream(stream)))
+
+    def dg_coarse_apply(self, d, x, accumulate=False, stream=None):
+        lc = len(self.levels) - 1
+        self._chk(self._L.dg_coarse_apply(self.h, self._ptr(d, lc), self._ptr(x, lc), 1 if accumulate else 0,
+                                          self._stream(stream)))
+
+    def dg_coarse_pairs(self, d, x, X, T, s, q=None, stream=None):
+        import torch
+        lc = len(self.levels) - 1
+        qp = None if q is None else self._ptr(q, lc)
+        self._chk(self._L.dg_coarse_pairs(self.h, self._ptr(d, lc), self._ptr(x, lc), qp,
+                                          _tptr(X, torch.float32, self.ne * DG_MLP_IN),
+                                          _tptr(T, torch.float32, self.ne * DG_MLP_OUT),
+                                          _tptr(s, torch.float32, self.ne), self._stream(stream)))
+
+    def dg_record_coarse(self, buf, capacity=None):
+        import torch
+        if buf is None:
+            self._chk(self._L.dg_record_coarse(self.h, None, 0))
+            self._rec = None
+            return
+        lc = len(self.levels) - 1
+        cap = buf.numel() // self.n[lc] if capacity is None else int(capacity)
+        if cap < 1 or cap * self.n[lc] > buf.numel():
+            raise ValueError("recording buffer too small")
+        self._chk(self._L.dg_record_coarse(self.h, _tptr(buf, torch.float64), cap))
+        self._rec = buf  # keep it alive while recording
+
+    def dg_recorded(self):
+        c = ctypes.c_int()
+        self._chk(self._L.dg_recorded(self.h, ctypes.byref(c)))
+        return c.value
 
     def fgmres_solve(self, g, x, opts=None, stream=None, check=True):
         o = opts or solve_opts()

@@ -258,6 +258,7 @@ static void free_all(Handle* h) {
   if (h->hcol_host) cudaFreeHost(h->hcol_host);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) F(h->smV[l]);
   F(h->smSmall);
+  F(h->net);
 }
 
 static int create(const dg_params* p, Handle* h) {

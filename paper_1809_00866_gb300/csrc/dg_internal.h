@@ -132,6 +132,13 @@ struct Handle {
   double* smV[DG_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};  // [(its+1)][n_l]
   int smV_its[DG_MAX_LEVELS] = {0, 0, 0, 0};
   double* smSmall = nullptr;  // H, dots, squared norms, beta^2, -y
+  // learned coarse correction: packed BF16 network (dg_set_coarse_network)
+  unsigned char* net = nullptr;
+  bool net_ready = false;
+  // recording of the coarsest-level right-hand sides (dg_record_coarse)
+  double* rec_buf = nullptr;
+  int rec_cap = 0;
+  int rec_count = 0;
   std::string err;
   // instrumentation
   long long launches = 0;
@@ -210,5 +217,11 @@ int launch_axpby(Handle* h, long long n, double a, const double* x, double b, do
 int assemble_all(Handle* h, int precision, cudaStream_t st);
 int prepare_lin_fp32(Handle* h, cudaStream_t st);
 int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st);  // y = G_lvl x
+
+// learned coarse correction (dg_learned.cu): x <- s_e N(X_e) on the coarsest level
+// (accumulate: x <- x + s_e N(X_e))
+template <class R>
+int learned_coarse(Handle* h, const R* g, R* x, bool accumulate, cudaStream_t st);
+int net_bytes();
 
 }  // namespace dg

@@ -156,6 +156,35 @@ __global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr,
   }
 }
 
+// y[e] = alpha * (G^T x)[e] + beta * y[e]: the blocks of column e are B[e][0] and, for each face
+// slot s of e, B[nbr(e,s)][opposite(s)] (the neighbour's block pointing back across that face).
+template <class R>
+__global__ void __launch_bounds__(128) bsr_t_kernel(int ne, int b, const int* nbr, const R* B, R alpha,
+                                                    const R* x, R beta, R* y) {
+  extern __shared__ __align__(16) unsigned char sraw_[];
+  R* sx = reinterpret_cast<R*>(sraw_);  // [7][b]
+  __shared__ int src[7];
+  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+    if (threadIdx.x < 7) src[threadIdx.x] = threadIdx.x == 0 ? e : nbr[e * 6 + threadIdx.x - 1];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 7 * b; t += blockDim.x) {
+      const int s = t / b, c = t - s * b;
+      sx[t] = x[(size_t)src[s] * b + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < b; r += blockDim.x) {
+      R acc = R(0);
+      for (int s = 0; s < 7; ++s) {
+        const int opp = s == 0 ? 0 : ((s & 1) ? s + 1 : s - 1);
+        const R* blk = B + ((size_t)src[s] * 7 + opp) * b * b + (size_t)r * b;  // column r of that block
+        for (int c = 0; c < b; ++c) acc += blk[c] * sx[s * b + c];
+      }
+      y[(size_t)e * b + r] = alpha * acc + (beta == R(0) ? R(0) : beta * y[(size_t)e * b + r]);
+    }
+    __syncthreads();
+  }
+}
+
 // x[e] = x[e] + omega * D[e]^-1 (g[e] - Gx[e]) with the LU factors of D[e]
 // (Gx == nullptr: Gx = 0; x_zero: the old x is 0). One warp per element: the
 // residual is gathered in row order pi into shared memory, then forward substitution
@@ -391,12 +420,91 @@ static int prolong_add(Handle* h, int lvl, const double* xc, double* xf, cudaStr
   return DG_OK;
 }
 
+// a = (c.x)/(c.c) for the constant-pressure vector c (c_e = sqrt|K_e| = sqrt(8) s_e on the
+// pressure mode 0); one block, fixed summation order
+__global__ void __launch_bounds__(1024) pressure_dot_kernel(int ne, int nb, const double* geo, const double* x,
+                                                            double* a) {
+  __shared__ double sn[1024], sd[1024];
+  double num = 0.0, den = 0.0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const double c = sqrt(8.0) * geo[(size_t)e * kGeo + 3];
+    num += c * x[(size_t)e * 4 * nb + 3 * nb];
+    den += c * c;
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sn[threadIdx.x] += sn[threadIdx.x + o];
+      sd[threadIdx.x] += sd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a = sd[0] > 0.0 ? sn[0] / sd[0] : 0.0;
+}
+__global__ void pressure_sub_kernel(int ne, int nb, const double* geo, const double* a, double* x) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ne) x[(size_t)e * 4 * nb + 3 * nb] -= *a * sqrt(8.0) * geo[(size_t)e * kGeo + 3];
+}
+
+// copy the coarsest-level right-hand side into the recording buffer (dg_record_coarse)
+static int record_coarse(Handle* h, const double* g, cudaStream_t st) {
+  if (!h->rec_buf || h->rec_count >= h->rec_cap) return DG_OK;
+  const long long n = h->lev[h->nlev - 1].n;
+  DG_CUDA(h, cudaMemcpyAsync(h->rec_buf + (size_t)h->rec_count * n, g, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                             st));
+  ++h->rec_count;
+  return DG_OK;
+}
+static int record_coarse_f(Handle* h, const float* g, cudaStream_t st) {
+  if (!h->rec_buf || h->rec_count >= h->rec_cap) return DG_OK;
+  const long long n = h->lev[h->nlev - 1].n;
+  convert_kernel<float, double><<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, g, h->rec_buf + (size_t)h->rec_count * n);
+  DG_LAUNCH_CHECK(h);
+  ++h->rec_count;
+  return DG_OK;
+}
+
+// The coarsest-level SOLVE of the cycles (Sec. 2.4.3): smoother iterations from zero, GMRES
+// left-preconditioned by the element block inverses (restarted every DG_SMOOTH_MAX_ITS), or
+// the learned correction followed by smoother iterations. x = 0 on entry is not assumed.
+static int coarse_solve(Handle* h, const double* g, double* x, const dg_solve_opts& o, cudaStream_t st) {
+  const int Lc = h->nlev - 1;
+  int rc;
+  if ((rc = record_coarse(h, g, st))) return rc;
+  if (o.coarse_solver == DG_COARSE_LEARNED) {
+    if ((rc = learned_coarse<double>(h, g, x, false, st))) return rc;
+    return smooth(h, Lc, g, x, o.coarse_sweeps, o.omega, false, o.smoother, st);
+  }
+  if (o.coarse_solver == DG_COARSE_LEARNED_ITER) {  // x <- x + N(g - G x)
+    Level& C = h->lev[Lc];
+    if ((rc = learned_coarse<double>(h, g, x, false, st))) return rc;
+    for (int it = 0; it < o.coarse_sweeps; ++it) {
+      if ((rc = run_bsr(h, Lc, 1.0, x, 0.0, C.t2, st))) return rc;
+      axpby_kernel<double><<<grid_for(h, C.n / 256 + 1), 256, 0, st>>>(C.n, 1.0, g, -1.0, C.t2);
+      DG_LAUNCH_CHECK(h);
+      if ((rc = learned_coarse<double>(h, C.t2, x, true, st))) return rc;
+    }
+    return DG_OK;
+  }
+  if (o.coarse_solver == DG_COARSE_GMRES) {
+    if (o.coarse_sweeps == 0) return gmres_smooth(h, Lc, g, x, 0, true, st);
+    for (int done = 0; done < o.coarse_sweeps; done += DG_SMOOTH_MAX_ITS) {
+      const int c = std::min(DG_SMOOTH_MAX_ITS, o.coarse_sweeps - done);
+      if ((rc = gmres_smooth(h, Lc, g, x, c, done == 0, st))) return rc;
+    }
+    return DG_OK;
+  }
+  return smooth(h, Lc, g, x, o.coarse_sweeps, o.omega, true, o.smoother, st);
+}
+
 // MG_V(l, g, x) of Algorithm 2 (x in/out; x_zero: the incoming x is 0).
 // Level l >= 1 keeps its right-hand side in t0 and its iterate in t1; t2 is scratch.
 static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const dg_solve_opts& o, cudaStream_t st) {
   int rc;
   const int Lc = h->nlev - 1;
-  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, o.smoother, st);
+  if (l == Lc) return coarse_solve(h, g, x, o, st);
   if ((rc = smooth(h, l, g, x, o.pre_sweeps, o.omega, x_zero, o.smoother, st))) return rc;
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
@@ -419,7 +527,7 @@ static int mg_v(Handle* h, int l, const double* g, double* x, bool x_zero, const
 static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_opts& o, cudaStream_t st) {
   int rc;
   const int Lc = h->nlev - 1;
-  if (l == Lc) return smooth(h, l, g, x, o.coarse_sweeps, o.omega, true, o.smoother, st);
+  if (l == Lc) return coarse_solve(h, g, x, o, st);
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
   // g_{l+1} = I g_l; w_{l+1} = MG_full(l+1, g_{l+1}); keep them in the coarse level's t0/t1
@@ -518,7 +626,25 @@ static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const
   int rc;
   const int Lc = h->nlev - 1;
   const float om = (float)o.omega;
-  if (l == Lc) return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, true, st);
+  if (l == Lc) {
+    if ((rc = record_coarse_f(h, g, st))) return rc;
+    if (o.coarse_solver == DG_COARSE_LEARNED) {
+      if ((rc = learned_coarse<float>(h, g, x, false, st))) return rc;
+      return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, false, st);
+    }
+    if (o.coarse_solver == DG_COARSE_LEARNED_ITER) {  // x <- x + N(g - G x)
+      Level& C = h->lev[l];
+      if ((rc = learned_coarse<float>(h, g, x, false, st))) return rc;
+      for (int it = 0; it < o.coarse_sweeps; ++it) {
+        if ((rc = level_matvec_f(h, l, x, C.t2f, st))) return rc;
+        axpby_kernel<float><<<grid_for(h, C.n / 256 + 1), 256, 0, st>>>(C.n, 1.0f, g, -1.0f, C.t2f);
+        DG_LAUNCH_CHECK(h);
+        if ((rc = learned_coarse<float>(h, C.t2f, x, true, st))) return rc;
+      }
+      return DG_OK;
+    }
+    return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, true, st);
+  }
   if ((rc = jacobi_sweeps_f(h, l, g, x, o.pre_sweeps, om, x_zero, st))) return rc;
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
@@ -553,6 +679,10 @@ static int vcycle_fp32(Handle* h, const dg_solve_opts& o, const double* v, doubl
   return DG_OK;
 }
 
+static bool is_learned(int coarse_solver) {
+  return coarse_solver == DG_COARSE_LEARNED || coarse_solver == DG_COARSE_LEARNED_ITER;
+}
+
 static int check_opts(Handle* h, const dg_solve_opts* o) {
   if (!o) return fail(h, DG_ERR_ARG, "null options");
   if (o->pre_sweeps < 0 || o->post_sweeps < 0 || o->coarse_sweeps < 0) return fail(h, DG_ERR_ARG, "negative sweeps");
@@ -562,6 +692,19 @@ static int check_opts(Handle* h, const dg_solve_opts* o) {
     return fail(h, DG_ERR_ARG, "unknown preconditioner precision");
   if (o->precision == DG_PRECOND_FP32 && (o->smoother != DG_SMOOTH_JACOBI || o->precond == DG_PREC_FULLV))
     return fail(h, DG_ERR_ARG, "the FP32 preconditioner supports block-Jacobi smoothing in V-cycles only");
+  if (o->coarse_solver != DG_COARSE_SMOOTHER && o->coarse_solver != DG_COARSE_GMRES &&
+      o->coarse_solver != DG_COARSE_LEARNED && o->coarse_solver != DG_COARSE_LEARNED_ITER)
+    return fail(h, DG_ERR_ARG, "unknown coarse solver");
+  const bool learned = o->coarse_solver == DG_COARSE_LEARNED || o->coarse_solver == DG_COARSE_LEARNED_ITER;
+  if (o->coarse_solver == DG_COARSE_GMRES && o->precision != DG_PRECOND_FP64)
+    return fail(h, DG_ERR_ARG, "the GMRES coarse solver runs in the FP64 cycle only");
+  if (learned) {
+    if (h->nlev < 2) return fail(h, DG_ERR_ARG, "the learned coarse correction needs at least two levels");
+    if (h->lev[h->nlev - 1].k != 1) return fail(h, DG_ERR_ARG, "the learned coarse correction needs k = 1 there");
+    if (!h->net_ready) return fail(h, DG_ERR_STATE, "no coarse network set (dg_set_coarse_network)");
+    if (o->fallback_its < 0 || (o->fallback_its > 0 && !(o->fallback_rho > 0.0 && o->fallback_rho < 1.0)))
+      return fail(h, DG_ERR_ARG, "fallback_its >= 0 and fallback_rho in (0, 1) needed");
+  }
   if (o->smoother == DG_SMOOTH_GMRES &&
       (o->pre_sweeps > DG_SMOOTH_MAX_ITS || o->post_sweeps > DG_SMOOTH_MAX_ITS || o->coarse_sweeps > DG_SMOOTH_MAX_ITS))
     return fail(h, DG_ERR_ARG, "GMRES smoother iterations above DG_SMOOTH_MAX_ITS");
@@ -652,6 +795,10 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
   double est = beta0;
   bool converged = beta0 == 0.0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), s(m + 1), y(m);
+  // the preconditioner in use: the learned coarse correction is dropped for the rest of the
+  // solve when it stalls the residual or produces a non-finite vector
+  dg_solve_opts cur = o;
+  int fallback_at = -1;
   while (!converged && its < limit) {
     double beta;
     if ((rc = norm(r, &beta))) return rc;
@@ -666,19 +813,31 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
       double* vj = V + (size_t)j * n;
       double* zj = Z + (size_t)j * n;
       double* w = V + (size_t)(j + 1) * n;
-      if ((rc = apply_prec(h, o, vj, zj, st))) return rc;
-      if ((rc = outer_matvec(h, o, zj, w, st))) return rc;
-      // classical Gram-Schmidt, twice
-      for (int pass = 0; pass < 2; ++pass) {
-        if ((rc = multidot(h, n, j + 1, V, w, h->hcol, st))) return rc;
-        multi_axpy_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, j + 1, V, n, h->hcol, w);
-        DG_LAUNCH_CHECK(h);
-        DG_CUDA(h, cudaMemcpyAsync(h->hcol_host, h->hcol, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
-        DG_CUDA(h, cudaStreamSynchronize(st));
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h->hcol_host[i];
+      double hn = 0.0;
+      for (int attempt = 0;; ++attempt) {
+        if ((rc = apply_prec(h, cur, vj, zj, st))) return rc;
+        if ((rc = outer_matvec(h, o, zj, w, st))) return rc;
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = 0.0;
+        // classical Gram-Schmidt, twice
+        for (int pass = 0; pass < 2; ++pass) {
+          if ((rc = multidot(h, n, j + 1, V, w, h->hcol, st))) return rc;
+          multi_axpy_kernel<<<grid_for(h, n / 256 + 1), 256, 0, st>>>(n, j + 1, V, n, h->hcol, w);
+          DG_LAUNCH_CHECK(h);
+          DG_CUDA(h, cudaMemcpyAsync(h->hcol_host, h->hcol, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+          DG_CUDA(h, cudaStreamSynchronize(st));
+          for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h->hcol_host[i];
+        }
+        if ((rc = norm(w, &hn))) return rc;
+        bool finite = std::isfinite(hn);
+        for (int i = 0; i <= j; ++i) finite = finite && std::isfinite(H[(size_t)i * m + j]);
+        if (finite) break;
+        if (attempt == 0 && is_learned(cur.coarse_solver)) {  // redo with the plain cycle
+          cur.coarse_solver = DG_COARSE_SMOOTHER;
+          fallback_at = its;
+          continue;
+        }
+        return fail(h, DG_ERR_NONFINITE, "non-finite Arnoldi vector");
       }
-      double hn;
-      if ((rc = norm(w, &hn))) return rc;
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0 && (rc = launch_axpby(h, n, 1.0 / hn, w, 0.0, w, st))) return rc;
       for (int i = 0; i < j; ++i) {
@@ -696,6 +855,11 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
       ++its;
       jdone = j + 1;
       est = std::fabs(s[j + 1]);
+      if (is_learned(cur.coarse_solver) && o.fallback_its > 0 && its >= o.fallback_its &&
+          est > std::pow(o.fallback_rho, (double)its) * beta0) {
+        cur.coarse_solver = DG_COARSE_SMOOTHER;
+        fallback_at = its;
+      }
       if (o.fixed_its <= 0 && est <= o.rtol * beta0) break;
       if (hn == 0.0) break;
     }
@@ -723,6 +887,7 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
     if (beta0 == 0.0) info->true_relres = 0.0;
     info->rho = (its > 0 && info->true_relres > 0) ? std::exp(std::log(info->true_relres) / its) : 0.0;
     info->status = (converged || o.fixed_its > 0) ? DG_OK : DG_ERR_NOT_CONVERGED;
+    info->fallback_at = fallback_at;
   }
   if (!converged && o.fixed_its <= 0) return fail(h, DG_ERR_NOT_CONVERGED, "FGMRES did not reach the tolerance");
   return DG_OK;
@@ -765,6 +930,27 @@ int bsr_spmv(dg_handle* hh, int lvl, double alpha, const double* x, double beta,
   return run_bsr(h, lvl, alpha, x, beta, y, as_stream(stream));
 }
 
+int bsr_spmv_t(dg_handle* hh, int lvl, double alpha, const double* x, double beta, double* y, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 1 || lvl >= h->nlev || !x || !y || x == y) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "bsr_spmv_t needs an FP64 dg_assemble first");
+  const Level& L = h->lev[lvl];
+  bsr_t_kernel<double><<<grid_for(h, h->ne), 128, sizeof(double) * 7 * L.b, as_stream(stream)>>>(
+      h->ne, L.b, h->nbr, L.Bsr, alpha, x, beta, y);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+int dg_coarse_apply(dg_handle* hh, const double* d, double* x, int accumulate, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!d || !x || d == x) return fail(h, DG_ERR_ARG, "bad pointer");
+  if (h->nlev < 2 || h->lev[h->nlev - 1].k != 1)
+    return fail(h, DG_ERR_ARG, "the learned coarse correction needs at least two levels and k = 1 on the last");
+  return learned_coarse<double>(h, d, x, accumulate != 0, as_stream(stream));
+}
+
 int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
@@ -775,6 +961,72 @@ int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* o
   if (opts->precision == DG_PRECOND_FP32) return vcycle_fp32(h, *opts, g, x, as_stream(stream));
   if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "the FP64 cycle needs an FP64 assembly");
   return mg_v(h, 0, g, x, true, *opts, as_stream(stream));
+}
+
+int pmg_project_pressure(dg_handle* hh, int lvl, double* x, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 0 || lvl >= h->nlev || !x) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  cudaStream_t st = as_stream(stream);
+  const Level& L = h->lev[lvl];
+  pressure_dot_kernel<<<1, 1024, 0, st>>>(h->ne, L.nb, h->geo, x, h->red_out);
+  DG_LAUNCH_CHECK(h);
+  pressure_sub_kernel<<<(h->ne + 255) / 256, 256, 0, st>>>(h->ne, L.nb, h->geo, h->red_out, x);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+int pmg_level_solve(dg_handle* hh, int lvl, const double* g, double* x, double rtol, int maxit, int x0_is_zero,
+                    dg_solve_info* info, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (lvl < 1 || lvl >= h->nlev || !g || !x || g == x) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (!(rtol > 0.0) || maxit < 1) return fail(h, DG_ERR_ARG, "bad rtol or maxit");
+  if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "pmg_level_solve needs an FP64 dg_assemble first");
+  cudaStream_t st = as_stream(stream);
+  Level& L = h->lev[lvl];
+  int rc;
+  // r = g - G x into t1 (t2 is the smoother's scratch); returns ||r||
+  auto resnorm = [&](bool zero, double* out) -> int {
+    if (zero) {
+      if (int c = vec_norm2(h, g, L.n, h->red_out, st)) return c;
+    } else {
+      if (int c = run_bsr(h, lvl, 1.0, x, 0.0, L.t1, st)) return c;
+      axpby_kernel<double><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0, g, -1.0, L.t1);
+      DG_LAUNCH_CHECK(h);
+      if (int c = vec_norm2(h, L.t1, L.n, h->red_out, st)) return c;
+    }
+    double v = 0.0;
+    DG_CUDA(h, cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(h, cudaStreamSynchronize(st));
+    *out = std::sqrt(v);
+    return DG_OK;
+  };
+  double r0 = 0.0, rn = 0.0;
+  if ((rc = resnorm(x0_is_zero != 0, &r0))) return rc;
+  if (x0_is_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
+  int its = 0;
+  bool conv = r0 == 0.0;
+  rn = r0;
+  while (!conv && its < maxit) {
+    const int c = std::min(DG_SMOOTH_MAX_ITS, maxit - its);
+    if ((rc = gmres_smooth(h, lvl, g, x, c, false, st))) return rc;
+    its += c;
+    if ((rc = resnorm(false, &rn))) return rc;
+    if (!std::isfinite(rn)) return fail(h, DG_ERR_NONFINITE, "non-finite residual in pmg_level_solve");
+    conv = rn <= rtol * r0;
+  }
+  if (info) {
+    *info = dg_solve_info{};
+    info->its = its;
+    info->r0 = r0;
+    info->true_relres = r0 > 0.0 ? rn / r0 : 0.0;
+    info->relres_est = info->true_relres;
+    info->rho = (its > 0 && info->true_relres > 0) ? std::exp(std::log(info->true_relres) / its) : 0.0;
+    info->status = conv ? DG_OK : DG_ERR_NOT_CONVERGED;
+    info->fallback_at = -1;
+  }
+  return conv ? DG_OK : fail(h, DG_ERR_NOT_CONVERGED, "pmg_level_solve did not reach the tolerance");
 }
 
 int fgmres_solve(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,

@@ -1,0 +1,88 @@
+"""Small, fixed workloads for profiling the library's kernels (e.g. under Nsight Compute).
+
+    python -m paper_1809_00866_gb300.profile jv [--n 16] [--reps 3]
+        TGV n^3 P4 handle (levels 4-2-1), linearisation at the TGV field, `reps` exact
+        Jacobian actions (face_kernel + vol_kernel per action).
+    python -m paper_1809_00866_gb300.profile stage [--n 16] [--form fp32|fp64] [--learned]
+        one implicit stage to rel-res 1e-8 after two warm-up solves; only the timed FGMRES solve
+        lies between cudaProfilerStart and cudaProfilerStop (ncu --profile-from-start off).
+
+Prints the wall time of the profiled region. Inputs are the synthetic Taylor-Green states.
+"""
+import argparse
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("what", choices=["jv", "stage"])
+    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--form", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--learned", action="store_true", help="train the coarse network first and use it")
+    a = ap.parse_args(argv)
+    import torch
+
+    import synthetic as S
+
+    from . import DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP64, build, solve_opts
+    build()
+    un = S.uniform_nodes(a.n)
+    levels = [4, 2, 1]
+    dg = DG(un, un, un, levels, S.NU_TGV, S.AC_C, S.ETA)
+    inv = 1.0 / S.acoustic_dt(a.n, levels[0])
+    w = dg.empty()
+    dg.dg_project_tgv(w)
+    if a.what == "jv":
+        dg.dg_set_linearization(w, inv)
+        v = torch.from_numpy(S.direction(dg.ne, levels[0], S.SEED_V)).cuda()
+        out = dg.empty()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            dg.dg_jvp(v, out)
+        torch.cuda.synchronize()
+        print("jv: %d actions, %.3f ms each" % (a.reps, 1e3 * (time.perf_counter() - t0) / a.reps))
+        return 0
+    fp32 = a.form == "fp32"
+    o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.7 if fp32 else 1.0,
+                   precision=DG_PRECOND_FP32 if fp32 else DG_PRECOND_FP64)
+    if a.learned:
+        from . import learned as Lrn
+        states = [w.clone()]
+        for _ in range(3):
+            f = dg.empty()
+            dg.dg_residual(states[-1], f)
+            dg.dg_set_linearization(states[-1], inv)
+            dg.dg_assemble()
+            x = dg.empty()
+            dg.fgmres_solve((-f).contiguous(), x, o)
+            states.append((states[-1] + x).contiguous())
+        D = Lrn.collect_rhs(dg, states, inv, o, per_state=40)
+        dg.dg_set_linearization(states[-1], inv)
+        dg.dg_assemble()
+        Lrn.train_residual(dg, D, steps=2000, lr=1e-3, seed=0)
+        o.coarse_solver = DG_COARSE_LEARNED
+    f = dg.empty()
+    dg.dg_residual(w, f)
+    g = (-f).contiguous()
+    dg.dg_set_linearization(w, inv)
+    dg.dg_assemble(precision=o.precision)
+    x = dg.empty()
+    for _ in range(2):
+        dg.fgmres_solve(g, x, o)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    info, rc = dg.fgmres_solve(g, x, o)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    print("stage solve: %d iterations, %.4f s (%.3f ms per iteration), rc %d" % (info.its, t, 1e3 * t / max(1, info.its),
+                                                                               rc))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
