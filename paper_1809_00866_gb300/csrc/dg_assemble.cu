@@ -578,6 +578,7 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
       Level& L = h->lev[l];
       if ((rc = factor_blocks<float>(h, ne, L.b, L.LUf, L.LUf, L.perm, st))) return rc;
     }
+    if ((rc = invert_levels_f32(h, st))) return rc;  // the FP32 smoother applies explicit inverses
   }
   DG_CUDA(h, cudaStreamSynchronize(st));
   unsigned s = 0;

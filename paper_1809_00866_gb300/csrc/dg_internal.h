@@ -74,7 +74,7 @@ struct Level {
   double* t1 = nullptr;
   double* t2 = nullptr;
   // FP32 copies for the reduced-precision preconditioner (allocated on first use)
-  float* LUf = nullptr;      // [ne][b][b]
+  float* LUf = nullptr;      // [ne][b][b] explicit inverses D^-1 (column-major) once assembled
   float* Bsrf = nullptr;     // [ne][7][b][b] (level >= 1)
   float* t0f = nullptr;
   float* t1f = nullptr;
@@ -217,6 +217,14 @@ int launch_axpby(Handle* h, long long n, double a, const double* x, double b, do
 int assemble_all(Handle* h, int precision, cudaStream_t st);
 int prepare_lin_fp32(Handle* h, cudaStream_t st);
 int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st);  // y = G_lvl x
+
+// element-block products streamed through shared memory (dg_blocks.cu). The FP32 cycle keeps
+// explicit inverses in Level::LUf (invert_levels_f32 turns the FP32 LU factors into them).
+int invert_levels_f32(Handle* h, cudaStream_t st);
+int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
+                    cudaStream_t st);  // x <- (x_zero ? 0 : x) + omega D^-1 (g - Gx); Gx may be null
+template <class R>
+int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y, cudaStream_t st);  // -1: n/a
 
 // learned coarse correction (dg_learned.cu): x <- s_e N(X_e) on the coarsest level
 // (accumulate: x <- x + s_e N(X_e))

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dg_async.h"
 #include "dg_internal.h"
 
 namespace dg {
@@ -35,40 +36,8 @@ constexpr int kPBytes = kPB + (2 * kHid + kOut) * 4;
 static_assert(kPW2 % 16 == 0 && kPW3 % 16 == 0 && kPB % 16 == 0 && kPBytes % 16 == 0, "16-byte parts");
 
 constexpr int kWarps = 4, kRows = 16 * kWarps;  // rows (elements or samples) per CTA
-constexpr unsigned kWaitLimit = 1u << 22;        // try_wait polls before a wait gives up
 
 // ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// one bulk copy global -> shared (sizes and both addresses multiples of 16 bytes)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// bounded wait for phase `parity` of the barrier; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
 // D += A B, m16n8k16, A row-major bf16, B column-major bf16, FP32 accumulators
 __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm volatile(

@@ -244,6 +244,8 @@ static int apply_grid(const Handle* h) {
 
 static int run_bsr(Handle* h, int lvl, double alpha, const double* x, double beta, double* y, cudaStream_t st) {
   const Level& L = h->lev[lvl];
+  const int rc = staged_bsr<double>(h, lvl, L.Bsr, alpha, x, beta, y, st);
+  if (rc >= 0) return rc;  // -1: the blocks do not fit the staged kernel
   bsr_kernel<double><<<grid_for(h, h->ne), 128, sizeof(double) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsr, alpha, x, beta, y);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
@@ -587,6 +589,7 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
         DG_LAUNCH_CHECK(h);
       }
     }
+    if (int rc2 = invert_levels_f32(h, st)) return rc2;  // the LU factors (rounded) -> explicit inverses
     h->asm_f_ready = true;
   }
   return DG_OK;
@@ -595,6 +598,8 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
 static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, cudaStream_t st) {
   if (lvl == 0) return op_tangent_f32(h, x, y, st);
   const Level& L = h->lev[lvl];
+  const int rc = staged_bsr<float>(h, lvl, L.Bsrf, 1.0f, x, 0.0f, y, st);
+  if (rc >= 0) return rc;
   bsr_kernel<float><<<grid_for(h, h->ne), 128, sizeof(float) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsrf, 1.0f, x,
                                                                                0.0f, y);
   DG_LAUNCH_CHECK(h);
@@ -604,17 +609,13 @@ static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, cudaStre
 static int jacobi_sweeps_f(Handle* h, int lvl, const float* g, float* x, int sweeps, float omega, bool x_zero,
                            cudaStream_t st) {
   Level& L = h->lev[lvl];
-  const size_t smem = sizeof(float) * L.b * kApplyWarps;
   for (int s = 0; s < sweeps; ++s) {
     const bool zero = x_zero && s == 0;
-    if (!zero) {
-      int rc = level_matvec_f(h, lvl, x, L.t2f, st);
-      if (rc) return rc;
-    }
-    bj_update_kernel<float><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.LUf, L.perm, g,
-                                                                           zero ? nullptr : L.t2f, omega,
-                                                                           zero ? 1 : 0, x);
-    DG_LAUNCH_CHECK(h);
+    int rc;
+    if (!zero && (rc = level_matvec_f(h, lvl, x, L.t2f, st))) return rc;
+    rc = staged_jacobi_f(h, lvl, g, zero ? nullptr : L.t2f, omega, zero, x, st);
+    if (rc < 0) return fail(h, DG_ERR_ARG, "element block too large for the FP32 smoother");
+    if (rc) return rc;
   }
   if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * L.n, st));
   return DG_OK;
