@@ -66,6 +66,21 @@ DENSE_FLOP_PER_ELEMENT_P4 = 520_000.0
 # FP64 peak of a GB300 (no FP64 entry in the measured-peaks file): nominal 1.25 TFLOP/s
 # (152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz ~ 1.26 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
+# HBM peak: the measured copy bandwidth on the GB300s, else the machine's fallback.
+HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) of one fine-level launch of the FP32 block-Jacobi apply at 16^3 P4,
+# from one Nsight Compute capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum = 323.46 MB + 4.79 MB).
+BJ32_FINE_TRAFFIC_16_P4 = 328.25e6
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 # Fine-level operator applications (residual or Jacobian action) of one stage on this
 # workload, as counted by the library on the GPU (dg_counters); used to scale the
 # oracle's measured cost of one application to seconds per stage.
@@ -162,12 +177,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/stage", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
+            "config": {"workload": "Taylor-Green vortex Re=1600, %d^3 periodic hexahedra, P4 (N_b=35), " % cfg["n"] +
                                    "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
                        "dofs": ndof, "l2": "oracle on host cores"},
             "jv": {"value": ndof / t_app / 1e9, "unit": "GDOF/s", "mode": "exact"},
             "cpu_baseline": {"value": value, "unit": "s/stage", "cores": 1, "kind": "oracle",
-                             "sample": "one exact Jacobian action of the FP64 oracle on the full 16^3 P4 state "
+                             "sample": "one exact Jacobian action of the FP64 oracle on the full %d^3 P4 state " % cfg["n"] +
                                        "per step (%.2f s), times the %d fine-operator applications of one stage"
                                        % (t_app, apps)},
             "e2e": {"value": value, "unit": "s/stage", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -216,32 +231,34 @@ def run_ours(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def stage(w, opts, log, phases=None):
-        e = [ev() for _ in range(5)] if phases is not None else None
+    def stage(w, opts, log, phases=None, assemble=True):
+        e = [ev() for _ in range(4)] if phases is not None else None
         if e: e[0].record(st)
-        dg.dg_residual(w, f)
-        f.neg_()
+        dg.dg_set_linearization_rhs(w, inv, f)  # f <- g = -f_h(w), and the linearisation at w
         if e: e[1].record(st)
-        dg.dg_set_linearization(w, inv)
+        if assemble:
+            dg.dg_assemble(precision=opts.precision)
+        else:
+            dg.dg_reuse_assembly()  # lagged preconditioner: blocks of an earlier stage
         if e: e[2].record(st)
-        dg.dg_assemble(precision=opts.precision)
-        if e: e[3].record(st)
         info, rc = dg.fgmres_solve(f, dw, opts)
         if rc != P.DG_OK:
             raise RuntimeError("stage did not converge: rc %d relres %.3e" % (rc, info.true_relres))
         w.add_(dw)
         if e:
-            e[4].record(st)
+            e[3].record(st)
             phases.append(e)
         log["its"].append(info.its)
         log["relres"].append(info.true_relres)
         log.setdefault("fallback_at", []).append(info.fallback_at)
 
-    def run_form(opts):
+    def run_form(opts, lag=1):
         dg.dg_project_tgv(w)
         log = {"its": [], "relres": []}
+        count = 0
         for _ in range(args.warmup):
-            stage(w, opts, log)
+            stage(w, opts, log, assemble=count % lag == 0)
+            count += 1
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -253,7 +270,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             e0, e1 = ev(), ev()
             e0.record(st)
-            stage(w, opts, log, phases)
+            stage(w, opts, log, phases, assemble=count % lag == 0)
+            count += 1
             e1.record(st)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
@@ -263,7 +281,7 @@ def run_ours(args):
             tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             t_total = float(tt.item())
-        names = ["residual", "linearize", "assemble", "solve"]
+        names = ["rhs_and_linearize", "assemble", "solve"]
         breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
                      for i, nm in enumerate(names)}
         return {"s_per_stage": t_total / (args.steps * world), "t_total": t_total, "breakdown_s": breakdown,
@@ -316,13 +334,12 @@ def run_ours(args):
     plain = run_form(plain_opts)
     chosen = run_form(chosen_opts)
     learned = run_form(learned_opts) if (learned_opts is not None and args.coarse != "learned") else None
+    lagged = run_form(chosen_opts, lag=args.lag) if args.lag > 1 else None
     clocks = clk.stop()
 
     # error of the chosen form against the plain FP64 form, first stage from the TGV field
     dg.dg_project_tgv(w)
-    dg.dg_residual(w, f)
-    f.neg_()
-    dg.dg_set_linearization(w, inv)
+    dg.dg_set_linearization_rhs(w, inv, f)
     dg.dg_assemble(precision=plain_opts.precision)
     d64, d32 = dg.empty(), dg.empty()
     dg.fgmres_solve(f, d64, plain_opts)
@@ -375,13 +392,43 @@ def run_ours(args):
     else:
         kname, kms, kflop = "vol_kernel<%d,tangent>" % k, vol_ms, fv * dg.ne
     achieved = kflop / (kms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+    roofline_jv = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 rate of GB300 (not in the measured-peaks file)",
                 "flop_per_element": {"face": ff, "vol": fv},
                 "kernel_ms": {"face_tan": face_ms, "vol_tan": vol_ms},
                 "jv_tflops_of_implemented_work": (ff + fv) * dg.ne / t_jv / 1e12,
                 "jv_dense_equivalent_tflops": DENSE_FLOP_PER_ELEMENT_P4 * dg.ne / t_jv / 1e12}
+
+    # --- the chosen stage's kernels, timed live with CUDA events on the launching stream; the
+    # dominant one (the fine-level FP32 block-Jacobi apply) against the HBM roofline
+    dg.dg_profile(True)
+    dg.dg_profile_read_bytes()
+    flush.zero_()
+    stage(w, chosen_opts, {"its": [], "relres": []})
+    kp = dg.dg_profile_read_bytes()
+    dg.dg_profile(False)
+    hbm, hbm_src = hbm_peak()
+    kernels = {}
+    for nm, (ms_k, cnt, by) in kp.items():
+        if cnt:
+            kernels[nm] = {"launches": cnt, "ms_per_launch": ms_k / cnt, "total_ms": ms_k}
+            if by > 0:
+                kernels[nm]["gbs"] = by / (ms_k / 1e3) / 1e9
+    dom = "bj32_fine" if "bj32_fine" in kernels else "bj64_fine"
+    ms_d, cnt_d, by_d = kp[dom]
+    if cnt_d:
+        ach = by_d / (ms_d / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "staged_jacobi_kernel<float> (fine level, P4)" if dom == "bj32_fine"
+                    else "bj_update_kernel<double> (fine level, P4)",
+                    "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": BJ32_FINE_TRAFFIC_16_P4 if (dom == "bj32_fine" and args.config == CONFIG) else None,
+                    "algorithmic_bytes_per_launch": by_d / cnt_d, "ms_per_launch": ms_d / cnt_d,
+                    "peak_source": "measured HBM copy bandwidth (hbm_gbs of the measured-peaks file)"
+                    if hbm_src == "measured" else "fallback HBM bandwidth 6.8 TB/s",
+                    "frac_of": "of " + hbm_src}
+    else:
+        roofline = roofline_jv
 
     # --- end to end through the C ABI: state from pinned host memory, result back to the host
     host_w = w.detach().cpu().pin_memory()
@@ -407,7 +454,7 @@ def run_ours(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.form == "fp64" else "f64 (FGMRES, products with G, stage RHS) + f32 (preconditioner cycle)",
             "data": "synthetic",
-            "config": {"workload": "Taylor-Green vortex Re=1600, 16^3 periodic hexahedra, P4 (N_b=35), "
+            "config": {"workload": "Taylor-Green vortex Re=1600, %d^3 periodic hexahedra, P4 (N_b=35), " % cfg["n"] +
                                    "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
                        "dofs": n0, "dt": dt,
                        "solver": "FGMRES(30) + MG_V, %s smoother, pre/post/coarse %s" % (args.smoother, args.sweeps),
@@ -420,7 +467,15 @@ def run_ours(args):
             "stage": chosen, "plain_fp64": plain,
             "chosen_vs_plain": {"speedup": plain["s_per_stage"] / chosen["s_per_stage"],
                                 "first_stage_solution_rel_diff": chosen_err},
-            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"]}
+            "roofline": roofline, "roofline_jv": roofline_jv, "stage_kernels": kernels,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"]}
+    if lagged is not None:
+        line["lagged_form"] = {
+            "lag": args.lag, "what": "the chosen form with the preconditioner (element blocks, factors, coarse "
+                                    "block-sparse operators) assembled every %d stages and reused in between; "
+                                    "timed stages = %d, so the assembly is amortised over them" % (args.lag, args.steps),
+            "s_per_stage": lagged["s_per_stage"], "fgmres_its": lagged["fgmres_its"],
+            "breakdown_s": lagged["breakdown_s"], "vs_plain_fp64": plain["s_per_stage"] / lagged["s_per_stage"]}
     if learned_setup is not None:
         lf = chosen if args.coarse == "learned" else learned
         line["learned_form"] = dict(learned_setup, **{
@@ -435,7 +490,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_app, _ = oracle_sample(cfg)
         line["cpu_baseline"] = {"value": t_app * apps_per_stage, "unit": "s/stage", "cores": 1, "kind": "oracle",
-                                "sample": "one exact Jacobian action of the FP64 oracle on the full 16^3 P4 state "
+                                "sample": "one exact Jacobian action of the FP64 oracle on the full %d^3 P4 state " % cfg["n"] +
                                           "(%.2f s) times the %d fine-operator applications of one GPU stage"
                                           % (t_app, apps_per_stage)}
     if rank == 0:
@@ -464,6 +519,8 @@ def main():
                     help="coarsest-level solve of the chosen form (the learned form is also measured separately)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip training the coarse network")
     ap.add_argument("--learn-steps", type=int, default=2000)
+    ap.add_argument("--lag", type=int, default=2, help="also time the chosen form with the preconditioner "
+                                                       "assembled every LAG stages (1: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -169,6 +169,11 @@ int dg_residual(dg_handle* h, const double* w, double* f, void* stream);
  * face points, and sets 1/(gamma dt) (>= 0). Synchronises (reads ||w||). */
 int dg_set_linearization(dg_handle* h, const double* w, double inv_gamma_dt, void* stream);
 
+/* dg_set_linearization that also writes the right-hand side of the stage started from w,
+ * g <- -f_h(w) (Eq. (rosSysOp) with no earlier stages), from the residual it evaluates anyway:
+ * one nonlinear face pass (exact Riemann solves) per stage instead of two. g must not alias w. */
+int dg_set_linearization_rhs(dg_handle* h, const double* w, double inv_gamma_dt, double* g, void* stream);
+
 /* out <- G v = J(w) v + (1/(gamma dt)) M v on the fine level, M the
  * velocity-only mass form (Eq. (massBil)). mode DG_JVP_TANGENT: exact
  * linearisation (Eqs. (jacTrilFnotNU), (jacTrilnu)); DG_JVP_FD:
@@ -190,6 +195,12 @@ int dg_assemble(dg_handle* h, void* stream);
  * factors are computed in FP32 (the mesh-only linear part is probed once in FP64), for
  * the FP32 preconditioner cycle only. Synchronises. */
 int dg_assemble_precision(dg_handle* h, int precision, void* stream);
+
+/* Preconditioner lagging (Sec. 4.1, T3L1 case): keep the element blocks, their factors and the
+ * coarse block-sparse operators assembled at an earlier linearisation for the current one (the
+ * paper freezes them for several time steps). The matrix-free fine-level products of the cycle
+ * and of FGMRES still use the current linearisation. DG_ERR_STATE if nothing has been assembled. */
+int dg_reuse_assembly(dg_handle* h);
 
 /* ------------------------------------------------------------ p-multigrid */
 
@@ -337,7 +348,11 @@ int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
 #define DG_PROF_VOL_TAN 3   /* volume pass of the exact Jacobian action */
 #define DG_PROF_FACE_TAN32 4 /* face pass of the FP32 Jacobian action (reduced-precision preconditioner) */
 #define DG_PROF_VOL_TAN32 5  /* volume pass of the FP32 Jacobian action */
-#define DG_PROF_N 6
+#define DG_PROF_BJ32 6       /* fine-level block-Jacobi apply of the FP32 cycle (explicit inverses) */
+#define DG_PROF_BSR32 7      /* level-1 block-sparse product of the FP32 cycle */
+#define DG_PROF_BJ64 8       /* fine-level block-Jacobi apply of the FP64 cycle (LU factors) */
+#define DG_PROF_BSR64 9      /* level-1 block-sparse product of the FP64 cycle */
+#define DG_PROF_N 10
 
 /* Counters since dg_create: kernels launched by the library, and applications
  * of the fine-level operator (residual or Jacobian action). Host-only, no sync. */
@@ -351,6 +366,11 @@ int dg_profile(dg_handle* h, int enable);
  * last read (arrays of DG_PROF_N entries); resets them. Synchronises the
  * device. */
 int dg_profile_read(dg_handle* h, double* ms, long long* counts);
+
+/* dg_profile_read plus the algorithmic HBM bytes of the timed launches per class (each value
+ * read and each value written once: the blocks, the input and output vectors; for the operator
+ * classes 0-5 nothing is counted and 0 is returned). bytes: DG_PROF_N entries. */
+int dg_profile_read_bytes(dg_handle* h, double* ms, long long* counts, double* bytes);
 
 #ifdef __cplusplus
 }

@@ -49,9 +49,11 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_profile_read", "dg_residual_noalloc", "dg_assemble_precision", "pmg_level_solve",
            "dg_mlp_workspace_bytes", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_adam", "dg_set_coarse_network",
            "dg_coarse_pairs", "dg_record_coarse", "dg_recorded", "pmg_project_pressure",
-           "bsr_spmv_t", "dg_coarse_apply")
-DG_PROF_N = 6
-PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32")
+           "bsr_spmv_t", "dg_coarse_apply", "dg_profile_read_bytes",
+           "dg_reuse_assembly", "dg_set_linearization_rhs")
+DG_PROF_N = 10
+PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32", "bj32_fine", "bsr32_l1",
+              "bj64_fine", "bsr64_l1")
 
 
 class DgParams(ctypes.Structure):
@@ -125,6 +127,10 @@ def load(path=None):
     L.dg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.dg_profile.argtypes = [vp, i]
     L.dg_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    L.dg_profile_read_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double)]
+    L.dg_reuse_assembly.argtypes = [vp]
+    L.dg_set_linearization_rhs.argtypes = [vp, vp, d, vp, vp]
     for name in EXPORTS:
         if name != "dg_last_error":
             getattr(L, name).restype = ctypes.c_int
@@ -286,6 +292,10 @@ class DG:
     def dg_set_linearization(self, w, inv_gamma_dt, stream=None):
         self._chk(self._L.dg_set_linearization(self.h, self._ptr(w), float(inv_gamma_dt), self._stream(stream)))
 
+    def dg_set_linearization_rhs(self, w, inv_gamma_dt, g, stream=None):
+        self._chk(self._L.dg_set_linearization_rhs(self.h, self._ptr(w), float(inv_gamma_dt), self._ptr(g),
+                                                   self._stream(stream)))
+
     def dg_jvp(self, v, out, mode=DG_JVP_TANGENT, stream=None):
         self._chk(self._L.dg_jvp(self.h, self._ptr(v), self._ptr(out), int(mode), self._stream(stream)))
 
@@ -326,6 +336,17 @@ class DG:
         cnt = (ctypes.c_longlong * DG_PROF_N)()
         self._chk(self._L.dg_profile_read(self.h, ms, cnt))
         return {PROF_NAMES[i]: (ms[i], cnt[i]) for i in range(DG_PROF_N)}
+
+    def dg_profile_read_bytes(self):
+        """{class: (ms, launches, algorithmic bytes)} since the last read."""
+        ms = (ctypes.c_double * DG_PROF_N)()
+        cnt = (ctypes.c_longlong * DG_PROF_N)()
+        by = (ctypes.c_double * DG_PROF_N)()
+        self._chk(self._L.dg_profile_read_bytes(self.h, ms, cnt, by))
+        return {PROF_NAMES[i]: (ms[i], cnt[i], by[i]) for i in range(DG_PROF_N)}
+
+    def dg_reuse_assembly(self):
+        self._chk(self._L.dg_reuse_assembly(self.h))
 
     def pmg_level_solve(self, lvl, g, x, rtol=1e-8, maxit=1000, x0_is_zero=True, stream=None, check=True):
         info = DgSolveInfo()

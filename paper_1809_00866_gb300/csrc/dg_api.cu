@@ -222,12 +222,12 @@ int prof_begin(Handle* h, cudaStream_t st, cudaEvent_t* a) {
   return DG_OK;
 }
 
-int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a) {
+int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a, double bytes) {
   if (!h->prof || !a) return DG_OK;
   cudaEvent_t b = prof_event(h);
   if (!b) return fail(h, DG_ERR_CUDA, "cudaEventCreate failed");
   DG_CUDA(h, cudaEventRecord(b, st));
-  h->prof_pending.push_back(Handle::ProfEv{cls, a, b});
+  h->prof_pending.push_back(Handle::ProfEv{cls, a, b, bytes});
   return DG_OK;
 }
 
@@ -375,6 +375,15 @@ int dg_destroy(dg_handle* hh) {
   return DG_OK;
 }
 
+int dg_reuse_assembly(dg_handle* hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!h->asm64_ready && !h->asm_f_ready) return fail(h, DG_ERR_STATE, "no assembled preconditioner to reuse");
+  if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_reuse_assembly needs dg_set_linearization first");
+  h->assembled = true;
+  return DG_OK;
+}
+
 const char* dg_last_error(const dg_handle* hh) {
   if (!hh) return g_create_error.c_str();
   return reinterpret_cast<const Handle*>(hh)->err.c_str();
@@ -429,6 +438,15 @@ int dg_set_linearization(dg_handle* hh, const double* w, double inv_gamma_dt, vo
   return DG_OK;
 }
 
+int dg_set_linearization_rhs(dg_handle* hh, const double* w, double inv_gamma_dt, double* g, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!g || g == w) return fail(h, DG_ERR_ARG, "g must be a non-null device pointer distinct from w");
+  int rc = dg_set_linearization(hh, w, inv_gamma_dt, stream);
+  if (rc) return rc;
+  return launch_axpby(h, h->lev[0].n, -1.0, h->flin, 0.0, g, as_stream(stream));  // g = -f_h(w)
+}
+
 int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
@@ -472,6 +490,10 @@ int dg_profile(dg_handle* hh, int enable) {
 }
 
 int dg_profile_read(dg_handle* hh, double* ms, long long* counts) {
+  return dg_profile_read_bytes(hh, ms, counts, nullptr);
+}
+
+int dg_profile_read_bytes(dg_handle* hh, double* ms, long long* counts, double* bytes) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !ms || !counts) return h ? fail(h, DG_ERR_ARG, "null output") : DG_ERR_ARG;
   DG_CUDA(h, cudaDeviceSynchronize());
@@ -480,6 +502,7 @@ int dg_profile_read(dg_handle* hh, double* ms, long long* counts) {
     DG_CUDA(h, cudaEventElapsedTime(&t, p.a, p.b));
     h->prof_ms[p.cls] += t;
     h->prof_cnt[p.cls] += 1;
+    h->prof_bytes[p.cls] += p.bytes;
     h->ev_pool.push_back(p.a);
     h->ev_pool.push_back(p.b);
   }
@@ -487,8 +510,10 @@ int dg_profile_read(dg_handle* hh, double* ms, long long* counts) {
   for (int i = 0; i < DG_PROF_N; ++i) {
     ms[i] = h->prof_ms[i];
     counts[i] = h->prof_cnt[i];
+    if (bytes) bytes[i] = h->prof_bytes[i];
     h->prof_ms[i] = 0.0;
     h->prof_cnt[i] = 0;
+    h->prof_bytes[i] = 0.0;
   }
   return DG_OK;
 }

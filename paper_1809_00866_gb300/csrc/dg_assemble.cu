@@ -574,10 +574,6 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
     float* Bl[DG_MAX_LEVELS];
     for (int l = 0; l < h->nlev; ++l) { Dl[l] = h->lev[l].LUf; Bl[l] = h->lev[l].Bsrf; }
     if ((rc = assemble_levels<float>(h, a, Dl, Bl, st))) return rc;
-    for (int l = 0; l < h->nlev; ++l) {
-      Level& L = h->lev[l];
-      if ((rc = factor_blocks<float>(h, ne, L.b, L.LUf, L.LUf, L.perm, st))) return rc;
-    }
     if ((rc = invert_levels_f32(h, st))) return rc;  // the FP32 smoother applies explicit inverses
   }
   DG_CUDA(h, cudaStreamSynchronize(st));

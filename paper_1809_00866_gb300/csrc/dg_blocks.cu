@@ -8,7 +8,7 @@
 // memory by bulk asynchronous copies (two stages per CTA); the block-sparse rows (seven 40 x 40
 // blocks per element at P2) are fastest read straight from global memory by many small CTAs.
 // Both use one thread per output row. The smoother uses explicit inverses D^-1, formed once per
-// assembly from the LU factors.
+// assembly by Gauss-Jordan elimination in shared memory.
 #include <algorithm>
 
 #include "dg_async.h"
@@ -18,42 +18,101 @@ namespace dg {
 
 namespace {
 
-// In place: LU factors (unit L below the diagonal, U above it with 1/U_kk on the diagonal,
-// column-major, row permutation pi: row i of P D is row pi[i] of D) -> D^-1, column-major.
-// D^-1 = U^-1 L^-1 P, and column c of P^T-free W = U^-1 L^-1 is column pinv[c] of D^-1's
-// source, so thread j computes column j of W by substitution with uniform loop bounds (the
-// leading zeros of e_j make the extra terms vanish) and the store permutes the columns.
-template <class R>
-__global__ void lu_to_inverse_kernel(int ne, int b, R* __restrict__ M, const int* __restrict__ perm) {
+// In place D -> D^-1 (column-major FP32 blocks, b a multiple of 4) by Gauss-Jordan elimination
+// with partial (row) pivoting, one block per CTA in shared memory (row-major, leading dimension
+// b + 4 so that rows are float4-aligned). Step k: pick the pivot row, keep column k in `col`
+// and the scaled pivot row in `row` (row[k] = 1/pivot), zero column k, then one uniform rank-1
+// update A[i][:] -= col[i] row[:] for every i != k and A[k][:] = row; each thread owns four
+// adjacent columns (one float4) and every RG-th row. b^3 multiply-adds per block; the row
+// interchanges are undone on the columns at the end, in reverse order.
+__global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
-  R* LU = reinterpret_cast<R*>(sraw_);  // [b][b] column-major
-  R* X = LU + (size_t)b * b;             // [b][b] row-major: X[i*b + j] = W[i][j]
-  int* pinv = reinterpret_cast<int*>(X + (size_t)b * b);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
-    R* Me = M + (size_t)e * b * b;
-    for (int t = tid; t < b * b; t += nt) LU[t] = Me[t];
-    for (int i = tid; i < b; i += nt) pinv[perm[(size_t)e * b + i]] = i;
-    __syncthreads();
-    for (int j = tid; j < b; j += nt) {
-      // forward: y = L^-1 e_j
-      for (int i = 0; i < b; ++i) {
-        R acc = i == j ? R(1) : R(0);
-        for (int k = 0; k < i; ++k) acc = fma(-LU[(size_t)k * b + i], X[(size_t)k * b + j], acc);
-        X[(size_t)i * b + j] = acc;
-      }
-      // backward: x = U^-1 y (the diagonal holds 1/U_ii)
-      for (int i = b - 1; i >= 0; --i) {
-        R acc = X[(size_t)i * b + j];
-        for (int k = i + 1; k < b; ++k) acc = fma(-LU[(size_t)k * b + i], X[(size_t)k * b + j], acc);
-        X[(size_t)i * b + j] = acc * LU[(size_t)i * b + i];
-      }
+  const int LD = b + 4;
+  float* A = reinterpret_cast<float*>(sraw_);  // [b][LD]
+  float* col = A + (size_t)b * LD;             // [b] column k before step k
+  float* row = col + b;                         // [b] scaled pivot row
+  int* piv = reinterpret_cast<int*>(row + b);
+  __shared__ int s_p;
+  __shared__ float s_inv;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int NG = b / 4;                      // float4 column groups
+  const int CW = 32 * ((NG + 31) / 32);      // group slots (whole warps)
+  const int RG = nt / CW;                    // row groups; blockDim.x is a multiple of CW
+  const int jg = tid % CW, ig = tid / CW;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    float* Mb = M + (size_t)blk * b * b;
+    for (int t = tid; t < b * b; t += nt) {
+      const int c = t / b, r = t - c * b;
+      A[r * LD + c] = Mb[t];
     }
     __syncthreads();
-    // D^-1[:, c] = W[:, pinv[c]]
+    for (int k = 0; k < b; ++k) {
+      if (warp == 0) {
+        float best = -1.0f;
+        int bi = k;
+        for (int i = k + lane; i < b; i += 32) {
+          const float v = fabsf(A[i * LD + k]);
+          if (v > best) { best = v; bi = i; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const float ov = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) {
+          s_p = bi;
+          piv[k] = bi;
+          s_inv = 1.0f / A[bi * LD + k];
+          if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
+        }
+      }
+      __syncthreads();
+      const int p = s_p;
+      const float inv = s_inv;
+      for (int i = tid; i < b; i += nt) {
+        const int src = i == k ? p : (i == p ? k : i);  // rows as after the interchange
+        col[i] = A[src * LD + k];
+      }
+      for (int j = tid; j < b; j += nt) row[j] = j == k ? inv : A[p * LD + j] * inv;
+      __syncthreads();
+      // row k moves to row p (its column-k entry becomes 0), and column k is zeroed elsewhere
+      if (p != k)
+        for (int j = tid; j < b; j += nt) A[p * LD + j] = j == k ? 0.0f : A[k * LD + j];
+      for (int i = tid; i < b; i += nt)
+        if (i != p) A[i * LD + k] = 0.0f;
+      __syncthreads();
+      if (jg < NG) {
+        const float4 r4 = *reinterpret_cast<const float4*>(row + 4 * jg);
+        for (int i = ig; i < b; i += RG) {
+          float4* a4 = reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * jg);
+          if (i == k) {
+            *a4 = r4;
+          } else {
+            const float c = col[i];
+            float4 v = *a4;
+            v.x = fmaf(-c, r4.x, v.x);
+            v.y = fmaf(-c, r4.y, v.y);
+            v.z = fmaf(-c, r4.z, v.z);
+            v.w = fmaf(-c, r4.w, v.w);
+            *a4 = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int k = b - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k)
+        for (int i = tid; i < b; i += nt) {
+          const float t = A[i * LD + k];
+          A[i * LD + k] = A[i * LD + p];
+          A[i * LD + p] = t;
+        }
+      __syncthreads();
+    }
     for (int t = tid; t < b * b; t += nt) {
-      const int c = t / b, i = t - c * b;
-      Me[t] = X[(size_t)i * b + pinv[c]];
+      const int c = t / b, r = t - c * b;
+      Mb[t] = A[r * LD + c];
     }
     __syncthreads();
   }
@@ -222,12 +281,29 @@ int launch_staged_jacobi(Handle* h, int b, const R* A, const R* g, const R* Gx, 
 int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
                     cudaStream_t st) {
   const Level& L = h->lev[lvl];
-  return launch_staged_jacobi<float>(h, L.b, L.LUf, g, Gx, omega, x_zero ? 1 : 0, x, st);
+  cudaEvent_t e0 = nullptr;
+  int rc;
+  if (lvl == 0 && (rc = prof_begin(h, st, &e0))) return rc;
+  rc = launch_staged_jacobi<float>(h, L.b, L.LUf, g, Gx, omega, x_zero ? 1 : 0, x, st);
+  if (rc) return rc;
+  // algorithmic bytes: the inverses, g, Gx and the old x read once, x written once
+  const double vec = (double)h->ne * L.b * sizeof(float);
+  const double bytes = (double)h->ne * L.b * L.b * sizeof(float) + vec * (2 + (Gx ? 1 : 0) + (x_zero ? 0 : 1));
+  return lvl == 0 ? prof_end(h, DG_PROF_BJ32, st, e0, bytes) : DG_OK;
 }
 
 template <class R>
 int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y, cudaStream_t st) {
-  return launch_direct<R, 7>(h, h->lev[lvl].b, B, x, nullptr, alpha, beta, 0, y, st);
+  const int b = h->lev[lvl].b;
+  cudaEvent_t e0 = nullptr;
+  int rc;
+  if (lvl == 1 && (rc = prof_begin(h, st, &e0))) return rc;
+  rc = launch_direct<R, 7>(h, b, B, x, nullptr, alpha, beta, 0, y, st);
+  if (rc) return rc;
+  // algorithmic bytes: the 7 blocks of every row, x and the old y read once, y written once
+  const double vec = (double)h->ne * b * sizeof(R);
+  const double bytes = 7.0 * h->ne * b * b * sizeof(R) + vec * (2 + (beta != R(0) ? 1 : 0));
+  return lvl == 1 ? prof_end(h, sizeof(R) == 4 ? DG_PROF_BSR32 : DG_PROF_BSR64, st, e0, bytes) : DG_OK;
 }
 template int staged_bsr<float>(Handle*, int, const float*, float, const float*, float, float*, cudaStream_t);
 template int staged_bsr<double>(Handle*, int, const double*, double, const double*, double, double*, cudaStream_t);
@@ -235,14 +311,14 @@ template int staged_bsr<double>(Handle*, int, const double*, double, const doubl
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
-    const size_t smem = 2 * sizeof(float) * (size_t)L.b * L.b + sizeof(int) * L.b;
-    if (smem > kSmemLimit) return fail(h, DG_ERR_ARG, "element block too large for the FP32 inverse");
-    DG_CUDA(h, cudaFuncSetAttribute(lu_to_inverse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kSmemLimit));
-    const int threads = 32 * ((L.b + 31) / 32);
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
+    const size_t smem = sizeof(float) * ((size_t)L.b * (L.b + 4) + 2 * L.b) + sizeof(int) * L.b;
+    if (smem > kSmemLimit || L.b % 4 != 0) return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
+    DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
     const int grid = std::min(h->ne, h->nsm * per_sm);
-    lu_to_inverse_kernel<float><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, L.perm);
+    const int cw = 32 * ((L.b / 4 + 31) / 32);
+    const int threads = cw * std::max(1, 512 / cw);  // a multiple of the group slots, <= 512
+    gj_inverse_kernel<<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
     DG_LAUNCH_CHECK(h);
   }
   return DG_OK;

@@ -144,11 +144,12 @@ struct Handle {
   long long launches = 0;
   long long op_apps = 0;
   bool prof = false;
-  struct ProfEv { int cls; cudaEvent_t a, b; };
+  struct ProfEv { int cls; cudaEvent_t a, b; double bytes; };
   std::vector<ProfEv> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[DG_PROF_N] = {};
   long long prof_cnt[DG_PROF_N] = {};
+  double prof_bytes[DG_PROF_N] = {};
 };
 
 // error helpers
@@ -168,7 +169,7 @@ int fail(Handle* h, int code, const std::string& msg);
 // CUDA events around the launches of one kernel class (when profiling is on)
 cudaEvent_t prof_event(Handle* h);
 int prof_begin(Handle* h, cudaStream_t st, cudaEvent_t* a);
-int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a);
+int prof_end(Handle* h, int cls, cudaStream_t st, cudaEvent_t a, double bytes = 0.0);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -219,7 +220,7 @@ int prepare_lin_fp32(Handle* h, cudaStream_t st);
 int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st);  // y = G_lvl x
 
 // element-block products streamed through shared memory (dg_blocks.cu). The FP32 cycle keeps
-// explicit inverses in Level::LUf (invert_levels_f32 turns the FP32 LU factors into them).
+// explicit inverses in Level::LUf (invert_levels_f32 turns the FP32 blocks held there into them).
 int invert_levels_f32(Handle* h, cudaStream_t st);
 int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
                     cudaStream_t st);  // x <- (x_zero ? 0 : x) + omega D^-1 (g - Gx); Gx may be null

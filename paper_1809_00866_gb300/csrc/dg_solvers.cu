@@ -267,9 +267,18 @@ static int jacobi_sweeps(Handle* h, int lvl, const double* g, double* x, int swe
       int rc = level_matvec(h, lvl, x, L.t2, st);
       if (rc) return rc;
     }
+    cudaEvent_t e0 = nullptr;
+    int rc;
+    if (lvl == 0 && (rc = prof_begin(h, st, &e0))) return rc;
     bj_update_kernel<double><<<apply_grid(h), 32 * kApplyWarps, smem, st>>>(h->ne, L.b, L.Dinv, L.perm, g,
                                                                     zero ? nullptr : L.t2, omega, zero ? 1 : 0, x);
     DG_LAUNCH_CHECK(h);
+    if (lvl == 0) {  // algorithmic bytes: LU factors and permutation, g, Gx, old x read; x written
+      const double vec = (double)h->ne * L.b * sizeof(double);
+      const double bytes = (double)h->ne * L.b * ((double)L.b * sizeof(double) + sizeof(int)) +
+                           vec * (2 + (zero ? 0 : 2));
+      if ((rc = prof_end(h, DG_PROF_BJ64, st, e0, bytes))) return rc;
+    }
   }
   if (sweeps == 0 && x_zero) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(double) * L.n, st));
   return DG_OK;
@@ -554,7 +563,8 @@ static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_
 }
 
 // ------------------------------------------------------ FP32 preconditioner cycle
-// FP32 copies of the linearisation cache (for the FP32 operator) and of the LU factors
+// FP32 copies of the linearisation cache (for the FP32 operator), explicit FP32 inverses of the
+// element blocks
 // and block-sparse coarse operators; refreshed after every linearisation / assembly.
 int prepare_lin_fp32(Handle* h, cudaStream_t st) {
   if (h->lin_f_ready) return DG_OK;
@@ -581,7 +591,7 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
       if (!L.t0f) DG_CUDA(h, cudaMalloc((void**)&L.t0f, sizeof(float) * L.n));
       if (!L.t1f) DG_CUDA(h, cudaMalloc((void**)&L.t1f, sizeof(float) * L.n));
       if (!L.t2f) DG_CUDA(h, cudaMalloc((void**)&L.t2f, sizeof(float) * L.n));
-      convert_kernel<double, float><<<grid_for(h, nbb / 256 + 1), 256, 0, st>>>(nbb, L.Dinv, L.LUf);
+      convert_kernel<double, float><<<grid_for(h, nbb / 256 + 1), 256, 0, st>>>(nbb, L.Dblk, L.LUf);
       DG_LAUNCH_CHECK(h);
       if (l >= 1) {
         if (!L.Bsrf) DG_CUDA(h, cudaMalloc((void**)&L.Bsrf, sizeof(float) * nbb * 7));
@@ -589,7 +599,7 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
         DG_LAUNCH_CHECK(h);
       }
     }
-    if (int rc2 = invert_levels_f32(h, st)) return rc2;  // the LU factors (rounded) -> explicit inverses
+    if (int rc2 = invert_levels_f32(h, st)) return rc2;  // the blocks (rounded) -> explicit inverses
     h->asm_f_ready = true;
   }
   return DG_OK;

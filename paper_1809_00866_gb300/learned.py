@@ -45,10 +45,8 @@ def collect_rhs(dg, states, inv_gamma_dt, opts, per_state=32):
     nc = dg.n[lc]
     out = []
     for w in states:
-        f = dg.empty()
-        dg.dg_residual(w, f)
-        g = (-f).contiguous()
-        dg.dg_set_linearization(w, inv_gamma_dt)
+        g = dg.empty()
+        dg.dg_set_linearization_rhs(w, inv_gamma_dt, g)
         dg.dg_assemble()
         buf = torch.empty(per_state * nc, dtype=torch.float64, device="cuda")
         dg.dg_record_coarse(buf, per_state)
@@ -140,10 +138,8 @@ def collect_pairs(dg, states, inv_gamma_dt, opts, per_state=32, level_rtol=1e-6,
     Xs, Ts = [], []
     its_level, nrec = [], 0
     for w in states:
-        f = dg.empty()
-        dg.dg_residual(w, f)
-        g = (-f).contiguous()
-        dg.dg_set_linearization(w, inv_gamma_dt)
+        g = dg.empty()
+        dg.dg_set_linearization_rhs(w, inv_gamma_dt, g)
         dg.dg_assemble()  # FP64: the level solves below need it (the FP32 cycle rounds it)
         buf = torch.empty(per_state * nc, dtype=torch.float64, device="cuda")
         dg.dg_record_coarse(buf, per_state)

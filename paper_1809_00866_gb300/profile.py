@@ -3,6 +3,8 @@
     python -m paper_1809_00866_gb300.profile jv [--n 16] [--reps 3]
         TGV n^3 P4 handle (levels 4-2-1), linearisation at the TGV field, `reps` exact
         Jacobian actions (face_kernel + vol_kernel per action).
+    python -m paper_1809_00866_gb300.profile assemble [--n 16] [--form fp32|fp64]
+        one preconditioner assembly after a warm-up one, between cudaProfilerStart/Stop.
     python -m paper_1809_00866_gb300.profile stage [--n 16] [--form fp32|fp64] [--learned]
         one implicit stage to rel-res 1e-8 after two warm-up solves; only the timed FGMRES solve
         lies between cudaProfilerStart and cudaProfilerStop (ncu --profile-from-start off).
@@ -16,7 +18,7 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("what", choices=["jv", "stage"])
+    ap.add_argument("what", choices=["jv", "stage", "assemble"])
     ap.add_argument("--n", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--form", choices=["fp32", "fp64"], default="fp32")
@@ -45,6 +47,20 @@ def main(argv=None):
         torch.cuda.synchronize()
         print("jv: %d actions, %.3f ms each" % (a.reps, 1e3 * (time.perf_counter() - t0) / a.reps))
         return 0
+    if a.what == "assemble":
+        prec = DG_PRECOND_FP32 if a.form == "fp32" else DG_PRECOND_FP64
+        g = dg.empty()
+        dg.dg_set_linearization_rhs(w, inv, g)
+        dg.dg_assemble(precision=prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        dg.dg_assemble(precision=prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        torch.cuda.profiler.stop()
+        print("assemble (%s): %.4f s" % (a.form, t))
+        return 0
     fp32 = a.form == "fp32"
     o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.7 if fp32 else 1.0,
                    precision=DG_PRECOND_FP32 if fp32 else DG_PRECOND_FP64)
@@ -52,22 +68,19 @@ def main(argv=None):
         from . import learned as Lrn
         states = [w.clone()]
         for _ in range(3):
-            f = dg.empty()
-            dg.dg_residual(states[-1], f)
-            dg.dg_set_linearization(states[-1], inv)
+            g = dg.empty()
+            dg.dg_set_linearization_rhs(states[-1], inv, g)
             dg.dg_assemble()
             x = dg.empty()
-            dg.fgmres_solve((-f).contiguous(), x, o)
+            dg.fgmres_solve(g, x, o)
             states.append((states[-1] + x).contiguous())
         D = Lrn.collect_rhs(dg, states, inv, o, per_state=40)
         dg.dg_set_linearization(states[-1], inv)
         dg.dg_assemble()
         Lrn.train_residual(dg, D, steps=2000, lr=1e-3, seed=0)
         o.coarse_solver = DG_COARSE_LEARNED
-    f = dg.empty()
-    dg.dg_residual(w, f)
-    g = (-f).contiguous()
-    dg.dg_set_linearization(w, inv)
+    g = dg.empty()
+    dg.dg_set_linearization_rhs(w, inv, g)
     dg.dg_assemble(precision=o.precision)
     x = dg.empty()
     for _ in range(2):

@@ -111,3 +111,17 @@ def test_argument_errors_do_not_launch():
     with pytest.raises(P.DgError) as e:
         dg.dg_residual(w, w)  # aliasing
     assert e.value.code == P.DG_ERR_ARG
+
+
+def test_linearization_rhs_is_minus_residual():
+    # one nonlinear face pass gives both the linearisation and the stage right-hand side -f(w)
+    dg, m = pair(*meshes()["box233"], [3, 1])
+    w = O.project_tgv(m) + S.perturbation(m.ne, m.k, 0.2, 21)
+    g = dg.empty()
+    inv = 1.0 / S.acoustic_dt(m.nx, m.k)
+    dg.dg_set_linearization_rhs(dev(w), inv, g)
+    assert rel(host(g), -O.residual(m, w)) < 1e-12
+    v = S.direction(m.ne, m.k, 22)
+    out = dg.empty()
+    dg.dg_jvp(dev(v), out)
+    assert rel(host(out), O.jvp(m, w, v, inv)) < 1e-12
