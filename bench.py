@@ -68,10 +68,11 @@ DENSE_FLOP_PER_ELEMENT_P4 = 520_000.0
 FP64_PEAK_TFLOPS = 1.25
 # HBM peak: the measured copy bandwidth on the GB300s, else the machine's fallback.
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) of one fine-level launch of the FP32 block-Jacobi apply at 16^3 P4,
-# from one Nsight Compute capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum = 323.46 MB + 4.79 MB).
-BJ32_FINE_TRAFFIC_16_P4 = 328.25e6
+# DRAM bytes (read + write) of one fine-level launch of the block-Jacobi apply at 16^3 P4, per
+# block storage of the chosen form, from one Nsight Compute capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum; FP16: 162.88 MB + 4.31 MB); None where not
+# captured for the current kernel.
+BJ_FINE_TRAFFIC_16_P4 = {"fp32": None, "h16": 167.19e6, "bf16": None}
 
 
 def hbm_peak():
@@ -220,7 +221,8 @@ def run_ours(args):
                             post_sweeps=b_, coarse_sweeps=c, omega=omega, smoother=smoother,
                             precision=precision)
 
-    chosen_prec = P.DG_PRECOND_FP32 if args.form == "fp32" else P.DG_PRECOND_FP64
+    chosen_prec = {"fp32": P.DG_PRECOND_FP32, "fp64": P.DG_PRECOND_FP64, "h16": P.DG_PRECOND_FP32_H16,
+                   "bf16": P.DG_PRECOND_FP32_BF16}[args.form]
     chosen_opts = opts_for(chosen_prec, args.omega)
     # the plain form at its own best measured setting (undamped, 2/2/2 sweeps)
     plain_opts = opts_for(P.DG_PRECOND_FP64, 1.0, args.plain_sweeps)
@@ -421,10 +423,11 @@ def run_ours(args):
     ms_d, cnt_d, by_d = kp[dom]
     if cnt_d:
         ach = by_d / (ms_d / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "staged_jacobi_kernel<float> (fine level, P4)" if dom == "bj32_fine"
-                    else "bj_update_kernel<double> (fine level, P4)",
+        storage = {"fp32": "float", "h16": "half", "bf16": "bfloat16"}.get(args.form)
+        roofline = {"bound": "hbm", "kernel": "staged_jacobi_kernel<float, %s> (fine level, P4)" % storage
+                    if dom == "bj32_fine" else "bj_update_kernel<double> (fine level, P4)",
                     "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": BJ32_FINE_TRAFFIC_16_P4 if (dom == "bj32_fine" and args.config == CONFIG) else None,
+                    "traffic": BJ_FINE_TRAFFIC_16_P4.get(args.form) if args.config == CONFIG else None,
                     "algorithmic_bytes_per_launch": by_d / cnt_d, "ms_per_launch": ms_d / cnt_d,
                     "peak_source": "measured HBM copy bandwidth (hbm_gbs of the measured-peaks file)"
                     if hbm_src == "measured" else "fallback HBM bandwidth 6.8 TB/s",
@@ -454,7 +457,10 @@ def run_ours(args):
     line = {"metric": METRIC, "value": chosen["s_per_stage"], "unit": "s/stage", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * chosen["t_total"] / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.form == "fp64" else "f64 (FGMRES, products with G, stage RHS) + f32 (preconditioner cycle)",
+            "dtype": {"fp64": "f64", "fp32": "f64 (FGMRES, products with G, stage RHS) + f32 (preconditioner cycle)",
+                      "h16": "f64 (FGMRES, products with G, stage RHS) + f32 (preconditioner cycle) with f16 "
+                             "block storage", "bf16": "f64 (FGMRES, products with G, stage RHS) + f32 "
+                             "(preconditioner cycle) with bf16 block storage"}[args.form],
             "data": "synthetic",
             "config": {"workload": "Taylor-Green vortex Re=1600, %d^3 periodic hexahedra, P4 (N_b=35), " % cfg["n"] +
                                    "p-levels 4-2-1, one linearly implicit stage to rel-res 1e-8",
@@ -518,7 +524,8 @@ def main():
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi")
     ap.add_argument("--sweeps", default="3,3,2", help="pre,post,coarse smoothing iterations of the chosen form")
     ap.add_argument("--plain-sweeps", default="2,2,2", help="pre,post,coarse smoothing iterations of the plain form")
-    ap.add_argument("--form", choices=["fp64", "fp32"], default="fp32", help="precision of the chosen form's cycle")
+    ap.add_argument("--form", choices=["fp64", "fp32", "h16", "bf16"], default="h16",
+                    help="precision of the chosen form's cycle (h16 / bf16: FP32 cycle with 16-bit block storage)")
     ap.add_argument("--omega", type=float, default=0.9, help="block-Jacobi damping of the chosen form")
     ap.add_argument("--coarse", choices=["smoother", "learned"], default="smoother",
                     help="coarsest-level solve of the chosen form (the learned form is also measured separately)")

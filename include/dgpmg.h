@@ -86,6 +86,9 @@ typedef struct dg_handle dg_handle;
 /* Precision of the preconditioner cycle (and of its assembly, dg_assemble_precision). */
 #define DG_PRECOND_FP64 0
 #define DG_PRECOND_FP32 1 /* block-Jacobi smoothing only */
+#define DG_PRECOND_FP32_H16 2  /* the FP32 cycle with its element-block inverses and block-sparse coarse
+                                  operators stored in FP16 (IEEE half), products accumulated in FP32 */
+#define DG_PRECOND_FP32_BF16 3 /* the same with bfloat16 storage */
 
 /* Coarsest-level SOLVE of the cycles (Sec. 2.4.3 uses a preconditioned GMRES there). */
 #define DG_COARSE_SMOOTHER 0 /* coarse_sweeps iterations of the level smoother from zero */
@@ -189,7 +192,8 @@ int dg_jvp(dg_handle* h, const double* v, double* out, int mode, void* stream);
  * degree of level 1 only (Sec. 2.4.3). Synchronises. */
 int dg_assemble(dg_handle* h, void* stream);
 
-/* dg_assemble in the precision of the preconditioner that will use it:
+/* dg_assemble in the precision of the preconditioner that will use it (DG_PRECOND_FP32_H16 and
+ * _BF16 assemble as DG_PRECOND_FP32; their 16-bit block copies are rounded from it at first use):
  * DG_PRECOND_FP64 (= dg_assemble; also usable by the FP32 cycle after rounding), or
  * DG_PRECOND_FP32: the state-dependent blocks, the inherited coarse blocks and the LU
  * factors are computed in FP32 (the mesh-only linear part is probed once in FP64), for

@@ -30,6 +30,8 @@ DG_SMOOTH_JACOBI = 0
 DG_SMOOTH_GMRES = 1
 DG_PRECOND_FP64 = 0
 DG_PRECOND_FP32 = 1
+DG_PRECOND_FP32_H16 = 2
+DG_PRECOND_FP32_BF16 = 3
 DG_COARSE_SMOOTHER = 0
 DG_COARSE_GMRES = 1
 DG_COARSE_LEARNED = 2

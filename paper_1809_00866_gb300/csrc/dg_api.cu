@@ -252,6 +252,7 @@ static void free_all(Handle* h) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
     F(h->lev[l].Dlin); F(h->lev[l].Blin); F(h->lev[l].perm);
     F(h->lev[l].LUf); F(h->lev[l].Bsrf); F(h->lev[l].t0f); F(h->lev[l].t1f); F(h->lev[l].t2f);
+    F(h->lev[l].LU16); F(h->lev[l].Bsr16);
   }
   F(h->face_out); F(h->face_lift); F(h->wlin); F(h->flin); F(h->ubar); F(h->dFlux); F(h->wnorm2);
   F(h->fd_w); F(h->fd_f); F(h->red); F(h->red_out); F(h->status); F(h->V); F(h->Z); F(h->hcol);
@@ -461,8 +462,11 @@ int dg_assemble_precision(dg_handle* hh, int precision, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");
+  if (precision == DG_PRECOND_FP32_H16 || precision == DG_PRECOND_FP32_BF16)
+    precision = DG_PRECOND_FP32;  // the 16-bit copies are rounded from the FP32 assembly at first use
   if (precision != DG_PRECOND_FP64 && precision != DG_PRECOND_FP32) return fail(h, DG_ERR_ARG, "unknown precision");
   h->assembled = h->asm64_ready = h->asm_f_ready = false;
+  h->asm16 = 0;
   const int rc = assemble_all(h, precision, as_stream(stream));
   if (rc == DG_OK) {
     h->assembled = true;

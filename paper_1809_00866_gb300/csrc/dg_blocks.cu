@@ -9,6 +9,9 @@
 // blocks per element at P2) are fastest read straight from global memory by many small CTAs.
 // Both use one thread per output row. The smoother uses explicit inverses D^-1, formed once per
 // assembly by Gauss-Jordan elimination in shared memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "dg_async.h"
@@ -17,6 +20,30 @@
 namespace dg {
 
 namespace {
+
+// value of a stored block entry in the arithmetic type R (blocks may be stored narrower)
+template <class R> __device__ __forceinline__ R wide(float v) { return R(v); }
+template <class R> __device__ __forceinline__ R wide(double v) { return R(v); }
+template <class R> __device__ __forceinline__ R wide(__half v) { return R(__half2float(v)); }
+template <class R> __device__ __forceinline__ R wide(__nv_bfloat16 v) { return R(__bfloat162float(v)); }
+
+// two adjacent stored entries (rows i, i + 1 of one column; i even) as R
+template <class R> __device__ __forceinline__ void wide2(const float* p, R& a, R& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = R(v.x); b = R(v.y);
+}
+template <class R> __device__ __forceinline__ void wide2(const double* p, R& a, R& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = R(v.x); b = R(v.y);
+}
+template <class R> __device__ __forceinline__ void wide2(const __half* p, R& a, R& b) {
+  const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+  a = R(v.x); b = R(v.y);
+}
+template <class R> __device__ __forceinline__ void wide2(const __nv_bfloat16* p, R& a, R& b) {
+  const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  a = R(v.x); b = R(v.y);
+}
 
 // In place D -> D^-1 (column-major FP32 blocks, b a multiple of 4) by Gauss-Jordan elimination
 // with partial (row) pivoting, one block per CTA in shared memory (row-major, leading dimension
@@ -122,20 +149,26 @@ __global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float*
 // be null): stages of G consecutive elements, whose inverses (contiguous) arrive by one bulk
 // asynchronous copy into one of two shared-memory buffers while the previous stage is
 // multiplied; stages are dealt to the CTAs round-robin, so neighbouring CTAs stream
-// neighbouring memory. One thread per output row, four independent accumulators.
-template <class R>
-__global__ void __launch_bounds__(256) staged_jacobi_kernel(int ne, int b, int G, const R* __restrict__ A,
-                                                            const R* __restrict__ g, const R* __restrict__ Gx,
-                                                            R alpha, int x_zero, R* __restrict__ x,
-                                                            unsigned* status) {
+// neighbouring memory. A task is two adjacent rows (one paired load per column) over every
+// CS-th column; when a stage has few rows, CS > 1 column slices meet in shared memory.
+constexpr int kJacobiThreads = 512;
+
+template <class R, class S>
+__global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, int b, int G, const S* __restrict__ A,
+                                                                       const R* __restrict__ g,
+                                                                       const R* __restrict__ Gx, R alpha, int x_zero,
+                                                                       R* __restrict__ x, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sraw_[];
   __shared__ uint64_t bar[2];
+  __shared__ R red[2 * kJacobiThreads];  // partial sums of the column slices
   const size_t per = (size_t)b * b;  // values per element
-  R* const buf0 = reinterpret_cast<R*>(sraw_);
-  R* const buf1 = buf0 + (size_t)G * per;
-  R* const rv = buf1 + (size_t)G * per;  // [G][b] residuals of the stage
+  S* const buf0 = reinterpret_cast<S*>(sraw_);
+  S* const buf1 = buf0 + (size_t)G * per;
+  R* const rv = reinterpret_cast<R*>(buf1 + (size_t)G * per);  // [G][b] residuals of the stage
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nstages = (ne + G - 1) / G;
+  const int hb = b / 2;  // row pairs per element
+  const int CS = max(1, min(8, nt / (G * hb)));
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -143,7 +176,7 @@ __global__ void __launch_bounds__(256) staged_jacobi_kernel(int ne, int b, int G
   __syncthreads();
   auto issue = [&](int stg, int slot) {
     const int e0 = stg * G;
-    const unsigned bytes = (unsigned)(min(G, ne - e0) * per * sizeof(R));
+    const unsigned bytes = (unsigned)(min(G, ne - e0) * per * sizeof(S));
     mbar_expect_tx(&bar[slot], bytes);
     bulk_g2s(slot ? buf1 : buf0, A + (size_t)e0 * per, bytes, &bar[slot]);
   };
@@ -168,33 +201,66 @@ __global__ void __launch_bounds__(256) staged_jacobi_kernel(int ne, int b, int G
       }
       return;
     }
-    const R* Ab = slot ? buf1 : buf0;
-    for (int t = tid; t < cnt * b; t += nt) {
-      const int el = t / b, i = t - el * b;
-      const R* Ae = Ab + (size_t)el * per + i;
+    const S* Ab = slot ? buf1 : buf0;
+    const int npairs = cnt * hb;
+    for (int t = tid; t < npairs * CS; t += nt) {
+      const int pr = t % npairs, cs = t / npairs;
+      const int el = pr / hb, i0 = 2 * (pr - el * hb);
+      const S* Ae = Ab + (size_t)el * per + i0;
       const R* re = rv + (size_t)el * b;
-      R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0);
-      int j = 0;
-      for (; j + 3 < b; j += 4) {
-        a0 = fma(Ae[(size_t)j * b], re[j], a0);
-        a1 = fma(Ae[(size_t)(j + 1) * b], re[j + 1], a1);
-        a2 = fma(Ae[(size_t)(j + 2) * b], re[j + 2], a2);
-        a3 = fma(Ae[(size_t)(j + 3) * b], re[j + 3], a3);
+      R a0 = R(0), a1 = R(0), c0 = R(0), c1 = R(0);
+      int j = cs;
+      for (; j + CS < b; j += 2 * CS) {
+        R u0, u1, v0, v1;
+        wide2<R>(Ae + (size_t)j * b, u0, u1);
+        wide2<R>(Ae + (size_t)(j + CS) * b, v0, v1);
+        a0 = fma(u0, re[j], a0);
+        a1 = fma(u1, re[j], a1);
+        c0 = fma(v0, re[j + CS], c0);
+        c1 = fma(v1, re[j + CS], c1);
       }
-      for (; j < b; ++j) a0 = fma(Ae[(size_t)j * b], re[j], a0);
-      R* xe = x + (size_t)e0 * b + t;
-      *xe = (x_zero ? R(0) : *xe) + alpha * ((a0 + a1) + (a2 + a3));
+      if (j < b) {
+        R u0, u1;
+        wide2<R>(Ae + (size_t)j * b, u0, u1);
+        a0 = fma(u0, re[j], a0);
+        a1 = fma(u1, re[j], a1);
+      }
+      a0 += c0;
+      a1 += c1;
+      if (CS == 1) {
+        R* xe = x + (size_t)(e0 + el) * b + i0;
+        xe[0] = (x_zero ? R(0) : xe[0]) + alpha * a0;
+        xe[1] = (x_zero ? R(0) : xe[1]) + alpha * a1;
+      } else {
+        red[2 * t] = a0;
+        red[2 * t + 1] = a1;
+      }
     }
-    __syncthreads();  // both buffers and rv free for the next stage
+    if (CS > 1) {
+      __syncthreads();
+      for (int pr = tid; pr < npairs; pr += nt) {
+        R a0 = R(0), a1 = R(0);
+        for (int cs = 0; cs < CS; ++cs) {
+          a0 += red[2 * (cs * npairs + pr)];
+          a1 += red[2 * (cs * npairs + pr) + 1];
+        }
+        const int el = pr / hb, i0 = 2 * (pr - el * hb);
+        R* xe = x + (size_t)(e0 + el) * b + i0;
+        xe[0] = (x_zero ? R(0) : xe[0]) + alpha * a0;
+        xe[1] = (x_zero ? R(0) : xe[1]) + alpha * a1;
+      }
+    }
+    __syncthreads();  // both buffers, rv and red free for the next stage
   }
 }
 
 // The same row products read straight from global memory: one thread per output row, `epc`
 // elements per CTA (b rows each), the input vectors in shared memory. Loads of one warp cover
 // 32 consecutive rows of a column (coalesced); eight independent accumulators keep eight loads
-// in flight per thread, and small CTAs keep many elements in flight per SM.
-template <class R, int NBLK>
-__global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int epc, const R* __restrict__ A,
+// in flight per thread, and small CTAs keep many elements in flight per SM. (One thread per
+// pair of rows with paired loads halves the threads and was slower: 61 against 45 us at P2.)
+template <class R, int NBLK, class S>
+__global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int epc, const S* __restrict__ A,
                                                            const int* __restrict__ nbr, const R* __restrict__ v,
                                                            const R* __restrict__ w, R alpha, R beta, int x_zero,
                                                            R* __restrict__ y) {
@@ -218,7 +284,7 @@ __global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int ep
     __syncthreads();
     if (tid < cnt * b) {
       const int el = tid / b, i = tid - el * b;
-      const R* Ae = A + (size_t)(e0 + el) * ncol * b + i;
+      const S* Ae = A + (size_t)(e0 + el) * ncol * b + i;
       const R* re = rv + (size_t)el * ncol;
       R a[8];
 #pragma unroll
@@ -226,9 +292,9 @@ __global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int ep
       int q = 0;
       for (; q + 7 < ncol; q += 8) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = fma(__ldg(Ae + (size_t)(q + u) * b), re[q + u], a[u]);
+        for (int u = 0; u < 8; ++u) a[u] = fma(wide<R>(__ldg(Ae + (size_t)(q + u) * b)), re[q + u], a[u]);
       }
-      for (; q < ncol; ++q) a[0] = fma(__ldg(Ae + (size_t)q * b), re[q], a[0]);
+      for (; q < ncol; ++q) a[0] = fma(wide<R>(__ldg(Ae + (size_t)q * b)), re[q], a[0]);
       const R acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
       R* ye = y + (size_t)(e0 + el) * b + i;
       if (NBLK == 1) *ye = (x_zero ? R(0) : *ye) + alpha * acc;
@@ -238,15 +304,16 @@ __global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int ep
   }
 }
 
-template <class R, int NBLK>
-int launch_direct(Handle* h, int b, const R* A, const R* v, const R* w, R alpha, R beta, int x_zero, R* y,
+template <class R, int NBLK, class S>
+int launch_direct(Handle* h, int b, const S* A, const R* v, const R* w, R alpha, R beta, int x_zero, R* y,
                   cudaStream_t st) {
   if (b > 256) return -1;
   const int epc = std::max(1, 256 / b);
   const int threads = 32 * ((epc * b + 31) / 32);
   const size_t smem = sizeof(R) * (size_t)epc * NBLK * b;
   const int grid = (h->ne + epc - 1) / epc;
-  direct_apply_kernel<R, NBLK><<<grid, threads, smem, st>>>(h->ne, b, epc, A, h->nbr, v, w, alpha, beta, x_zero, y);
+  direct_apply_kernel<R, NBLK, S><<<grid, threads, smem, st>>>(h->ne, b, epc, A, h->nbr, v, w, alpha, beta, x_zero,
+                                                               y);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -254,41 +321,86 @@ int launch_direct(Handle* h, int b, const R* A, const R* v, const R* w, R alpha,
 constexpr size_t kStageTarget = 96 * 1024;  // bytes of inverses per stage (one buffer)
 constexpr size_t kSmemLimit = 220 * 1024;    // dynamic shared memory a kernel may take
 
-template <class R>
-int launch_staged_jacobi(Handle* h, int b, const R* A, const R* g, const R* Gx, R alpha, int x_zero, R* x,
+template <class R, class S>
+int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, R alpha, int x_zero, R* x,
                          cudaStream_t st) {
-  const size_t per = (size_t)b * b * sizeof(R);
+  const size_t per = (size_t)b * b * sizeof(S);
   int G = (int)std::max<size_t>(1, kStageTarget / per);
   G = std::max(1, std::min(G, (h->ne + 2 * h->nsm - 1) / (2 * h->nsm)));  // >= 2 stages per SM when possible
   const size_t smem = 2 * (size_t)G * per + (size_t)G * b * sizeof(R);
   if (smem > kSmemLimit || per % 16 != 0) return -1;
   static bool opted = false;  // per template instance; one device per process
   if (!opted) {
-    DG_CUDA(h, cudaFuncSetAttribute(staged_jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DG_CUDA(h, cudaFuncSetAttribute(staged_jacobi_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemLimit));
     opted = true;
   }
   const int nstages = (h->ne + G - 1) / G;
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
   const int grid = std::min(nstages, h->nsm * per_sm);
-  staged_jacobi_kernel<R><<<grid, 256, smem, st>>>(h->ne, b, G, A, g, Gx, alpha, x_zero, x, h->status);
+  staged_jacobi_kernel<R, S><<<grid, kJacobiThreads, smem, st>>>(h->ne, b, G, A, g, Gx, alpha, x_zero, x,
+                                                                h->status);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
 
 }  // namespace
 
+namespace {
+__global__ void narrow_half_kernel(long long n, const float* __restrict__ x, __half* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2half_rn(x[i]);
+}
+__global__ void narrow_bf16_kernel(long long n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+int narrow(Handle* h, int storage, long long n, const float* x, void* y, cudaStream_t st) {
+  const int grid = (int)std::min<long long>((long long)h->nsm * 8, n / 256 + 1);
+  if (storage == DG_PRECOND_FP32_H16)
+    narrow_half_kernel<<<grid, 256, 0, st>>>(n, x, static_cast<__half*>(y));
+  else
+    narrow_bf16_kernel<<<grid, 256, 0, st>>>(n, x, static_cast<__nv_bfloat16*>(y));
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+size_t storage_size(int storage) { return storage == DG_PRECOND_FP32 ? sizeof(float) : 2; }
+}  // namespace
+
+int prepare_blocks16(Handle* h, int storage, cudaStream_t st) {
+  if (h->asm16 == storage) return DG_OK;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->lev[l];
+    const long long nbb = (long long)h->ne * L.b * L.b;
+    if (!L.LU16) DG_CUDA(h, cudaMalloc(&L.LU16, 2 * (size_t)nbb));
+    if (int rc = narrow(h, storage, nbb, L.LUf, L.LU16, st)) return rc;
+    if (l >= 1) {
+      if (!L.Bsr16) DG_CUDA(h, cudaMalloc(&L.Bsr16, 2 * (size_t)nbb * 7));
+      if (int rc = narrow(h, storage, 7 * nbb, L.Bsrf, L.Bsr16, st)) return rc;
+    }
+  }
+  h->asm16 = storage;
+  return DG_OK;
+}
+
 int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
-                    cudaStream_t st) {
+                    int storage, cudaStream_t st) {
   const Level& L = h->lev[lvl];
   cudaEvent_t e0 = nullptr;
   int rc;
   if (lvl == 0 && (rc = prof_begin(h, st, &e0))) return rc;
-  rc = launch_staged_jacobi<float>(h, L.b, L.LUf, g, Gx, omega, x_zero ? 1 : 0, x, st);
+  const int xz = x_zero ? 1 : 0;
+  if (storage == DG_PRECOND_FP32_H16)
+    rc = launch_staged_jacobi<float, __half>(h, L.b, static_cast<const __half*>(L.LU16), g, Gx, omega, xz, x, st);
+  else if (storage == DG_PRECOND_FP32_BF16)
+    rc = launch_staged_jacobi<float, __nv_bfloat16>(h, L.b, static_cast<const __nv_bfloat16*>(L.LU16), g, Gx, omega, xz,
+                                                    x, st);
+  else
+    rc = launch_staged_jacobi<float, float>(h, L.b, L.LUf, g, Gx, omega, xz, x, st);
   if (rc) return rc;
   // algorithmic bytes: the inverses, g, Gx and the old x read once, x written once
   const double vec = (double)h->ne * L.b * sizeof(float);
-  const double bytes = (double)h->ne * L.b * L.b * sizeof(float) + vec * (2 + (Gx ? 1 : 0) + (x_zero ? 0 : 1));
+  const double bytes = (double)h->ne * L.b * L.b * storage_size(storage) + vec * (2 + (Gx ? 1 : 0) + (x_zero ? 0 : 1));
   return lvl == 0 ? prof_end(h, DG_PROF_BJ32, st, e0, bytes) : DG_OK;
 }
 
@@ -298,7 +410,7 @@ int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y
   cudaEvent_t e0 = nullptr;
   int rc;
   if (lvl == 1 && (rc = prof_begin(h, st, &e0))) return rc;
-  rc = launch_direct<R, 7>(h, b, B, x, nullptr, alpha, beta, 0, y, st);
+  rc = launch_direct<R, 7, R>(h, b, B, x, nullptr, alpha, beta, 0, y, st);
   if (rc) return rc;
   // algorithmic bytes: the 7 blocks of every row, x and the old y read once, y written once
   const double vec = (double)h->ne * b * sizeof(R);
@@ -307,6 +419,22 @@ int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y
 }
 template int staged_bsr<float>(Handle*, int, const float*, float, const float*, float, float*, cudaStream_t);
 template int staged_bsr<double>(Handle*, int, const double*, double, const double*, double, double*, cudaStream_t);
+
+int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float beta, float* y, cudaStream_t st) {
+  const Level& L = h->lev[lvl];
+  cudaEvent_t e0 = nullptr;
+  int rc;
+  if (lvl == 1 && (rc = prof_begin(h, st, &e0))) return rc;
+  if (storage == DG_PRECOND_FP32_H16)
+    rc = launch_direct<float, 7, __half>(h, L.b, static_cast<const __half*>(L.Bsr16), x, nullptr, alpha, beta, 0, y, st);
+  else
+    rc = launch_direct<float, 7, __nv_bfloat16>(h, L.b, static_cast<const __nv_bfloat16*>(L.Bsr16), x, nullptr, alpha,
+                                                beta, 0, y, st);
+  if (rc) return rc;
+  const double vec = (double)h->ne * L.b * sizeof(float);
+  const double bytes = 7.0 * h->ne * L.b * L.b * 2 + vec * (2 + (beta != 0.0f ? 1 : 0));
+  return lvl == 1 ? prof_end(h, DG_PROF_BSR32, st, e0, bytes) : DG_OK;
+}
 
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {

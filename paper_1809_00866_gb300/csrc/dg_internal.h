@@ -79,6 +79,9 @@ struct Level {
   float* t0f = nullptr;
   float* t1f = nullptr;
   float* t2f = nullptr;
+  // 16-bit copies of LUf and Bsrf (FP16 or bfloat16, Handle::asm16 says which)
+  void* LU16 = nullptr;
+  void* Bsr16 = nullptr;
 };
 
 struct Handle {
@@ -106,6 +109,7 @@ struct Handle {
   bool lin_f_ready = false;      // the FP32 copies match the current linearisation
   bool asm_f_ready = false;      // the FP32 factors / blocks match the current assembly
   bool asm64_ready = false;      // the FP64 factors / blocks match the current assembly
+  int asm16 = 0;                 // storage type of the 16-bit block copies that match it (0: none)
   // linearisation cache
   bool linearized = false;
   bool assembled = false;
@@ -223,7 +227,9 @@ int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st
 // explicit inverses in Level::LUf (invert_levels_f32 turns the FP32 blocks held there into them).
 int invert_levels_f32(Handle* h, cudaStream_t st);
 int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
-                    cudaStream_t st);  // x <- (x_zero ? 0 : x) + omega D^-1 (g - Gx); Gx may be null
+                    int storage, cudaStream_t st);  // x <- (x_zero ? 0 : x) + omega D^-1 (g - Gx); Gx may be null
+int prepare_blocks16(Handle* h, int storage, cudaStream_t st);  // LUf, Bsrf -> 16-bit copies
+int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float beta, float* y, cudaStream_t st);
 template <class R>
 int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y, cudaStream_t st);  // -1: n/a
 

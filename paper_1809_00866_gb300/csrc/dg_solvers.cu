@@ -605,9 +605,17 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
   return DG_OK;
 }
 
-static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, cudaStream_t st) {
+static bool is16(int precision) { return precision == DG_PRECOND_FP32_H16 || precision == DG_PRECOND_FP32_BF16; }
+
+// y = G_lvl x in the FP32 cycle; `storage` (the cycle's precision) says how the blocks are stored
+static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, int storage, cudaStream_t st) {
   if (lvl == 0) return op_tangent_f32(h, x, y, st);
   const Level& L = h->lev[lvl];
+  if (is16(storage)) {
+    const int r16 = bsr16_f(h, lvl, storage, 1.0f, x, 0.0f, y, st);
+    if (r16 >= 0) return r16;
+    return fail(h, DG_ERR_ARG, "block size unsuited to the 16-bit block-sparse product");
+  }
   const int rc = staged_bsr<float>(h, lvl, L.Bsrf, 1.0f, x, 0.0f, y, st);
   if (rc >= 0) return rc;
   bsr_kernel<float><<<grid_for(h, h->ne), 128, sizeof(float) * 7 * L.b, st>>>(h->ne, L.b, h->nbr, L.Bsrf, 1.0f, x,
@@ -617,13 +625,14 @@ static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, cudaStre
 }
 
 static int jacobi_sweeps_f(Handle* h, int lvl, const float* g, float* x, int sweeps, float omega, bool x_zero,
+                           int storage,
                            cudaStream_t st) {
   Level& L = h->lev[lvl];
   for (int s = 0; s < sweeps; ++s) {
     const bool zero = x_zero && s == 0;
     int rc;
-    if (!zero && (rc = level_matvec_f(h, lvl, x, L.t2f, st))) return rc;
-    rc = staged_jacobi_f(h, lvl, g, zero ? nullptr : L.t2f, omega, zero, x, st);
+    if (!zero && (rc = level_matvec_f(h, lvl, x, L.t2f, storage, st))) return rc;
+    rc = staged_jacobi_f(h, lvl, g, zero ? nullptr : L.t2f, omega, zero, x, storage, st);
     if (rc < 0) return fail(h, DG_ERR_ARG, "element block too large for the FP32 smoother");
     if (rc) return rc;
   }
@@ -641,22 +650,22 @@ static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const
     if ((rc = record_coarse_f(h, g, st))) return rc;
     if (o.coarse_solver == DG_COARSE_LEARNED) {
       if ((rc = learned_coarse<float>(h, g, x, false, st))) return rc;
-      return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, false, st);
+      return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, false, o.precision, st);
     }
     if (o.coarse_solver == DG_COARSE_LEARNED_ITER) {  // x <- x + N(g - G x)
       Level& C = h->lev[l];
       if ((rc = learned_coarse<float>(h, g, x, false, st))) return rc;
       for (int it = 0; it < o.coarse_sweeps; ++it) {
-        if ((rc = level_matvec_f(h, l, x, C.t2f, st))) return rc;
+        if ((rc = level_matvec_f(h, l, x, C.t2f, o.precision, st))) return rc;
         axpby_kernel<float><<<grid_for(h, C.n / 256 + 1), 256, 0, st>>>(C.n, 1.0f, g, -1.0f, C.t2f);
         DG_LAUNCH_CHECK(h);
         if ((rc = learned_coarse<float>(h, C.t2f, x, true, st))) return rc;
       }
       return DG_OK;
     }
-    return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, true, st);
+    return jacobi_sweeps_f(h, l, g, x, o.coarse_sweeps, om, true, o.precision, st);
   }
-  if ((rc = jacobi_sweeps_f(h, l, g, x, o.pre_sweeps, om, x_zero, st))) return rc;
+  if ((rc = jacobi_sweeps_f(h, l, g, x, o.pre_sweeps, om, x_zero, o.precision, st))) return rc;
   Level& L = h->lev[l];
   Level& C = h->lev[l + 1];
   const bool xz = x_zero && o.pre_sweeps == 0;
@@ -664,7 +673,7 @@ static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const
     restrict_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, g, C.t0f);
     DG_LAUNCH_CHECK(h);
   } else {
-    if ((rc = level_matvec_f(h, l, x, L.t2f, st))) return rc;
+    if ((rc = level_matvec_f(h, l, x, L.t2f, o.precision, st))) return rc;
     axpby_kernel<float><<<grid_for(h, L.n / 256 + 1), 256, 0, st>>>(L.n, 1.0f, g, -1.0f, L.t2f);
     DG_LAUNCH_CHECK(h);
     restrict_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, L.t2f, C.t0f);
@@ -674,13 +683,14 @@ static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const
   if (xz) DG_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * L.n, st));
   prolong_add_kernel<float><<<grid_for(h, C.n / 64 + 1), 256, 0, st>>>(h->ne, L.nb, C.nb, C.t1f, x);
   DG_LAUNCH_CHECK(h);
-  return jacobi_sweeps_f(h, l, g, x, o.post_sweeps, om, false, st);
+  return jacobi_sweeps_f(h, l, g, x, o.post_sweeps, om, false, o.precision, st);
 }
 
 // z = MG_V(v) with the cycle in FP32: v rounded to FP32, the result widened to FP64.
 static int vcycle_fp32(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st) {
   int rc;
   if ((rc = prepare_fp32(h, st))) return rc;
+  if (is16(o.precision) && (rc = prepare_blocks16(h, o.precision, st))) return rc;
   Level& L0 = h->lev[0];
   convert_kernel<double, float><<<grid_for(h, L0.n / 256 + 1), 256, 0, st>>>(L0.n, v, L0.t0f);
   DG_LAUNCH_CHECK(h);
@@ -699,9 +709,9 @@ static int check_opts(Handle* h, const dg_solve_opts* o) {
   if (o->pre_sweeps < 0 || o->post_sweeps < 0 || o->coarse_sweeps < 0) return fail(h, DG_ERR_ARG, "negative sweeps");
   if (!(o->omega > 0.0 && o->omega <= 1.0)) return fail(h, DG_ERR_ARG, "omega must be in (0, 1]");
   if (o->smoother != DG_SMOOTH_JACOBI && o->smoother != DG_SMOOTH_GMRES) return fail(h, DG_ERR_ARG, "unknown smoother");
-  if (o->precision != DG_PRECOND_FP64 && o->precision != DG_PRECOND_FP32)
+  if (o->precision != DG_PRECOND_FP64 && o->precision != DG_PRECOND_FP32 && !is16(o->precision))
     return fail(h, DG_ERR_ARG, "unknown preconditioner precision");
-  if (o->precision == DG_PRECOND_FP32 && (o->smoother != DG_SMOOTH_JACOBI || o->precond == DG_PREC_FULLV))
+  if (o->precision != DG_PRECOND_FP64 && (o->smoother != DG_SMOOTH_JACOBI || o->precond == DG_PREC_FULLV))
     return fail(h, DG_ERR_ARG, "the FP32 preconditioner supports block-Jacobi smoothing in V-cycles only");
   if (o->coarse_solver != DG_COARSE_SMOOTHER && o->coarse_solver != DG_COARSE_GMRES &&
       o->coarse_solver != DG_COARSE_LEARNED && o->coarse_solver != DG_COARSE_LEARNED_ITER)
@@ -730,7 +740,7 @@ static int apply_prec(Handle* h, const dg_solve_opts& o, const double* v, double
   if (o.precision == DG_PRECOND_FP64 && !h->asm64_ready)
     return fail(h, DG_ERR_STATE, "the FP64 preconditioner needs an FP64 assembly");
   if (o.precond == DG_PREC_VCYCLE) {
-    if (o.precision == DG_PRECOND_FP32) return vcycle_fp32(h, o, v, z, st);
+    if (o.precision != DG_PRECOND_FP64) return vcycle_fp32(h, o, v, z, st);
     return mg_v(h, 0, v, z, true, o, st);
   }
   if (o.precond == DG_PREC_FULLV) {
@@ -969,7 +979,7 @@ int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* o
   if (rc) return rc;
   if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
   if (!h->assembled) return fail(h, DG_ERR_STATE, "pmg_vcycle needs dg_assemble first");
-  if (opts->precision == DG_PRECOND_FP32) return vcycle_fp32(h, *opts, g, x, as_stream(stream));
+  if (opts->precision != DG_PRECOND_FP64) return vcycle_fp32(h, *opts, g, x, as_stream(stream));
   if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "the FP64 cycle needs an FP64 assembly");
   return mg_v(h, 0, g, x, true, *opts, as_stream(stream));
 }

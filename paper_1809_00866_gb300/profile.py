@@ -5,7 +5,7 @@
         Jacobian actions (face_kernel + vol_kernel per action).
     python -m paper_1809_00866_gb300.profile assemble [--n 16] [--form fp32|fp64]
         one preconditioner assembly after a warm-up one, between cudaProfilerStart/Stop.
-    python -m paper_1809_00866_gb300.profile stage [--n 16] [--form fp32|fp64] [--learned]
+    python -m paper_1809_00866_gb300.profile stage [--n 16] [--form fp32|fp64|h16|bf16] [--learned]
         one implicit stage to rel-res 1e-8 after two warm-up solves; only the timed FGMRES solve
         lies between cudaProfilerStart and cudaProfilerStop (ncu --profile-from-start off).
 
@@ -21,14 +21,15 @@ def main(argv=None):
     ap.add_argument("what", choices=["jv", "stage", "assemble"])
     ap.add_argument("--n", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--form", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "fp64", "h16", "bf16"], default="fp32")
     ap.add_argument("--learned", action="store_true", help="train the coarse network first and use it")
     a = ap.parse_args(argv)
     import torch
 
     import synthetic as S
 
-    from . import DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP64, build, solve_opts
+    from . import (DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP32_BF16, DG_PRECOND_FP32_H16,
+                   DG_PRECOND_FP64, build, solve_opts)
     build()
     un = S.uniform_nodes(a.n)
     levels = [4, 2, 1]
@@ -48,7 +49,7 @@ def main(argv=None):
         print("jv: %d actions, %.3f ms each" % (a.reps, 1e3 * (time.perf_counter() - t0) / a.reps))
         return 0
     if a.what == "assemble":
-        prec = DG_PRECOND_FP32 if a.form == "fp32" else DG_PRECOND_FP64
+        prec = DG_PRECOND_FP64 if a.form == "fp64" else DG_PRECOND_FP32
         g = dg.empty()
         dg.dg_set_linearization_rhs(w, inv, g)
         dg.dg_assemble(precision=prec)
@@ -61,9 +62,13 @@ def main(argv=None):
         torch.cuda.profiler.stop()
         print("assemble (%s): %.4f s" % (a.form, t))
         return 0
-    fp32 = a.form == "fp32"
-    o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.7 if fp32 else 1.0,
-                   precision=DG_PRECOND_FP32 if fp32 else DG_PRECOND_FP64)
+    # the settings of the benchmark's forms: reduced-precision cycles damped 0.9 with 3/3/2
+    # sweeps, the FP64 cycle undamped with 2/2/2
+    prec = {"fp32": DG_PRECOND_FP32, "fp64": DG_PRECOND_FP64, "h16": DG_PRECOND_FP32_H16,
+            "bf16": DG_PRECOND_FP32_BF16}[a.form]
+    low = prec != DG_PRECOND_FP64
+    o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.9 if low else 1.0, pre_sweeps=3 if low else 2,
+                   post_sweeps=3 if low else 2, coarse_sweeps=2, precision=prec)
     if a.learned:
         from . import learned as Lrn
         states = [w.clone()]

@@ -265,3 +265,39 @@ def test_lagged_preconditioner():
     Gb = O.dense_G(m, wb, inv)
     gr = host(g).reshape(-1)
     assert np.linalg.norm(gr - Gb @ host(x).reshape(-1)) <= 2e-9 * np.linalg.norm(gr)
+
+
+@pytest.mark.parametrize("name,levels", [("u3", [2, 1]), ("box233", [4, 2, 1])])
+@pytest.mark.parametrize("storage,bound", [("H16", 5e-3), ("BF16", 4e-2)])
+def test_16bit_block_storage(name, levels, storage, bound):
+    # the FP32 cycle with its block inverses and block-sparse operators stored in 16 bits and
+    # multiplied with FP32 accumulation: each stored entry carries a relative rounding error of
+    # at most 2^-11 (FP16) or 2^-8 (bfloat16), which the cycle passes on to its result; the
+    # bounds are 10x those unit roundoffs
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    lv = [SV.Level(lambda v, G=G: G @ v, D, m.ne, nb) for G, D, nb in zip(Gs, Ds, nbs)]
+    g = -O.residual(m, w).reshape(-1)
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g))
+    prec = getattr(P, "DG_PRECOND_FP32_" + storage)
+    x16 = dg.empty()
+    dg.pmg_vcycle(dev(g.reshape(x16.shape)), x16, P.solve_opts(precision=prec))
+    assert rel(host(x16).reshape(-1), ref) < bound
+
+
+def test_16bit_block_storage_reaches_fp64_accuracy():
+    # FGMRES stays FP64: with FP16 block storage in the cycle one implicit stage of the 4^3 P2
+    # Taylor-Green workload still reaches 1e-10, checked with the oracle's exact operator
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()["u4"], [2, 1])
+    w = O.project_tgv(m)
+    inv = 1.0 / S.acoustic_dt(4, 2)
+    g = dg.empty()
+    dg.dg_set_linearization_rhs(dev(w), inv, g)
+    dg.dg_assemble(precision=P.DG_PRECOND_FP32_H16)
+    x = dg.empty()
+    info, rc = dg.fgmres_solve(g, x, P.solve_opts(rtol=1e-10, maxit=300, omega=0.7,
+                                                   precision=P.DG_PRECOND_FP32_H16))
+    assert rc == P.DG_OK
+    G0 = O.dense_G(m, w, inv)
+    gr = host(g).reshape(-1)
+    assert np.linalg.norm(gr - G0 @ host(x).reshape(-1)) / np.linalg.norm(gr) < 1e-9
