@@ -45,6 +45,21 @@ def inherited_operator(G0, ne, nb0, nbl):
     return G0[np.ix_(idx, idx)].copy()
 
 
+def stb_scaling(k0, kl, d=3):
+    """Scaling factor S_0^l = k_l (k_l + d) / (k_0 (k_0 + d)) of the stabilisation term on level l
+    (Appendix A: the trace-inequality constant grows like k (k + d))."""
+    return kl * (kl + d) / (k0 * (k0 + d))
+
+
+def rescaled_inherited_operator(G0, Gstb, ne, nb0, nbl, k0, kl, d=3):
+    """Rescaled inherited coarse operator of Appendix A: the Galerkin projection of the fine
+    operator with its viscous stabilisation part Gstb (the BR2 penalty terms) weighted by S_0^l:
+    M (G0 - Gstb) M^T + S_0^l M Gstb M^T."""
+    idx = coarse_index(ne, nb0, nbl)
+    S = stb_scaling(k0, kl, d)
+    return G0[np.ix_(idx, idx)] + (S - 1.0) * Gstb[np.ix_(idx, idx)]
+
+
 def diag_blocks(G, ne, nb):
     """Element diagonal blocks of G (block size 4*nb)."""
     b = 4 * nb

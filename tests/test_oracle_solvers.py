@@ -141,3 +141,36 @@ def test_gmres_smoother_is_the_krylov_minimiser(setup3, iters):
     res = lambda y: np.linalg.norm(SV.apply_block_inverse(D, g - G0 @ y))
     assert res(got) <= res(x0) * (1 + 1e-12)
 
+
+
+def test_stabilisation_part_and_its_rescaling():
+    # The viscous stabilisation (BR2 penalty) part of G is G(eta) - G(0): linear in eta, and a
+    # symmetric positive semidefinite form (eta times the lifted jumps' inner product, Sec. 2.1,
+    # Appendix A). The rescaled inherited operator reduces to the inherited one for S = 1 and
+    # scales exactly that part by S_0^l = k_l (k_l + 3) / (k_0 (k_0 + 3)).
+    n, k = 2, 2
+    xs = S.uniform_nodes(n)
+    w = None
+    Gs = {}
+    for eta in (0.0, 7.0, 14.0):
+        m = O.Mesh(xs, xs, xs, k, S.NU_TGV, S.AC_C, eta)
+        if w is None:
+            w = O.project_tgv(m) + S.perturbation(m.ne, k, 0.1, 4)
+        Gs[eta] = O.dense_G(m, w, 0.5)
+    stb = Gs[7.0] - Gs[0.0]
+    np.testing.assert_allclose(Gs[14.0] - Gs[0.0], 2.0 * stb, atol=1e-11 * np.abs(stb).max())
+    np.testing.assert_allclose(stb, stb.T, atol=1e-12 * np.abs(stb).max())
+    assert np.linalg.eigvalsh(0.5 * (stb + stb.T)).min() > -1e-10 * np.abs(stb).max()
+    # only the velocity rows and columns carry it (the penalty acts on the velocity jumps)
+    nb = O.nb(k)
+    p_idx = [e * 4 * nb + 3 * nb + j for e in range(m.ne) for j in range(nb)]
+    assert np.abs(stb[p_idx]).max() == 0.0 and np.abs(stb[:, p_idx]).max() == 0.0
+    assert abs(SV.stb_scaling(4, 2) - 10.0 / 28.0) < 1e-15 and SV.stb_scaling(3, 3) == 1.0
+    G = Gs[7.0]
+    nbc = O.nb(1)
+    np.testing.assert_array_equal(SV.rescaled_inherited_operator(G, stb, m.ne, nb, nb, k, k),
+                                  SV.inherited_operator(G, m.ne, nb, nb))
+    Gr = SV.rescaled_inherited_operator(G, stb, m.ne, nb, nbc, k, 1)
+    Gi = SV.inherited_operator(G, m.ne, nb, nbc)
+    Si = SV.inherited_operator(stb, m.ne, nb, nbc)
+    np.testing.assert_allclose(Gr - Gi, (SV.stb_scaling(k, 1) - 1.0) * Si, atol=1e-14 * np.abs(G).max())
