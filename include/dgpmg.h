@@ -200,6 +200,14 @@ int dg_assemble(dg_handle* h, void* stream);
  * the FP32 preconditioner cycle only. Synchronises. */
 int dg_assemble_precision(dg_handle* h, int precision, void* stream);
 
+/* Rescaled-inherited coarse operators (Appendix A): enable != 0 makes every later assembly
+ * weight the viscous stabilisation part (the BR2 penalty terms, the part of G proportional to
+ * eta) of each inherited coarse operator by S_0^l = k_l (k_l + 3) / (k_0 (k_0 + 3)):
+ * G_l = M (G_0 - G_stb) M^T + S_0^l M G_stb M^T. The fine level is unchanged. The first
+ * assembly after enabling probes G_stb's level-1 block rows once (G(eta) - G(0), FP64).
+ * Off by default (plain Galerkin inheritance). Invalidates the current assembly. */
+int dg_set_stb_rescaling(dg_handle* h, int enable);
+
 /* Preconditioner lagging (Sec. 4.1, T3L1 case): keep the element blocks, their factors and the
  * coarse block-sparse operators assembled at an earlier linearisation for the current one (the
  * paper freezes them for several time steps). The matrix-free fine-level products of the cycle

@@ -52,7 +52,7 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_mlp_workspace_bytes", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_adam", "dg_set_coarse_network",
            "dg_coarse_pairs", "dg_record_coarse", "dg_recorded", "pmg_project_pressure",
            "bsr_spmv_t", "dg_coarse_apply", "dg_profile_read_bytes",
-           "dg_reuse_assembly", "dg_set_linearization_rhs")
+           "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling")
 DG_PROF_N = 10
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32", "bj32_fine", "bsr32_l1",
               "bj64_fine", "bsr64_l1")
@@ -132,6 +132,7 @@ def load(path=None):
     L.dg_profile_read_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]
     L.dg_reuse_assembly.argtypes = [vp]
+    L.dg_set_stb_rescaling.argtypes = [vp, i]
     L.dg_set_linearization_rhs.argtypes = [vp, vp, d, vp, vp]
     for name in EXPORTS:
         if name != "dg_last_error":
@@ -349,6 +350,9 @@ class DG:
 
     def dg_reuse_assembly(self):
         self._chk(self._L.dg_reuse_assembly(self.h))
+
+    def dg_set_stb_rescaling(self, enable=True):
+        self._chk(self._L.dg_set_stb_rescaling(self.h, 1 if enable else 0))
 
     def pmg_level_solve(self, lvl, g, x, rtol=1e-8, maxit=1000, x0_is_zero=True, stream=None, check=True):
         info = DgSolveInfo()

@@ -259,6 +259,7 @@ static void free_all(Handle* h) {
   if (h->hcol_host) cudaFreeHost(h->hcol_host);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) F(h->smV[l]);
   F(h->smSmall);
+  F(h->stb1);
   F(h->net);
 }
 
@@ -373,6 +374,16 @@ int dg_destroy(dg_handle* hh) {
   cudaDeviceSynchronize();
   free_all(h);
   delete h;
+  return DG_OK;
+}
+
+int dg_set_stb_rescaling(dg_handle* hh, int enable) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (enable && h->nlev < 2) return fail(h, DG_ERR_ARG, "the rescaling acts on coarse levels: needs two or more");
+  h->stb_rescale = enable != 0;
+  h->assembled = h->asm64_ready = h->asm_f_ready = false;  // the coarse operators change
+  h->asm16 = 0;
   return DG_OK;
 }
 

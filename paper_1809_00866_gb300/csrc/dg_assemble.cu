@@ -309,6 +309,45 @@ __global__ void scatter_offdiag_kernel(int ne, int nb0, int nb1, const int* nbr,
   }
 }
 
+// Row-block probing: for every element p, slot 0 (p itself, when p has colour c) and each face
+// slot f whose neighbour e = nbr[p][f] has colour c (first slot facing e only):
+// A[p][slot][jc][rc] += sign * out[p][fine row of rc] (level-1 modes nb1 of nb0).
+__global__ void scatter_rows_kernel(int ne, int nb0, int nb1, const int* nbr, const int* colour, int c, int jc,
+                                    const double* out, double sign, double* A) {
+  const int b1 = 4 * nb1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)ne * 7 * b1;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / (7 * b1);
+    const int rem = (int)(i - p * 7 * b1), s = rem / b1, rc = rem - s * b1;
+    const int e = s == 0 ? (int)p : nbr[p * 6 + s - 1];
+    if (colour[e] != c) continue;
+    if (s > 0) {
+      bool first = true;
+      for (int g = 0; g < s - 1; ++g)
+        if (nbr[p * 6 + g] == e) first = false;
+      if (!first || e == (int)p) continue;
+    }
+    const int var = rc / nb1, m = rc - var * nb1;
+    A[(((p * 7 + s) * (long long)b1) + jc) * b1 + rc] += sign * out[(p * 4 + var) * nb0 + m];
+  }
+}
+
+// dst block (level-l size, nbl modes) += coef * leading sub-block of the level-1 stabilisation
+// block of the same slot (nb1 modes): the rescaled-inherited correction of Appendix A.
+template <class R>
+__global__ void stb_add_kernel(long long nblocks, int nb1, int nbl, const double* stb, long long stb_stride,
+                               double coef, R* dst, long long dst_stride) {
+  const int b1 = 4 * nb1, bl = 4 * nbl;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblocks * bl * bl;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long blk = i / ((long long)bl * bl);
+    const int t = (int)(i - blk * bl * bl), jc = t / bl, rc = t - jc * bl;
+    const int sj = (jc / nbl) * nb1 + jc % nbl, sr = (rc / nbl) * nb1 + rc % nbl;
+    R& d = dst[blk * dst_stride + t];
+    d = R((double)d + coef * stb[blk * stb_stride + (long long)sj * b1 + sr]);
+  }
+}
+
 // dst block (size bd, nbd modes/variable) = leading sub-block of src block (bs, nbs).
 template <class R>
 __global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const R* src, long long src_stride,
@@ -463,6 +502,42 @@ static int probe_linear_part(Handle* h, cudaStream_t st) {
   return DG_OK;
 }
 
+// The stabilisation part of the level-1 block rows, G(eta) - G(0) probed with the linear part
+// (the eta term is linear and state independent), distance-2 colouring.
+static int probe_stb(Handle* h, cudaStream_t st) {
+  const int ne = h->ne;
+  Level& L0 = h->lev[0];
+  Level& L1 = h->lev[1];
+  const int b0 = L0.b, b1 = L1.b;
+  const int grid = h->nsm * 8;
+  int rc;
+  if (!h->stb1) DG_CUDA(h, cudaMalloc((void**)&h->stb1, sizeof(double) * (size_t)b1 * b1 * 7 * ne));
+  DG_CUDA(h, cudaMemsetAsync(h->stb1, 0, sizeof(double) * (size_t)b1 * b1 * 7 * ne, st));
+  if (!h->colour) DG_CUDA(h, cudaMalloc((void**)&h->colour, sizeof(int) * ne));
+  int* dcol = h->colour;
+  double* probe = L0.t0;
+  double* out = L0.t1;
+  const std::vector<int> c2 = greedy_colouring(h, 2);
+  const int nc2 = *std::max_element(c2.begin(), c2.end()) + 1;
+  DG_CUDA(h, cudaMemcpyAsync(dcol, c2.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+  const double eta = h->p.eta;
+  for (int pass = 0; pass < 2; ++pass) {
+    h->p.eta = pass == 0 ? eta : 0.0;
+    for (int c = 0; c < nc2; ++c)
+      for (int jc = 0; jc < b1; ++jc) {
+        const int jf = (jc / L1.nb) * L0.nb + jc % L1.nb;
+        probe_kernel<<<grid, 256, 0, st>>>(L0.n, b0, dcol, c, jf, probe);
+        DG_LAUNCH_CHECK(h);
+        if ((rc = op_linear_part(h, probe, out, st))) { h->p.eta = eta; return rc; }
+        scatter_rows_kernel<<<grid, 256, 0, st>>>(ne, L0.nb, L1.nb, h->nbr, dcol, c, jc, out,
+                                                  pass == 0 ? 1.0 : -1.0, h->stb1);
+        DG_LAUNCH_CHECK(h);
+      }
+  }
+  h->p.eta = eta;
+  return DG_OK;
+}
+
 static int alloc_fp32_levels(Handle* h) {
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];
@@ -492,12 +567,21 @@ static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* co
   if (rc) return rc;
   const Level& L0 = h->lev[0];
   const int b0 = L0.b;
-  // coarse levels: inherited sub-blocks (taken before the fine blocks are factored in place)
+  // coarse levels: inherited sub-blocks (taken before the fine blocks are factored in place);
+  // with the rescaling of Appendix A, the stabilisation part of level l is weighted by S_0^l
+  const int k0 = L0.k, nb1 = h->nlev > 1 ? h->lev[1].nb : 0, b1 = 4 * nb1;
+  double s_prev = 1.0;
   for (int l = 1; l < h->nlev; ++l) {
     Level& L = h->lev[l];
     const size_t bb = (size_t)L.b * L.b;
+    const double S = (double)(L.k * (L.k + 3)) / (double)(k0 * (k0 + 3));
     subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, Dlev[0], (long long)b0 * b0, Dlev[l], (long long)bb);
     DG_LAUNCH_CHECK(h);
+    if (h->stb_rescale) {
+      stb_add_kernel<R><<<grid, 256, 0, st>>>(ne, nb1, L.nb, h->stb1, (long long)b1 * b1 * 7, S - 1.0, Dlev[l],
+                                              (long long)bb);
+      DG_LAUNCH_CHECK(h);
+    }
     subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L.nb, L.nb, Dlev[l], (long long)bb, Bsrlev[l], (long long)bb * 7);
     DG_LAUNCH_CHECK(h);
     if (l >= 2) {
@@ -508,6 +592,14 @@ static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* co
         DG_LAUNCH_CHECK(h);
       }
     }
+    if (h->stb_rescale)  // off-diagonal slots: level 1 carries S - 1, level l >= 2 inherits s_prev - 1
+      for (int s = 1; s < 7; ++s) {
+        stb_add_kernel<R><<<grid, 256, 0, st>>>(ne, nb1, L.nb, h->stb1 + (size_t)s * b1 * b1, (long long)b1 * b1 * 7,
+                                                l == 1 ? S - 1.0 : S - s_prev, Bsrlev[l] + (size_t)s * bb,
+                                                (long long)bb * 7);
+        DG_LAUNCH_CHECK(h);
+      }
+    s_prev = S;
   }
   return DG_OK;
 }
@@ -523,6 +615,10 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
   if (!h->linpart_ready) {
     if ((rc = probe_linear_part(h, st))) return rc;
     h->linpart_ready = true;
+  }
+  if (h->stb_rescale && !h->stb_ready) {
+    if ((rc = probe_stb(h, st))) return rc;
+    h->stb_ready = true;
   }
   if (precision == DG_PRECOND_FP64) {
     for (int l = 0; l < h->nlev; ++l) {

@@ -114,6 +114,11 @@ struct Handle {
   bool linearized = false;
   bool assembled = false;
   bool linpart_ready = false;  // Dlin / Blin probed (they depend on the mesh only)
+  // rescaled-inherited coarse operators (Appendix A): the stabilisation (BR2 penalty) part of
+  // the level-1 block rows, [ne][7][b1][b1] with slot 0 the diagonal, probed once when enabled
+  bool stb_rescale = false;
+  bool stb_ready = false;
+  double* stb1 = nullptr;
   double inv_gdt = 0.0;
   double* wlin = nullptr;   // [n0]
   double* flin = nullptr;   // [n0] f_h(wlin)

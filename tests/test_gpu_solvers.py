@@ -301,3 +301,31 @@ def test_16bit_block_storage_reaches_fp64_accuracy():
     G0 = O.dense_G(m, w, inv)
     gr = host(g).reshape(-1)
     assert np.linalg.norm(gr - G0 @ host(x).reshape(-1)) / np.linalg.norm(gr) < 1e-9
+
+
+@pytest.mark.parametrize("name,levels", [("u3", [2, 1]), ("box233", [4, 2, 1]), ("u2", [3, 2, 1])])
+def test_rescaled_inherited_coarse_operators(name, levels):
+    # Appendix A: coarse operators with the stabilisation part weighted by S_0^l, against the
+    # oracle's M (G0 + (S - 1) Gstb) M^T with Gstb = G(eta) - G(0); and one V-cycle on them
+    P, dg, m, w, inv, Gs, Ds, nbs = setup(name, levels)
+    dg.dg_set_stb_rescaling(True)
+    dg.dg_assemble()
+    m0 = O.Mesh(m.xn, m.yn, m.zn, m.k, S.NU_TGV, S.AC_C, 0.0)
+    stb = Gs[0] - O.dense_G(m0, w, inv)
+    rng = np.random.default_rng(23)
+    Gr = [Gs[0]]
+    for lvl in range(1, len(levels)):
+        G = SV.rescaled_inherited_operator(Gs[0], stb, m.ne, m.nb, nbs[lvl], levels[0], levels[lvl])
+        Gr.append(G)
+        x = rng.standard_normal(G.shape[0])
+        y = dg.empty(lvl)
+        dg.bsr_spmv(lvl, 1.0, dev(x.reshape(y.shape)), 0.0, y)
+        np.testing.assert_allclose(host(y).reshape(-1), G @ x, rtol=0, atol=1e-12 * np.abs(G).max() * np.abs(x).max() * 40)
+        # the rescaling changed the operator (S < 1 for every coarse level here)
+        assert np.abs(G - SV.inherited_operator(Gs[0], m.ne, m.nb, nbs[lvl])).max() > 1e-6 * np.abs(G).max()
+    lv = [SV.Level(lambda v, G=G: G @ v, SV.block_inverses(G, m.ne, nb), m.ne, nb) for G, nb in zip(Gr, nbs)]
+    g = -O.residual(m, w).reshape(-1)
+    ref = SV.mg_v(lv, 0, g, np.zeros_like(g))
+    x = dg.empty()
+    dg.pmg_vcycle(dev(g.reshape(x.shape)), x, P.solve_opts())
+    assert rel(host(x).reshape(-1), ref) < 1e-12
