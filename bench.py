@@ -534,8 +534,9 @@ def main():
                     help="coarsest-level solve of the chosen form (the learned form is also measured separately)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip training the coarse network")
     ap.add_argument("--learn-steps", type=int, default=2000)
-    ap.add_argument("--stb-rescale", action="store_true",
-                    help="rescale the stabilisation part of the inherited coarse operators (Appendix A)")
+    ap.add_argument("--no-stb-rescale", dest="stb_rescale", action="store_false",
+                    help="keep the plain inherited coarse operators (default: rescale their stabilisation "
+                         "part, Appendix A)")
     ap.add_argument("--lag", type=int, default=2, help="also time the chosen form with the preconditioner "
                                                        "assembled every LAG stages (1: skip)")
     args = ap.parse_args()
