@@ -349,6 +349,73 @@ int dg_recorded(const dg_handle* h, int* count);
 #define DG_NOALLOC_SCRATCH_DOUBLES (1 << 20)
 int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
 
+/* ----------------------------------------------------------------- batching
+ * Many independent implicit-stage solves at once. The paper solves one system per process
+ * group (Sec. 2.3); on one GPU, small problems leave most of the device idle, so a handle can
+ * hold several independent periodic boxes and a plan solves all of them together. */
+
+/* Create a handle holding nprob independent periodic boxes with the degrees, viscosity,
+ * constant and penalty of p (p->nx, ny, nz, xn, yn, zn are ignored).
+ *  - dims: HOST [nprob][3] cells per axis of each box, each >= 2.
+ *  - nodes: HOST array with, box after box, the nx+1, then ny+1, then nz+1 increasing node
+ *    coordinates of that box; copied.
+ * Elements are numbered box after box (x fastest within a box), so every vector of the handle
+ * is the concatenation of the boxes' vectors; dg_problems gives the offsets. Face neighbours
+ * stay within a box. Every element kernel acts on all boxes in one launch. Calls that reduce
+ * over the whole vector (fgmres_solve, DG_JVP_FD, the GMRES smoother or coarse solve,
+ * pmg_level_solve, pmg_project_pressure) return DG_ERR_ARG on a handle of nprob > 1; it is
+ * solved by dg_plan_solve. Synchronises. */
+int dg_create_batch(const dg_params* p, int nprob, const int* dims, const double* nodes, dg_handle** out);
+
+/* Number of problems of h and, if elem_start is not NULL, the HOST array [nprob + 1] of their
+ * first elements (elem_start[nprob] = N_e). */
+int dg_problems(const dg_handle* h, int* nprob, int* elem_start);
+
+/* Per-problem multipliers of the mass shift: problem q solves with 1/(gamma dt_q) =
+ * mult[q] * inv_gamma_dt of dg_set_linearization (default 1). mult: HOST [nprob], finite and
+ * >= 0. The assembled preconditioner holds the shift: assemble again after this call. */
+int dg_set_problem_shifts(dg_handle* h, const double* mult, void* stream);
+
+/* A plan: FGMRES(m) right-preconditioned by the options' cycle for every problem of nh
+ * handles, each problem with its own Krylov space, Hessenberg matrix, Givens rotations and
+ * stopping test ||g_q - G_q x_q|| <= rtol ||g_q - G_q x0_q|| (Sec. 2.3). All problems of a
+ * handle advance in lockstep (a converged problem stops contributing); the reductions are per
+ * problem in a fixed order. The Givens rotations, the tests and the triangular solves run on
+ * the device, so a restart cycle needs no host synchronisation.
+ *  - hs[i], g[i], x[i]: distinct handles and their device vectors (g[i] != x[i]); kept by the
+ *    plan, which must be destroyed before them.
+ *  - opts: as for fgmres_solve, with DG_JVP_TANGENT, block-Jacobi smoothing and the smoother
+ *    (or learned, no fallback) coarse solve.
+ *  - use_graph != 0: the first dg_plan_solve captures the restart cycle of every handle as one
+ *    CUDA graph: the handles become parallel branches, and the Arnoldi step is the body of a
+ *    conditional WHILE node (continue while some problem of the handle is active and j < m).
+ *    Every later solve replays it: one graph launch per restart cycle for the whole batch.
+ *    The graph keeps the pointers of g, x and the handles' buffers; the state, the assembly
+ *    and the vectors' contents may change between solves.
+ *  - use_graph == 0: the same kernels launched one by one, with the loop condition read on
+ *    the host after every step.
+ * Allocates the Krylov workspaces ((2m+6) vectors per handle plus small arrays). */
+typedef struct dg_plan dg_plan;
+int dg_plan_create(int nh, dg_handle* const* hs, const double* const* g, double* const* x,
+                   const dg_solve_opts* opts, int use_graph, dg_plan** out);
+
+/* Solve with the current linearisation and assembly of every handle (x[i] is the initial guess
+ * unless opts.x0_is_zero). Synchronises. DG_ERR_NOT_CONVERGED when some problem missed the
+ * tolerance within opts.maxit steps, DG_ERR_NONFINITE when a Krylov quantity was not finite. */
+int dg_plan_solve(dg_plan* plan, void* stream);
+
+/* Per-problem outcome of handle i's problems after the last solve (HOST arrays of nprob
+ * entries, each may be NULL): Arnoldi steps, true relative residual, converged flag. */
+int dg_plan_result(const dg_plan* plan, int i, int* its, double* relres, int* converged);
+
+/* Restart cycles and maximal Arnoldi steps of the last solve; graph launches so far. */
+int dg_plan_stats(const dg_plan* plan, int* cycles, int* steps, long long* graph_launches);
+
+/* Text of the last error of plan (or of the last failed dg_plan_create when plan is NULL). */
+const char* dg_plan_error(const dg_plan* plan);
+
+int dg_plan_destroy(dg_plan* plan);
+
 /* --------------------------------------------------------- instrumentation
  * The paper profiles its solver per linear system (Sec. 3.1: code profiling
  * over 10 time steps); these calls expose the same information per kernel. */

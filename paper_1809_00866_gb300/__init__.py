@@ -52,7 +52,9 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_mlp_workspace_bytes", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_adam", "dg_set_coarse_network",
            "dg_coarse_pairs", "dg_record_coarse", "dg_recorded", "pmg_project_pressure",
            "bsr_spmv_t", "dg_coarse_apply", "dg_profile_read_bytes",
-           "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling")
+           "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling",
+           "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
+           "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy")
 DG_PROF_N = 10
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32", "bj32_fine", "bsr32_l1",
               "bj64_fine", "bsr64_l1")
@@ -134,8 +136,20 @@ def load(path=None):
     L.dg_reuse_assembly.argtypes = [vp]
     L.dg_set_stb_rescaling.argtypes = [vp, i]
     L.dg_set_linearization_rhs.argtypes = [vp, vp, d, vp, vp]
+    L.dg_create_batch.argtypes = [ctypes.POINTER(DgParams), i, ctypes.POINTER(i), ctypes.POINTER(d),
+                                  ctypes.POINTER(vp)]
+    L.dg_problems.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.dg_set_problem_shifts.argtypes = [vp, ctypes.POINTER(d), vp]
+    L.dg_plan_create.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 ctypes.POINTER(DgSolveOpts), i, ctypes.POINTER(vp)]
+    L.dg_plan_solve.argtypes = [vp, vp]
+    L.dg_plan_result.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(i)]
+    L.dg_plan_stats.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+    L.dg_plan_error.argtypes = [vp]
+    L.dg_plan_error.restype = ctypes.c_char_p
+    L.dg_plan_destroy.argtypes = [vp]
     for name in EXPORTS:
-        if name != "dg_last_error":
+        if name not in ("dg_last_error", "dg_plan_error"):
             getattr(L, name).restype = ctypes.c_int
     L.dg_mlp_workspace_bytes.restype = ctypes.c_longlong
     _lib = L
@@ -220,22 +234,36 @@ class DG:
     contiguous float64 CUDA tensors laid out [element][u, v, w, p][mode].
     """
 
-    def __init__(self, xn, yn, zn, levels, nu, ac_c=1.0, eta=7.0):
+    def __init__(self, xn, yn, zn, levels, nu, ac_c=1.0, eta=7.0, boxes=None):
+        """One periodic box with node coordinates xn, yn, zn; or, with ``boxes`` (a list of
+        (xn, yn, zn) triples, xn etc. None), a handle of several independent boxes
+        (``dg_create_batch``)."""
         import numpy as np
         self._L = load()
-        self._nodes = [np.ascontiguousarray(a, dtype=np.float64) for a in (xn, yn, zn)]
         P = ctypes.POINTER(ctypes.c_double)
         ks = (ctypes.c_int * DG_MAX_LEVELS)(*(list(levels) + [0] * (DG_MAX_LEVELS - len(levels))))
-        self.params = DgParams(len(xn) - 1, len(yn) - 1, len(zn) - 1,
-                               self._nodes[0].ctypes.data_as(P), self._nodes[1].ctypes.data_as(P),
-                               self._nodes[2].ctypes.data_as(P), len(levels), ks, nu, ac_c, eta)
         h = ctypes.c_void_p()
-        rc = self._L.dg_create(ctypes.byref(self.params), ctypes.byref(h))
+        if boxes is None:
+            self._nodes = [np.ascontiguousarray(a, dtype=np.float64) for a in (xn, yn, zn)]
+            self.params = DgParams(len(xn) - 1, len(yn) - 1, len(zn) - 1,
+                                   self._nodes[0].ctypes.data_as(P), self._nodes[1].ctypes.data_as(P),
+                                   self._nodes[2].ctypes.data_as(P), len(levels), ks, nu, ac_c, eta)
+            rc = self._L.dg_create(ctypes.byref(self.params), ctypes.byref(h))
+            self.ne = self.params.nx * self.params.ny * self.params.nz
+        else:
+            dims = np.array([[len(a) - 1 for a in b] for b in boxes], dtype=np.int32).ravel()
+            nodes = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64) for b in boxes for a in b]))
+            self._nodes = [nodes, dims]
+            self.params = DgParams(0, 0, 0, None, None, None, len(levels), ks, nu, ac_c, eta)
+            rc = self._L.dg_create_batch(ctypes.byref(self.params), len(boxes),
+                                         dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), nodes.ctypes.data_as(P),
+                                         ctypes.byref(h))
+            self.ne = int(sum(int(np.prod([len(a) - 1 for a in b])) for b in boxes))
         if rc != DG_OK:
             raise DgError(rc, self._L.dg_last_error(None).decode())
         self.h = h
         self.levels = list(levels)
-        self.ne = self.params.nx * self.params.ny * self.params.nz
+        self.nprob, self.elem_start = self.dg_problems()
         self.nb = []
         self.n = []
         for lvl in range(len(levels)):
@@ -281,6 +309,17 @@ class DG:
             pass
 
     # -- C ABI, one method per entry point
+    def dg_problems(self):
+        n = ctypes.c_int()
+        self._chk(self._L.dg_problems(self.h, ctypes.byref(n), None))
+        es = (ctypes.c_int * (n.value + 1))()
+        self._chk(self._L.dg_problems(self.h, ctypes.byref(n), es))
+        return n.value, list(es)
+
+    def dg_set_problem_shifts(self, mult, stream=None):
+        arr = (ctypes.c_double * self.nprob)(*[float(v) for v in mult])
+        self._chk(self._L.dg_set_problem_shifts(self.h, arr, self._stream(stream)))
+
     def dg_get_status(self, stream=None):
         s = ctypes.c_uint()
         self._chk(self._L.dg_get_status(self.h, ctypes.byref(s), self._stream(stream)))
@@ -414,3 +453,59 @@ class DG:
         if check and rc not in (DG_OK, DG_ERR_NOT_CONVERGED):
             self._chk(rc)
         return info, rc
+
+
+class Plan:
+    """``dg_plan_*``: FGMRES over every problem of several handles, optionally as one CUDA
+    graph. ``dgs``, ``gs``, ``xs``: handles and their right-hand sides / solutions (kept alive
+    by the plan)."""
+
+    def __init__(self, dgs, gs, xs, opts, use_graph=True):
+        self._L = load()
+        self._keep = (list(dgs), list(gs), list(xs))
+        nh = len(dgs)
+        V = ctypes.c_void_p * nh
+        hs = V(*[d.h.value for d in dgs])
+        gp = V(*[d._ptr(g).value for d, g in zip(dgs, gs)])
+        xp = V(*[d._ptr(x).value for d, x in zip(dgs, xs)])
+        self.opts = opts
+        p = ctypes.c_void_p()
+        rc = self._L.dg_plan_create(nh, hs, gp, xp, ctypes.byref(opts), 1 if use_graph else 0, ctypes.byref(p))
+        if rc != DG_OK:
+            raise DgError(rc, self._L.dg_plan_error(None).decode())
+        self.p = p
+        self.nh = nh
+
+    def _chk(self, rc):
+        if rc != DG_OK:
+            raise DgError(rc, self._L.dg_plan_error(self.p).decode())
+        return rc
+
+    def dg_plan_solve(self, stream=None, check=True):
+        rc = self._L.dg_plan_solve(self.p, DG._stream(stream))
+        if check:
+            self._chk(rc)
+        return rc
+
+    def dg_plan_result(self, i):
+        """(its, relres, converged) lists for handle i's problems."""
+        n = self._keep[0][i].nprob
+        its, rr, cv = (ctypes.c_int * n)(), (ctypes.c_double * n)(), (ctypes.c_int * n)()
+        self._chk(self._L.dg_plan_result(self.p, i, its, rr, cv))
+        return list(its), list(rr), [bool(c) for c in cv]
+
+    def dg_plan_stats(self):
+        c, s, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        self._chk(self._L.dg_plan_stats(self.p, ctypes.byref(c), ctypes.byref(s), ctypes.byref(g)))
+        return {"cycles": c.value, "steps": s.value, "graph_launches": g.value}
+
+    def close(self):
+        if getattr(self, "p", None):
+            self._L.dg_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

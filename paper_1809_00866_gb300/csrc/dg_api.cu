@@ -1,4 +1,5 @@
 // Handle management, basis/quadrature tables and the operator entry points of the C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -247,6 +248,7 @@ static void free_all(Handle* h) {
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
   F(h->nbr);
+  F(h->elem_prob); F(h->dshift); F(h->chunk); F(h->chunk_prob); F(h->pchunk0);
   F(h->colour);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
@@ -263,15 +265,39 @@ static void free_all(Handle* h) {
   F(h->net);
 }
 
-static int create(const dg_params* p, Handle* h) {
+__global__ void write_shifts_kernel(int ne, const int* elem_prob, const double* shift, double* geo) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+    geo[(size_t)e * kGeo + 11] = shift[elem_prob[e]];
+}
+
+static int write_shifts(Handle* h, cudaStream_t st) {
+  write_shifts_kernel<<<(h->ne + 255) / 256, 256, 0, st>>>(h->ne, h->elem_prob, h->dshift, h->geo);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+// One periodic box of a handle: cells per axis and host node coordinates per axis.
+struct Box {
+  int n[3];
+  const double* node[3];
+};
+
+// Reduction chunks of about kChunkDoubles level-0 entries, never across two problems.
+constexpr int kChunkDoubles = 2048;
+
+static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) {
   if (!p) return fail(h, DG_ERR_ARG, "null params");
-  const int nn[3] = {p->nx, p->ny, p->nz};
-  const double* nodes[3] = {p->xn, p->yn, p->zn};
-  for (int d = 0; d < 3; ++d) {
-    if (nn[d] < 2) return fail(h, DG_ERR_ARG, "every axis needs at least 2 cells");
-    if (!nodes[d]) return fail(h, DG_ERR_ARG, "null node array");
-    for (int i = 0; i < nn[d]; ++i)
-      if (!(nodes[d][i + 1] > nodes[d][i])) return fail(h, DG_ERR_ARG, "node coordinates must increase");
+  if (boxes.empty()) return fail(h, DG_ERR_ARG, "no problem");
+  long long ne = 0;
+  for (const Box& bx : boxes) {
+    for (int d = 0; d < 3; ++d) {
+      if (bx.n[d] < 2) return fail(h, DG_ERR_ARG, "every axis needs at least 2 cells");
+      if (!bx.node[d]) return fail(h, DG_ERR_ARG, "null node array");
+      for (int i = 0; i < bx.n[d]; ++i)
+        if (!(bx.node[d][i + 1] > bx.node[d][i])) return fail(h, DG_ERR_ARG, "node coordinates must increase");
+    }
+    ne += (long long)bx.n[0] * bx.n[1] * bx.n[2];
+    if (ne > (1LL << 28)) return fail(h, DG_ERR_ARG, "mesh too large");
   }
   if (p->nlevels < 1 || p->nlevels > DG_MAX_LEVELS) return fail(h, DG_ERR_ARG, "nlevels out of range");
   for (int l = 0; l < p->nlevels; ++l) {
@@ -279,44 +305,70 @@ static int create(const dg_params* p, Handle* h) {
     if (l > 0 && p->k[l] >= p->k[l - 1]) return fail(h, DG_ERR_ARG, "degrees must decrease with the level");
   }
   if (!(p->nu > 0.0) || !(p->ac_c > 0.0) || !(p->eta > 0.0)) return fail(h, DG_ERR_ARG, "nu, ac_c, eta must be > 0");
-  const long long ne = (long long)nn[0] * nn[1] * nn[2];
-  if (ne > (1LL << 28)) return fail(h, DG_ERR_ARG, "mesh too large");
   h->p = *p;
   h->p.xn = h->p.yn = h->p.zn = nullptr;
-  for (int d = 0; d < 3; ++d) h->n[d] = nn[d];
+  h->nprob = (int)boxes.size();
+  for (int d = 0; d < 3; ++d) h->n[d] = h->nprob == 1 ? boxes[0].n[d] : 0;  // structured sizes: single box only
   h->ne = (int)ne;
   h->nlev = p->nlevels;
   int dev = 0;
   DG_CUDA(h, cudaGetDevice(&dev));
   DG_CUDA(h, cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
   int rc;
-  for (int d = 0; d < 3; ++d) {
-    h->node[d].assign(nodes[d], nodes[d] + nn[d] + 1);
-    if ((rc = upload(h, &h->dnode[d], h->node[d]))) return rc;
-  }
-  std::vector<int> nbr((size_t)ne * 6);
-  for (long long e = 0; e < ne; ++e) {
-    const int i = (int)(e % nn[0]), j = (int)((e / nn[0]) % nn[1]), k = (int)(e / ((long long)nn[0] * nn[1]));
-    auto id = [&](int a, int b, int c) {
-      a = (a + nn[0]) % nn[0]; b = (b + nn[1]) % nn[1]; c = (c + nn[2]) % nn[2];
-      return a + nn[0] * (b + nn[1] * c);
-    };
-    nbr[e * 6 + 0] = id(i - 1, j, k); nbr[e * 6 + 1] = id(i + 1, j, k);
-    nbr[e * 6 + 2] = id(i, j - 1, k); nbr[e * 6 + 3] = id(i, j + 1, k);
-    nbr[e * 6 + 4] = id(i, j, k - 1); nbr[e * 6 + 5] = id(i, j, k + 1);
+  if (h->nprob == 1)
+    for (int d = 0; d < 3; ++d) h->node[d].assign(boxes[0].node[d], boxes[0].node[d] + boxes[0].n[d] + 1);
+  // elements problem by problem, x fastest within a box; periodic neighbours within the box
+  h->pe0.assign(h->nprob + 1, 0);
+  std::vector<int>& nbr = h->nbr_host;
+  nbr.assign((size_t)ne * 6, 0);
+  std::vector<int> eprob((size_t)ne);
+  std::vector<double> geo((size_t)ne * kGeo, 0.0);
+  for (int q = 0; q < h->nprob; ++q) {
+    const Box& bx = boxes[q];
+    const int* nn = bx.n;
+    const long long e0 = h->pe0[q], nq = (long long)nn[0] * nn[1] * nn[2];
+    h->pe0[q + 1] = (int)(e0 + nq);
+    for (long long el = 0; el < nq; ++el) {
+      const long long e = e0 + el;
+      const int I[3] = {(int)(el % nn[0]), (int)((el / nn[0]) % nn[1]), (int)(el / ((long long)nn[0] * nn[1]))};
+      auto id = [&](int a, int b, int c) {
+        a = (a + nn[0]) % nn[0]; b = (b + nn[1]) % nn[1]; c = (c + nn[2]) % nn[2];
+        return (int)(e0 + a + nn[0] * (b + nn[1] * c));
+      };
+      nbr[e * 6 + 0] = id(I[0] - 1, I[1], I[2]); nbr[e * 6 + 1] = id(I[0] + 1, I[1], I[2]);
+      nbr[e * 6 + 2] = id(I[0], I[1] - 1, I[2]); nbr[e * 6 + 3] = id(I[0], I[1] + 1, I[2]);
+      nbr[e * 6 + 4] = id(I[0], I[1], I[2] - 1); nbr[e * 6 + 5] = id(I[0], I[1], I[2] + 1);
+      eprob[e] = q;
+      double* G = &geo[(size_t)e * kGeo];
+      for (int d = 0; d < 3; ++d) {
+        G[d] = bx.node[d][I[d] + 1] - bx.node[d][I[d]];
+        G[5 + d] = 2.0 / G[d];
+        G[8 + d] = bx.node[d][I[d]];
+      }
+      G[3] = std::sqrt(G[0] * G[1] * G[2] * 0.125);
+      G[4] = 1.0 / G[3];
+      G[11] = 1.0;
+    }
   }
   if ((rc = upload(h, &h->nbr, nbr))) return rc;
-  std::vector<double> geo((size_t)ne * kGeo, 0.0);
-  for (long long e = 0; e < ne; ++e) {
-    const int I[3] = {(int)(e % nn[0]), (int)((e / nn[0]) % nn[1]), (int)(e / ((long long)nn[0] * nn[1]))};
-    double* G = &geo[(size_t)e * kGeo];
-    for (int d = 0; d < 3; ++d) {
-      G[d] = nodes[d][I[d] + 1] - nodes[d][I[d]];
-      G[5 + d] = 2.0 / G[d];
-      G[8 + d] = nodes[d][I[d]];
+  if ((rc = upload(h, &h->elem_prob, eprob))) return rc;
+  if ((rc = upload(h, &h->dshift, std::vector<double>(h->nprob, 1.0)))) return rc;
+  {
+    const int b0 = 4 * nb_of(p->k[0]);
+    const int ce = std::max(1, kChunkDoubles / b0);
+    std::vector<int2> ch;
+    std::vector<int> cp, pc0(h->nprob + 1, 0);
+    for (int q = 0; q < h->nprob; ++q) {
+      pc0[q] = (int)ch.size();
+      for (int e = h->pe0[q]; e < h->pe0[q + 1]; e += ce) {
+        ch.push_back(make_int2(e, std::min(e + ce, h->pe0[q + 1])));
+        cp.push_back(q);
+      }
     }
-    G[3] = std::sqrt(G[0] * G[1] * G[2] * 0.125);
-    G[4] = 1.0 / G[3];
+    pc0[h->nprob] = (int)ch.size();
+    h->nchunk = (int)ch.size();
+    if ((rc = upload(h, &h->chunk, ch)) || (rc = upload(h, &h->chunk_prob, cp)) || (rc = upload(h, &h->pchunk0, pc0)))
+      return rc;
   }
   if ((rc = upload(h, &h->geo, geo))) return rc;
   if ((rc = build_tables(h, p->k[0]))) return rc;
@@ -328,7 +380,6 @@ static int create(const dg_params* p, Handle* h) {
     L.n = ne * L.b;
     if ((rc = dalloc(h, &L.t0, L.n)) || (rc = dalloc(h, &L.t1, L.n)) || (rc = dalloc(h, &L.t2, L.n))) return rc;
   }
-  const int nb0 = h->lev[0].nb;
   const long long n0 = h->lev[0].n;
   const int n2f = h->tab.n2;
   if ((rc = dalloc(h, &h->face_out, (size_t)ne * 6 * 4 * n2f)) || (rc = dalloc(h, &h->face_lift, (size_t)ne * 6 * 3 * n2f)) ||
@@ -357,7 +408,9 @@ int dg_create(const dg_params* p, dg_handle** out) {
   *out = nullptr;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return fail(nullptr, DG_ERR_ARG, "out of host memory");
-  const int rc = create(p, h);
+  std::vector<Box> boxes;
+  if (p) boxes.push_back(Box{{p->nx, p->ny, p->nz}, {p->xn, p->yn, p->zn}});
+  const int rc = create(p, boxes, h);
   if (rc != DG_OK) {
     g_create_error = h->err;
     free_all(h);
@@ -365,6 +418,56 @@ int dg_create(const dg_params* p, dg_handle** out) {
     return rc;
   }
   *out = reinterpret_cast<dg_handle*>(h);
+  return DG_OK;
+}
+
+int dg_create_batch(const dg_params* p, int nprob, const int* dims, const double* nodes, dg_handle** out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "null output handle pointer");
+  *out = nullptr;
+  if (!p || nprob < 1 || !dims || !nodes) return fail(nullptr, DG_ERR_ARG, "null argument or nprob < 1");
+  std::vector<Box> boxes((size_t)nprob);
+  size_t off = 0;
+  for (int q = 0; q < nprob; ++q)
+    for (int d = 0; d < 3; ++d) {
+      boxes[q].n[d] = dims[3 * q + d];
+      if (boxes[q].n[d] < 2) return fail(nullptr, DG_ERR_ARG, "every axis needs at least 2 cells");
+      boxes[q].node[d] = nodes + off;
+      off += (size_t)boxes[q].n[d] + 1;
+    }
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return fail(nullptr, DG_ERR_ARG, "out of host memory");
+  const int rc = create(p, boxes, h);
+  if (rc != DG_OK) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = reinterpret_cast<dg_handle*>(h);
+  return DG_OK;
+}
+
+int dg_problems(const dg_handle* hh, int* nprob, int* elem_start) {
+  const Handle* h = reinterpret_cast<const Handle*>(hh);
+  if (!h || !nprob) return DG_ERR_ARG;
+  *nprob = h->nprob;
+  if (elem_start)
+    for (int q = 0; q <= h->nprob; ++q) elem_start[q] = h->pe0[q];
+  return DG_OK;
+}
+
+int dg_set_problem_shifts(dg_handle* hh, const double* mult, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!mult) return fail(h, DG_ERR_ARG, "null multipliers");
+  for (int q = 0; q < h->nprob; ++q)
+    if (!(mult[q] >= 0.0) || !std::isfinite(mult[q])) return fail(h, DG_ERR_ARG, "multipliers must be finite and >= 0");
+  cudaStream_t st = as_stream(stream);
+  DG_CUDA(h, cudaMemcpyAsync(h->dshift, mult, sizeof(double) * h->nprob, cudaMemcpyHostToDevice, st));
+  if (int rc = write_shifts(h, st)) return rc;
+  DG_CUDA(h, cudaStreamSynchronize(st));
+  h->assembled = h->asm64_ready = h->asm_f_ready = false;  // the blocks hold the shift
+  h->asm16 = 0;
   return DG_OK;
 }
 
@@ -465,7 +568,10 @@ int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) 
   if (!v || !out || v == out) return fail(h, DG_ERR_ARG, "v and out must be distinct non-null device pointers");
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_jvp needs dg_set_linearization first");
   if (mode == DG_JVP_TANGENT) return op_tangent(h, v, out, as_stream(stream));
-  if (mode == DG_JVP_FD) return op_fd(h, v, out, as_stream(stream));
+  if (mode == DG_JVP_FD) {
+    if (h->nprob > 1) return fail(h, DG_ERR_ARG, "the FD step size is global: one problem per handle only");
+    return op_fd(h, v, out, as_stream(stream));
+  }
   return fail(h, DG_ERR_ARG, "unknown jvp mode");
 }
 

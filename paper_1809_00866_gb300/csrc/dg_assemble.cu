@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
         for (int t = tid; t < NB * NB; t += nt) {
           const int n = t / NB, m = t - n * NB;  // column-major within the pair: consecutive threads, consecutive rows
           R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
-          if (i == j && i < 3 && m == n) v += R(a.inv_gdt);
+          if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
           if (i < 3 && j < 3) {
             // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
             R cv = R(0);
@@ -232,19 +232,9 @@ static int launch_assemble_state(Handle* h, const AsmArgs<R>& a, cudaStream_t st
 
 static std::vector<int> greedy_colouring(const Handle* h, int dist) {
   const int ne = h->ne;
-  std::vector<int> nb6((size_t)ne * 6);
-  for (int e = 0; e < ne; ++e) {
-    const int i = e % h->n[0], j = (e / h->n[0]) % h->n[1], k = e / (h->n[0] * h->n[1]);
-    auto id = [&](int a, int b, int c) {
-      a = (a + h->n[0]) % h->n[0]; b = (b + h->n[1]) % h->n[1]; c = (c + h->n[2]) % h->n[2];
-      return a + h->n[0] * (b + h->n[1] * c);
-    };
-    nb6[e * 6 + 0] = id(i - 1, j, k); nb6[e * 6 + 1] = id(i + 1, j, k);
-    nb6[e * 6 + 2] = id(i, j - 1, k); nb6[e * 6 + 3] = id(i, j + 1, k);
-    nb6[e * 6 + 4] = id(i, j, k - 1); nb6[e * 6 + 5] = id(i, j, k + 1);
-  }
+  const std::vector<int>& nb6 = h->nbr_host;
   std::vector<int> col(ne, -1);
-  if (dist == 2 && h->n[0] % 8 == 0 && h->n[1] % 8 == 0 && h->n[2] % 8 == 0) {
+  if (dist == 2 && h->nprob == 1 && h->n[0] % 8 == 0 && h->n[1] % 8 == 0 && h->n[2] % 8 == 0) {
     // (i + 2j + 3k) mod 8: the six neighbour offsets +-1, +-2, +-3 are distinct and non-zero mod 8,
     // so no element shares a colour with a neighbour or with a neighbour's neighbour
     for (int e = 0; e < ne; ++e) {

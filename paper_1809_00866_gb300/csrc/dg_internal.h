@@ -93,6 +93,19 @@ struct Handle {
   double* dnode[3] = {nullptr, nullptr, nullptr};
   double* geo = nullptr;        // [ne][kGeo] per-element geometry
   int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z
+  std::vector<int> nbr_host;    // host copy of nbr
+  // independent problems (periodic boxes) sharing the handle: problem p owns the elements
+  // [pe0[p], pe0[p+1]); every face neighbour of an element lies in its own problem
+  int nprob = 1;
+  std::vector<int> pe0;         // host [nprob+1]
+  int* elem_prob = nullptr;     // device [ne] problem of each element
+  double* dshift = nullptr;     // device [nprob] mass-shift multipliers (geo slot 11 holds them per element)
+  // per-problem reduction chunks: chunk c covers the elements [chunk[c].x, chunk[c].y) of
+  // problem chunk_prob[c]; the chunks of problem p are pchunk0[p] .. pchunk0[p+1]-1
+  int nchunk = 0;
+  int2* chunk = nullptr;
+  int* chunk_prob = nullptr;
+  int* pchunk0 = nullptr;
   int* colour = nullptr;        // [ne] element colouring used by the assembly probes
   Tables tab;                   // fine-level tables (the matrix-free level)
   TablesF tabf;                 // their FP32 copies
@@ -184,7 +197,8 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // mesh geometry on the device
 // Per-element geometry, computed once on the host: h[3], s = sqrt(|K|/8) (phi = phi_hat/s),
-// 1/s, J = 2/h[3] (reference-to-physical derivative factors), lower corner lo[3].
+// 1/s, J = 2/h[3] (reference-to-physical derivative factors), lower corner lo[3], and the
+// multiplier of the handle's mass shift 1/(gamma dt) for the element's problem (1 by default).
 constexpr int kGeo = 12;
 struct MeshDev {
   int nx, ny, nz, ne;
@@ -199,6 +213,7 @@ struct ElemGeom {
   double s;      // sqrt(|K|/8)
   double is;     // 1/s
   double J[3];   // 2/h
+  double sh;     // multiplier of the mass shift
 };
 __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
   ElemGeom g;
@@ -208,6 +223,7 @@ __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
   g.is = G[4];
   g.J[0] = G[5]; g.J[1] = G[6]; g.J[2] = G[7];
   g.lo[0] = G[8]; g.lo[1] = G[9]; g.lo[2] = G[10];
+  g.sh = G[11];
   return g;
 }
 
@@ -237,6 +253,11 @@ int prepare_blocks16(Handle* h, int storage, cudaStream_t st);  // LUf, Bsrf -> 
 int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float beta, float* y, cudaStream_t st);
 template <class R>
 int staged_bsr(Handle* h, int lvl, const R* B, R alpha, const R* x, R beta, R* y, cudaStream_t st);  // -1: n/a
+
+// the preconditioner as the batched solver uses it (dg_solvers.cu)
+int solve_opts_check(Handle* h, const dg_solve_opts* o);
+int precond_prepare(Handle* h, const dg_solve_opts& o, cudaStream_t st);  // FP32 / 16-bit copies, eagerly
+int precond_apply(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st);
 
 // learned coarse correction (dg_learned.cu): x <- s_e N(X_e) on the coarsest level
 // (accumulate: x <- x + s_e N(X_e))

@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(128) vol_kernel(OpArgsT<R> a) {
         const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
         acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
       }
-      if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt) * sC[t];
+      if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt * g.sh) * sC[t];
       a.out[(size_t)e * 4 * NB + t] = acc;
     }
     __syncthreads();
@@ -700,12 +700,14 @@ __global__ void fd_perturb_kernel(long long n, const double* w, const double* v,
     out[i] = w[i] + delta * v[i];
 }
 __global__ void fd_finish_kernel(long long n, int nb, const double* f1, const double* f0, const double* v,
-                                 const double* wnorm2, const double* vnorm2, double inv_gdt, double* out) {
+                                 const double* wnorm2, const double* vnorm2, double inv_gdt, const double* geo,
+                                 double* out) {
   const double nv = sqrt(*vnorm2);
   const double delta = nv > 0.0 ? 1e-9 * sqrt(1.0 + sqrt(*wnorm2)) / nv : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int var = (int)((i / nb) & 3);
-    const double mass = var < 3 ? inv_gdt * v[i] : 0.0;
+    const long long e = i / (4 * nb);
+    const double mass = var < 3 ? inv_gdt * geo[e * kGeo + 11] * v[i] : 0.0;
     out[i] = (delta > 0.0 ? (f1[i] - f0[i]) / delta : 0.0) + mass;
   }
 }
@@ -822,7 +824,7 @@ int op_fd(Handle* h, const double* v, double* out, cudaStream_t st) {
   rc = op_residual(h, h->fd_w, h->fd_f, false, st);
   if (rc) return rc;
   fd_finish_kernel<<<blocks, 256, 0, st>>>(n, h->lev[0].nb, h->fd_f, h->flin, v, h->wnorm2, h->red_out,
-                                           h->inv_gdt, out);
+                                           h->inv_gdt, h->geo, out);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }

@@ -726,6 +726,9 @@ static int check_opts(Handle* h, const dg_solve_opts* o) {
     if (o->fallback_its < 0 || (o->fallback_its > 0 && !(o->fallback_rho > 0.0 && o->fallback_rho < 1.0)))
       return fail(h, DG_ERR_ARG, "fallback_its >= 0 and fallback_rho in (0, 1) needed");
   }
+  if (h->nprob > 1 && (o->smoother == DG_SMOOTH_GMRES || o->coarse_solver == DG_COARSE_GMRES || o->jvp_mode == DG_JVP_FD))
+    return fail(h, DG_ERR_ARG, "GMRES smoothing, the GMRES coarse solve and FD products reduce over the whole "
+                               "vector: not available on a handle of several problems");
   if (o->smoother == DG_SMOOTH_GMRES &&
       (o->pre_sweeps > DG_SMOOTH_MAX_ITS || o->post_sweeps > DG_SMOOTH_MAX_ITS || o->coarse_sweeps > DG_SMOOTH_MAX_ITS))
     return fail(h, DG_ERR_ARG, "GMRES smoother iterations above DG_SMOOTH_MAX_ITS");
@@ -914,6 +917,25 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
   return DG_OK;
 }
 
+// Entry points of the preconditioner for the batched solver (dg_batch.cu).
+int solve_opts_check(Handle* h, const dg_solve_opts* o) { return check_opts(h, o); }
+
+int precond_prepare(Handle* h, const dg_solve_opts& o, cudaStream_t st) {
+  if (o.precond == DG_PREC_NONE) return DG_OK;
+  if (o.precision == DG_PRECOND_FP64) {
+    if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "the FP64 preconditioner needs an FP64 assembly");
+    return DG_OK;
+  }
+  int rc;
+  if ((rc = prepare_fp32(h, st))) return rc;
+  if (is16(o.precision) && (rc = prepare_blocks16(h, o.precision, st))) return rc;
+  return DG_OK;
+}
+
+int precond_apply(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st) {
+  return apply_prec(h, o, v, z, st);
+}
+
 }  // namespace dg
 
 using namespace dg;
@@ -988,6 +1010,7 @@ int pmg_project_pressure(dg_handle* hh, int lvl, double* x, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (lvl < 0 || lvl >= h->nlev || !x) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (h->nprob > 1) return fail(h, DG_ERR_ARG, "one problem per handle only");
   cudaStream_t st = as_stream(stream);
   const Level& L = h->lev[lvl];
   pressure_dot_kernel<<<1, 1024, 0, st>>>(h->ne, L.nb, h->geo, x, h->red_out);
@@ -1002,6 +1025,7 @@ int pmg_level_solve(dg_handle* hh, int lvl, const double* g, double* x, double r
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (lvl < 1 || lvl >= h->nlev || !g || !x || g == x) return fail(h, DG_ERR_ARG, "bad level or pointer");
+  if (h->nprob > 1) return fail(h, DG_ERR_ARG, "one problem per handle only");
   if (!(rtol > 0.0) || maxit < 1) return fail(h, DG_ERR_ARG, "bad rtol or maxit");
   if (!h->asm64_ready) return fail(h, DG_ERR_STATE, "pmg_level_solve needs an FP64 dg_assemble first");
   cudaStream_t st = as_stream(stream);
@@ -1057,6 +1081,7 @@ int fgmres_solve(dg_handle* hh, const double* g, double* x, const dg_solve_opts*
   int rc = check_opts(h, opts);
   if (rc) return rc;
   if (!g || !x || g == x) return fail(h, DG_ERR_ARG, "bad pointer");
+  if (h->nprob > 1) return fail(h, DG_ERR_ARG, "a handle of several problems is solved by dg_plan_solve");
   if (opts->restart < 1 || opts->restart > 64) return fail(h, DG_ERR_ARG, "restart must be in 1..64");
   if (opts->fixed_its <= 0 && (opts->maxit < 1 || !(opts->rtol > 0.0))) return fail(h, DG_ERR_ARG, "bad maxit/rtol");
   if (!h->linearized) return fail(h, DG_ERR_STATE, "fgmres_solve needs dg_set_linearization first");
