@@ -347,6 +347,9 @@ class DG:
         else:
             self._chk(self._L.dg_assemble_precision(self.h, int(precision), self._stream(stream)))
 
+    def dg_assemble_precision(self, precision, stream=None):
+        self._chk(self._L.dg_assemble_precision(self.h, int(precision), self._stream(stream)))
+
     def pmg_restrict(self, lvl, xf, xc, stream=None):
         self._chk(self._L.pmg_restrict(self.h, lvl, self._ptr(xf, lvl), self._ptr(xc, lvl + 1), self._stream(stream)))
 

@@ -30,6 +30,7 @@ constexpr int kCtlCond = 1;   // continue the cycle (some problem active and j <
 constexpr int kCtlSteps = 2;  // steps executed in this solve
 constexpr int kCtlDone = 3;   // every problem converged or at its iteration limit
 constexpr int kCtlBad = 4;    // a non-finite Krylov quantity was met
+constexpr int kCtlConv = 5;   // every problem converged
 constexpr int kCtlN = 8;
 
 struct BatchDev {
@@ -258,7 +259,7 @@ __global__ void batch_update_kernel(long long n, int per_e, const int* elem_prob
 
 // After the true residual of a cycle (its squared norms in nrm2): convergence per problem.
 __global__ void __launch_bounds__(1024) batch_cycle_end_kernel(int np, int limit, double rtol, int fixed, BatchDev d) {
-  int undone = 0;
+  int undone = 0, missed = 0;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     const double rn = sqrt(d.nrm2[p]);
     if (!isfinite(rn)) atomicOr(&d.ctl[kCtlBad], 1);
@@ -266,9 +267,14 @@ __global__ void __launch_bounds__(1024) batch_cycle_end_kernel(int np, int limit
     const int c = fixed ? d.its[p] >= limit : (d.beta0[p] == 0.0 || rn <= rtol * d.beta0[p]);
     d.conv[p] = c;
     undone |= !c && d.its[p] < limit && isfinite(rn);
+    missed |= !c;
   }
   undone = __syncthreads_or(undone);
-  if (threadIdx.x == 0) d.ctl[kCtlDone] = !undone;
+  missed = __syncthreads_or(missed);
+  if (threadIdx.x == 0) {
+    d.ctl[kCtlDone] = !undone;
+    d.ctl[kCtlConv] = !missed;
+  }
 }
 
 // ------------------------------------------------------------------ plan
@@ -703,13 +709,14 @@ int dg_plan_solve(dg_plan* pp, void* stream) {
       }
     }
   }
-  int bad = 0;
+  int bad = 0, conv = 1;
   for (auto& b : P->ws) {
     bad |= b.host_ctl[kCtlBad];
+    conv &= b.host_ctl[kCtlConv];
     P->steps = std::max(P->steps, b.host_ctl[kCtlSteps]);
   }
   if (bad) return pfail(P, DG_ERR_NONFINITE, "non-finite Krylov quantity in a problem of the batch");
-  if (!done) return pfail(P, DG_ERR_NOT_CONVERGED, "some problem did not reach the tolerance");
+  if (!done || !conv) return pfail(P, DG_ERR_NOT_CONVERGED, "some problem did not reach the tolerance");
   return DG_OK;
 }
 

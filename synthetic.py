@@ -81,3 +81,16 @@ def acoustic_dt(n, k, cfl=50.0, c=AC_C, umax=1.0, length=TWO_PI):
     """Time step for an acoustic CFL: cfl * h / ((2k+1) * (|u| + sqrt(|u|^2 + c^2)))."""
     h = length / n
     return cfl * h / ((2 * k + 1) * (umax + math.sqrt(umax * umax + c * c)))
+
+
+# Batch of independent periodic Taylor-Green boxes of uneven size and degree: n^3 cells with
+# n drawn uniformly from 4..12, k uniformly from {2, 3, 4}; p-levels per degree.
+BATCH_LEVELS = {2: (2, 1), 3: (3, 2, 1), 4: (4, 2, 1)}
+
+
+def batch_boxes(count=64, seed=64, n_min=4, n_max=12, degrees=(2, 3, 4)):
+    """List of (n, k) for the batch workload (seeded)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_min, n_max + 1, size=count)
+    ks = rng.choice(np.asarray(degrees), size=count)
+    return [(int(n), int(k)) for n, k in zip(ns, ks)]

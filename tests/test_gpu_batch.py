@@ -18,9 +18,15 @@ from _gpu_common import dev, host, meshes, rel, require_gpu
 pytestmark = pytest.mark.gpu
 
 
+def boxes_of(names):
+    u = S.uniform_nodes
+    extra = {"u345": (u(3), u(4), u(5))}
+    return [extra[n] if n in extra else meshes()[n] for n in names]
+
+
 def make_batch(names, levels, mults, seed=1, amp=0.2):
     torch, P = require_gpu()
-    boxes = [meshes()[n] for n in names]
+    boxes = boxes_of(names)
     dg = P.DG(None, None, None, levels, S.NU_TGV, S.AC_C, S.ETA, boxes=boxes)
     ms = [O.Mesh(*b, levels[0], S.NU_TGV, S.AC_C, S.ETA) for b in boxes]
     ws = [O.project_tgv(m) + S.perturbation(m.ne, m.k, amp, seed + q) for q, m in enumerate(ms)]
@@ -50,6 +56,11 @@ def oracle_levels(m, w, inv, levels):
 
 NAMES = ["u2", "box233", "u3", "box345"]
 MULTS = [1.0, 0.5, 2.0, 1.3]
+# boxes whose stage systems restarted FGMRES solves in the oracle too (the 2-cell and
+# perturbed-node boxes above stall at these time steps: their operators are close to the
+# singular constant-pressure mode of the periodic box)
+CONV = ["u3", "u345", "u3"]
+CONV_MULTS = [2.0, 2.5, 3.0]
 
 
 def test_batch_layout():
@@ -164,25 +175,25 @@ def test_plan_fixed_iterations_vs_oracle(use_graph):
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_plan_converges_vs_oracle(use_graph):
     levels = [3, 2, 1]
-    P, dg, ms, ws, inv = make_batch(NAMES, levels, MULTS)
+    P, dg, ms, ws, inv = make_batch(CONV, levels, CONV_MULTS, amp=0.05)
     dg.dg_set_linearization(dev(cat(ws).reshape(dg.ne, 4, -1)), inv)
     dg.dg_assemble()
     g = rhs(dg, ms, ws)
     x = dg.empty()
-    plan = P.Plan([dg], [g], [x], P.solve_opts(rtol=1e-10, maxit=200, restart=8), use_graph=use_graph)
+    plan = P.Plan([dg], [g], [x], P.solve_opts(rtol=1e-10, maxit=300, restart=8), use_graph=use_graph)
     plan.dg_plan_solve()  # restart 8: several restart cycles
     its, relres, conv = plan.dg_plan_result(0)
     assert all(conv) and max(relres) <= 1e-10
     assert plan.dg_plan_stats()["cycles"] >= 2
     for q, m in enumerate(ms):
-        G0 = O.dense_G(m, ws[q], inv * MULTS[q])
+        G0 = O.dense_G(m, ws[q], inv * CONV_MULTS[q])
         gq = -O.residual(m, ws[q]).reshape(-1)
         assert np.linalg.norm(gq - G0 @ split(dg, ms, x)[q]) / np.linalg.norm(gq) < 1e-9, q
 
 
 def test_plan_graph_equals_eager():
     levels = [3, 2, 1]
-    P, dg, ms, ws, inv = make_batch(NAMES, levels, MULTS)
+    P, dg, ms, ws, inv = make_batch(CONV, levels, CONV_MULTS, amp=0.05)
     dg.dg_set_linearization(dev(cat(ws).reshape(dg.ne, 4, -1)), inv)
     dg.dg_assemble()
     g = rhs(dg, ms, ws)
@@ -194,8 +205,10 @@ def test_plan_graph_equals_eager():
     pg.dg_plan_solve()
     assert np.array_equal(host(xe), host(xg))
     assert pe.dg_plan_result(0) == pg.dg_plan_result(0)
-    # a second solve replays the captured graph with new right-hand-side values
-    g.mul_(0.5).add_(0.01)
+    # a second solve replays the captured graph with new right-hand-side values (the stage
+    # right-hand sides of other states: consistent with the operator's range)
+    ws2 = [w + S.perturbation(m.ne, m.k, 0.02, 40 + q) for q, (m, w) in enumerate(zip(ms, ws))]
+    g.copy_(rhs(dg, ms, ws2))
     pe.dg_plan_solve()
     pg.dg_plan_solve()
     assert np.array_equal(host(xe), host(xg))
@@ -207,17 +220,17 @@ def test_plan_two_handles_one_graph(precision):
     # a k = 2 batch and a k = 3 batch as parallel branches of one graph equal their eager solves
     torch, P = require_gpu()
     prec = P.DG_PRECOND_FP64 if precision == "fp64" else P.DG_PRECOND_FP32_H16
-    sets = [(["u3", "box233", "u2"], [2, 1], [1.0, 0.7, 1.5]), (["box345", "u2"], [3, 2, 1], [1.0, 2.0])]
+    sets = [(["u345", "u3"], [2, 1], [2.5, 3.0]), (["u3", "u345", "u345"], [3, 2, 1], [2.0, 2.5, 3.5])]
     dgs, gs, ms_all, ws_all = [], [], [], []
     for names, levels, mults in sets:
-        P, dg, ms, ws, inv = make_batch(names, levels, mults, seed=11)
+        P, dg, ms, ws, inv = make_batch(names, levels, mults, seed=11, amp=0.05)
         dg.dg_set_linearization(dev(cat(ws).reshape(dg.ne, 4, -1)), inv)
         dg.dg_assemble_precision(P.DG_PRECOND_FP64 if prec == P.DG_PRECOND_FP64 else P.DG_PRECOND_FP32)
         dgs.append(dg)
         gs.append(rhs(dg, ms, ws))
         ms_all.append(ms)
         ws_all.append(ws)
-    opts = P.solve_opts(rtol=1e-8, maxit=100, precision=prec, omega=0.9 if precision != "fp64" else 1.0)
+    opts = P.solve_opts(rtol=1e-8, maxit=200, precision=prec, omega=0.9 if precision != "fp64" else 1.0)
     xg = [d.empty() for d in dgs]
     pg = P.Plan(dgs, gs, xg, opts, use_graph=True)
     pg.dg_plan_solve()
@@ -252,6 +265,20 @@ def test_plan_single_problem_matches_fgmres():
         b = SV.remove_mean_pressure(host(x2).reshape(-1), m.ne, m.nb, vol)
         assert rel(b, a) < 1e-10, its
         plan.close()
+
+
+def test_plan_reports_missed_tolerance():
+    # a problem that exhausts maxit is reported, with the converged flags per problem
+    P, dg, ms, ws, inv = make_batch(NAMES, [2, 1], MULTS)
+    dg.dg_set_linearization(dev(cat(ws).reshape(dg.ne, 4, -1)), inv)
+    dg.dg_assemble()
+    g = rhs(dg, ms, ws)
+    x = dg.empty()
+    plan = P.Plan([dg], [g], [x], P.solve_opts(rtol=1e-12, maxit=3, restart=30), use_graph=True)
+    assert plan.dg_plan_solve(check=False) == P.DG_ERR_NOT_CONVERGED
+    its, relres, conv = plan.dg_plan_result(0)
+    assert its == [3] * len(ms) and not any(conv)
+    assert all(r > 1e-12 for r in relres)
 
 
 def test_batch_rejects_whole_vector_reductions():
