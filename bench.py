@@ -293,6 +293,19 @@ def run_batch(args, P, make_opts, prec, stream, flush, world):
         dg.dg_assemble(precision=asm_prec)
     plan_g.dg_plan_solve()
     first_its = single_stage()
+    tuned = {}
+    if args.autotune:  # every handle measured (one-box handles of the same shape share the result)
+        for gi, (k, dg) in enumerate(zip(sorted(groups), hs)):
+            tuned["k%d_batched" % k] = {}
+            for nm, which in (("fp64_products", P.DG_TUNE_FP64), ("fp32_cycle", P.DG_TUNE_FP32)):
+                dg.dg_autotune(which, use_cache=False)
+                tuned["k%d_batched" % k][nm] = dg.dg_get_tuning(which).as_dict()
+        for d1, *_ in singles:
+            for which in (P.DG_TUNE_FP64, P.DG_TUNE_FP32):
+                d1.dg_autotune(which, use_cache=True)
+        plan_g.close()  # capture again with the tuned shapes
+        plan_g = P.Plan(hs, gs, xs, opts, use_graph=True)
+        plan_g.dg_plan_solve()
     diffs, batch_its, relres = [], [], []
     for gi, k in enumerate(sorted(groups)):
         its, rr, _ = plan_g.dg_plan_result(gi)
@@ -321,6 +334,7 @@ def run_batch(args, P, make_opts, prec, stream, flush, world):
         "speedup_graph_vs_sequential": t_single / t_graph, "speedup_graph_vs_eager": t_eager / t_graph,
         "kernel_launches_per_stage": {"graph": l_graph, "eager": l_eager, "sequential": l_single},
         "graph_launches_per_solve": st["cycles"], "arnoldi_steps_max": st["steps"],
+        "tuning": tuned or None,
         "first_stage": {"its_batch_min_max": [min(its_by_q.values()), max(its_by_q.values())],
                         "its_sequential_min_max": [min(first_its), max(first_its)],
                         "its_equal_problems": sum(1 for q in its_by_q if its_by_q[q] == first_its[q]),
@@ -439,6 +453,19 @@ def run_ours(args):
                 "fgmres_its": log["its"], "true_relres": log["relres"], "fallback_at": log.get("fallback_at"),
                 "operator_applications": (a1 - a0) / max(1, args.steps),
                 "gpu_launches": (l1 - l0) // max(1, args.steps)}
+
+    # --- launch shapes of the hot kernels measured on this handle (untimed setup): the first stage's
+    # linearisation and FP32 assembly, one cycle to make the 16-bit block copies, then the tuner
+    tuning = None
+    if args.autotune:
+        dg.dg_project_tgv(w)
+        dg.dg_set_linearization_rhs(w, inv, f)
+        dg.dg_assemble(precision=chosen_opts.precision)
+        dg.pmg_vcycle(f, dw, chosen_opts)
+        tuning = {}
+        for nm, which in (("fp64_products", P.DG_TUNE_FP64), ("fp32_cycle", P.DG_TUNE_FP32)):
+            rep = dg.dg_autotune(which, use_cache=False)
+            tuning[nm] = {"chosen": dg.dg_get_tuning(which).as_dict(), "device_ms_default_vs_chosen": rep}
 
     # --- learned coarse correction: trained here (untimed setup) by the library's BF16 kernels on
     # the coarse right-hand sides that the chosen cycle produces in the stages of the first states
@@ -626,7 +653,7 @@ def run_ours(args):
             "chosen_vs_plain": {"speedup": plain["s_per_stage"] / chosen["s_per_stage"],
                                 "first_stage_solution_rel_diff": chosen_err},
             "roofline": roofline, "roofline_jv": roofline_jv, "stage_kernels": kernels,
-            "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"]}
+            "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"], "tuning": tuning}
     if lagged is not None:
         line["lagged_form"] = {
             "lag": args.lag, "what": "the chosen form with the preconditioner (element blocks, factors, coarse "
@@ -685,6 +712,8 @@ def main():
     ap.add_argument("--no-stb-rescale", dest="stb_rescale", action="store_false",
                     help="keep the plain inherited coarse operators (default: rescale their stabilisation "
                          "part, Appendix A)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shapes (no dg_autotune)")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batch of 64 uneven independent solves")
     ap.add_argument("--lag", type=int, default=2, help="also time the chosen form with the preconditioner "

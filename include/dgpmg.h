@@ -416,6 +416,37 @@ const char* dg_plan_error(const dg_plan* plan);
 
 int dg_plan_destroy(dg_plan* plan);
 
+/* ------------------------------------------------------------ launch shapes
+ * The paper's kernels are CPU loops; here the launch shapes of the hot GPU kernels are chosen per
+ * (degree k, quadrature size N_q = (k+1)^3) and mesh size. None of them changes a result: every
+ * output entry is computed by the same arithmetic in the same order for every shape. */
+#define DG_TUNE_FP64 0  /* the FP64 Jacobian action (outer FGMRES products, FP64 cycle) */
+#define DG_TUNE_FP32 1  /* the FP32 Jacobian action and block-Jacobi apply of the FP32 cycle */
+typedef struct dg_tuning {
+  int face_warps;        /* faces per CTA of the face pass (one warp each): 2, 4 or 8 (default 4) */
+  int vol_threads;       /* threads per CTA of the volume pass (one element per CTA): 64, 128 or 256 (128) */
+  int face_ctas_per_sm;  /* cap on resident CTAs per SM of the face pass, 0..32 (0: shared memory decides) */
+  int vol_ctas_per_sm;   /* the same for the volume pass */
+  int jacobi_stage_kb;   /* FP32 cycle: KB of element inverses per bulk-copy stage of the fine-level
+                            block-Jacobi apply, 8..224 (96); capped by shared memory */
+} dg_tuning;
+
+int dg_get_tuning(const dg_handle* h, int which, dg_tuning* t);
+
+/* Set the shapes of class `which`. A plan captured as a graph keeps the shapes it was captured
+ * with. DG_ERR_ARG outside the listed values. */
+int dg_set_tuning(dg_handle* h, int which, const dg_tuning* t);
+
+/* Measure the candidate shapes on h (CUDA events around the real kernels at h's current
+ * linearisation; for DG_TUNE_FP32 the block-Jacobi stages too when an FP32 assembly exists) and
+ * keep the fastest per kernel. The candidates: face_warps 2/4/8; vol_threads 64/128/256 with no
+ * CTA cap and with 4 CTAs per SM; jacobi_stage_kb 48/96/144/200. use_cache != 0: reuse the result
+ * of an earlier call in this process on the same (which, k, N_q, SM count, log2 N_e, block
+ * storage). report: NULL or HOST [6] = device ms per launch of the default and of the chosen face
+ * pass, volume pass and block-Jacobi apply (0 where not measured or taken from the cache).
+ * Overwrites the level-0 work vectors; keeps the profiler's accumulated counts. Synchronises. */
+int dg_autotune(dg_handle* h, int which, int use_cache, double* report, void* stream);
+
 /* --------------------------------------------------------- instrumentation
  * The paper profiles its solver per linear system (Sec. 3.1: code profiling
  * over 10 time steps); these calls expose the same information per kernel. */

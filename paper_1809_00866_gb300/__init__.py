@@ -54,7 +54,10 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "bsr_spmv_t", "dg_coarse_apply", "dg_profile_read_bytes",
            "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling",
            "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
-           "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy")
+           "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy",
+           "dg_get_tuning", "dg_set_tuning", "dg_autotune")
+DG_TUNE_FP64 = 0
+DG_TUNE_FP32 = 1
 DG_PROF_N = 10
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32", "bj32_fine", "bsr32_l1",
               "bj64_fine", "bsr64_l1")
@@ -75,6 +78,14 @@ class DgSolveOpts(ctypes.Structure):
                 ("jvp_mode", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("precision", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("fallback_its", ctypes.c_int),
                 ("fallback_rho", ctypes.c_double)]
+
+
+class DgTuning(ctypes.Structure):
+    _fields_ = [("face_warps", ctypes.c_int), ("vol_threads", ctypes.c_int), ("face_ctas_per_sm", ctypes.c_int),
+                ("vol_ctas_per_sm", ctypes.c_int), ("jacobi_stage_kb", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class DgSolveInfo(ctypes.Structure):
@@ -148,6 +159,9 @@ def load(path=None):
     L.dg_plan_error.argtypes = [vp]
     L.dg_plan_error.restype = ctypes.c_char_p
     L.dg_plan_destroy.argtypes = [vp]
+    L.dg_get_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
+    L.dg_set_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
+    L.dg_autotune.argtypes = [vp, i, i, ctypes.POINTER(d), vp]
     for name in EXPORTS:
         if name not in ("dg_last_error", "dg_plan_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -319,6 +333,26 @@ class DG:
     def dg_set_problem_shifts(self, mult, stream=None):
         arr = (ctypes.c_double * self.nprob)(*[float(v) for v in mult])
         self._chk(self._L.dg_set_problem_shifts(self.h, arr, self._stream(stream)))
+
+    def dg_get_tuning(self, which):
+        t = DgTuning()
+        self._chk(self._L.dg_get_tuning(self.h, int(which), ctypes.byref(t)))
+        return t
+
+    def dg_set_tuning(self, which, t=None, **kw):
+        t = t if t is not None else self.dg_get_tuning(which)
+        for key, val in kw.items():
+            setattr(t, key, int(val))
+        self._chk(self._L.dg_set_tuning(self.h, int(which), ctypes.byref(t)))
+
+    def dg_autotune(self, which, use_cache=True, stream=None):
+        """Returns the report: device ms of the default and chosen face pass, volume pass and
+        block-Jacobi apply."""
+        rep = (ctypes.c_double * 6)()
+        self._chk(self._L.dg_autotune(self.h, int(which), 1 if use_cache else 0, rep, self._stream(stream)))
+        keys = ("face_default_ms", "face_chosen_ms", "vol_default_ms", "vol_chosen_ms", "jacobi_default_ms",
+                "jacobi_chosen_ms")
+        return dict(zip(keys, list(rep)))
 
     def dg_get_status(self, stream=None):
         s = ctypes.c_uint()

@@ -325,7 +325,9 @@ template <class R, class S>
 int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, R alpha, int x_zero, R* x,
                          cudaStream_t st) {
   const size_t per = (size_t)b * b * sizeof(S);
-  int G = (int)std::max<size_t>(1, kStageTarget / per);
+  const size_t target = h->tune[1].jacobi_stage_kb > 0 ? (size_t)h->tune[1].jacobi_stage_kb * 1024 : kStageTarget;
+  int G = (int)std::max<size_t>(1, target / per);
+  G = std::min(G, (int)std::max<size_t>(1, kSmemLimit / (2 * per + (size_t)b * sizeof(R))));  // fits shared memory
   G = std::max(1, std::min(G, (h->ne + 2 * h->nsm - 1) / (2 * h->nsm)));  // >= 2 stages per SM when possible
   const size_t smem = 2 * (size_t)G * per + (size_t)G * b * sizeof(R);
   if (smem > kSmemLimit || per % 16 != 0) return -1;

@@ -84,8 +84,19 @@ struct Level {
   void* Bsr16 = nullptr;
 };
 
+// Launch shapes of the tangent operator passes and of the staged block-Jacobi apply
+// (dg_set_tuning / dg_autotune); every shape gives the same results.
+struct OpTune {
+  int face_warps = 4;         // faces per CTA of the face pass: 2, 4 or 8
+  int vol_threads = 128;      // threads per CTA of the volume pass: 64, 128 or 256
+  int face_per_sm = 0;        // cap on CTAs per SM (0: shared memory decides)
+  int vol_per_sm = 0;
+  int jacobi_stage_kb = 96;   // element blocks staged per bulk copy of the block-Jacobi apply (KB)
+};
+
 struct Handle {
   dg_params p{};
+  OpTune tune[2];               // [0] FP64 products, [1] FP32 products (and the FP32 block-Jacobi apply)
   int n[3] = {0, 0, 0};
   int ne = 0;
   int nlev = 0;

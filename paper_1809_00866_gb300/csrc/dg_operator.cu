@@ -241,9 +241,9 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
 }
 
 // ---------------------------------------------------------------- face pass
-constexpr int kFaceWarps = 4;  // faces per CTA, one warp each
+constexpr int kFaceWarps = 4;  // default faces per CTA, one warp each (the tangent pass's is tunable)
 
-template <int K, class R = double>
+template <int K, class R = double, int FW = kFaceWarps>
 struct FaceSmem {
   using S = Sz2<K>;
   // per warp
@@ -255,7 +255,7 @@ struct FaceSmem {
   static constexpr int P = F + 4 * S::NQF;              // [4][N2] its projection
   static constexpr int WARP = P + 4 * S::N2;
   // per CTA tables (after the warps)
-  static constexpr int B2 = kFaceWarps * WARP;          // [NQF][N2]
+  static constexpr int B2 = FW * WARP;                  // [NQF][N2]
   static constexpr int W2 = B2 + S::NQF * S::N2;        // [NQF]
   static constexpr int PV = W2 + S::NQF;                // [2][K+1]
   static constexpr int PD = PV + 2 * (K + 1);           // [2][K+1]
@@ -269,10 +269,10 @@ struct FaceSmem {
   static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
 
-template <int K, int MODE, class R>
-__global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgsT<R> a) {
+template <int K, int MODE, class R, int FW = kFaceWarps>
+__global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
   using S = Sz2<K>;
-  using L = FaceSmem<K, R>;
+  using L = FaceSmem<K, R, FW>;
   constexpr int NB = S::NB, NQF = S::NQF, N2 = S::N2, K1 = K + 1, DW = Tables::kDw;
   extern __shared__ __align__(16) unsigned char smraw_[];
   R* sm = reinterpret_cast<R*>(smraw_);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_kernel(OpArgsT<R> a) {
   R* sF = W + L::F;
   R* sP = W + L::P;
   const int nfaces = 3 * a.M.ne;
-  for (int f = blockIdx.x * kFaceWarps + warp; f < nfaces; f += gridDim.x * kFaceWarps) {
+  for (int f = blockIdx.x * FW + warp; f < nfaces; f += gridDim.x * FW) {
     const int e0 = f / 3, d = f - 3 * e0;
     const int e1 = a.M.nbr[e0 * 6 + 2 * d + 1];
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
@@ -473,7 +473,7 @@ struct VolSmem {
 __device__ __forceinline__ int sym_index(int p, int i) { return p == i ? p : (p + i + 2); }  // 01->3 02->4 12->5
 
 template <int K, int MODE, class R>
-__global__ void __launch_bounds__(128) vol_kernel(OpArgsT<R> a) {
+__global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   using L = VolSmem<K, R>;
   constexpr int NB = L::NB, N1 = L::N1, NQ = L::NQ, N2 = L::N2, K1 = L::K1, DW = Tables::kDw;
   extern __shared__ __align__(16) unsigned char smraw_[];
@@ -753,30 +753,54 @@ static OpArgsT<float> make_args_f(Handle* h, const float* in, float* out) {
   return a;
 }
 
+// Launch shapes of the tangent passes (the hot products of the solver): faces per CTA of the face
+// pass, threads per CTA of the volume pass, CTAs per SM of each (0: as many as shared memory
+// allows, at most 8 / 12). Every output entry is computed by the same arithmetic in the same order
+// whatever the shape, so the results do not depend on it.
+template <int K, int MODE, class R, int FW>
+static int launch_face(Handle* h, const OpArgsT<R>& a, int per_sm_cap, cudaStream_t st) {
+  const size_t fs = FaceSmem<K, R, FW>::bytes();
+  DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE, R, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+  int per_sm = (int)((200 * 1024) / fs);
+  per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+  if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+  const int fblocks = (3 * h->ne + FW - 1) / FW;
+  int gf = h->nsm * per_sm;
+  if (gf > fblocks) gf = fblocks;
+  face_kernel<K, MODE, R, FW><<<gf, 32 * FW, fs, st>>>(a);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
 template <int K, int MODE, class R>
 static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
-  const size_t fs = FaceSmem<K, R>::bytes(), vs = VolSmem<K, R>::bytes();
-  DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
-  DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
-  const int nfaces = 3 * h->ne;
-  int per_sm_f = (int)((200 * 1024) / fs), per_sm_v = (int)((200 * 1024) / vs);
-  per_sm_f = per_sm_f < 1 ? 1 : (per_sm_f > 8 ? 8 : per_sm_f);
-  per_sm_v = per_sm_v < 1 ? 1 : (per_sm_v > 12 ? 12 : per_sm_v);
-  int gf = h->nsm * per_sm_f, gv = h->nsm * per_sm_v;
-  const int fblocks = (nfaces + kFaceWarps - 1) / kFaceWarps;
-  if (gf > fblocks) gf = fblocks;
-  if (gv > h->ne) gv = h->ne;
   const bool tan = (MODE == MODE_TAN || MODE == MODE_LINPART);
+  const OpTune tu = MODE == MODE_TAN ? h->tune[sizeof(R) == 4 ? 1 : 0] : OpTune{};
+  const size_t vs = VolSmem<K, R>::bytes();
+  DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
+  int per_sm_v = (int)((200 * 1024) / vs);
+  per_sm_v = per_sm_v < 1 ? 1 : (per_sm_v > 12 ? 12 : per_sm_v);
+  if (tu.vol_per_sm > 0 && per_sm_v > tu.vol_per_sm) per_sm_v = tu.vol_per_sm;
+  int gv = h->nsm * per_sm_v;
+  if (gv > h->ne) gv = h->ne;
   const int cf = tan ? (sizeof(R) == 4 ? DG_PROF_FACE_TAN32 : DG_PROF_FACE_TAN) : DG_PROF_FACE_RES;
   const int cv = tan ? (sizeof(R) == 4 ? DG_PROF_VOL_TAN32 : DG_PROF_VOL_TAN) : DG_PROF_VOL_RES;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc;
   if ((rc = prof_begin(h, st, &e0))) return rc;
-  face_kernel<K, MODE, R><<<gf, 32 * kFaceWarps, fs, st>>>(a);
-  DG_LAUNCH_CHECK(h);
+  if constexpr (MODE == MODE_TAN) {
+    switch (tu.face_warps) {
+      case 2: rc = launch_face<K, MODE, R, 2>(h, a, tu.face_per_sm, st); break;
+      case 8: rc = launch_face<K, MODE, R, 8>(h, a, tu.face_per_sm, st); break;
+      default: rc = launch_face<K, MODE, R, 4>(h, a, tu.face_per_sm, st); break;
+    }
+  } else {
+    rc = launch_face<K, MODE, R, kFaceWarps>(h, a, 0, st);
+  }
+  if (rc) return rc;
   if ((rc = prof_end(h, cf, st, e0))) return rc;
   if ((rc = prof_begin(h, st, &e1))) return rc;
-  vol_kernel<K, MODE, R><<<gv, 128, vs, st>>>(a);
+  vol_kernel<K, MODE, R><<<gv, tu.vol_threads, vs, st>>>(a);
   DG_LAUNCH_CHECK(h);
   if ((rc = prof_end(h, cv, st, e1))) return rc;
   ++h->op_apps;

@@ -1,0 +1,105 @@
+"""Launch shapes of the hot kernels (dg_set_tuning / dg_autotune) change no result.
+
+Every output entry of the face pass, the volume pass and the staged block-Jacobi apply is
+computed by the same arithmetic in the same order whatever the faces per CTA, threads per CTA,
+CTAs per SM or elements per bulk-copy stage, so the products and the cycles must be bitwise equal
+to those of the default shapes; the default shapes themselves are pinned to the oracle by the
+operator and solver parity tests.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from _gpu_common import dev, host, meshes, pair, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(name, levels, precision):
+    import paper_1809_00866_gb300 as P
+    dg, m = pair(*meshes()[name], levels)
+    w = O.project_tgv(m) + S.perturbation(m.ne, m.k, 0.2, 2)
+    dg.dg_set_linearization(dev(w), 1.0 / S.acoustic_dt(m.nx, m.k))
+    dg.dg_assemble(precision=precision)
+    return P, dg, m, w
+
+
+SHAPES = [dict(face_warps=fw, vol_threads=vt, face_ctas_per_sm=fc, vol_ctas_per_sm=vc, jacobi_stage_kb=kb)
+          for (fw, vt), (fc, vc), kb in itertools.product([(2, 64), (4, 128), (8, 256)], [(0, 0), (1, 3)],
+                                                          [16, 96, 200])]
+
+
+@pytest.mark.parametrize("name,levels", [("box345", [2, 1]), ("u3", [4, 2, 1])])
+def test_fp64_products_do_not_depend_on_the_shape(name, levels):
+    import paper_1809_00866_gb300 as P
+    P, dg, m, w = setup(name, levels, P.DG_PRECOND_FP64)
+    v = dev(S.direction(m.ne, m.k, 5))
+    ref = dg.empty()
+    dg.dg_jvp(v, ref)
+    assert rel(host(ref).reshape(-1), O.jvp(m, w, host(v), 1.0 / S.acoustic_dt(m.nx, m.k)).reshape(-1)) < 1e-12
+    out = dg.empty()
+    for sh in SHAPES[::3]:
+        dg.dg_set_tuning(P.DG_TUNE_FP64, **sh)
+        dg.dg_jvp(v, out)
+        assert np.array_equal(host(out), host(ref)), sh
+
+
+@pytest.mark.parametrize("name,levels,storage", [("box345", [2, 1], "FP32"), ("u3", [4, 2, 1], "FP32_H16")])
+def test_fp32_cycle_does_not_depend_on_the_shape(name, levels, storage):
+    import paper_1809_00866_gb300 as P
+    prec = getattr(P, "DG_PRECOND_" + storage)
+    P, dg, m, w = setup(name, levels, P.DG_PRECOND_FP32)
+    g = dev(S.direction(m.ne, m.k, 6))
+    opts = P.solve_opts(precision=prec, omega=0.9, pre_sweeps=3, post_sweeps=3, coarse_sweeps=2)
+    ref = dg.empty()
+    dg.pmg_vcycle(g, ref, opts)
+    out = dg.empty()
+    for sh in SHAPES:
+        dg.dg_set_tuning(P.DG_TUNE_FP32, **sh)
+        dg.pmg_vcycle(g, out, opts)
+        assert np.array_equal(host(out), host(ref)), sh
+
+
+def test_autotune_keeps_results_and_caches():
+    import paper_1809_00866_gb300 as P
+    P, dg, m, w = setup("u3", [4, 2, 1], P.DG_PRECOND_FP32)
+    g = dev(S.direction(m.ne, m.k, 7))
+    opts = P.solve_opts(precision=P.DG_PRECOND_FP32_H16, omega=0.9)
+    ref = dg.empty()
+    dg.pmg_vcycle(g, ref, opts)  # also makes the 16-bit copies the tuner times
+    v = dev(S.direction(m.ne, m.k, 8))
+    jref = dg.empty()
+    dg.dg_jvp(v, jref)
+    for which in (P.DG_TUNE_FP64, P.DG_TUNE_FP32):
+        rep = dg.dg_autotune(which, use_cache=False)
+        assert rep["face_chosen_ms"] <= rep["face_default_ms"] and rep["vol_chosen_ms"] <= rep["vol_default_ms"]
+        if which == P.DG_TUNE_FP32:
+            assert 0 < rep["jacobi_chosen_ms"] <= rep["jacobi_default_ms"]
+        t = dg.dg_get_tuning(which).as_dict()
+        assert t["face_warps"] in (2, 4, 8) and t["vol_threads"] in (64, 128, 256)
+    out = dg.empty()
+    dg.pmg_vcycle(g, out, opts)
+    assert np.array_equal(host(out), host(ref))
+    dg.dg_jvp(v, out)
+    assert np.array_equal(host(out), host(jref))
+    # a second handle of the same shape takes the cached result without measuring
+    dg2, m2 = pair(*meshes()["u3"], [4, 2, 1])
+    dg2.dg_set_linearization(dev(w), 1.0)
+    dg2.dg_assemble(precision=P.DG_PRECOND_FP32)
+    dg2.pmg_vcycle(g, out, opts)
+    rep2 = dg2.dg_autotune(P.DG_TUNE_FP32, use_cache=True)
+    assert all(x == 0.0 for x in rep2.values())
+    assert dg2.dg_get_tuning(P.DG_TUNE_FP32).as_dict() == dg.dg_get_tuning(P.DG_TUNE_FP32).as_dict()
+
+
+def test_set_tuning_rejects_unsupported_shapes():
+    import paper_1809_00866_gb300 as P
+    P, dg, m, w = setup("u3", [2, 1], P.DG_PRECOND_FP64)
+    for bad in (dict(face_warps=3), dict(vol_threads=96), dict(jacobi_stage_kb=4), dict(vol_ctas_per_sm=-1)):
+        with pytest.raises(P.DgError):
+            dg.dg_set_tuning(P.DG_TUNE_FP64, **bad)
+    with pytest.raises(P.DgError):
+        dg.dg_autotune(7)
