@@ -67,7 +67,13 @@ typedef struct dg_params {
   double nu;             /* kinematic viscosity (> 0) */
   double ac_c;           /* artificial-compressibility constant c of the Riemann flux (> 0) */
   double eta;            /* BR2 penalty eta_sigma (> 6 for hexahedra, Sec. 2.1) */
+  int walls;             /* DG_WALLS_NONE: periodic in y; DG_WALLS_Y: no-slip walls (data f = 0) at
+                            y = yn[0] and y = yn[ny] (Sec. 2.1: Dirichlet viscous flux with the
+                            one-sided lifting of [u] = u_K - f, inviscid flux against the ghost
+                            state (f, p_K)); x and z stay periodic. ny >= 2 with walls. */
 } dg_params;
+#define DG_WALLS_NONE 0
+#define DG_WALLS_Y 1
 
 typedef struct dg_handle dg_handle;
 

@@ -43,7 +43,7 @@ class _Mesh(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("k", ctypes.c_int),
                 ("nq", ctypes.c_int), ("nu", ctypes.c_double), ("c", ctypes.c_double), ("eta", ctypes.c_double),
                 ("xn", ctypes.POINTER(ctypes.c_double)), ("yn", ctypes.POINTER(ctypes.c_double)),
-                ("zn", ctypes.POINTER(ctypes.c_double))]
+                ("zn", ctypes.POINTER(ctypes.c_double)), ("wall_y", ctypes.c_int)]
 
 
 def lib():
@@ -106,28 +106,30 @@ def gauss(n):
 
 
 class Mesh:
-    """Periodic box mesh of nx*ny*nz hexahedra with node coordinates per axis.
+    """Box mesh of nx*ny*nz hexahedra with node coordinates per axis, periodic in every
+    direction, or with no-slip walls at y = yn[0] and y = yn[-1] (``walls=True``).
 
     Elements are numbered e = i + nx*(j + ny*k); unknowns are laid out
     [element][u, v, w, p][mode].
     """
 
-    def __init__(self, xn, yn, zn, k, nu, c=1.0, eta=7.0, nq=0):
+    def __init__(self, xn, yn, zn, k, nu, c=1.0, eta=7.0, nq=0, walls=False):
         self.xn = np.ascontiguousarray(xn, dtype=np.float64)
         self.yn = np.ascontiguousarray(yn, dtype=np.float64)
         self.zn = np.ascontiguousarray(zn, dtype=np.float64)
         self.nx, self.ny, self.nz = len(self.xn) - 1, len(self.yn) - 1, len(self.zn) - 1
         self.k, self.nu, self.c, self.eta = int(k), float(nu), float(c), float(eta)
         self.nq = int(nq) if nq else self.k + 1
+        self.walls = bool(walls)
         self.ne = self.nx * self.ny * self.nz
         self.nb = nb(self.k)
         self.n = self.ne * 4 * self.nb
 
     def with_k(self, k, nq=0):
-        return Mesh(self.xn, self.yn, self.zn, k, self.nu, self.c, self.eta, nq)
+        return Mesh(self.xn, self.yn, self.zn, k, self.nu, self.c, self.eta, nq, self.walls)
 
     def with_nu(self, nu):
-        return Mesh(self.xn, self.yn, self.zn, self.k, nu, self.c, self.eta, self.nq)
+        return Mesh(self.xn, self.yn, self.zn, self.k, nu, self.c, self.eta, self.nq, self.walls)
 
     def vol(self):
         hx, hy, hz = np.diff(self.xn), np.diff(self.yn), np.diff(self.zn)
@@ -138,13 +140,17 @@ class Mesh:
         e = np.arange(self.ne)
         i, j, k = e % self.nx, (e // self.nx) % self.ny, e // (self.nx * self.ny)
         idx = lambda a, b, c: (a % self.nx) + self.nx * ((b % self.ny) + self.ny * (c % self.nz))
-        return np.stack([idx(i - 1, j, k), idx(i + 1, j, k), idx(i, j - 1, k), idx(i, j + 1, k),
-                         idx(i, j, k - 1), idx(i, j, k + 1)], axis=1)
+        nbr = np.stack([idx(i - 1, j, k), idx(i + 1, j, k), idx(i, j - 1, k), idx(i, j + 1, k),
+                        idx(i, j, k - 1), idx(i, j, k + 1)], axis=1)
+        if self.walls:  # no neighbour across a wall
+            nbr[j == 0, 2] = -1
+            nbr[j == self.ny - 1, 3] = -1
+        return nbr
 
     def _c(self):
         m = _Mesh(self.nx, self.ny, self.nz, self.k, self.nq if self.nq != self.k + 1 else 0,
                   self.nu, self.c, self.eta,
-                  _p(self.xn), _p(self.yn), _p(self.zn))
+                  _p(self.xn), _p(self.yn), _p(self.zn), 1 if self.walls else 0)
         self._keep = m
         return ctypes.byref(m)
 

@@ -31,7 +31,14 @@
 //    (u_n)_t + (u_n^2 + p)_x = 0, (u_t)_t + (u_n u_t)_x = 0, including the
 //    change of the tangential velocity across the two acoustic waves;
 //    when |u*| is within a rounding band of zero the two contact sides are
-//    averaged.
+//    averaged;
+//  * walls (optional, at y = yn[0] and y = yn[ny], no-slip data f = 0; Sec. 2.1,
+//    Dirichlet viscous flux and ghost boundary state): the ghost state keeps the
+//    Riemann invariants of the interior and makes the interface velocity the data,
+//    (u_gb, p_gb) = (2 f - u_K, p_K); the same exact Riemann solver then gives
+//    u* = f.n, so no mass crosses a wall; the jump is [u] = u_K - f; the lifting of
+//    a wall face lives on K alone, int_K r . tau = int_s [u] tau . n (the one-sided
+//    average), and the viscous flux is F^nu(grad u_K - eta r([u])).
 
 #include <cmath>
 #include <cstdio>
@@ -139,6 +146,7 @@ typedef struct orc_mesh {
   const double* xn;  // nx+1 node coordinates along x (periodic box)
   const double* yn;
   const double* zn;
+  int wall_y;  // 1: no-slip walls at y = yn[0] and y = yn[ny] (else periodic)
 } orc_mesh;
 }
 
@@ -152,6 +160,7 @@ struct Disc {
   std::vector<Mode> md;
   std::vector<double> gx, gw;
   int ne;
+  bool wall_y;
   Disc(const orc_mesh* m) {
     n[0] = m->nx; n[1] = m->ny; n[2] = m->nz;
     k = m->k;
@@ -164,6 +173,7 @@ struct Disc {
     nq = m->nq > 0 ? m->nq : k + 1;
     gauss(nq, gx, gw);
     ne = n[0] * n[1] * n[2];
+    wall_y = m->wall_y != 0;
   }
   void ijk(int e, int* I) const {
     I[0] = e % n[0];
@@ -171,10 +181,12 @@ struct Disc {
     I[2] = e / (n[0] * n[1]);
   }
   int elem(const int* I) const { return I[0] + n[0] * (I[1] + n[1] * I[2]); }
-  // neighbour across the face normal to axis d, on the + side (s=+1) or - side (s=-1)
+  // neighbour across the face normal to axis d, on the + side (s=+1) or - side (s=-1);
+  // -1 across a wall
   int nbr(int e, int d, int s) const {
     int I[3];
     ijk(e, I);
+    if (wall_y && d == 1 && (I[1] + s < 0 || I[1] + s >= n[1])) return -1;
     I[d] = (I[d] + s + n[d]) % n[d];
     return elem(I);
   }
@@ -330,6 +342,9 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
   auto LIFT = [&](int e, int d, int side, int a, int m) -> T& {
     return lift[((((size_t)e * 3 + d) * 2 + side) * 3 + a) * nb + m];
   };
+  // lifting of the wall face at the - side (y = yn[0]) of K, on K
+  std::vector<T> liftb((size_t)ne * 3 * nb, T(0.0));
+  auto LIFTB = [&](int e, int a, int m) -> T& { return liftb[((size_t)e * 3 + a) * nb + m]; };
   for (int K = 0; K < ne; ++K)
     for (int d = 0; d < 3; ++d) {
       int P = D.nbr(K, d, +1);
@@ -342,17 +357,41 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
           xiK[t2] = xiP[t2] = D.gx[q2];
           double wq = D.gw[q1] * D.gw[q2] * 0.25 * D.h(K, t1) * D.h(K, t2);
           D.eval(K, xiK, phiK.data(), nullptr);
-          D.eval(P, xiP, phiP.data(), nullptr);
+          if (P >= 0) D.eval(P, xiP, phiP.data(), nullptr);
           for (int a = 0; a < 3; ++a) {
             T uk = T(0.0), up = T(0.0);
-            for (int m = 0; m < nb; ++m) { uk += W(K, a, m) * phiK[m]; up += W(P, a, m) * phiP[m]; }
-            T jump = uk - up;
             for (int m = 0; m < nb; ++m) {
-              LIFT(K, d, 0, a, m) += 0.5 * wq * jump * phiK[m];
-              LIFT(K, d, 1, a, m) += 0.5 * wq * jump * phiP[m];
+              uk += W(K, a, m) * phiK[m];
+              if (P >= 0) up += W(P, a, m) * phiP[m];
+            }
+            T jump = uk - up;  // at a wall: u_K - f with f = 0
+            for (int m = 0; m < nb; ++m) {
+              if (P >= 0) {
+                LIFT(K, d, 0, a, m) += 0.5 * wq * jump * phiK[m];
+                LIFT(K, d, 1, a, m) += 0.5 * wq * jump * phiP[m];
+              } else {
+                LIFT(K, d, 0, a, m) += wq * jump * phiK[m];
+              }
             }
           }
         }
+      // the wall face below K (K on the + side of the face): [u] = f - u_K
+      if (d == 1 && D.nbr(K, 1, -1) < 0)
+        for (int q1 = 0; q1 < nq; ++q1)
+          for (int q2 = 0; q2 < nq; ++q2) {
+            double xiK[3];
+            xiK[1] = -1.0;
+            xiK[t1] = D.gx[q1];
+            xiK[t2] = D.gx[q2];
+            double wq = D.gw[q1] * D.gw[q2] * 0.25 * D.h(K, t1) * D.h(K, t2);
+            D.eval(K, xiK, phiK.data(), nullptr);
+            for (int a = 0; a < 3; ++a) {
+              T uk = T(0.0);
+              for (int m = 0; m < nb; ++m) uk += W(K, a, m) * phiK[m];
+              T jump = -uk;
+              for (int m = 0; m < nb; ++m) LIFTB(K, a, m) += wq * jump * phiK[m];
+            }
+          }
     }
 
   // 2. volume terms: - int_K Ftilde_{p,i}(w) d_p z_i with the BR2 corrected
@@ -382,7 +421,8 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
             int Km = D.nbr(K, b, -1);
             for (int a = 0; a < 3; ++a) {
               T r = T(0.0);
-              for (int m = 0; m < nb; ++m) r += (LIFT(K, b, 0, a, m) + LIFT(Km, b, 1, a, m)) * phiK[m];
+              for (int m = 0; m < nb; ++m)
+                r += (LIFT(K, b, 0, a, m) + (Km >= 0 ? LIFT(Km, b, 1, a, m) : LIFTB(K, a, m))) * phiK[m];
               g[a][b] -= r;
             }
           }
@@ -405,7 +445,8 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
   }
 
   // 3. face terms: + int_s n.(Fhat^c - Fhat^nu) [z] with the exact AC Riemann
-  //    flux and Fhat^nu = F^nu({grad u - eta r^s([u])}).
+  //    flux and Fhat^nu = F^nu({grad u - eta r^s([u])}); at a wall the ghost
+  //    state (f, p_K) on the missing side and the one-sided Dirichlet flux.
   for (int K = 0; K < ne; ++K)
     for (int d = 0; d < 3; ++d) {
       int P = D.nbr(K, d, +1);
@@ -418,7 +459,7 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
           xiK[t2] = xiP[t2] = D.gx[q2];
           double wq = D.gw[q1] * D.gw[q2] * 0.25 * D.h(K, t1) * D.h(K, t2);
           D.eval(K, xiK, phiK.data(), dK.data());
-          D.eval(P, xiP, phiP.data(), dP.data());
+          if (P >= 0) D.eval(P, xiP, phiP.data(), dP.data());
           T uk[3], up[3], pk = T(0.0), pp_ = T(0.0), gk[3][3], gp[3][3], rk[3], rp[3];
           for (int a = 0; a < 3; ++a) {
             uk[a] = up[a] = rk[a] = rp[a] = T(0.0);
@@ -427,23 +468,32 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
           for (int m = 0; m < nb; ++m) {
             for (int a = 0; a < 3; ++a) {
               uk[a] += W(K, a, m) * phiK[m];
-              up[a] += W(P, a, m) * phiP[m];
-              for (int b = 0; b < 3; ++b) {
-                gk[a][b] += W(K, a, m) * dK[3 * m + b];
-                gp[a][b] += W(P, a, m) * dP[3 * m + b];
-              }
+              for (int b = 0; b < 3; ++b) gk[a][b] += W(K, a, m) * dK[3 * m + b];
               rk[a] += LIFT(K, d, 0, a, m) * phiK[m];
-              rp[a] += LIFT(K, d, 1, a, m) * phiP[m];
+              if (P >= 0) {
+                up[a] += W(P, a, m) * phiP[m];
+                for (int b = 0; b < 3; ++b) gp[a][b] += W(P, a, m) * dP[3 * m + b];
+                rp[a] += LIFT(K, d, 1, a, m) * phiP[m];
+              }
             }
             pk += W(K, 3, m) * phiK[m];
-            pp_ += W(P, 3, m) * phiP[m];
+            if (P >= 0) pp_ += W(P, 3, m) * phiP[m];
           }
           T gh[3][3];
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-              gh[a][b] = 0.5 * (gk[a][b] + gp[a][b]);
-              if (b == d) gh[a][b] -= eta * 0.5 * (rk[a] + rp[a]);
+              if (P >= 0) {
+                gh[a][b] = 0.5 * (gk[a][b] + gp[a][b]);
+                if (b == d) gh[a][b] -= eta * 0.5 * (rk[a] + rp[a]);
+              } else {  // wall: one-sided gradient and the full lifting of [u] = u_K - f
+                gh[a][b] = gk[a][b];
+                if (b == d) gh[a][b] -= eta * rk[a];
+              }
             }
+          if (P < 0) {  // ghost state (2 f - u_K, p_K), f = 0
+            for (int a = 0; a < 3; ++a) up[a] = -uk[a];
+            pp_ = pk;
+          }
           T divh = gh[0][0] + gh[1][1] + gh[2][2];
           T fc[4];
           riemann_flux<T>(uk, pk, up, pp_, d, D.c, fc, nullptr, nullptr, nullptr);
@@ -456,9 +506,48 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
           for (int i = 0; i < 4; ++i)
             for (int m = 0; m < nb; ++m) {
               F(K, i, m) += wq * fn[i] * phiK[m];
-              F(P, i, m) -= wq * fn[i] * phiP[m];
+              if (P >= 0) F(P, i, m) -= wq * fn[i] * phiP[m];
             }
         }
+      // the wall face below K: the ghost state on the - side, K on the + side
+      if (d == 1 && D.nbr(K, 1, -1) < 0)
+        for (int q1 = 0; q1 < nq; ++q1)
+          for (int q2 = 0; q2 < nq; ++q2) {
+            double xiK[3];
+            xiK[1] = -1.0;
+            xiK[t1] = D.gx[q1];
+            xiK[t2] = D.gx[q2];
+            double wq = D.gw[q1] * D.gw[q2] * 0.25 * D.h(K, t1) * D.h(K, t2);
+            D.eval(K, xiK, phiK.data(), dK.data());
+            T uk[3], ug[3], pk = T(0.0), gk[3][3], rk[3];
+            for (int a = 0; a < 3; ++a) {
+              uk[a] = ug[a] = rk[a] = T(0.0);
+              for (int b = 0; b < 3; ++b) gk[a][b] = T(0.0);
+            }
+            for (int m = 0; m < nb; ++m) {
+              for (int a = 0; a < 3; ++a) {
+                uk[a] += W(K, a, m) * phiK[m];
+                for (int b = 0; b < 3; ++b) gk[a][b] += W(K, a, m) * dK[3 * m + b];
+                rk[a] += LIFTB(K, a, m) * phiK[m];
+              }
+              pk += W(K, 3, m) * phiK[m];
+            }
+            for (int a = 0; a < 3; ++a) ug[a] = -uk[a];  // ghost state (2 f - u_K, p_K), f = 0
+            T gh[3][3];
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) gh[a][b] = gk[a][b] - (b == 1 ? eta * rk[a] : T(0.0));
+            T divh = gh[0][0] + gh[1][1] + gh[2][2];
+            T fc[4];
+            riemann_flux<T>(ug, pk, uk, pk, 1, D.c, fc, nullptr, nullptr, nullptr);
+            T fn[4];
+            for (int i = 0; i < 3; ++i) {
+              T fv = nu * (gh[i][1] + gh[1][i]) - (i == 1 ? (2.0 / 3.0) * nu * divh : T(0.0));
+              fn[i] = fc[i] - fv;
+            }
+            fn[3] = fc[3];
+            for (int i = 0; i < 4; ++i)
+              for (int m = 0; m < nb; ++m) F(K, i, m) -= wq * fn[i] * phiK[m];
+          }
     }
 }
 

@@ -88,7 +88,8 @@ def features(dL, nbr, nb1):
     """Per-element features: the element's and its 6 neighbours' P1 coefficients (4 variables x nb1),
     divided by their norm. dL: [ne, 4, nb1]; nbr: [ne, 6]. Returns (X [ne, 7*4*nb1], s [ne])."""
     D = np.asarray(dL).reshape(-1, 4 * nb1)
-    F = np.concatenate([D] + [D[nbr[:, f]] for f in range(6)], axis=1)
+    # a missing neighbour (index -1, across a wall) contributes zeros
+    F = np.concatenate([D] + [np.where((nbr[:, f] >= 0)[:, None], D[nbr[:, f]], 0.0) for f in range(6)], axis=1)
     s = np.linalg.norm(F, axis=1)
     s = np.where(s > 0.0, s, 1.0)
     return F / s[:, None], s
@@ -110,7 +111,8 @@ def coarse_correction(theta, dL, nbr, nb1, bf16=True):
     x_e = s_e * net(X_e) with X_e the normalised features of the element and its face
     neighbours and s_e their norm (x_e = 0 where s_e = 0). Returns x [ne, 4, nb1]."""
     D = np.asarray(dL).reshape(-1, 4 * nb1)
-    F = np.concatenate([D] + [D[nbr[:, f]] for f in range(6)], axis=1)
+    # a missing neighbour (index -1, across a wall) contributes zeros
+    F = np.concatenate([D] + [np.where((nbr[:, f] >= 0)[:, None], D[nbr[:, f]], 0.0) for f in range(6)], axis=1)
     s = np.linalg.norm(F, axis=1)
     X = F / np.where(s > 0.0, s, 1.0)[:, None]
     y = forward_bf16(theta, X) if bf16 else forward(theta, X)[0]

@@ -56,6 +56,8 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
            "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy",
            "dg_get_tuning", "dg_set_tuning", "dg_autotune")
+DG_WALLS_NONE = 0
+DG_WALLS_Y = 1
 DG_TUNE_FP64 = 0
 DG_TUNE_FP32 = 1
 DG_PROF_N = 10
@@ -68,7 +70,7 @@ class DgParams(ctypes.Structure):
                 ("xn", ctypes.POINTER(ctypes.c_double)), ("yn", ctypes.POINTER(ctypes.c_double)),
                 ("zn", ctypes.POINTER(ctypes.c_double)), ("nlevels", ctypes.c_int),
                 ("k", ctypes.c_int * DG_MAX_LEVELS), ("nu", ctypes.c_double), ("ac_c", ctypes.c_double),
-                ("eta", ctypes.c_double)]
+                ("eta", ctypes.c_double), ("walls", ctypes.c_int)]
 
 
 class DgSolveOpts(ctypes.Structure):
@@ -248,10 +250,10 @@ class DG:
     contiguous float64 CUDA tensors laid out [element][u, v, w, p][mode].
     """
 
-    def __init__(self, xn, yn, zn, levels, nu, ac_c=1.0, eta=7.0, boxes=None):
-        """One periodic box with node coordinates xn, yn, zn; or, with ``boxes`` (a list of
-        (xn, yn, zn) triples, xn etc. None), a handle of several independent boxes
-        (``dg_create_batch``)."""
+    def __init__(self, xn, yn, zn, levels, nu, ac_c=1.0, eta=7.0, boxes=None, walls=False):
+        """One box with node coordinates xn, yn, zn, periodic, or with no-slip walls at
+        y = yn[0] and y = yn[-1] (``walls``); or, with ``boxes`` (a list of (xn, yn, zn) triples,
+        xn etc. None), a handle of several independent boxes (``dg_create_batch``)."""
         import numpy as np
         self._L = load()
         P = ctypes.POINTER(ctypes.c_double)
@@ -261,14 +263,16 @@ class DG:
             self._nodes = [np.ascontiguousarray(a, dtype=np.float64) for a in (xn, yn, zn)]
             self.params = DgParams(len(xn) - 1, len(yn) - 1, len(zn) - 1,
                                    self._nodes[0].ctypes.data_as(P), self._nodes[1].ctypes.data_as(P),
-                                   self._nodes[2].ctypes.data_as(P), len(levels), ks, nu, ac_c, eta)
+                                   self._nodes[2].ctypes.data_as(P), len(levels), ks, nu, ac_c, eta,
+                                   DG_WALLS_Y if walls else DG_WALLS_NONE)
             rc = self._L.dg_create(ctypes.byref(self.params), ctypes.byref(h))
             self.ne = self.params.nx * self.params.ny * self.params.nz
         else:
             dims = np.array([[len(a) - 1 for a in b] for b in boxes], dtype=np.int32).ravel()
             nodes = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64) for b in boxes for a in b]))
             self._nodes = [nodes, dims]
-            self.params = DgParams(0, 0, 0, None, None, None, len(levels), ks, nu, ac_c, eta)
+            self.params = DgParams(0, 0, 0, None, None, None, len(levels), ks, nu, ac_c, eta,
+                                   DG_WALLS_Y if walls else DG_WALLS_NONE)
             rc = self._L.dg_create_batch(ctypes.byref(self.params), len(boxes),
                                          dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), nodes.ctypes.data_as(P),
                                          ctypes.byref(h))

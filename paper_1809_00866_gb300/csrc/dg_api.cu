@@ -248,7 +248,7 @@ static void free_all(Handle* h) {
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
   F(h->nbr);
-  F(h->elem_prob); F(h->dshift); F(h->chunk); F(h->chunk_prob); F(h->pchunk0);
+  F(h->elem_prob); F(h->dshift); F(h->chunk); F(h->chunk_prob); F(h->pchunk0); F(h->bface); F(h->bslot);
   F(h->colour);
   for (int l = 0; l < DG_MAX_LEVELS; ++l) {
     F(h->lev[l].Dblk); F(h->lev[l].Dinv); F(h->lev[l].Bsr); F(h->lev[l].t0); F(h->lev[l].t1); F(h->lev[l].t2);
@@ -305,6 +305,10 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
     if (l > 0 && p->k[l] >= p->k[l - 1]) return fail(h, DG_ERR_ARG, "degrees must decrease with the level");
   }
   if (!(p->nu > 0.0) || !(p->ac_c > 0.0) || !(p->eta > 0.0)) return fail(h, DG_ERR_ARG, "nu, ac_c, eta must be > 0");
+  if (p->walls != DG_WALLS_NONE && p->walls != DG_WALLS_Y) return fail(h, DG_ERR_ARG, "unknown walls flag");
+  const bool walls = p->walls == DG_WALLS_Y;
+  for (const Box& bx : boxes)
+    if (walls && bx.n[1] < 2) return fail(h, DG_ERR_ARG, "walls need at least 2 cells across the channel");
   h->p = *p;
   h->p.xn = h->p.yn = h->p.zn = nullptr;
   h->nprob = (int)boxes.size();
@@ -322,6 +326,7 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
   std::vector<int>& nbr = h->nbr_host;
   nbr.assign((size_t)ne * 6, 0);
   std::vector<int> eprob((size_t)ne);
+  std::vector<int> bface, bslot((size_t)ne, -1);
   std::vector<double> geo((size_t)ne * kGeo, 0.0);
   for (int q = 0; q < h->nprob; ++q) {
     const Box& bx = boxes[q];
@@ -338,6 +343,12 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
       nbr[e * 6 + 0] = id(I[0] - 1, I[1], I[2]); nbr[e * 6 + 1] = id(I[0] + 1, I[1], I[2]);
       nbr[e * 6 + 2] = id(I[0], I[1] - 1, I[2]); nbr[e * 6 + 3] = id(I[0], I[1] + 1, I[2]);
       nbr[e * 6 + 4] = id(I[0], I[1], I[2] - 1); nbr[e * 6 + 5] = id(I[0], I[1], I[2] + 1);
+      if (walls && I[1] == 0) {  // the wall below: no neighbour, one extra face
+        nbr[e * 6 + 2] = -1;
+        bslot[e] = (int)bface.size();
+        bface.push_back((int)e);
+      }
+      if (walls && I[1] == nn[1] - 1) nbr[e * 6 + 3] = -1;
       eprob[e] = q;
       double* G = &geo[(size_t)e * kGeo];
       for (int d = 0; d < 3; ++d) {
@@ -351,6 +362,8 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
     }
   }
   if ((rc = upload(h, &h->nbr, nbr))) return rc;
+  h->nbf = (int)bface.size();
+  if ((rc = upload(h, &h->bface, bface)) || (rc = upload(h, &h->bslot, bslot))) return rc;
   if ((rc = upload(h, &h->elem_prob, eprob))) return rc;
   if ((rc = upload(h, &h->dshift, std::vector<double>(h->nprob, 1.0)))) return rc;
   {
@@ -385,13 +398,13 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
   if ((rc = dalloc(h, &h->face_out, (size_t)ne * 6 * 4 * n2f)) || (rc = dalloc(h, &h->face_lift, (size_t)ne * 6 * 3 * n2f)) ||
       (rc = dalloc(h, &h->wlin, n0)) || (rc = dalloc(h, &h->flin, n0)) || (rc = dalloc(h, &h->fd_w, n0)) ||
       (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
-      (rc = dalloc(h, &h->dFlux, (size_t)3 * ne * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
+      (rc = dalloc(h, &h->dFlux, (size_t)(3 * ne + h->nbf) * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
       (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 1)))
     return rc;
   if ((rc = dalloc(h, &h->face_out_f, (size_t)ne * 6 * 4 * n2f)) ||
       (rc = dalloc(h, &h->face_lift_f, (size_t)ne * 6 * 3 * n2f)) ||
       (rc = dalloc(h, &h->ubar_f, (size_t)ne * 3 * h->tab.nq)) ||
-      (rc = dalloc(h, &h->dFlux_f, (size_t)3 * ne * h->tab.nqf * 32)))
+      (rc = dalloc(h, &h->dFlux_f, (size_t)(3 * ne + h->nbf) * h->tab.nqf * 32)))
     return rc;
   DG_CUDA(h, cudaDeviceSynchronize());
   return DG_OK;

@@ -119,8 +119,14 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
         // Jacobian entry (i, own j) at the points of the six faces
         for (int t = tid; t < 6 * NQF; t += nt) {
           const int sl = t / NQF, q = t - sl * NQF, d = sl >> 1, side = (sl & 1) ? 0 : 1;
-          const int f = side == 0 ? 3 * e + d : 3 * a.M.nbr[e * 6 + 2 * d] + d;
-          sJ[t] = a.dFlux[((size_t)f * NQF + q) * 32 + i * 8 + (side == 0 ? 0 : 4) + j] * sW2[q];
+          const int nb_ = a.M.nbr[e * 6 + sl];
+          const int f = side == 0 ? 3 * e + d : (nb_ >= 0 ? 3 * nb_ + d : 3 * a.M.ne + a.M.bslot[e]);
+          const R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32 + i * 8;
+          R v = Jq[(side == 0 ? 0 : 4) + j];
+          // at a wall the ghost state (-u_K, p_K) is the element's own: its columns add with
+          // sign -1 (velocity) and +1 (pressure)
+          if (nb_ < 0) v += (j == 3 ? R(1) : -R(1)) * Jq[(side == 0 ? 4 : 0) + j];
+          sJ[t] = v * sW2[q];
         }
         __syncthreads();
         for (int t = tid; t < 6 * N2 * N2; t += nt) {
@@ -176,6 +182,11 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       for (int sl = 0; sl < 6; ++sl) {
         const int d = sl >> 1, side = (sl & 1) ? 0 : 1, other = 1 - side;
         const int p = a.M.nbr[e * 6 + sl];
+        if (p < 0) {  // a wall: no neighbour block (the ghost's dependence is in the diagonal)
+          R* wb = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
+          for (int t = tid; t < b1 * b1; t += nt) wb[t] = R(0);
+          continue;
+        }
         const int f = side == 0 ? 3 * e + d : 3 * p + d;
         int tgt = sl;
         for (int s2 = 0; s2 < sl; ++s2)
@@ -248,9 +259,11 @@ static std::vector<int> greedy_colouring(const Handle* h, int dist) {
     std::vector<int> around;
     for (int f = 0; f < 6; ++f) {
       const int p = nb6[e * 6 + f];
+      if (p < 0) continue;  // a wall
       around.push_back(p);
       if (dist >= 2)
-        for (int g = 0; g < 6; ++g) around.push_back(nb6[p * 6 + g]);
+        for (int g = 0; g < 6; ++g)
+          if (nb6[p * 6 + g] >= 0) around.push_back(nb6[p * 6 + g]);
     }
     for (int p : around)
       if (p != e && col[p] >= 0) mark[col[p]] = e;
@@ -289,7 +302,7 @@ __global__ void scatter_offdiag_kernel(int ne, int nb0, int nb1, const int* nbr,
     const long long p = i / (6 * b1);
     const int rem = (int)(i - p * 6 * b1), f = rem / b1, rc = rem - f * b1;
     const int e = nbr[p * 6 + f];
-    if (colour[e] != c) continue;
+    if (e < 0 || colour[e] != c) continue;
     bool first = true;
     for (int g = 0; g < f; ++g)
       if (nbr[p * 6 + g] == e) first = false;
@@ -310,7 +323,7 @@ __global__ void scatter_rows_kernel(int ne, int nb0, int nb1, const int* nbr, co
     const long long p = i / (7 * b1);
     const int rem = (int)(i - p * 7 * b1), s = rem / b1, rc = rem - s * b1;
     const int e = s == 0 ? (int)p : nbr[p * 6 + s - 1];
-    if (colour[e] != c) continue;
+    if (e < 0 || colour[e] != c) continue;
     if (s > 0) {
       bool first = true;
       for (int g = 0; g < s - 1; ++g)
@@ -600,8 +613,11 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
   int rc;
   // the linear part (FP64, mesh only) and the FP64 fine diagonal-block buffer it lives next to
   if (!L0.Dlin) DG_CUDA(h, cudaMalloc((void**)&L0.Dlin, sizeof(double) * (size_t)L0.b * L0.b * ne));
-  if (h->nlev > 1 && !h->lev[1].Blin)
-    DG_CUDA(h, cudaMalloc((void**)&h->lev[1].Blin, sizeof(double) * (size_t)h->lev[1].b * h->lev[1].b * 7 * ne));
+  if (h->nlev > 1 && !h->lev[1].Blin) {
+    const size_t nbl = sizeof(double) * (size_t)h->lev[1].b * h->lev[1].b * 7 * ne;
+    DG_CUDA(h, cudaMalloc((void**)&h->lev[1].Blin, nbl));
+    DG_CUDA(h, cudaMemsetAsync(h->lev[1].Blin, 0, nbl, st));  // slots across a wall stay zero
+  }
   if (!h->linpart_ready) {
     if ((rc = probe_linear_part(h, st))) return rc;
     h->linpart_ready = true;

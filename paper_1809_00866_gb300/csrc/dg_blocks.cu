@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int ep
         rv[t] = v[(size_t)e * b + c] - (w ? w[(size_t)e * b + c] : R(0));
       } else {
         const int src = s == 0 ? e : nbr[(size_t)e * 6 + s - 1];
-        rv[t] = v[(size_t)src * b + c];
+        rv[t] = src >= 0 ? v[(size_t)src * b + c] : R(0);  // no neighbour across a wall (zero block)
       }
     }
     __syncthreads();

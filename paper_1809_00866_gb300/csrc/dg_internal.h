@@ -103,8 +103,14 @@ struct Handle {
   std::vector<double> node[3];  // host node coordinates
   double* dnode[3] = {nullptr, nullptr, nullptr};
   double* geo = nullptr;        // [ne][kGeo] per-element geometry
-  int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z
+  int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z; -1 across a wall
   std::vector<int> nbr_host;    // host copy of nbr
+  // faces: 3 per element (its +x, +y, +z faces; a +y face on a wall has no neighbour), then the
+  // nbf wall faces below the elements of the first row (bface[b] = that element); bslot[e] =
+  // b for those elements, else -1
+  int nbf = 0;
+  int* bface = nullptr;
+  int* bslot = nullptr;
   // independent problems (periodic boxes) sharing the handle: problem p owns the elements
   // [pe0[p], pe0[p+1]); every face neighbour of an element lies in its own problem
   int nprob = 1;
@@ -215,8 +221,13 @@ struct MeshDev {
   int nx, ny, nz, ne;
   const double* geo;  // [ne][kGeo]
   const int* nbr;
+  int nbf;            // wall faces below the first row (faces 3 ne .. 3 ne + nbf - 1)
+  const int* bface;   // [nbf] element above each of them
+  const int* bslot;   // [ne] index of the wall face below the element, or -1
 };
-inline MeshDev mesh_dev(const Handle* h) { return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->geo, h->nbr}; }
+inline MeshDev mesh_dev(const Handle* h) {
+  return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->geo, h->nbr, h->nbf, h->bface, h->bslot};
+}
 
 struct ElemGeom {
   double h[3];   // box sizes

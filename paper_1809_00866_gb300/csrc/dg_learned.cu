@@ -226,12 +226,12 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_forward_kernel(const unsigned
     R qa = R(0), qb = R(0);
 #pragma unroll
     for (int kk = 0; kk < 7; ++kk) {
-      if (va) {
+      if (va && ea[kk] >= 0) {  // a missing neighbour (wall) contributes zero features
         const R* p = d + (size_t)ea[kk] * 16;
         const R u0 = p[2 * t], u1 = p[2 * t + 1], u2 = p[8 + 2 * t], u3 = p[9 + 2 * t];
         qa += u0 * u0 + u1 * u1 + u2 * u2 + u3 * u3;
       }
-      if (vb) {
+      if (vb && eb[kk] >= 0) {
         const R* p = d + (size_t)eb[kk] * 16;
         const R u0 = p[2 * t], u1 = p[2 * t + 1], u2 = p[8 + 2 * t], u3 = p[9 + 2 * t];
         qb += u0 * u0 + u1 * u1 + u2 * u2 + u3 * u3;
@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_forward_kernel(const unsigned
 #pragma unroll
     for (int kk = 0; kk < 7; ++kk) {
       float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
-      if (va) {
+      if (va && ea[kk] >= 0) {
         const R* p = d + (size_t)ea[kk] * 16;
         f0 = (float)(p[2 * t] * ia); f1 = (float)(p[2 * t + 1] * ia);
         f2 = (float)(p[8 + 2 * t] * ia); f3 = (float)(p[9 + 2 * t] * ia);
       }
-      if (vb) {
+      if (vb && eb[kk] >= 0) {
         const R* p = d + (size_t)eb[kk] * 16;
         h0 = (float)(p[2 * t] * ib); h1 = (float)(p[2 * t + 1] * ib);
         h2 = (float)(p[8 + 2 * t] * ib); h3 = (float)(p[9 + 2 * t] * ib);
@@ -622,13 +622,14 @@ __global__ void pairs_kernel(int ne, const double* __restrict__ d, const double*
   double ss = 0.0;
   for (int k = 0; k < 7; ++k)
     for (int i = 0; i < 16; ++i) {
-      const double u = d[(size_t)src[k] * 16 + i];
+      const double u = src[k] >= 0 ? d[(size_t)src[k] * 16 + i] : 0.0;  // zero across a wall
       ss += u * u;
     }
   const double nrm = sqrt(ss);
   const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
   for (int k = 0; k < 7; ++k)
-    for (int i = 0; i < 16; ++i) X[(size_t)e * kIn + 16 * k + i] = (float)(d[(size_t)src[k] * 16 + i] * inv);
+    for (int i = 0; i < 16; ++i)
+      X[(size_t)e * kIn + 16 * k + i] = src[k] >= 0 ? (float)(d[(size_t)src[k] * 16 + i] * inv) : 0.0f;
   for (int i = 0; i < 16; ++i)
     T[(size_t)e * kOut + i] = (float)(x[(size_t)e * 16 + i] * inv + (q ? nrm * q[(size_t)e * 16 + i] : 0.0));
   s[e] = (float)nrm;

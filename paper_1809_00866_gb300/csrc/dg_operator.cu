@@ -301,10 +301,23 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
   R* sV = W + L::V;
   R* sF = W + L::F;
   R* sP = W + L::P;
-  const int nfaces = 3 * a.M.ne;
+  const int nint = 3 * a.M.ne, nfaces = nint + a.M.nbf;
   for (int f = blockIdx.x * FW + warp; f < nfaces; f += gridDim.x * FW) {
-    const int e0 = f / 3, d = f - 3 * e0;
-    const int e1 = a.M.nbr[e0 * 6 + 2 * d + 1];
+    // face f: element e0 on its - side, e1 on its + side, normal along d. A wall face has one
+    // real element; its other side is the ghost state (2f - u_K, p_K) with f = 0 (wall 1: the
+    // ghost on the + side, wall 2: on the - side); both sides then read the real element here.
+    int e0, d, e1, wall = 0;
+    if (f < nint) {
+      e0 = f / 3;
+      d = f - 3 * e0;
+      e1 = a.M.nbr[e0 * 6 + 2 * d + 1];
+      if (e1 < 0) { e1 = e0; wall = 1; }
+    } else {
+      e1 = a.M.bface[f - nint];
+      e0 = e1;
+      d = 1;
+      wall = 2;
+    }
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const R A4 = R(0.25 * g0.h[t1] * g0.h[t2]);
@@ -332,6 +345,15 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * R(side ? g1.J[d] : g0.J[d]);
     }
     __syncwarp();
+    if (wall) {  // ghost traces: velocity 2f - u_K = -u_K, the real pressure and normal derivatives
+      const int rs = wall == 1 ? 0 : 1, gs = 1 - rs;
+      for (int t = lane; t < 7 * N2; t += 32) {
+        const int fl = t / N2, j = t - fl * N2;
+        if (fl < 4) sT[gs * 4 * N2 + t] = fl < 3 ? -sT[rs * 4 * N2 + t] : sT[rs * 4 * N2 + t];
+        else sN[gs * 3 * N2 + (fl - 4) * N2 + j] = sN[rs * 3 * N2 + (fl - 4) * N2 + j];
+      }
+      __syncwarp();
+    }
     // point values of the four variables on both sides
     for (int t = lane; t < 8 * NQF; t += 32) {
       const int sv = t / NQF, q = t - sv * NQF;
@@ -391,11 +413,16 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       // {r^s} of the normal gradient component, 2D mode j of total degree bj:
       // (k - bj + 1)^2 / 4 * (1/h_K + 1/h_K') * [u]
       const int bj = DEG[j];
-      const R lr = R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]));
+      // at a wall the lifting lives on the real element alone, with the full jump:
+      // (k - bj + 1)^2 / 2 * (2/h_K) * [u]
+      const R lr = wall ? R(0.5 * (double)((K - bj + 1) * (K - bj + 1)) * g0.J[d])
+                        : R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]));
       R jump[3], Gd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        jump[c] = T0[c * N2 + j] - T1[c * N2 + j];
+        // [u] = u_K - u_K' inside; at a wall u_K - f (upper) or f - u_K (lower), half the
+        // difference of the real and the mirrored ghost traces
+        jump[c] = (wall ? R(0.5) : R(1)) * (T0[c * N2 + j] - T1[c * N2 + j]);
         Gd[c] = R(0.5) * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - R(a.eta) * lr * jump[c];  // Ghat[c][d]
       }
       // tangential derivatives (2D modal) of the normal component and of the tangential ones
@@ -409,10 +436,13 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         return acc;
       };
       const R it1 = R(g0.J[t1]), it2 = R(g0.J[t2]);
-      const R Gdt1 = R(0.5) * (tder(T0 + d * N2, 0) + tder(T1 + d * N2, 0)) * it1;    // Ghat[d][t1]
-      const R Gdt2 = R(0.5) * (tder(T0 + d * N2, 1) + tder(T1 + d * N2, 1)) * it2;    // Ghat[d][t2]
-      const R Gt1 = R(0.5) * (tder(T0 + t1 * N2, 0) + tder(T1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
-      const R Gt2 = R(0.5) * (tder(T0 + t2 * N2, 1) + tder(T1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
+      // tangential derivatives: the average of both sides, or the real side's at a wall
+      const R* A0 = wall == 2 ? T1 : T0;
+      const R* A1 = wall == 1 ? T0 : T1;
+      const R Gdt1 = R(0.5) * (tder(A0 + d * N2, 0) + tder(A1 + d * N2, 0)) * it1;    // Ghat[d][t1]
+      const R Gdt2 = R(0.5) * (tder(A0 + d * N2, 1) + tder(A1 + d * N2, 1)) * it2;    // Ghat[d][t2]
+      const R Gt1 = R(0.5) * (tder(A0 + t1 * N2, 0) + tder(A1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
+      const R Gt2 = R(0.5) * (tder(A0 + t2 * N2, 1) + tder(A1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
       const R trG = Gd[d] + Gt1 + Gt2;
       R Fv[3];
       Fv[d] = R(a.nu) * (2.0 * Gd[d] - R(2.0 / 3.0) * trG);
@@ -422,19 +452,22 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Fn[i] = A4 * (sP[i * N2 + j] - Fv[i]);
       Fn[3] = A4 * sP[3 * N2 + j];
-      R* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
-      R* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
+      const R lw = wall ? R(1) : R(0.5);  // share of the lifting on each real side
+      if (wall != 2) {
+        R* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
+        R* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        o0[i * N2 + j] = Fn[i] * is0;
-        o1[i * N2 + j] = -Fn[i] * is1;
+        for (int i = 0; i < 4; ++i) o0[i * N2 + j] = Fn[i] * is0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) l0[c * N2 + j] = lw * A4 * is0 * jump[c];
       }
-      R* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
-      R* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
+      if (wall != 1) {
+        R* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
+        R* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        l0[c * N2 + j] = R(0.5) * A4 * is0 * jump[c];
-        l1[c * N2 + j] = R(0.5) * A4 * is1 * jump[c];
+        for (int i = 0; i < 4; ++i) o1[i * N2 + j] = -Fn[i] * is1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) l1[c * N2 + j] = lw * A4 * is1 * jump[c];
       }
     }
     __syncwarp();
@@ -764,7 +797,7 @@ static int launch_face(Handle* h, const OpArgsT<R>& a, int per_sm_cap, cudaStrea
   int per_sm = (int)((200 * 1024) / fs);
   per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
   if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
-  const int fblocks = (3 * h->ne + FW - 1) / FW;
+  const int fblocks = (3 * h->ne + h->nbf + FW - 1) / FW;
   int gf = h->nsm * per_sm;
   if (gf > fblocks) gf = fblocks;
   face_kernel<K, MODE, R, FW><<<gf, 32 * FW, fs, st>>>(a);

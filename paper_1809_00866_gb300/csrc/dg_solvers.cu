@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(128) bsr_kernel(int ne, int b, const int* nbr,
     for (int t = threadIdx.x; t < 7 * b; t += blockDim.x) {
       const int s = t / b, c = t - s * b;
       const int col = s == 0 ? e : nbr[e * 6 + s - 1];
-      sx[t] = x[(size_t)col * b + c];
+      sx[t] = col >= 0 ? x[(size_t)col * b + c] : R(0);  // no neighbour across a wall (zero block)
     }
     __syncthreads();
     for (int r = threadIdx.x; r < b; r += blockDim.x) {
@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(128) bsr_t_kernel(int ne, int b, const int* nb
     __syncthreads();
     for (int t = threadIdx.x; t < 7 * b; t += blockDim.x) {
       const int s = t / b, c = t - s * b;
-      sx[t] = x[(size_t)src[s] * b + c];
+      sx[t] = src[s] >= 0 ? x[(size_t)src[s] * b + c] : R(0);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < b; r += blockDim.x) {
       R acc = R(0);
       for (int s = 0; s < 7; ++s) {
+        if (src[s] < 0) continue;  // a wall
         const int opp = s == 0 ? 0 : ((s & 1) ? s + 1 : s - 1);
         const R* blk = B + ((size_t)src[s] * 7 + opp) * b * b + (size_t)r * b;  // column r of that block
         for (int c = 0; c < b; ++c) acc += blk[c] * sx[s * b + c];
@@ -569,7 +570,7 @@ static int mg_full(Handle* h, int l, const double* g, double* x, const dg_solve_
 int prepare_lin_fp32(Handle* h, cudaStream_t st) {
   if (h->lin_f_ready) return DG_OK;
   const int ne = h->ne;
-  const long long nu = (long long)ne * 3 * h->tab.nq, nf = (long long)3 * ne * h->tab.nqf * 32;
+  const long long nu = (long long)ne * 3 * h->tab.nq, nf = (long long)(3 * ne + h->nbf) * h->tab.nqf * 32;
   convert_kernel<double, float><<<grid_for(h, nu / 256 + 1), 256, 0, st>>>(nu, h->ubar, h->ubar_f);
   DG_LAUNCH_CHECK(h);
   convert_kernel<double, float><<<grid_for(h, nf / 256 + 1), 256, 0, st>>>(nf, h->dFlux, h->dFlux_f);

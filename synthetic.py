@@ -94,3 +94,39 @@ def batch_boxes(count=64, seed=64, n_min=4, n_max=12, degrees=(2, 3, 4)):
     ns = rng.integers(n_min, n_max + 1, size=count)
     ks = rng.choice(np.asarray(degrees), size=count)
     return [(int(n), int(k)) for n, k in zip(ns, ks)]
+
+
+# Channel of the batching configuration: box 2pi x 2 x pi, walls at y = -1 and y = 1, tanh
+# wall-normal stretching whose second cell is 1.15 times the first; laminar parabolic profile
+# plus 5% seeded noise.
+CHANNEL = dict(nx=24, ny=12, nz=12, k=3, levels=(3, 2, 1), lx=TWO_PI, ly=2.0, lz=math.pi, ratio=1.15,
+               re_tau=180.0)
+
+
+def tanh_nodes(n, ratio, lo=-1.0, hi=1.0):
+    """n+1 nodes on [lo, hi], y = tanh(g s)/tanh(g) on s uniform in [-1, 1], with g chosen so
+    that the second cell from either wall is `ratio` times the first."""
+    s = np.linspace(-1.0, 1.0, n + 1)
+
+    def growth(g):
+        y = np.tanh(g * s) / np.tanh(g)
+        h = np.diff(y)
+        return h[1] / h[0]
+
+    a, b = 1e-6, 10.0
+    if growth(b) < ratio:
+        b = 50.0
+    for _ in range(200):
+        mid = 0.5 * (a + b)
+        if growth(mid) < ratio:
+            a = mid
+        else:
+            b = mid
+    y = np.tanh(0.5 * (a + b) * s) / np.tanh(0.5 * (a + b))
+    return lo + (hi - lo) * 0.5 * (y + 1.0)
+
+
+def channel_nodes(cfg=None):
+    c = CHANNEL if cfg is None else cfg
+    return (uniform_nodes(c["nx"], c["lx"]), tanh_nodes(c["ny"], c["ratio"], -0.5 * c["ly"], 0.5 * c["ly"]),
+            uniform_nodes(c["nz"], c["lz"]))
