@@ -166,6 +166,14 @@ int dg_get_status(dg_handle* h, unsigned* status, void* stream);
  * p = (cos 2x + cos 2y)(cos 2z + 2)/16 onto the fine level. */
 int dg_project_tgv(dg_handle* h, double* w, void* stream);
 
+/* Coordinates of the fine level's volume Gauss points: xyz [N_e][(k+1)^3][3] (device), point
+ * q = (q0 (k+1) + q1)(k+1) + q2 with q0, q1, q2 the Gauss-node indices along x, y, z. */
+int dg_quad_points(dg_handle* h, double* xyz, void* stream);
+
+/* w <- the L2 projection (Gauss rule) onto the fine level of a field given by its values at the
+ * points of dg_quad_points: vals [N_e][4][(k+1)^3] (device; u, v, w, p). */
+int dg_project_points(dg_handle* h, const double* vals, double* w, void* stream);
+
 /* f <- f_h(w; phi_m e_i) for every test function (Eq. (NSdiscrRes)): volume
  * terms with the BR2 corrected gradient grad u - R^K(u), face terms with the
  * exact artificial-compressibility Riemann flux and the BR2 viscous flux

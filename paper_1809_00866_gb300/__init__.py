@@ -55,7 +55,7 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling",
            "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
            "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy",
-           "dg_get_tuning", "dg_set_tuning", "dg_autotune")
+           "dg_get_tuning", "dg_set_tuning", "dg_autotune", "dg_quad_points", "dg_project_points")
 DG_WALLS_NONE = 0
 DG_WALLS_Y = 1
 DG_TUNE_FP64 = 0
@@ -161,6 +161,8 @@ def load(path=None):
     L.dg_plan_error.argtypes = [vp]
     L.dg_plan_error.restype = ctypes.c_char_p
     L.dg_plan_destroy.argtypes = [vp]
+    L.dg_quad_points.argtypes = [vp, vp, vp]
+    L.dg_project_points.argtypes = [vp, vp, vp, vp]
     L.dg_get_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
     L.dg_set_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
     L.dg_autotune.argtypes = [vp, i, i, ctypes.POINTER(d), vp]
@@ -365,6 +367,20 @@ class DG:
 
     def dg_project_tgv(self, w, stream=None):
         self._chk(self._L.dg_project_tgv(self.h, self._ptr(w), self._stream(stream)))
+
+    def dg_quad_points(self, stream=None):
+        """[N_e, (k+1)^3, 3] float64 CUDA tensor of the volume Gauss points."""
+        import torch
+        nq = (self.levels[0] + 1) ** 3
+        xyz = torch.empty((self.ne, nq, 3), dtype=torch.float64, device="cuda")
+        self._chk(self._L.dg_quad_points(self.h, ctypes.c_void_p(xyz.data_ptr()), self._stream(stream)))
+        return xyz
+
+    def dg_project_points(self, vals, w, stream=None):
+        import torch
+        nq = (self.levels[0] + 1) ** 3
+        v = _tptr(vals, torch.float64, self.ne * 4 * nq)
+        self._chk(self._L.dg_project_points(self.h, v, self._ptr(w), self._stream(stream)))
 
     def dg_residual(self, w, f, stream=None):
         self._chk(self._L.dg_residual(self.h, self._ptr(w), self._ptr(f), self._stream(stream)))

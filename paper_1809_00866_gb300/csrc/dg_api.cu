@@ -541,6 +541,18 @@ int dg_project_tgv(dg_handle* hh, double* w, void* stream) {
   return op_project_tgv(h, w, as_stream(stream));
 }
 
+int dg_quad_points(dg_handle* hh, double* xyz, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !xyz) return h ? fail(h, DG_ERR_ARG, "null pointer") : DG_ERR_ARG;
+  return op_quad_points(h, xyz, as_stream(stream));
+}
+
+int dg_project_points(dg_handle* hh, const double* vals, double* w, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !vals || !w) return h ? fail(h, DG_ERR_ARG, "null pointer") : DG_ERR_ARG;
+  return op_project_points(h, vals, w, as_stream(stream));
+}
+
 int dg_residual(dg_handle* hh, const double* w, double* f, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;

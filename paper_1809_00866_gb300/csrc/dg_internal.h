@@ -256,6 +256,8 @@ int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_tangent_f32(Handle* h, const float* v, float* out, cudaStream_t st);
 int op_fd(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_project_tgv(Handle* h, double* w, cudaStream_t st);
+int op_quad_points(Handle* h, double* xyz, cudaStream_t st);
+int op_project_points(Handle* h, const double* vals, double* w, cudaStream_t st);
 
 // vector helpers (dg_solvers.cu)
 int vec_norm2(Handle* h, const double* x, long long n, double* dev_out, cudaStream_t st);

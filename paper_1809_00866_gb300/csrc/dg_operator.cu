@@ -29,6 +29,7 @@
 // (lower index) to K'; [v] = v_K - v_K'; the lifting is defined by
 // int r . tau = + int_s [v] {tau} . n so that grad u - R^K is the consistent
 // gradient (Sec. 2.1).
+#include <algorithm>
 #include <mutex>
 
 #include "dg_internal.h"
@@ -724,6 +725,41 @@ __global__ void __launch_bounds__(128) tgv_kernel(MeshDev M, const double* Bvol,
   }
 }
 
+// ------------------------------------------------ points and projections of given fields
+template <int K>
+__global__ void __launch_bounds__(128) quad_points_kernel(MeshDev M, const double* xg, double* xyz) {
+  constexpr int N1 = K + 1, NQ = N1 * N1 * N1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)M.ne * NQ;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i / NQ), q = (int)(i - (long long)e * NQ);
+    const int q0 = q / (N1 * N1), q1 = (q / N1) % N1, q2 = q % N1;
+    const ElemGeom g = elem_geom(M, e);
+    double* o = xyz + i * 3;
+    o[0] = g.lo[0] + 0.5 * g.h[0] * (xg[q0] + 1.0);
+    o[1] = g.lo[1] + 0.5 * g.h[1] * (xg[q1] + 1.0);
+    o[2] = g.lo[2] + 0.5 * g.h[2] * (xg[q2] + 1.0);
+  }
+}
+
+// w[e][v][m] = s_e sum_q phi_hat_m(x_q) wvol_q vals[e][v][q]: the Gauss-rule L2 projection onto the
+// orthonormal basis phi_m = phi_hat_m / s_e (the |K|/8 of dx and the 1/s of phi_m give s_e)
+template <int K>
+__global__ void __launch_bounds__(128) project_points_kernel(MeshDev M, const double* Bvol, const double* wvol,
+                                                             const double* vals, double* w) {
+  using S = Sz<K>;
+  constexpr int NB = S::NB, NQ = S::NQ;
+  for (int e = blockIdx.x; e < M.ne; e += gridDim.x) {
+    const ElemGeom g = elem_geom(M, e);
+    const double* ve = vals + (size_t)e * 4 * NQ;
+    for (int t = threadIdx.x; t < 4 * NB; t += blockDim.x) {
+      const int v = t / NB, m = t - v * NB;
+      double acc = 0.0;
+      for (int q = 0; q < NQ; ++q) acc += Bvol[q * NB + m] * wvol[q] * ve[v * NQ + q];
+      w[(size_t)e * 4 * NB + t] = acc * g.s;
+    }
+  }
+}
+
 // ------------------------------------------------------------- FD helpers
 __global__ void fd_perturb_kernel(long long n, const double* w, const double* v, const double* wnorm2,
                                   const double* vnorm2, double* out) {
@@ -882,6 +918,32 @@ int op_fd(Handle* h, const double* v, double* out, cudaStream_t st) {
   if (rc) return rc;
   fd_finish_kernel<<<blocks, 256, 0, st>>>(n, h->lev[0].nb, h->fd_f, h->flin, v, h->wnorm2, h->red_out,
                                            h->inv_gdt, h->geo, out);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+int op_quad_points(Handle* h, double* xyz, cudaStream_t st) {
+  const MeshDev M = mesh_dev(h);
+  const int grid = h->nsm * 8;
+  switch (h->tab.k) {
+    case 1: quad_points_kernel<1><<<grid, 128, 0, st>>>(M, h->tab.xg, xyz); break;
+    case 2: quad_points_kernel<2><<<grid, 128, 0, st>>>(M, h->tab.xg, xyz); break;
+    case 3: quad_points_kernel<3><<<grid, 128, 0, st>>>(M, h->tab.xg, xyz); break;
+    case 4: quad_points_kernel<4><<<grid, 128, 0, st>>>(M, h->tab.xg, xyz); break;
+  }
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
+int op_project_points(Handle* h, const double* vals, double* w, cudaStream_t st) {
+  const MeshDev M = mesh_dev(h);
+  const int grid = std::min(h->ne, h->nsm * 8);
+  switch (h->tab.k) {
+    case 1: project_points_kernel<1><<<grid, 128, 0, st>>>(M, h->tab.Bvol, h->tab.wvol, vals, w); break;
+    case 2: project_points_kernel<2><<<grid, 128, 0, st>>>(M, h->tab.Bvol, h->tab.wvol, vals, w); break;
+    case 3: project_points_kernel<3><<<grid, 128, 0, st>>>(M, h->tab.Bvol, h->tab.wvol, vals, w); break;
+    case 4: project_points_kernel<4><<<grid, 128, 0, st>>>(M, h->tab.Bvol, h->tab.wvol, vals, w); break;
+  }
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }

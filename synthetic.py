@@ -130,3 +130,56 @@ def channel_nodes(cfg=None):
     c = CHANNEL if cfg is None else cfg
     return (uniform_nodes(c["nx"], c["lx"]), tanh_nodes(c["ny"], c["ratio"], -0.5 * c["ly"], 0.5 * c["ly"]),
             uniform_nodes(c["nz"], c["lz"]))
+
+
+def channel_noise_modes(seed, modes=8):
+    """Seeded modes of the vector potential of the channel's perturbation: per component of psi
+    and per mode, (kx, kz, ky, phase_xz, phase_y, amplitude); kx, kz integer multiples of the
+    box's wavenumbers 2pi/lx = 1 and 2pi/lz = 2."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((3, modes, 6))
+    out[..., 0] = rng.integers(1, 4, size=(3, modes))
+    out[..., 1] = 2.0 * rng.integers(1, 3, size=(3, modes))
+    out[..., 2] = rng.uniform(0.5, 3.0, size=(3, modes))
+    out[..., 3] = rng.uniform(0.0, TWO_PI, size=(3, modes))
+    out[..., 4] = rng.uniform(0.0, TWO_PI, size=(3, modes))
+    out[..., 5] = rng.standard_normal((3, modes))
+    return out
+
+
+def channel_field(x, y, z, seed=180, amp=0.05, modes=8):
+    """Channel initial field at points (arrays of equal shape): the laminar profile
+    u = 1 - y^2 (walls at y = -1, 1) plus amp times a unit-rms divergence-free perturbation,
+    the curl of psi = (1 - y^2)^2 sum_m a cos(kx x + kz z + t1) cos(ky y + t2), which vanishes
+    with its first derivatives on the walls. Returns (u, v, w, p)."""
+    md = channel_noise_modes(seed, modes)
+    up = _channel_curl(md, x, y, z)
+    # unit rms over a fixed sampling of the box, independent of the points asked for
+    gx = np.linspace(0.0, TWO_PI, 17)[:-1]
+    gy = np.linspace(-1.0, 1.0, 17)
+    gz = np.linspace(0.0, math.pi, 9)[:-1]
+    X, Y, Z = np.meshgrid(gx, gy, gz, indexing="ij")
+    rms = math.sqrt(np.mean(np.sum(_channel_curl(md, X, Y, Z) ** 2, axis=0)))
+    up = up * (amp / rms)
+    return 1.0 - y * y + up[0], up[1], up[2], 0.0 * y
+
+
+def _channel_curl(md, x, y, z):
+    g = (1.0 - y * y) ** 2
+    dg = -4.0 * y * (1.0 - y * y)
+    d = np.zeros((3, 3) + np.shape(x))
+    for i in range(3):
+        for kx, kz, ky, t1, t2, a in md[i]:
+            A = kx * x + kz * z + t1
+            B = ky * y + t2
+            ca, sa, cb, sb = np.cos(A), np.sin(A), np.cos(B), np.sin(B)
+            d[i, 0] += -a * kx * sa * cb * g
+            d[i, 1] += a * ca * (cb * dg - ky * sb * g)
+            d[i, 2] += -a * kz * sa * cb * g
+    return np.stack([d[2, 1] - d[1, 2], d[0, 2] - d[2, 0], d[1, 0] - d[0, 1]])
+
+
+def channel_nu(re_tau=180.0, u_center=1.0):
+    """Viscosity for which the laminar profile u_c (1 - y^2) has friction Reynolds number re_tau
+    (half-height 1): u_tau^2 = nu |du/dy|_wall = 2 nu u_c, re_tau = u_tau / nu."""
+    return 2.0 * u_center / (re_tau * re_tau)

@@ -160,3 +160,15 @@ def test_wall_learned_features():
     ref = SV.prolong(M.coarse_correction(th.astype(np.float64), dc, m.neighbours(), O.nb(1)).reshape(-1),
                      m.ne, m.nb, O.nb(1))
     assert rel(host(zc).reshape(-1), ref) < 2e-3
+
+
+def test_quad_points_and_projection():
+    # the channel field at the handle's Gauss points, projected on the GPU and by the oracle
+    P, dg, m = wall_pair(chan_nodes(3, 4, 2, seed=2), [3])
+    xyz = host(dg.dg_quad_points())
+    xo, _ = O.quad_points(m)
+    np.testing.assert_allclose(xyz, xo, rtol=0, atol=1e-14)
+    vals = np.ascontiguousarray(np.stack(S.channel_field(xo[..., 0], xo[..., 1], xo[..., 2]), axis=1))
+    w = dg.empty()
+    dg.dg_project_points(dev(vals), w)
+    assert rel(host(w).reshape(-1), O.project_points(m, vals).reshape(-1)) < 1e-13
