@@ -350,13 +350,12 @@ def run_batch(args, P, make_opts, prec, stream, flush, world):
     return out
 
 
-def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
-    """The channel workload: 24 x 12 x 12 hexahedra on 2pi x 2 x pi with no-slip walls at
-    y = -1, 1 and tanh stretching (second cell 1.15 x the first), P3, p-levels 3-2-1, viscosity
-    for Re_tau = 180 of the laminar profile, initial field the laminar profile plus a 5%
-    divergence-free perturbation (seed 180), acoustic CFL 50 on the smallest cell; one linearly
-    implicit stage from that field to rel-res 1e-8, the chosen form against the plain FP64 form.
-    Every timed step recomputes the whole stage (right-hand side, linearisation, assembly, solve)."""
+def channel_setup(args, P):
+    """The channel workload's handle and fields: 24 x 12 x 12 hexahedra on 2pi x 2 x pi with
+    no-slip walls at y = -1, 1 and tanh stretching (second cell 1.15 x the first), P3, p-levels
+    3-2-1, viscosity for Re_tau = 180 of the laminar profile, initial field the laminar profile
+    plus a 5% divergence-free perturbation (seed 180; other seeds give training states), acoustic
+    CFL 50 on the smallest cell."""
     import numpy as np
     import torch
     c = S.CHANNEL
@@ -367,12 +366,25 @@ def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
     if args.stb_rescale:
         dg.dg_set_stb_rescaling(True)
     pts = dg.dg_quad_points().cpu().numpy()
-    vals = np.ascontiguousarray(np.stack(S.channel_field(pts[..., 0], pts[..., 1], pts[..., 2]), axis=1))
-    w0 = dg.empty()
-    dg.dg_project_points(torch.from_numpy(vals).cuda(), w0)
+
+    def field(seed):
+        vals = np.ascontiguousarray(np.stack(S.channel_field(pts[..., 0], pts[..., 1], pts[..., 2], seed=seed),
+                                             axis=1))
+        w = dg.empty()
+        dg.dg_project_points(torch.from_numpy(vals).cuda(), w)
+        return w
+
     umax = 1.05
     dt = 50.0 * float(np.diff(yn).min()) / ((2 * k + 1) * (umax + math.sqrt(umax * umax + S.AC_C ** 2)))
-    inv = 1.0 / dt
+    return {"dg": dg, "w0": field(180), "field": field, "inv": 1.0 / dt, "dt": dt, "nu": nu, "k": k}
+
+
+def run_channel(args, P, ch, make_opts, plain_opts, learned_opts, stream, flush):
+    """One linearly implicit stage of the channel from its initial field to rel-res 1e-8: the
+    chosen form, the plain FP64 form and (when trained) the learned form. Every timed step
+    recomputes the whole stage (right-hand side, linearisation, assembly, solve)."""
+    import torch
+    dg, w0, inv, dt, nu, k = ch["dg"], ch["w0"], ch["inv"], ch["dt"], ch["nu"], ch["k"]
     g, x = dg.empty(), dg.empty()
     asm = lambda o: P.DG_PRECOND_FP64 if o.precision == P.DG_PRECOND_FP64 else P.DG_PRECOND_FP32
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -391,7 +403,10 @@ def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
         for which in (P.DG_TUNE_FP64, P.DG_TUNE_FP32):
             dg.dg_autotune(which, use_cache=False)
     out = {}
-    for name, opts in (("plain_fp64", plain_opts), ("chosen", chosen)):
+    forms = [("plain_fp64", plain_opts), ("chosen", chosen)]
+    if learned_opts is not None:
+        forms.append(("learned", learned_opts))
+    for name, opts in forms:
         for _ in range(args.warmup):
             stage(opts)
         torch.cuda.synchronize()
@@ -408,6 +423,8 @@ def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
             its.append(info.its)
             rr.append(info.true_relres)
         out[name] = {"s_per_stage": statistics.mean(times), "fgmres_its": its, "true_relres": rr}
+        if name == "learned":
+            out[name]["fallback_at"] = info.fallback_at
     xs = {}
     for name, opts in (("plain_fp64", plain_opts), ("chosen", chosen)):
         stage(opts)
@@ -434,7 +451,7 @@ def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
                     "(nu = %.3e), laminar profile + 5%% divergence-free perturbation (seed 180), acoustic CFL 50 "
                     "on the smallest cell (dt = %.4f); one linearly implicit stage to rel-res 1e-8" % (nu, dt),
         "dofs": dg.n[0],
-        "chosen": out["chosen"], "plain_fp64": out["plain_fp64"],
+        "chosen": out["chosen"], "plain_fp64": out["plain_fp64"], "learned": out.get("learned"),
         "speedup_chosen_vs_plain": out["plain_fp64"]["s_per_stage"] / out["chosen"]["s_per_stage"],
         "first_stage_solution_rel_diff": float((xs["chosen"] - xs["plain_fp64"]).norm() / xs["plain_fp64"].norm()),
         "jv": {"value": dg.n[0] / statistics.median(jt) / 1e9, "unit": "GDOF/s", "mode": "exact (tangent), FP64",
@@ -442,6 +459,10 @@ def run_channel(args, P, make_opts, plain_opts, prec, stream, flush):
         "tuning": {"fp64_products": dg.dg_get_tuning(P.DG_TUNE_FP64).as_dict(),
                    "fp32_cycle": dg.dg_get_tuning(P.DG_TUNE_FP32).as_dict()} if args.autotune else None,
     }
+    if "learned" in out:
+        res["learned"]["vs_chosen_without_network"] = out["chosen"]["s_per_stage"] / out["learned"]["s_per_stage"]
+        res["learned"]["what"] = ("the chosen cycle with the network trained on Taylor-Green and channel states "
+                                  "(seeds other than the timed field's) replacing the coarsest solve")
     dg.close()
     return res
 
@@ -563,6 +584,8 @@ def run_ours(args):
             rep = dg.dg_autotune(which, use_cache=False)
             tuning[nm] = {"chosen": dg.dg_get_tuning(which).as_dict(), "device_ms_default_vs_chosen": rep}
 
+    chan = channel_setup(args, P) if args.channel else None
+
     # --- learned coarse correction: trained here (untimed setup) by the library's BF16 kernels on
     # the coarse right-hand sides that the chosen cycle produces in the stages of the first states
     learned_opts, learned_setup = None, None
@@ -576,11 +599,17 @@ def run_ours(args):
             stage(w, chosen_opts, {"its": [], "relres": []})
             states.append(w.clone())
         D = Lrn.collect_rhs(dg, states, inv, chosen_opts, per_state=40)
+        extra = []
+        if chan is not None:  # channel states of other seeds than the timed field
+            chan_states = [chan["field"](s) for s in (181, 182, 183)]
+            Dc = Lrn.collect_rhs(chan["dg"], chan_states, chan["inv"], opts_for(chosen_prec, args.omega),
+                                 per_state=40)
+            extra.append((chan["dg"], Dc))
         torch.cuda.synchronize()
         t_collect = time.perf_counter() - t0
         dg.dg_set_linearization(states[-1], inv)
         dg.dg_assemble()
-        theta, rep = Lrn.train_residual(dg, D, steps=args.learn_steps, lr=1e-3, seed=0)
+        theta, rep = Lrn.train_residual(dg, D, steps=args.learn_steps, lr=1e-3, seed=0, extra=extra)
         # coarse-level quality on the last state: the network vs the block-Jacobi sweeps it replaces
         r_net = Lrn.residual_ratio(dg, D[-8:])
         lc = len(levels) - 1
@@ -594,6 +623,8 @@ def run_ours(args):
             r_jac.append(float(rj.norm().item()) / float(d.norm().item()))
         learned_setup = {"collect_s": t_collect, "train_s": rep["train_s"], "train_steps": rep["steps"],
                          "coarse_vectors": rep["vectors"],
+                         "coarse_vectors_per_mesh": dict(zip(["taylor_green_16_p4", "channel_p3"],
+                                                             rep["vectors_per_set"])),
                          "coarse_residual_ratio": {"network": r_net,
                                                    "block_jacobi_%d_sweeps" % max(1, coarse): statistics.mean(r_jac)}}
         learned_opts = P.solve_opts(restart=30, maxit=300, rtol=RTOL, precond=P.DG_PREC_VCYCLE, pre_sweeps=pre,
@@ -768,9 +799,9 @@ def run_ours(args):
             "vs_plain_fp64": plain["s_per_stage"] / lf["s_per_stage"],
             "vs_precision_form_without_network": (chosen["s_per_stage"] / lf["s_per_stage"])
             if args.coarse != "learned" else None})
-    if args.channel:
-        line["channel_form"] = run_channel(args, P, lambda: opts_for(chosen_prec, args.omega), plain_opts, chosen_prec,
-                                           st, flush)
+    if chan is not None:
+        line["channel_form"] = run_channel(args, P, chan, lambda: opts_for(chosen_prec, args.omega), plain_opts,
+                                           learned_opts, st, flush)
     if args.batch:
         line["batch_form"] = run_batch(args, P, lambda: opts_for(chosen_prec, args.omega), chosen_prec, st, flush,
                                        world)

@@ -63,52 +63,65 @@ def collect_rhs(dg, states, inv_gamma_dt, opts, per_state=32):
     return torch.stack(out)
 
 
-def train_residual(dg, D, steps=2000, lr=1e-3, lr_final=5e-5, seed=0, theta=None, iterate_every=2, val=None):
+def train_residual(dg, D, steps=2000, lr=1e-3, lr_final=5e-5, seed=0, theta=None, iterate_every=2, val=None,
+                   extra=None):
     """Train N as a local approximate inverse of the coarsest-level operator G of the handle's
     current assembly: minimise ||d - G s N(X(d))||^2 over recorded right-hand sides d (whole
     coarse vectors, all elements form the batch). Each step: x = s N(X) (``dg_coarse_apply``),
     r = d - G x (``bsr_spmv``), q = G^T r (``bsr_spmv_t``), residual targets
     (``dg_coarse_pairs`` with q), BF16 gradient (``dg_mlp_grad``) and Adam. Every
     ``iterate_every``-th step trains on the residual d - G x of the current network instead, the
-    input that the next iteration of ``DG_COARSE_LEARNED_ITER`` sees. Returns (theta, report)."""
+    input that the next iteration of ``DG_COARSE_LEARNED_ITER`` sees. ``extra``: more
+    (handle, vectors) sets, for instance of another mesh; the steps cycle through the sets, each
+    with its own handle's operator. The network ends installed on every handle. Returns
+    (theta, report)."""
     import torch
-    lc = len(dg.levels) - 1
-    ne = dg.ne
+    sets = [(dg, D)] + list(extra or [])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     th = init_theta(seed, out_scale=0.01) if theta is None else theta.clone()
     m = torch.zeros_like(th)
     v = torch.zeros_like(th)
     grad = torch.empty_like(th)
-    X = torch.empty((ne, DG_MLP_IN), dtype=torch.float32, device="cuda")
-    T = torch.empty((ne, DG_MLP_OUT), dtype=torch.float32, device="cuda")
-    s = torch.empty(ne, dtype=torch.float32, device="cuda")
-    y, r, q, d2 = (dg.empty(lc) for _ in range(4))
-    ws = mlp_workspace(ne)
+    bufs = []
+    for h, _ in sets:
+        lc = len(h.levels) - 1
+        bufs.append({"X": torch.empty((h.ne, DG_MLP_IN), dtype=torch.float32, device="cuda"),
+                     "T": torch.empty((h.ne, DG_MLP_OUT), dtype=torch.float32, device="cuda"),
+                     "s": torch.empty(h.ne, dtype=torch.float32, device="cuda"),
+                     "vec": [h.empty(lc) for _ in range(4)], "ws": mlp_workspace(h.ne), "lc": lc})
     rng = np.random.default_rng(seed)
 
-    def residual(d):
-        dg.dg_coarse_apply(d, y)
-        r.copy_(d)
-        dg.bsr_spmv(lc, -1.0, y, 1.0, r)
-
     for it in range(1, steps + 1):
-        dg.dg_set_coarse_network(th)
-        d = D[int(rng.integers(len(D)))]
+        si = (it - 1) % len(sets)
+        h, Dh = sets[si]
+        b = bufs[si]
+        lc = b["lc"]
+        y, r, q, d2 = b["vec"]
+
+        def residual(d):
+            h.dg_coarse_apply(d, y)
+            r.copy_(d)
+            h.bsr_spmv(lc, -1.0, y, 1.0, r)
+
+        h.dg_set_coarse_network(th)
+        d = Dh[int(rng.integers(len(Dh)))]
         if iterate_every and it % iterate_every == 0:
             residual(d)
             d2.copy_(r)
             d = d2
         residual(d)
-        dg.bsr_spmv_t(lc, 1.0, r, 0.0, q)
-        dg.dg_coarse_pairs(d, y, X, T, s, q=q)
-        dg_mlp_grad(th, X, T, ne, grad, ws=ws)
+        h.bsr_spmv_t(lc, 1.0, r, 0.0, q)
+        h.dg_coarse_pairs(d, y, b["X"], b["T"], b["s"], q=q)
+        dg_mlp_grad(th, b["X"], b["T"], h.ne, grad, ws=b["ws"])
         c = 0.5 * (1.0 + math.cos(math.pi * (it - 1) / max(1, steps - 1)))
         dg_mlp_adam(th, grad, m, v, it, lr=lr_final + (lr - lr_final) * c)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    dg.dg_set_coarse_network(th)
-    rep = {"steps": steps, "train_s": t_train, "vectors": int(len(D))}
+    for h, _ in sets:
+        h.dg_set_coarse_network(th)
+    rep = {"steps": steps, "train_s": t_train, "vectors": int(sum(len(Dh) for _, Dh in sets)),
+           "vectors_per_set": [int(len(Dh)) for _, Dh in sets]}
     if val is not None:
         rep["val_residual_ratio"] = residual_ratio(dg, val)
     return th, rep
