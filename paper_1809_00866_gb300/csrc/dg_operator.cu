@@ -242,6 +242,33 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
 }
 
 // ---------------------------------------------------------------- face pass
+// eight consecutive values from 16-byte aligned shared memory (two 16-byte loads for float,
+// four for double), and the same from global memory (the cached Riemann Jacobian)
+__device__ __forceinline__ void load8(const float* p, float* o) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load8(const double* p, double* o) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 v = reinterpret_cast<const double2*>(p)[i];
+    o[2 * i] = v.x;
+    o[2 * i + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void load8g(const float* p, float* o) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load8g(const double* p, double* o) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+    o[2 * i] = v.x;
+    o[2 * i + 1] = v.y;
+  }
+}
+
 constexpr int kFaceWarps = 4;  // default faces per CTA, one warp each (the tangent pass's is tunable)
 
 template <int K, class R = double, int FW = kFaceWarps>
@@ -249,12 +276,11 @@ struct FaceSmem {
   using S = Sz2<K>;
   // per warp
   static constexpr int C = 0;                           // [2][4][NB] coefficients of K and K'
-  static constexpr int T = C + 8 * S::NB;               // [2][4][N2] value traces
+  static constexpr int T = C + 8 * S::NB;               // [N2][2][4] value traces (a 2D mode's 8 together)
   static constexpr int N = T + 8 * S::N2;               // [2][3][N2] normal-derivative traces of velocity
-  static constexpr int V = N + 6 * S::N2;               // [2][4][NQF] point values
-  static constexpr int F = V + 8 * S::NQF;              // [4][NQF] weighted Riemann flux
+  static constexpr int F = N + 6 * S::N2;               // [4][NQF] weighted Riemann flux
   static constexpr int P = F + 4 * S::NQF;              // [4][N2] its projection
-  static constexpr int WARP = P + 4 * S::N2;
+  static constexpr int WARP = (P + 4 * S::N2 + 3) / 4 * 4;  // 16-byte multiple (vector loads of T)
   // per CTA tables (after the warps)
   static constexpr int B2 = FW * WARP;                  // [NQF][N2]
   static constexpr int W2 = B2 + S::NQF * S::N2;        // [NQF]
@@ -299,7 +325,6 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
   R* sC = W + L::C;
   R* sT = W + L::T;
   R* sN = W + L::N;
-  R* sV = W + L::V;
   R* sF = W + L::F;
   R* sP = W + L::P;
   const int nint = 3 * a.M.ne, nfaces = nint + a.M.nbf;
@@ -321,66 +346,88 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
     }
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    const R A4 = R(0.25 * g0.h[t1] * g0.h[t2]);
+    // the geometry along the face's axes, read with selects (no run-time indexing of g0, g1)
+    auto sel3 = [](const double* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
+    const double J0d = sel3(g0.J, d), J1d = sel3(g1.J, d);
+    const double J0t1 = sel3(g0.J, t1), J0t2 = sel3(g0.J, t2);
+    const R A4 = R(0.25 * sel3(g0.h, t1) * sel3(g0.h, t2));
     const R is0 = R(g0.is), is1 = R(g1.is);
     for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
       sC[t] = a.in[(size_t)(side ? e1 : e0) * 4 * NB + r];
     }
     __syncwarp();
-    // 2D trace coefficients: values of u, v, w, p and normal derivatives of u, v, w
-    for (int t = lane; t < 14 * N2; t += 32) {
-      const int side = t / (7 * N2), r = t - side * 7 * N2, fl = r / N2, j = r - fl * N2;
-      const int var = fl < 4 ? fl : fl - 4;
-      const R* c = sC + side * 4 * NB + var * NB;
-      const R* pw = fl < 4 ? PV + side * K1 : PD + side * K1;
+    // 2D trace coefficients, one lane per (side, 2D mode j): the values of u, v, w, p and the
+    // normal derivatives of u, v, w (2 N2 <= 30 lanes for k <= 4)
+    if (lane < 2 * N2) {
+      const int side = lane >= N2 ? 1 : 0, j = lane - side * N2;
       const int* mm = M3 + (d * N2 + j) * K1;
-      R acc = R(0);
+      const R* cs = sC + side * 4 * NB;
+      const R* pw = PV + side * K1;
+      const R* pdw = PD + side * K1;
+      R val[4] = {R(0), R(0), R(0), R(0)}, der[3] = {R(0), R(0), R(0)};
 #pragma unroll
       for (int e = 0; e < K1; ++e) {
         const int m = mm[e];
-        if (m >= 0) acc += pw[e] * c[m];
+        if (m >= 0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const R c = cs[v * NB + m];
+            val[v] += pw[e] * c;
+            if (v < 3) der[v] += pdw[e] * c;
+          }
+        }
       }
       const R is = side ? is1 : is0;
-      if (fl < 4) sT[side * 4 * N2 + fl * N2 + j] = acc * is;
-      else sN[side * 3 * N2 + (fl - 4) * N2 + j] = acc * is * R(side ? g1.J[d] : g0.J[d]);
-    }
-    __syncwarp();
-    if (wall) {  // ghost traces: velocity 2f - u_K = -u_K, the real pressure and normal derivatives
-      const int rs = wall == 1 ? 0 : 1, gs = 1 - rs;
-      for (int t = lane; t < 7 * N2; t += 32) {
-        const int fl = t / N2, j = t - fl * N2;
-        if (fl < 4) sT[gs * 4 * N2 + t] = fl < 3 ? -sT[rs * 4 * N2 + t] : sT[rs * 4 * N2 + t];
-        else sN[gs * 3 * N2 + (fl - 4) * N2 + j] = sN[rs * 3 * N2 + (fl - 4) * N2 + j];
-      }
-      __syncwarp();
-    }
-    // point values of the four variables on both sides
-    for (int t = lane; t < 8 * NQF; t += 32) {
-      const int sv = t / NQF, q = t - sv * NQF;
-      const R* Tc = sT + sv * N2;
-      const R* b = B2 + q * N2;
-      R acc = R(0);
+      const R js = is * R(side ? J1d : J0d);
+      R* tt = sT + j * 8 + side * 4;
 #pragma unroll
-      for (int j = 0; j < N2; ++j) acc += b[j] * Tc[j];
-      sV[t] = acc;
+      for (int v = 0; v < 4; ++v) tt[v] = val[v] * is;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sN[side * 3 * N2 + c * N2 + j] = der[c] * js;
     }
     __syncwarp();
-    for (int q = lane; q < NQF; q += 32) {
-      const R* V0 = sV;
-      const R* V1 = sV + 4 * NQF;
-      R uL[3] = {V0[q], V0[NQF + q], V0[2 * NQF + q]};
-      R uR[3] = {V1[q], V1[NQF + q], V1[2 * NQF + q]};
-      const R pL = V0[3 * NQF + q], pR = V1[3 * NQF + q];
+    if (wall && lane < N2) {  // ghost traces: velocity 2f - u_K = -u_K, the real pressure and normal derivatives
+      const int rs = wall == 1 ? 0 : 1, gs = 1 - rs, j = lane;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const R x = sT[j * 8 + rs * 4 + v];
+        sT[j * 8 + gs * 4 + v] = v < 3 ? -x : x;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sN[gs * 3 * N2 + c * N2 + j] = sN[rs * 3 * N2 + c * N2 + j];
+    }
+    __syncwarp();
+    // one lane per face point: the point values of both sides (kept in registers) and the
+    // Riemann flux, or its linearisation, at that point
+    if (lane < NQF) {
+      const int q = lane;
+      R pvq[8];
+#pragma unroll
+      for (int s8 = 0; s8 < 8; ++s8) pvq[s8] = R(0);
+      const R* b = B2 + q * N2;
+#pragma unroll
+      for (int j = 0; j < N2; ++j) {
+        const R bj = b[j];
+        R tt[8];
+        load8(sT + j * 8, tt);
+#pragma unroll
+        for (int s8 = 0; s8 < 8; ++s8) pvq[s8] += bj * tt[s8];
+      }
+      R uL[3] = {pvq[0], pvq[1], pvq[2]};
+      R uR[3] = {pvq[4], pvq[5], pvq[6]};
+      const R pL = pvq[3], pR = pvq[7];
       R Fc[4] = {R(0), R(0), R(0), R(0)};
       if constexpr (MODE == MODE_TAN) {
         const R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
-        const R ds[8] = {uL[0], uL[1], uL[2], pL, uR[0], uR[1], uR[2], pR};
+        R Jr[32];
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) load8g(Jq + i, Jr + i);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           R acc = R(0);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc += Jq[i * 8 + j] * ds[j];
+          for (int j = 0; j < 8; ++j) acc += Jr[i * 8 + j] * pvq[j];
           Fc[i] = acc;
         }
       } else if constexpr (MODE == MODE_RES_LIN) {
@@ -409,49 +456,54 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
     __syncwarp();
     // viscous face flux in 2D modal space, total flux, lifting; one lane per 2D mode
     for (int j = lane; j < N2; j += 32) {
-      const R* T0 = sT;
-      const R* T1 = sT + 4 * N2;
+      // trace of variable v on side s at 2D mode jj
+      auto tr = [&](int s2, int v, int jj) { return sT[jj * 8 + s2 * 4 + v]; };
       // {r^s} of the normal gradient component, 2D mode j of total degree bj:
       // (k - bj + 1)^2 / 4 * (1/h_K + 1/h_K') * [u]
       const int bj = DEG[j];
       // at a wall the lifting lives on the real element alone, with the full jump:
       // (k - bj + 1)^2 / 2 * (2/h_K) * [u]
-      const R lr = wall ? R(0.5 * (double)((K - bj + 1) * (K - bj + 1)) * g0.J[d])
-                        : R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (g0.J[d] + g1.J[d]));
+      const R lr = wall ? R(0.5 * (double)((K - bj + 1) * (K - bj + 1)) * J0d)
+                        : R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (J0d + J1d));
       R jump[3], Gd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         // [u] = u_K - u_K' inside; at a wall u_K - f (upper) or f - u_K (lower), half the
         // difference of the real and the mirrored ghost traces
-        jump[c] = (wall ? R(0.5) : R(1)) * (T0[c * N2 + j] - T1[c * N2 + j]);
+        jump[c] = (wall ? R(0.5) : R(1)) * (tr(0, c, j) - tr(1, c, j));
         Gd[c] = R(0.5) * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - R(a.eta) * lr * jump[c];  // Ghat[c][d]
       }
       // tangential derivatives (2D modal) of the normal component and of the tangential ones
-      auto tder = [&](const R* Tc, int dir) {
+      auto tder = [&](int s2, int v, int dir) {
         R acc = R(0);
 #pragma unroll
         for (int q = 0; q < DW; ++q) {
           const int o = (dir * N2 + j) * DW + q;
-          acc += D2V[o] * Tc[D2I[o]];
+          acc += D2V[o] * tr(s2, v, D2I[o]);
         }
         return acc;
       };
-      const R it1 = R(g0.J[t1]), it2 = R(g0.J[t2]);
+      const R it1 = R(J0t1), it2 = R(J0t2);
       // tangential derivatives: the average of both sides, or the real side's at a wall
-      const R* A0 = wall == 2 ? T1 : T0;
-      const R* A1 = wall == 1 ? T0 : T1;
-      const R Gdt1 = R(0.5) * (tder(A0 + d * N2, 0) + tder(A1 + d * N2, 0)) * it1;    // Ghat[d][t1]
-      const R Gdt2 = R(0.5) * (tder(A0 + d * N2, 1) + tder(A1 + d * N2, 1)) * it2;    // Ghat[d][t2]
-      const R Gt1 = R(0.5) * (tder(A0 + t1 * N2, 0) + tder(A1 + t1 * N2, 0)) * it1;   // Ghat[t1][t1]
-      const R Gt2 = R(0.5) * (tder(A0 + t2 * N2, 1) + tder(A1 + t2 * N2, 1)) * it2;   // Ghat[t2][t2]
-      const R trG = Gd[d] + Gt1 + Gt2;
-      R Fv[3];
-      Fv[d] = R(a.nu) * (2.0 * Gd[d] - R(2.0 / 3.0) * trG);
-      Fv[t1] = R(a.nu) * (Gd[t1] + Gdt1);
-      Fv[t2] = R(a.nu) * (Gd[t2] + Gdt2);
+      const int A0 = wall == 2 ? 1 : 0;
+      const int A1 = wall == 1 ? 0 : 1;
+      const R Gdt1 = R(0.5) * (tder(A0, d, 0) + tder(A1, d, 0)) * it1;    // Ghat[d][t1]
+      const R Gdt2 = R(0.5) * (tder(A0, d, 1) + tder(A1, d, 1)) * it2;    // Ghat[d][t2]
+      const R Gt1 = R(0.5) * (tder(A0, t1, 0) + tder(A1, t1, 0)) * it1;   // Ghat[t1][t1]
+      const R Gt2 = R(0.5) * (tder(A0, t2, 1) + tder(A1, t2, 1)) * it2;   // Ghat[t2][t2]
+      // Ghat[c][d] of the components along d, t1, t2 (selects: no run-time array indexing)
+      auto pick = [&](int c) { return c == 0 ? Gd[0] : (c == 1 ? Gd[1] : Gd[2]); };
+      const R Gdd = pick(d), Gt1d = pick(t1), Gt2d = pick(t2);
+      const R trG = Gdd + Gt1 + Gt2;
+      const R Fvd = R(a.nu) * (2.0 * Gdd - R(2.0 / 3.0) * trG);
+      const R Fvt1 = R(a.nu) * (Gt1d + Gdt1);
+      const R Fvt2 = R(a.nu) * (Gt2d + Gdt2);
       R Fn[4];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Fn[i] = A4 * (sP[i * N2 + j] - Fv[i]);
+      for (int i = 0; i < 3; ++i) {
+        const R Fv = i == d ? Fvd : (i == t1 ? Fvt1 : Fvt2);
+        Fn[i] = A4 * (sP[i * N2 + j] - Fv);
+      }
       Fn[3] = A4 * sP[3 * N2 + j];
       const R lw = wall ? R(1) : R(0.5);  // share of the lifting on each real side
       if (wall != 2) {
