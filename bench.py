@@ -830,11 +830,11 @@ def main():
     ap.add_argument("--oracle-apps", type=int, default=ORACLE_APPS_PER_STAGE_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi")
-    ap.add_argument("--sweeps", default="3,3,2", help="pre,post,coarse smoothing iterations of the chosen form")
+    ap.add_argument("--sweeps", default="4,4,2", help="pre,post,coarse smoothing iterations of the chosen form")
     ap.add_argument("--plain-sweeps", default="2,2,2", help="pre,post,coarse smoothing iterations of the plain form")
     ap.add_argument("--form", choices=["fp64", "fp32", "h16", "bf16"], default="h16",
                     help="precision of the chosen form's cycle (h16 / bf16: FP32 cycle with 16-bit block storage)")
-    ap.add_argument("--omega", type=float, default=0.9, help="block-Jacobi damping of the chosen form")
+    ap.add_argument("--omega", type=float, default=0.95, help="block-Jacobi damping of the chosen form")
     ap.add_argument("--coarse", choices=["smoother", "learned"], default="smoother",
                     help="coarsest-level solve of the chosen form (the learned form is also measured separately)")
     ap.add_argument("--no-learned", dest="learned", action="store_false", help="skip training the coarse network")
