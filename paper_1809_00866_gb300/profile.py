@@ -23,17 +23,23 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--form", choices=["fp32", "fp64", "h16", "bf16"], default="fp32")
     ap.add_argument("--learned", action="store_true", help="train the coarse network first and use it")
+    ap.add_argument("--no-stb-rescale", dest="stb", action="store_false",
+                    help="plain inherited coarse operators (the bench rescales their stabilisation part)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="default launch shapes (the bench measures them with dg_autotune)")
     a = ap.parse_args(argv)
     import torch
 
     import synthetic as S
 
     from . import (DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP32_BF16, DG_PRECOND_FP32_H16,
-                   DG_PRECOND_FP64, build, solve_opts)
+                   DG_PRECOND_FP64, DG_TUNE_FP32, DG_TUNE_FP64, build, solve_opts)
     build()
     un = S.uniform_nodes(a.n)
     levels = [4, 2, 1]
     dg = DG(un, un, un, levels, S.NU_TGV, S.AC_C, S.ETA)
+    if a.stb:
+        dg.dg_set_stb_rescaling(True)
     inv = 1.0 / S.acoustic_dt(a.n, levels[0])
     w = dg.empty()
     dg.dg_project_tgv(w)
@@ -90,6 +96,9 @@ def main(argv=None):
     x = dg.empty()
     for _ in range(2):
         dg.fgmres_solve(g, x, o)
+    if a.autotune:  # the bench's launch shapes
+        for which in (DG_TUNE_FP64, DG_TUNE_FP32):
+            dg.dg_autotune(which, use_cache=False)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     t0 = time.perf_counter()
