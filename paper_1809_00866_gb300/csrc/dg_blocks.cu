@@ -152,56 +152,75 @@ __global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float*
 // neighbouring memory. A task is two adjacent rows (one paired load per column) over every
 // CS-th column; when a stage has few rows, CS > 1 column slices meet in shared memory.
 constexpr int kJacobiThreads = 512;
+constexpr int kJacobiSlots = 2;  // stage buffers in the ring (3 and 4 measured no faster at 16^3 P4)
 
 template <class R, class S>
-__global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, int b, int G, const S* __restrict__ A,
+__global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, int b, int G, int ns,
+                                                                       const S* __restrict__ A,
                                                                        const R* __restrict__ g,
                                                                        const R* __restrict__ Gx, R alpha, int x_zero,
                                                                        R* __restrict__ x, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sraw_[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[kJacobiSlots];
   __shared__ R red[2 * kJacobiThreads];  // partial sums of the column slices
   const size_t per = (size_t)b * b;  // values per element
-  S* const buf0 = reinterpret_cast<S*>(sraw_);
-  S* const buf1 = buf0 + (size_t)G * per;
-  R* const rv = reinterpret_cast<R*>(buf1 + (size_t)G * per);  // [G][b] residuals of the stage
+  // ns (2..4) stage buffers in a ring, each: the G element blocks, then the stage's slices of g,
+  // Gx and the old x, all brought by bulk copies on the buffer's barrier (no global load on the
+  // critical path); ns - 1 stages are in flight while one is multiplied
+  const size_t blk_bytes = (size_t)G * per * sizeof(S), vec = (size_t)G * b;
+  const size_t slot_bytes = blk_bytes + 3 * vec * sizeof(R);
+  auto blocks_of = [&](int slot) { return reinterpret_cast<S*>(sraw_ + slot * slot_bytes); };
+  auto vecs_of = [&](int slot) { return reinterpret_cast<R*>(sraw_ + slot * slot_bytes + blk_bytes); };
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nstages = (ne + G - 1) / G;
   const int hb = b / 2;  // row pairs per element
   const int CS = max(1, min(8, nt / (G * hb)));
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-  }
+  if (tid == 0)
+    for (int i = 0; i < ns; ++i) mbar_init(&bar[i], 1);
   __syncthreads();
   auto issue = [&](int stg, int slot) {
     const int e0 = stg * G;
-    const unsigned bytes = (unsigned)(min(G, ne - e0) * per * sizeof(S));
-    mbar_expect_tx(&bar[slot], bytes);
-    bulk_g2s(slot ? buf1 : buf0, A + (size_t)e0 * per, bytes, &bar[slot]);
+    const int cnt = min(G, ne - e0);
+    const unsigned bytes = (unsigned)(cnt * per * sizeof(S));
+    const unsigned vb = (unsigned)(cnt * b * sizeof(R));  // a multiple of 16 (b * 4 is)
+    const unsigned total = bytes + vb * (1 + (Gx ? 1 : 0) + (x_zero ? 0 : 1));
+    mbar_expect_tx(&bar[slot], total);
+    bulk_g2s(blocks_of(slot), A + (size_t)e0 * per, bytes, &bar[slot]);
+    R* v = vecs_of(slot);
+    bulk_g2s(v, g + (size_t)e0 * b, vb, &bar[slot]);
+    if (Gx) bulk_g2s(v + vec, Gx + (size_t)e0 * b, vb, &bar[slot]);
+    if (!x_zero) bulk_g2s(v + 2 * vec, x + (size_t)e0 * b, vb, &bar[slot]);
   };
-  if (tid == 0 && (int)blockIdx.x < nstages) issue(blockIdx.x, 0);
+  // iteration k of this CTA handles stage blockIdx.x + k * gridDim.x in slot k % ns (use k / ns)
+  if (tid == 0)
+    for (int i = 0; i < ns - 1; ++i) {
+      const int st0 = blockIdx.x + i * gridDim.x;
+      if (st0 < nstages) issue(st0, i);
+    }
   int k = 0;
   for (int stg = blockIdx.x; stg < nstages; stg += gridDim.x, ++k) {
-    const int slot = k & 1;
-    const int nxt = stg + gridDim.x;
-    if (tid == 0 && nxt < nstages) issue(nxt, slot ^ 1);  // its buffer was released at the end of k - 1
+    const int slot = k % ns;
+    const int ahead = stg + (ns - 1) * gridDim.x;  // into the slot released at the end of k - 1
+    if (tid == 0 && ahead < nstages) issue(ahead, (k + ns - 1) % ns);
     const int e0 = stg * G;
     const int cnt = min(G, ne - e0);
-    for (int t = tid; t < cnt * b; t += nt) {
-      const size_t o = (size_t)e0 * b + t;
-      rv[t] = g[o] - (Gx ? Gx[o] : R(0));
-    }
-    const bool got = mbar_wait(&bar[slot], (unsigned)((k >> 1) & 1));
+    const bool got = mbar_wait(&bar[slot], (unsigned)((k / ns) & 1));
     if (!__syncthreads_and(got)) {
-      // give up: report, let the copy issued for the next stage land (bounded), leave
+      // give up: report, let the copies in flight land (bounded waits), leave
       if (tid == 0) {
         atomicOr(status, (unsigned)DG_STATUS_WAIT);
-        if (nxt < nstages) mbar_wait(&bar[slot ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+        for (int i = 1; i < ns; ++i)
+          if (stg + i * gridDim.x < nstages) mbar_wait(&bar[(k + i) % ns], (unsigned)(((k + i) / ns) & 1));
       }
       return;
     }
-    const S* Ab = slot ? buf1 : buf0;
+    const S* Ab = blocks_of(slot);
+    R* const rv = vecs_of(slot);  // g, turned into the residual g - Gx in place
+    const R* const xo = rv + 2 * vec;
+    if (Gx) {
+      for (int t = tid; t < cnt * b; t += nt) rv[t] -= rv[vec + t];
+      __syncthreads();
+    }
     const int npairs = cnt * hb;
     for (int t = tid; t < npairs * CS; t += nt) {
       const int pr = t % npairs, cs = t / npairs;
@@ -229,8 +248,9 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
       a1 += c1;
       if (CS == 1) {
         R* xe = x + (size_t)(e0 + el) * b + i0;
-        xe[0] = (x_zero ? R(0) : xe[0]) + alpha * a0;
-        xe[1] = (x_zero ? R(0) : xe[1]) + alpha * a1;
+        const R* xs = xo + (size_t)el * b + i0;
+        xe[0] = (x_zero ? R(0) : xs[0]) + alpha * a0;
+        xe[1] = (x_zero ? R(0) : xs[1]) + alpha * a1;
       } else {
         red[2 * t] = a0;
         red[2 * t + 1] = a1;
@@ -246,11 +266,12 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
         }
         const int el = pr / hb, i0 = 2 * (pr - el * hb);
         R* xe = x + (size_t)(e0 + el) * b + i0;
-        xe[0] = (x_zero ? R(0) : xe[0]) + alpha * a0;
-        xe[1] = (x_zero ? R(0) : xe[1]) + alpha * a1;
+        const R* xs = xo + (size_t)el * b + i0;
+        xe[0] = (x_zero ? R(0) : xs[0]) + alpha * a0;
+        xe[1] = (x_zero ? R(0) : xs[1]) + alpha * a1;
       }
     }
-    __syncthreads();  // both buffers, rv and red free for the next stage
+    __syncthreads();  // this slot, its residual and red are free for the copy issued next
   }
 }
 
@@ -327,10 +348,13 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   const size_t per = (size_t)b * b * sizeof(S);
   const size_t target = h->tune[1].jacobi_stage_kb > 0 ? (size_t)h->tune[1].jacobi_stage_kb * 1024 : kStageTarget;
   int G = (int)std::max<size_t>(1, target / per);
-  G = std::min(G, (int)std::max<size_t>(1, kSmemLimit / (2 * per + (size_t)b * sizeof(R))));  // fits shared memory
+  const size_t per_slot = per + 3 * (size_t)b * sizeof(R);  // one buffer: block + g, Gx, x slices
+  G = std::min(G, (int)std::max<size_t>(1, kSmemLimit / (2 * per_slot)));  // two buffers fit
   G = std::max(1, std::min(G, (h->ne + 2 * h->nsm - 1) / (2 * h->nsm)));  // >= 2 stages per SM when possible
-  const size_t smem = 2 * (size_t)G * per + (size_t)G * b * sizeof(R);
-  if (smem > kSmemLimit || per % 16 != 0) return -1;
+  // as many buffers as fit (2..4): the stages in flight while one is multiplied
+  const int ns = (int)std::max<size_t>(2, std::min<size_t>(kJacobiSlots, kSmemLimit / ((size_t)G * per_slot)));
+  const size_t smem = (size_t)ns * G * per_slot;
+  if (smem > kSmemLimit || per % 16 != 0 || (b * sizeof(R)) % 16 != 0) return -1;
   static bool opted = false;  // per template instance; one device per process
   if (!opted) {
     DG_CUDA(h, cudaFuncSetAttribute(staged_jacobi_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -340,7 +364,7 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   const int nstages = (h->ne + G - 1) / G;
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
   const int grid = std::min(nstages, h->nsm * per_sm);
-  staged_jacobi_kernel<R, S><<<grid, kJacobiThreads, smem, st>>>(h->ne, b, G, A, g, Gx, alpha, x_zero, x,
+  staged_jacobi_kernel<R, S><<<grid, kJacobiThreads, smem, st>>>(h->ne, b, G, ns, A, g, Gx, alpha, x_zero, x,
                                                                 h->status);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
