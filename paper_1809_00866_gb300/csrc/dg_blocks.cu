@@ -45,16 +45,21 @@ template <class R> __device__ __forceinline__ void wide2(const __nv_bfloat16* p,
   a = R(v.x); b = R(v.y);
 }
 
+// The leading dimension of a block in shared memory: a multiple of 4 (float4 rows) that is 4 mod 8,
+// so that a column (stride LD) spreads over 8 banks instead of 2 (LD = b + 4 would be 0 mod 8 at
+// b = 140).
+__host__ __device__ inline int gj_ld(int b) { return (b + 4) % 8 == 4 ? b + 4 : b + 8; }
+
 // In place D -> D^-1 (column-major FP32 blocks, b a multiple of 4) by Gauss-Jordan elimination
 // with partial (row) pivoting, one block per CTA in shared memory (row-major, leading dimension
-// b + 4 so that rows are float4-aligned). Step k: pick the pivot row, keep column k in `col`
+// gj_ld(b) so that rows are float4-aligned). Step k: pick the pivot row, keep column k in `col`
 // and the scaled pivot row in `row` (row[k] = 1/pivot), zero column k, then one uniform rank-1
 // update A[i][:] -= col[i] row[:] for every i != k and A[k][:] = row; each thread owns four
 // adjacent columns (one float4) and every RG-th row. b^3 multiply-adds per block; the row
 // interchanges are undone on the columns at the end, in reverse order.
 __global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
-  const int LD = b + 4;
+  const int LD = gj_ld(b);
   float* A = reinterpret_cast<float*>(sraw_);  // [b][LD]
   float* col = A + (size_t)b * LD;             // [b] column k before step k
   float* row = col + b;                         // [b] scaled pivot row
@@ -465,7 +470,7 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
-    const size_t smem = sizeof(float) * ((size_t)L.b * (L.b + 4) + 2 * L.b) + sizeof(int) * L.b;
+    const size_t smem = sizeof(float) * ((size_t)L.b * gj_ld(L.b) + 2 * L.b) + sizeof(int) * L.b;
     if (smem > kSmemLimit || L.b % 4 != 0) return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
     DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
