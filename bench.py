@@ -66,13 +66,16 @@ DENSE_FLOP_PER_ELEMENT_P4 = 520_000.0
 # FP64 peak of a GB300 (no FP64 entry in the measured-peaks file): nominal 1.25 TFLOP/s
 # (152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz ~ 1.26 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
+# FP32 (non-tensor) peak from the unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
+# x 2 FLOP (FMA) x 2.07 GHz = 80.5 TFLOP/s.
+FP32_PEAK_TFLOPS = 80.5
 # HBM peak: the measured copy bandwidth on the GB300s, else the machine's fallback.
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) of one fine-level launch of the block-Jacobi apply at 16^3 P4, per
 # block storage of the chosen form, from one Nsight Compute capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum; FP16: 162.88 MB + 4.31 MB); None where not
-# captured for the current kernel.
-BJ_FINE_TRAFFIC_16_P4 = {"fp32": None, "h16": 167.19e6, "bf16": None}
+# (dram__bytes_read.sum + dram__bytes_write.sum of a sweep with a previous iterate: FP16:
+# 167.47 MB + 0.88 MB); None where not captured for the current kernel.
+BJ_FINE_TRAFFIC_16_P4 = {"fp32": None, "h16": 168.35e6, "bf16": None}
 
 
 def hbm_peak():
@@ -720,19 +723,44 @@ def run_ours(args):
             kernels[nm] = {"launches": cnt, "ms_per_launch": ms_k / cnt, "total_ms": ms_k}
             if by > 0:
                 kernels[nm]["gbs"] = by / (ms_k / 1e3) / 1e9
-    dom = "bj32_fine" if "bj32_fine" in kernels else "bj64_fine"
-    ms_d, cnt_d, by_d = kp[dom]
-    if cnt_d:
-        ach = by_d / (ms_d / 1e3) / 1e9
-        storage = {"fp32": "float", "h16": "half", "bf16": "bfloat16"}.get(args.form)
-        roofline = {"bound": "hbm", "kernel": "staged_jacobi_kernel<float, %s> (fine level, P4)" % storage
-                    if dom == "bj32_fine" else "bj_update_kernel<double> (fine level, P4)",
-                    "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": BJ_FINE_TRAFFIC_16_P4.get(args.form) if args.config == CONFIG else None,
-                    "algorithmic_bytes_per_launch": by_d / cnt_d, "ms_per_launch": ms_d / cnt_d,
-                    "peak_source": "measured HBM copy bandwidth (hbm_gbs of the measured-peaks file)"
-                    if hbm_src == "measured" else "fallback HBM bandwidth 6.8 TB/s",
-                    "frac_of": "of " + hbm_src}
+    # every timed class against its own bound, with live CUDA-event times: the block products
+    # against HBM (algorithmic bytes: blocks, inputs and outputs once), the operator passes
+    # against their arithmetic pipe (algorithmic FLOP of the formulation per element); the
+    # headline `roofline` is the class with the largest device time in the stage
+    storage = {"fp32": "float", "h16": "half", "bf16": "bfloat16"}.get(args.form)
+    names = {"bj32_fine": "staged_jacobi_kernel<float, %s> (fine level)" % storage,
+             "bj64_fine": "bj_update_kernel<double> (fine level)",
+             "bsr32_l1": "direct_apply_kernel<float, 7, %s> (P2 level)" % storage,
+             "bsr64_l1": "direct_apply_kernel<double, 7, double> (P2 level)",
+             "face_tan32": "face_kernel<%d, tangent, float>" % k, "vol_tan32": "vol_kernel<%d, tangent, float>" % k,
+             "face_tan": "face_kernel<%d, tangent, double>" % k, "vol_tan": "vol_kernel<%d, tangent, double>" % k}
+    hbm_note = ("measured HBM copy bandwidth (hbm_gbs of the measured-peaks file)" if hbm_src == "measured"
+                else "fallback HBM bandwidth 6.8 TB/s")
+    by_kernel = {}
+    for nm, (ms_k, cnt, by) in kp.items():
+        if not cnt or nm not in names:
+            continue
+        t = ms_k / cnt / 1e3
+        if by > 0:
+            ach = by / cnt / t / 1e9
+            ent = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                   "algorithmic_bytes_per_launch": by / cnt, "peak_source": hbm_note, "frac_of": "of " + hbm_src}
+        else:
+            flop = (ff if nm.startswith("face") else fv) * dg.ne
+            f32 = nm.endswith("32")
+            peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+            ach = flop / t / 1e12
+            ent = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                   "algorithmic_flop_per_launch": flop,
+                   "peak_source": ("FP32 lanes x clock: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz" if f32 else
+                                   "nominal FP64 rate of GB300 (not in the measured-peaks file)")}
+        ent.update({"kernel": names[nm], "ms_per_launch": t * 1e3, "launches": cnt, "total_ms": ms_k, "traffic": None})
+        if nm == "bj32_fine" and args.config == CONFIG:
+            ent["traffic"] = BJ_FINE_TRAFFIC_16_P4.get(args.form)
+        by_kernel[nm] = ent
+    if by_kernel:
+        top = max(by_kernel, key=lambda n: by_kernel[n]["total_ms"])
+        roofline = dict(by_kernel[top], profiler_class=top)
     else:
         roofline = roofline_jv
 
@@ -779,7 +807,8 @@ def run_ours(args):
             "stage": chosen, "plain_fp64": plain,
             "chosen_vs_plain": {"speedup": plain["s_per_stage"] / chosen["s_per_stage"],
                                 "first_stage_solution_rel_diff": chosen_err},
-            "roofline": roofline, "roofline_jv": roofline_jv, "stage_kernels": kernels,
+            "roofline": roofline, "roofline_by_kernel": by_kernel, "roofline_jv": roofline_jv,
+            "stage_kernels": kernels,
             "clocks": clocks, "e2e": e2e, "gpu_launches": chosen["gpu_launches"], "tuning": tuning}
     if lagged is not None:
         line["lagged_form"] = {
