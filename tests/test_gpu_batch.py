@@ -293,3 +293,45 @@ def test_batch_rejects_whole_vector_reductions():
         dg.dg_jvp(g, x, mode=P.DG_JVP_FD)
     with pytest.raises(P.DgError):
         P.Plan([dg], [g], [x], P.solve_opts(smoother=P.DG_SMOOTH_GMRES))
+
+
+def test_batch_of_channels():
+    # boxes with no-slip walls (the walls flag applies to every box of a batch): the operator
+    # equals one-box handles bit for bit, and the graph-captured solve of each problem passes the
+    # oracle's exact operator
+    torch, P = require_gpu()
+    boxes = [(S.uniform_nodes(3), S.tanh_nodes(4, 1.15), S.uniform_nodes(2, np.pi)),
+             (S.uniform_nodes(2), S.tanh_nodes(5, 1.15), S.uniform_nodes(3, np.pi))]
+    mults = [1.5, 2.5]
+    nu = S.NU_TGV * 20
+    dg = P.DG(None, None, None, [2, 1], nu, S.AC_C, S.ETA, boxes=boxes, walls=True)
+    dg.dg_set_problem_shifts(mults)
+    ms = [O.Mesh(*b, 2, nu, S.AC_C, S.ETA, walls=True) for b in boxes]
+    ws = []
+    for q, m in enumerate(ms):
+        x, _ = O.quad_points(m)
+        y = x[..., 1]
+        ws.append(O.project_points(m, np.stack([1 - y * y, 0 * y, 0 * y, 0 * y], axis=1))
+                  + S.perturbation(m.ne, 2, 0.05, 30 + q))
+    inv = 2.0
+    dg.dg_set_linearization(dev(cat(ws).reshape(dg.ne, 4, -1)), inv)
+    dg.dg_assemble()
+    vs = [S.direction(m.ne, 2, 40 + q) for q, m in enumerate(ms)]
+    out = dg.empty()
+    dg.dg_jvp(dev(cat(vs).reshape(dg.ne, 4, -1)), out)
+    for q, m in enumerate(ms):
+        one = P.DG(*boxes[q], [2, 1], nu, S.AC_C, S.ETA, walls=True)
+        one.dg_set_linearization(dev(ws[q]), inv * mults[q])
+        o = one.empty()
+        one.dg_jvp(dev(vs[q]), o)
+        assert np.array_equal(split(dg, ms, out)[q], host(o).reshape(-1)), q
+    g = rhs(dg, ms, ws)
+    x = dg.empty()
+    plan = P.Plan([dg], [g], [x], P.solve_opts(rtol=1e-10, maxit=200), use_graph=True)
+    plan.dg_plan_solve()
+    its, relres, conv = plan.dg_plan_result(0)
+    assert all(conv)
+    for q, m in enumerate(ms):
+        G0 = O.dense_G(m, ws[q], inv * mults[q])
+        gq = -O.residual(m, ws[q]).reshape(-1)
+        assert np.linalg.norm(gq - G0 @ split(dg, ms, x)[q]) / np.linalg.norm(gq) < 1e-9, q
