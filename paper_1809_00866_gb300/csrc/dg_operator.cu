@@ -596,6 +596,13 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   for (int t = tid; t < K1 * K1; t += nt) PIDX[t] = a.T.pidx[t];
   for (int t = tid; t < 2 * N2; t += nt) PAB[t] = a.T.pab[t];
   __syncthreads();
+  // the 1D table P_hat_a(x_q) in registers for the whole kernel: every sum-factorisation step
+  // below has a thread compute a pencil of K+1 outputs from values it loads once
+  R Lr[K1][N1];
+#pragma unroll
+  for (int pa = 0; pa < K1; ++pa)
+#pragma unroll
+    for (int q = 0; q < N1; ++q) Lr[pa][q] = L1[pa * N1 + q];
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
     const R is = R(g.is);
@@ -618,14 +625,35 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
       const R r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
       sG[t] = acc * Jd[b] - r;
     }
-    for (int t = tid; t < 3 * N2 * N1; t += nt) {
-      const int fl = t / (N2 * N1), r = t - fl * N2 * N1, pi = r / N1, q2 = r - pi * N1;
-      const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
-      const R* c = sC + fl * NB;
-      R acc = R(0);
-      const int* row = IDX3 + (pa * K1 + pb) * K1;
-      for (int cc = 0; cc <= K - pa - pb; ++cc) acc += c[row[cc]] * L1[cc * N1 + q2];
-      sT1[t] = acc;
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 3 * N2; t += nt) {  // pencil (field, pair (a, b)): all q2
+        const int fl = t / N2, pi = t - fl * N2;
+        const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+        const R* c = sC + fl * NB;
+        const int* row = IDX3 + (pa * K1 + pb) * K1;
+        R o[N1];
+  #pragma unroll
+        for (int q = 0; q < N1; ++q) o[q] = R(0);
+  #pragma unroll
+        for (int cc = 0; cc < K1; ++cc)
+          if (cc <= K - pa - pb) {
+            const R v = c[row[cc]];
+  #pragma unroll
+            for (int q = 0; q < N1; ++q) o[q] += v * Lr[cc][q];
+          }
+  #pragma unroll
+        for (int q = 0; q < N1; ++q) sT1[(fl * N2 + pi) * N1 + q] = o[q];
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 3 * N2 * N1; t += nt) {
+        const int fl = t / (N2 * N1), r = t - fl * N2 * N1, pi = r / N1, q2 = r - pi * N1;
+        const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+        const R* c = sC + fl * NB;
+        R acc = R(0);
+        const int* row = IDX3 + (pa * K1 + pb) * K1;
+        for (int cc = 0; cc <= K - pa - pb; ++cc) acc += c[row[cc]] * L1[cc * N1 + q2];
+        sT1[t] = acc;
+      }
     }
     __syncthreads();
     // (B) viscous flux coefficients; interpolation step 2
@@ -636,21 +664,56 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
       const R trG = sG[0 * NB + m] + sG[4 * NB + m] + sG[8 * NB + m];
       sFv[t] = R(a.nu) * (sG[(i * 3 + p) * NB + m] + sG[(p * 3 + i) * NB + m] - (p == i ? R(2.0 / 3.0) * trG : R(0)));
     }
-    for (int t = tid; t < 3 * K1 * N1 * N1; t += nt) {
-      const int fl = t / (K1 * N1 * N1), r = t - fl * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
-      const int q1 = r2 / N1, q2 = r2 - q1 * N1;
-      R acc = R(0);
-      for (int pb = 0; pb <= K - pa; ++pb) acc += sT1[fl * N2 * N1 + PIDX[pa * K1 + pb] * N1 + q2] * L1[pb * N1 + q1];
-      sT2[t] = acc;
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 3 * K1 * N1; t += nt) {  // pencil (field, a, q2): all q1
+        const int fl = t / (K1 * N1), r = t - fl * K1 * N1, pa = r / N1, q2 = r - pa * N1;
+        R o[N1];
+  #pragma unroll
+        for (int q = 0; q < N1; ++q) o[q] = R(0);
+  #pragma unroll
+        for (int pb = 0; pb < K1; ++pb)
+          if (pb <= K - pa) {
+            const R v = sT1[(fl * N2 + PIDX[pa * K1 + pb]) * N1 + q2];
+  #pragma unroll
+            for (int q1 = 0; q1 < N1; ++q1) o[q1] += v * Lr[pb][q1];
+          }
+  #pragma unroll
+        for (int q1 = 0; q1 < N1; ++q1) sT2[((fl * K1 + pa) * N1 + q1) * N1 + q2] = o[q1];
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 3 * K1 * N1 * N1; t += nt) {
+        const int fl = t / (K1 * N1 * N1), r = t - fl * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
+        const int q1 = r2 / N1, q2 = r2 - q1 * N1;
+        R acc = R(0);
+        for (int pb = 0; pb <= K - pa; ++pb) acc += sT1[fl * N2 * N1 + PIDX[pa * K1 + pb] * N1 + q2] * L1[pb * N1 + q1];
+        sT2[t] = acc;
+      }
     }
     __syncthreads();
     // (C) interpolation step 3: velocity (or its variation) at the Gauss points
-    for (int t = tid; t < 3 * NQ; t += nt) {
-      const int fl = t / NQ, q = t - fl * NQ, q0 = q / (N1 * N1), r = q - q0 * N1 * N1;
-      R acc = R(0);
-#pragma unroll
-      for (int pa = 0; pa < K1; ++pa) acc += sT2[(fl * K1 + pa) * N1 * N1 + r] * L1[pa * N1 + q0];
-      sU[t] = acc * is;
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 3 * N1 * N1; t += nt) {  // pencil (field, q1 q2): all q0
+        const int fl = t / (N1 * N1), r = t - fl * N1 * N1;
+        R o[N1];
+  #pragma unroll
+        for (int q = 0; q < N1; ++q) o[q] = R(0);
+  #pragma unroll
+        for (int pa = 0; pa < K1; ++pa) {
+          const R v = sT2[(fl * K1 + pa) * N1 * N1 + r];
+  #pragma unroll
+          for (int q0 = 0; q0 < N1; ++q0) o[q0] += v * Lr[pa][q0];
+        }
+  #pragma unroll
+        for (int q0 = 0; q0 < N1; ++q0) sU[fl * NQ + q0 * N1 * N1 + r] = o[q0] * is;
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 3 * NQ; t += nt) {
+        const int fl = t / NQ, q = t - fl * NQ, q0 = q / (N1 * N1), r = q - q0 * N1 * N1;
+        R acc = R(0);
+  #pragma unroll
+        for (int pa = 0; pa < K1; ++pa) acc += sT2[(fl * K1 + pa) * N1 * N1 + r] * L1[pa * N1 + q0];
+        sU[t] = acc * is;
+      }
     }
     __syncthreads();
     // (D) pointwise convective products, weighted
@@ -682,33 +745,85 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
     }
     __syncthreads();
     // (E) projection step 1: S1[sp][a][q1 q2] = sum_q0 L1[a][q0] Pr[sp][q0 q1 q2]
-    for (int t = tid; t < 6 * K1 * N1 * N1; t += nt) {
-      const int sp = t / (K1 * N1 * N1), r = t - sp * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
-      R acc = R(0);
-#pragma unroll
-      for (int q0 = 0; q0 < N1; ++q0) acc += L1[pa * N1 + q0] * sPr[sp * NQ + q0 * N1 * N1 + r2];
-      sS1[t] = acc;
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 6 * N1 * N1; t += nt) {  // pencil (product, q1 q2): all a
+        const int sp = t / (N1 * N1), r2 = t - sp * N1 * N1;
+        R v[N1];
+  #pragma unroll
+        for (int q0 = 0; q0 < N1; ++q0) v[q0] = sPr[sp * NQ + q0 * N1 * N1 + r2];
+  #pragma unroll
+        for (int pa = 0; pa < K1; ++pa) {
+          R acc = R(0);
+  #pragma unroll
+          for (int q0 = 0; q0 < N1; ++q0) acc += Lr[pa][q0] * v[q0];
+          sS1[(sp * K1 + pa) * N1 * N1 + r2] = acc;
+        }
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 6 * K1 * N1 * N1; t += nt) {
+        const int sp = t / (K1 * N1 * N1), r = t - sp * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
+        R acc = R(0);
+  #pragma unroll
+        for (int q0 = 0; q0 < N1; ++q0) acc += L1[pa * N1 + q0] * sPr[sp * NQ + q0 * N1 * N1 + r2];
+        sS1[t] = acc;
+      }
     }
     __syncthreads();
     // (F) projection step 2: S2[sp][pair(a,b)][q2] = sum_q1 L1[b][q1] S1[sp][a][q1 q2]
-    for (int t = tid; t < 6 * N2 * N1; t += nt) {
-      const int sp = t / (N2 * N1), r = t - sp * N2 * N1, pi = r / N1, q2 = r - pi * N1;
-      const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
-      R acc = R(0);
-#pragma unroll
-      for (int q1 = 0; q1 < N1; ++q1) acc += L1[pb * N1 + q1] * sS1[(sp * K1 + pa) * N1 * N1 + q1 * N1 + q2];
-      sS2[t] = acc;
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 6 * K1 * N1; t += nt) {  // pencil (product, a, q2): all b <= K - a
+        const int sp = t / (K1 * N1), r = t - sp * K1 * N1, pa = r / N1, q2 = r - pa * N1;
+        R v[N1];
+  #pragma unroll
+        for (int q1 = 0; q1 < N1; ++q1) v[q1] = sS1[(sp * K1 + pa) * N1 * N1 + q1 * N1 + q2];
+  #pragma unroll
+        for (int pb = 0; pb < K1; ++pb)
+          if (pb <= K - pa) {
+            R acc = R(0);
+  #pragma unroll
+            for (int q1 = 0; q1 < N1; ++q1) acc += Lr[pb][q1] * v[q1];
+            sS2[(sp * N2 + PIDX[pa * K1 + pb]) * N1 + q2] = acc;
+          }
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 6 * N2 * N1; t += nt) {
+        const int sp = t / (N2 * N1), r = t - sp * N2 * N1, pi = r / N1, q2 = r - pi * N1;
+        const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+        R acc = R(0);
+  #pragma unroll
+        for (int q1 = 0; q1 < N1; ++q1) acc += L1[pb * N1 + q1] * sS1[(sp * K1 + pa) * N1 * N1 + q1 * N1 + q2];
+        sS2[t] = acc;
+      }
     }
     __syncthreads();
     // (G) projection step 3: Cv[sp][m] = s * sum_q2 L1[c][q2] S2[sp][pair(a,b)][q2]
-    for (int t = tid; t < 6 * NB; t += nt) {
-      const int sp = t / NB, m = t - sp * NB;
-      const int pa = MD3[3 * m], pb = MD3[3 * m + 1], pc = MD3[3 * m + 2];
-      const R* s2 = sS2 + (sp * N2 + PIDX[pa * K1 + pb]) * N1;
-      R acc = R(0);
-#pragma unroll
-      for (int q2 = 0; q2 < N1; ++q2) acc += L1[pc * N1 + q2] * s2[q2];
-      sCv[t] = acc * R(g.s);
+    if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
+      for (int t = tid; t < 6 * N2; t += nt) {  // pencil (product, pair (a, b)): all c <= K - a - b
+        const int sp = t / N2, pi = t - sp * N2;
+        const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
+        const int* row = IDX3 + (pa * K1 + pb) * K1;
+        R v[N1];
+  #pragma unroll
+        for (int q2 = 0; q2 < N1; ++q2) v[q2] = sS2[(sp * N2 + pi) * N1 + q2];
+  #pragma unroll
+        for (int pc = 0; pc < K1; ++pc)
+          if (pc <= K - pa - pb) {
+            R acc = R(0);
+  #pragma unroll
+            for (int q2 = 0; q2 < N1; ++q2) acc += Lr[pc][q2] * v[q2];
+            sCv[sp * NB + row[pc]] = acc * R(g.s);
+          }
+      }
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+      for (int t = tid; t < 6 * NB; t += nt) {
+        const int sp = t / NB, m = t - sp * NB;
+        const int pa = MD3[3 * m], pb = MD3[3 * m + 1], pc = MD3[3 * m + 2];
+        const R* s2 = sS2 + (sp * N2 + PIDX[pa * K1 + pb]) * N1;
+        R acc = R(0);
+  #pragma unroll
+        for (int q2 = 0; q2 < N1; ++q2) acc += L1[pc * N1 + q2] * s2[q2];
+        sCv[t] = acc * R(g.s);
+      }
     }
     __syncthreads();
     // (H) assemble: modal derivatives of (F^nu - u(x)u) and p, continuity, face terms, mass shift
