@@ -611,19 +611,46 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
     __syncthreads();
     // (A) corrected gradient coefficients; interpolation step 1 of the velocity
     const R* Lf = a.face_lift + (size_t)e * 6 * 3 * N2;
-    for (int t = tid; t < 9 * NB; t += nt) {
-      const int ab = t / NB, m = t - ab * NB, av = ab / 3, b = ab - 3 * av;
-      const R* cv = sC + av * NB;
-      R acc = R(0);
+    if constexpr (sizeof(R) == 4) {  // FP32: one thread per (b, m) for the three components
+      for (int t = tid; t < 3 * NB; t += nt) {
+        const int b = t / NB, m = t - b * NB;
+        int di[DW];
+        R dv[DW];
 #pragma unroll
-      for (int j = 0; j < DW; ++j) {
-        const int o = (b * NB + m) * DW + j;
-        acc += a.rt.Drow_val[o] * cv[a.T.Drow_idx[o]];
+        for (int j = 0; j < DW; ++j) {
+          const int o = (b * NB + m) * DW + j;
+          di[j] = a.T.Drow_idx[o];
+          dv[j] = a.rt.Drow_val[o];
+        }
+        const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
+        const R p1 = PV[K1 + ex], p0 = PV[ex];
+        const R jb = b == 0 ? Jd[0] : (b == 1 ? Jd[1] : Jd[2]);
+#pragma unroll
+        for (int av = 0; av < 3; ++av) {
+          const R* cv = sC + av * NB;
+          R acc = R(0);
+#pragma unroll
+          for (int j = 0; j < DW; ++j) acc += dv[j] * cv[di[j]];
+          // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
+          const R r = p1 * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + p0 * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
+          sG[(av * 3 + b) * NB + m] = acc * jb - r;
+        }
       }
-      // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
-      const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
-      const R r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
-      sG[t] = acc * Jd[b] - r;
+    } else {
+      for (int t = tid; t < 9 * NB; t += nt) {
+        const int ab = t / NB, m = t - ab * NB, av = ab / 3, b = ab - 3 * av;
+        const R* cv = sC + av * NB;
+        R acc = R(0);
+  #pragma unroll
+        for (int j = 0; j < DW; ++j) {
+          const int o = (b * NB + m) * DW + j;
+          acc += a.rt.Drow_val[o] * cv[a.T.Drow_idx[o]];
+        }
+        // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
+        const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
+        const R r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
+        sG[t] = acc * Jd[b] - r;
+      }
     }
     if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
       for (int t = tid; t < 3 * N2; t += nt) {  // pencil (field, pair (a, b)): all q2
@@ -828,34 +855,71 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
     __syncthreads();
     // (H) assemble: modal derivatives of (F^nu - u(x)u) and p, continuity, face terms, mass shift
     const R* FO = a.face_out + (size_t)e * 6 * 4 * N2;
-    for (int t = tid; t < 4 * NB; t += nt) {
-      const int i = t / NB, m = t - i * NB;
-      R acc = R(0);
+    if constexpr (sizeof(R) == 4) {  // FP32: one thread per mode m for the four variables
+      for (int m = tid; m < NB; m += nt) {
+        R acc[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-      for (int pp = 0; pp < 3; ++pp) {
-        R s2 = R(0);
+        for (int pp = 0; pp < 3; ++pp) {
+          R s2[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-        for (int j = 0; j < DW; ++j) {
-          const int o = (pp * NB + m) * DW + j;
-          const int n = a.T.Dcol_idx[o];
-          R fld;
-          if (i < 3) {
-            const int sp = sym_index(pp, i);
-            fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0));
-          } else {
-            fld = -sC[pp * NB + n];
+          for (int j = 0; j < DW; ++j) {
+            const int o = (pp * NB + m) * DW + j;
+            const int n = a.T.Dcol_idx[o];
+            const R dv = a.rt.Dcol_val[o];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const int sp = sym_index(pp, i);
+              s2[i] += dv * (sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0)));
+            }
+            s2[3] += dv * (-sC[pp * NB + n]);
           }
-          s2 += a.rt.Dcol_val[o] * fld;
-        }
-        acc += Jd[pp] * s2;
-      }
 #pragma unroll
-      for (int sl = 0; sl < 6; ++sl) {
-        const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
-        acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
+          for (int i = 0; i < 4; ++i) acc[i] += Jd[pp] * s2[i];
+        }
+#pragma unroll
+        for (int sl = 0; sl < 6; ++sl) {
+          const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
+          const R pw = PV[side * K1 + FA[dd * NB + m]];
+          const int fm = FMAP[dd * NB + m];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i] += pw * FO[sl * 4 * N2 + i * N2 + fm];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (MODE == MODE_TAN && i < 3) acc[i] += R(a.inv_gdt * g.sh) * sC[i * NB + m];
+          a.out[(size_t)e * 4 * NB + i * NB + m] = acc[i];
+        }
       }
-      if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt * g.sh) * sC[t];
-      a.out[(size_t)e * 4 * NB + t] = acc;
+    } else {
+      for (int t = tid; t < 4 * NB; t += nt) {
+        const int i = t / NB, m = t - i * NB;
+        R acc = R(0);
+  #pragma unroll
+        for (int pp = 0; pp < 3; ++pp) {
+          R s2 = R(0);
+  #pragma unroll
+          for (int j = 0; j < DW; ++j) {
+            const int o = (pp * NB + m) * DW + j;
+            const int n = a.T.Dcol_idx[o];
+            R fld;
+            if (i < 3) {
+              const int sp = sym_index(pp, i);
+              fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0));
+            } else {
+              fld = -sC[pp * NB + n];
+            }
+            s2 += a.rt.Dcol_val[o] * fld;
+          }
+          acc += Jd[pp] * s2;
+        }
+  #pragma unroll
+        for (int sl = 0; sl < 6; ++sl) {
+          const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
+          acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
+        }
+        if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt * g.sh) * sC[t];
+        a.out[(size_t)e * 4 * NB + t] = acc;
+      }
     }
     __syncthreads();
   }
