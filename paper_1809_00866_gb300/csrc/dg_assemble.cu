@@ -103,14 +103,23 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
     const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
     for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
     __syncthreads();
-    // weighted mass matrices U_c (symmetric)
-    for (int t = tid; t < 3 * NB * NB; t += nt) {
-      const int c = t / (NB * NB), r = t - c * NB * NB, n1 = r / NB, n = r - n1 * NB;
-      if (n1 > n) continue;
-      R acc = R(0);
-      for (int q = 0; q < NQ; ++q) acc += sW[q] * sUb[c * NQ + q] * sB[q * NB + n1] * sB[q * NB + n];
-      sU[(c * NB + n1) * NB + n] = acc;
-      sU[(c * NB + n) * NB + n1] = acc;
+    // weighted mass matrices U_c (symmetric): one thread per mode pair n1 <= n computes all three
+    // c, so the two basis values of a point are loaded once
+    for (int t = tid; t < NB * (NB + 1) / 2; t += nt) {
+      int n1 = 0, r = t;
+      while (r >= NB - n1) { r -= NB - n1; ++n1; }
+      const int n = n1 + r;
+      R acc[3] = {R(0), R(0), R(0)};
+      for (int q = 0; q < NQ; ++q) {
+        const R b1 = sB[q * NB + n1], b2 = sB[q * NB + n], wq = sW[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += wq * sUb[c * NQ + q] * b1 * b2;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sU[(c * NB + n1) * NB + n] = acc[c];
+        sU[(c * NB + n) * NB + n1] = acc[c];
+      }
     }
     __syncthreads();
     // face geometry of the six slots: face index, own side, Jacobian column offset, scale
@@ -129,12 +138,18 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
           sJ[t] = v * sW2[q];
         }
         __syncthreads();
-        for (int t = tid; t < 6 * N2 * N2; t += nt) {
-          const int sl = t / (N2 * N2), r = t - sl * N2 * N2, j1 = r / N2, j2 = r - j1 * N2;
-          R acc = R(0);
+        // one thread per 2D mode pair computes the six face slots from one load of its basis values
+        for (int t = tid; t < N2 * N2; t += nt) {
+          const int j1 = t / N2, j2 = t - j1 * N2;
+          R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
-          for (int q = 0; q < NQF; ++q) acc += sJ[sl * NQF + q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
-          sE[t] = acc;
+          for (int q = 0; q < NQF; ++q) {
+            const R b1 = sB2[q * N2 + j1], b2 = sB2[q * N2 + j2];
+#pragma unroll
+            for (int sl = 0; sl < 6; ++sl) acc[sl] += sJ[sl * NQF + q] * b1 * b2;
+          }
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) sE[sl * N2 * N2 + t] = acc[sl];
         }
         __syncthreads();
         R* Dout = a.D + (size_t)e * BS * BS;
