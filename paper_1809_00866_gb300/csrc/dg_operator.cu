@@ -81,12 +81,17 @@ struct OpArgsT {
 using OpArgs = OpArgsT<double>;
 
 // ------------------------------------------------------------------ Riemann
+// The rarefaction branches below read a = sqrt(u^2+c^2) and A = asinh(u/c) at the star
+// velocity u and aL, AL (aR, AR) at the side's normal velocity. The caller computes each
+// once: the side values once per point, the star values once per Newton iterate, and only
+// when a rarefaction branch is taken.
+//
 // Pressure on the 1-wave curve through (uL, pL) at star velocity u, and its
 // partial derivatives in u and uL (dp/dpL = 1). Shock (u < uL): Rankine-Hugoniot
 // with the negative root s of s^2 - (uL+u)s - c^2 = 0, p = pL + c^2 (u-uL)/s.
 // Rarefaction: dp/du = -(u + sqrt(u^2+c^2)) integrated in closed form.
-__device__ __forceinline__ void wave1(double u, double uL, double pL, double c, double& p, double& dpdu,
-                                      double& dpduL) {
+__device__ __forceinline__ void wave1(double u, double a, double A, double uL, double aL, double AL, double pL,
+                                      double c, double& p, double& dpdu, double& dpduL) {
   const double c2 = c * c;
   if (u < uL) {
     const double sig = uL + u, Q = sqrt(sig * sig + 4.0 * c2), s = 0.5 * (sig - Q);
@@ -96,9 +101,8 @@ __device__ __forceinline__ void wave1(double u, double uL, double pL, double c, 
     dpdu = c2 * (is - du * ss * is * is);
     dpduL = c2 * (-is - du * ss * is * is);
   } else {
-    const double a = sqrt(u * u + c2), aL = sqrt(uL * uL + c2);
-    const double Gu = 0.5 * (u * u + u * a + c2 * asinh(u / c));
-    const double GL = 0.5 * (uL * uL + uL * aL + c2 * asinh(uL / c));
+    const double Gu = 0.5 * (u * u + u * a + c2 * A);
+    const double GL = 0.5 * (uL * uL + uL * aL + c2 * AL);
     p = pL - (Gu - GL);
     dpdu = -(u + a);
     dpduL = uL + aL;
@@ -106,8 +110,8 @@ __device__ __forceinline__ void wave1(double u, double uL, double pL, double c, 
 }
 // Pressure on the 3-wave curve through (uR, pR): shock for u > uR (positive root),
 // rarefaction dp/du = sqrt(u^2+c^2) - u otherwise. Partials in u and uR (dp/dpR = 1).
-__device__ __forceinline__ void wave3(double u, double uR, double pR, double c, double& p, double& dpdu,
-                                      double& dpduR) {
+__device__ __forceinline__ void wave3(double u, double a, double A, double uR, double aR, double AR, double pR,
+                                      double c, double& p, double& dpdu, double& dpduR) {
   const double c2 = c * c;
   if (u > uR) {
     const double sig = u + uR, Q = sqrt(sig * sig + 4.0 * c2), s = 0.5 * (sig + Q);
@@ -117,9 +121,8 @@ __device__ __forceinline__ void wave3(double u, double uR, double pR, double c, 
     dpdu = c2 * (is - du * ss * is * is);
     dpduR = c2 * (-is - du * ss * is * is);
   } else {
-    const double a = sqrt(u * u + c2), aR = sqrt(uR * uR + c2);
-    const double Hu = 0.5 * (u * a + c2 * asinh(u / c) - u * u);
-    const double HR = 0.5 * (uR * aR + c2 * asinh(uR / c) - uR * uR);
+    const double Hu = 0.5 * (u * a + c2 * A - u * u);
+    const double HR = 0.5 * (uR * aR + c2 * AR - uR * uR);
     p = pR - (HR - Hu);
     dpdu = a - u;
     dpduR = -(aR - uR);
@@ -127,7 +130,8 @@ __device__ __forceinline__ void wave3(double u, double uR, double pR, double c, 
 }
 // Tangential-velocity ratio across the 1-wave, tau = u_t(star)/u_t(L), with partials
 // in u* and uL. Rarefaction: u_t (u + a) invariant; shock: s [u_t] = [u_n u_t].
-__device__ __forceinline__ void tang1(double u, double uL, double c, double& t, double& dtdu, double& dtduL) {
+__device__ __forceinline__ void tang1(double u, double a, double uL, double aL, double c, double& t, double& dtdu,
+                                      double& dtduL) {
   const double c2 = c * c;
   if (u < uL) {
     const double sig = uL + u, Q = sqrt(sig * sig + 4.0 * c2), s = 0.5 * (sig - Q), ss = -s / Q;
@@ -136,14 +140,14 @@ __device__ __forceinline__ void tang1(double u, double uL, double c, double& t, 
     dtdu = (ss * den - num * (ss - 1.0)) * id * id;
     dtduL = ((ss - 1.0) * den - num * ss) * id * id;
   } else {
-    const double a = sqrt(u * u + c2), aL = sqrt(uL * uL + c2);
     t = (uL + aL) / (u + a);
     dtdu = -t / a;
     dtduL = t / aL;
   }
 }
 // Ratio across the 3-wave, tau = u_t(star)/u_t(R). Rarefaction: u_t/(u + a) invariant.
-__device__ __forceinline__ void tang3(double u, double uR, double c, double& t, double& dtdu, double& dtduR) {
+__device__ __forceinline__ void tang3(double u, double a, double uR, double aR, double c, double& t, double& dtdu,
+                                      double& dtduR) {
   const double c2 = c * c;
   if (u > uR) {
     const double sig = u + uR, Q = sqrt(sig * sig + 4.0 * c2), s = 0.5 * (sig + Q), ss = s / Q;
@@ -152,7 +156,6 @@ __device__ __forceinline__ void tang3(double u, double uR, double c, double& t, 
     dtdu = (ss * den - num * (ss - 1.0)) * id * id;
     dtduR = ((ss - 1.0) * den - num * ss) * id * id;
   } else {
-    const double a = sqrt(u * u + c2), aR = sqrt(uR * uR + c2);
     t = (u + a) / (uR + aR);
     dtdu = t / a;
     dtduR = -t / aR;
@@ -170,15 +173,27 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
                            double (*J)[8], unsigned* status) {
   const double ul = uL[d], ur = uR[d], c2 = c * c;
   const double al = sqrt(ul * ul + c2), ar = sqrt(ur * ur + c2);
+  const double Al = asinh(ul / c), Ar = asinh(ur / c);
   const double scale = fabs(ul) + fabs(ur) + c;
+  // sqrt(u^2+c^2) and asinh(u/c) at a star velocity, where a rarefaction branch reads them
+  auto at_star = [&](double u, double& as, double& As) {
+    if (!(u < ul) || !(u > ur)) {
+      as = sqrt(u * u + c2);
+      As = asinh(u / c);
+    } else {
+      as = 0.0;
+      As = 0.0;
+    }
+  };
   // two-rarefaction linearisation as the initial guess
   double us = (pL - pR + ul * (ul + al) + ur * (ar - ur)) / ((ul + al) + (ar - ur));
   double lo = -1e300, hi = 1e300;
   bool ok = false;
-  double p1, d1u, d1l, p3, d3u, d3r;
+  double p1, d1u, d1l, p3, d3u, d3r, as, As;
   for (int it = 0; it < 60; ++it) {
-    wave1(us, ul, pL, c, p1, d1u, d1l);
-    wave3(us, ur, pR, c, p3, d3u, d3r);
+    at_star(us, as, As);
+    wave1(us, as, As, ul, al, Al, pL, c, p1, d1u, d1l);
+    wave3(us, as, As, ur, ar, Ar, pR, c, p3, d3u, d3r);
     const double phi = p1 - p3, dphi = d1u - d3u;  // dphi < 0
     if (phi > 0.0) lo = us; else hi = us;
     double nxt = us - phi / dphi;
@@ -188,8 +203,9 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
     if (fabs(step) <= 1e-15 * scale) { ok = true; break; }
   }
   if (!ok && status) atomicOr(status, (unsigned)DG_STATUS_RIEMANN);
-  wave1(us, ul, pL, c, p1, d1u, d1l);
-  wave3(us, ur, pR, c, p3, d3u, d3r);
+  at_star(us, as, As);
+  wave1(us, as, As, ul, al, Al, pL, c, p1, d1u, d1l);
+  wave3(us, as, As, ur, ar, Ar, pR, c, p3, d3u, d3r);
   const double ps = p1;
   // implicit-function derivatives of u* and p* with respect to (ul, pL, ur, pR)
   const double iphi = 1.0 / (d1u - d3u);
@@ -198,8 +214,8 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
   const double dps_ur = d1u * dus_ur, dps_pr = d1u * dus_pr;
   // tangential ratios
   double tl, tlu, tll, tr, tru, trr;
-  tang1(us, ul, c, tl, tlu, tll);
-  tang3(us, ur, c, tr, tru, trr);
+  tang1(us, as, ul, al, c, tl, tlu, tll);
+  tang3(us, as, ur, ar, c, tr, tru, trr);
   const double band = 1e-12 * scale;
   double wl, wr;  // weights of the left / right star tangential values
   if (us > band) { wl = 1.0; wr = 0.0; }
