@@ -50,27 +50,45 @@ template <class R> __device__ __forceinline__ void wide2(const __nv_bfloat16* p,
 // b = 140).
 __host__ __device__ inline int gj_ld(int b) { return (b + 4) % 8 == 4 ? b + 4 : b + 8; }
 
+constexpr int kGjSlots = 5;  // panel rows per lane of the factoring warp: b <= 160
+
+__device__ __forceinline__ float f4get(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4set(float4& v, int q, float x) {
+  if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
+}
+
 // In place D -> D^-1 (column-major FP32 blocks, b a multiple of 4) by Gauss-Jordan elimination
 // with partial (row) pivoting, one block per CTA in shared memory (row-major, leading dimension
-// gj_ld(b) so that rows are float4-aligned). Step k: pick the pivot row, keep column k in `col`
-// and the scaled pivot row in `row` (row[k] = 1/pivot), zero column k, then one uniform rank-1
-// update A[i][:] -= col[i] row[:] for every i != k and A[k][:] = row; each thread owns four
-// adjacent columns (one float4) and every RG-th row. b^3 multiply-adds per block; the row
-// interchanges are undone on the columns at the end, in reverse order.
-__global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
+// gj_ld(b) so that rows are float4-aligned), in panels of four pivots. The four pivot columns K
+// of a panel are one float4 column group. With P the panel's pivot rows, O the other rows and
+// X = A[P,K]^-1, four elimination steps map
+//   A[:,K] -> T = [X; -A[O,K] X],   A[P,J] -> X A[P,J],   A[O,J] -> A[O,J] + T[O,:] A[P,J]
+// on every other column J (the in-place form of the inverse keeps T in the pivot columns).
+// Per panel:
+//  (1) one warp runs the four steps on the panel's columns alone, held in its registers (pivot
+//      search over the rows not yet pivoted, row interchange by shuffles, elimination), which
+//      leaves T in place; the pivots are those of the unblocked elimination, since a step
+//      reads only its own column and the pivot rows' entries in the panel;
+//  (2) the same warp, one lane per other column group, applies the four interchanges to those
+//      columns and copies the pivot rows A[P,J] to a buffer;
+//  (3) after one barrier, every row of every other column group takes the rank-4 update.
+// So four steps read and write the matrix once, and a thread applies each pivot-row float4 it
+// loads to all of its rows. b^3 multiply-adds per block; the row interchanges are undone on the
+// columns at the end, in reverse order.
+__global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
   const int LD = gj_ld(b);
   float* A = reinterpret_cast<float*>(sraw_);  // [b][LD]
-  float* col = A + (size_t)b * LD;             // [b] column k before step k
-  float* row = col + b;                         // [b] scaled pivot row
-  int* piv = reinterpret_cast<int*>(row + b);
-  __shared__ int s_p;
-  __shared__ float s_inv;
-  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
-  const int NG = b / 4;                      // float4 column groups
-  const int CW = 32 * ((NG + 31) / 32);      // group slots (whole warps)
-  const int RG = nt / CW;                    // row groups; blockDim.x is a multiple of CW
-  const int jg = tid % CW, ig = tid / CW;
+  float* Rp = A + (size_t)b * LD;             // [4][LD] the panel's pivot rows before the update
+  int* piv = reinterpret_cast<int*>(Rp + 4 * LD);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int NG = b / 4;  // float4 column groups = panels
+  int RG = nt / NG;      // row groups of the update
+  if (RG > b) RG = b;
+  const int jg = tid % NG, ig = tid / NG;
+  const bool upd = tid < NG * RG;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     float* Mb = M + (size_t)blk * b * b;
     for (int t = tid; t < b * b; t += nt) {
@@ -78,56 +96,137 @@ __global__ void __launch_bounds__(512) gj_inverse_kernel(int nblk, int b, float*
       A[r * LD + c] = Mb[t];
     }
     __syncthreads();
-    for (int k = 0; k < b; ++k) {
-      if (warp == 0) {
-        float best = -1.0f;
-        int bi = k;
-        for (int i = k + lane; i < b; i += 32) {
-          const float v = fabsf(A[i * LD + k]);
-          if (v > best) { best = v; bi = i; }
+    for (int g = 0; g < NG; ++g) {
+      const int k0 = 4 * g;
+      // (1) the panel's four elimination steps, by warp 0 with the panel in registers: lane l
+      // holds rows l + 32 m (m < kGjSlots)
+      if (tid < 32) {
+        float4 pv[kGjSlots];
+#pragma unroll
+        for (int m = 0; m < kGjSlots; ++m) {
+          const int i = lane + 32 * m;
+          pv[m] = i < b ? *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int off = 16; off > 0; off >>= 1) {
-          const float ov = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) {
-          s_p = bi;
-          piv[k] = bi;
-          s_inv = 1.0f / A[bi * LD + k];
-          if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
-        }
-      }
-      __syncthreads();
-      const int p = s_p;
-      const float inv = s_inv;
-      for (int i = tid; i < b; i += nt) {
-        const int src = i == k ? p : (i == p ? k : i);  // rows as after the interchange
-        col[i] = A[src * LD + k];
-      }
-      for (int j = tid; j < b; j += nt) row[j] = j == k ? inv : A[p * LD + j] * inv;
-      __syncthreads();
-      // row k moves to row p (its column-k entry becomes 0), and column k is zeroed elsewhere
-      if (p != k)
-        for (int j = tid; j < b; j += nt) A[p * LD + j] = j == k ? 0.0f : A[k * LD + j];
-      for (int i = tid; i < b; i += nt)
-        if (i != p) A[i * LD + k] = 0.0f;
-      __syncthreads();
-      if (jg < NG) {
-        const float4 r4 = *reinterpret_cast<const float4*>(row + 4 * jg);
-        for (int i = ig; i < b; i += RG) {
-          float4* a4 = reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * jg);
-          if (i == k) {
-            *a4 = r4;
-          } else {
-            const float c = col[i];
-            float4 v = *a4;
-            v.x = fmaf(-c, r4.x, v.x);
-            v.y = fmaf(-c, r4.y, v.y);
-            v.z = fmaf(-c, r4.z, v.z);
-            v.w = fmaf(-c, r4.w, v.w);
-            *a4 = v;
+        int pq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k = k0 + q;
+          float best = -1.0f;
+          int bi = k;
+#pragma unroll
+          for (int m = 0; m < kGjSlots; ++m) {
+            const int i = lane + 32 * m;
+            if (i >= k && i < b) {
+              const float v = fabsf(f4get(pv[m], q));
+              if (v > best) { best = v; bi = i; }
+            }
           }
+          for (int off = 16; off > 0; off >>= 1) {
+            const float ov = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+          }
+          const int p = __shfl_sync(0xffffffffu, bi, 0);
+          best = __shfl_sync(0xffffffffu, best, 0);
+          pq[q] = p;
+          if (lane == 0) {
+            piv[k] = p;
+            if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
+          }
+          // interchange rows k and p: each lane offers its slot's value, the owners exchange
+          const int sk = k >> 5, sp = p >> 5, lk = k & 31, lp = p & 31;
+          float4 rowp, rowk, o = pv[0];
+#pragma unroll
+          for (int m = 1; m < kGjSlots; ++m)
+            if (m == sp) o = pv[m];
+          rowp.x = __shfl_sync(0xffffffffu, o.x, lp);
+          rowp.y = __shfl_sync(0xffffffffu, o.y, lp);
+          rowp.z = __shfl_sync(0xffffffffu, o.z, lp);
+          rowp.w = __shfl_sync(0xffffffffu, o.w, lp);
+          o = pv[0];
+#pragma unroll
+          for (int m = 1; m < kGjSlots; ++m)
+            if (m == sk) o = pv[m];
+          rowk.x = __shfl_sync(0xffffffffu, o.x, lk);
+          rowk.y = __shfl_sync(0xffffffffu, o.y, lk);
+          rowk.z = __shfl_sync(0xffffffffu, o.z, lk);
+          rowk.w = __shfl_sync(0xffffffffu, o.w, lk);
+#pragma unroll
+          for (int m = 0; m < kGjSlots; ++m)
+            if (m == sp && lane == lp) pv[m] = rowk;
+          // the pivot row (old row p) is now row k: scale it, eliminate column k elsewhere
+          const float inv = 1.0f / f4get(rowp, q);
+          float4 r4 = make_float4(rowp.x * inv, rowp.y * inv, rowp.z * inv, rowp.w * inv);
+          f4set(r4, q, inv);
+#pragma unroll
+          for (int m = 0; m < kGjSlots; ++m) {
+            const int i = lane + 32 * m;
+            if (i == k) {
+              pv[m] = r4;
+            } else {
+              float4 v = pv[m];
+              const float c = f4get(v, q);
+              v.x = fmaf(-c, r4.x, v.x);
+              v.y = fmaf(-c, r4.y, v.y);
+              v.z = fmaf(-c, r4.z, v.z);
+              v.w = fmaf(-c, r4.w, v.w);
+              f4set(v, q, -c * inv);
+              pv[m] = v;
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < kGjSlots; ++m) {
+          const int i = lane + 32 * m;
+          if (i < b) *reinterpret_cast<float4*>(A + (size_t)i * LD + k0) = pv[m];
+        }
+        // (2) the interchanges on the other column groups, and their pivot rows to the buffer
+        for (int j = lane; j < NG; j += 32) {
+          if (j == g) continue;
+          for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q, p = pq[q];
+            if (p != k) {
+              float4* ak = reinterpret_cast<float4*>(A + (size_t)k * LD + 4 * j);
+              float4* ap = reinterpret_cast<float4*>(A + (size_t)p * LD + 4 * j);
+              const float4 t = *ak;
+              *ak = *ap;
+              *ap = t;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(Rp + q * LD + 4 * j) =
+                *reinterpret_cast<const float4*>(A + (size_t)(k0 + q) * LD + 4 * j);
+        }
+      }
+      __syncthreads();
+      // (3) the rank-4 update of the other column groups
+      if (upd && jg != g) {
+        const float4 r0 = *reinterpret_cast<const float4*>(Rp + 4 * jg);
+        const float4 r1 = *reinterpret_cast<const float4*>(Rp + LD + 4 * jg);
+        const float4 r2 = *reinterpret_cast<const float4*>(Rp + 2 * LD + 4 * jg);
+        const float4 r3 = *reinterpret_cast<const float4*>(Rp + 3 * LD + 4 * jg);
+        for (int i = ig; i < b; i += RG) {
+          const float4 t = *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0);
+          float4* ai = reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * jg);
+          float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f) : *ai;
+          v.x = fmaf(t.x, r0.x, v.x);
+          v.y = fmaf(t.x, r0.y, v.y);
+          v.z = fmaf(t.x, r0.z, v.z);
+          v.w = fmaf(t.x, r0.w, v.w);
+          v.x = fmaf(t.y, r1.x, v.x);
+          v.y = fmaf(t.y, r1.y, v.y);
+          v.z = fmaf(t.y, r1.z, v.z);
+          v.w = fmaf(t.y, r1.w, v.w);
+          v.x = fmaf(t.z, r2.x, v.x);
+          v.y = fmaf(t.z, r2.y, v.y);
+          v.z = fmaf(t.z, r2.z, v.z);
+          v.w = fmaf(t.z, r2.w, v.w);
+          v.x = fmaf(t.w, r3.x, v.x);
+          v.y = fmaf(t.w, r3.y, v.y);
+          v.z = fmaf(t.w, r3.z, v.z);
+          v.w = fmaf(t.w, r3.w, v.w);
+          *ai = v;
         }
       }
       __syncthreads();
@@ -470,13 +569,15 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
-    const size_t smem = sizeof(float) * ((size_t)L.b * gj_ld(L.b) + 2 * L.b) + sizeof(int) * L.b;
-    if (smem > kSmemLimit || L.b % 4 != 0) return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
+    const size_t smem = sizeof(float) * ((size_t)(L.b + 4) * gj_ld(L.b)) + sizeof(int) * L.b;
+    if (smem > kSmemLimit || L.b % 4 != 0 || L.b > 32 * kGjSlots)
+      return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
     DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
     const int grid = std::min(h->ne, h->nsm * per_sm);
-    const int cw = 32 * ((L.b / 4 + 31) / 32);
-    const int threads = cw * std::max(1, 512 / cw);  // a multiple of the group slots, <= 512
+    // (column group, row group) pairs of the update: at most 512 threads, at most b row groups
+    const int ng = L.b / 4, active = ng * std::min(L.b, 512 / ng);
+    const int threads = std::min(512, 32 * ((active + 31) / 32));
     gj_inverse_kernel<<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
     DG_LAUNCH_CHECK(h);
   }
