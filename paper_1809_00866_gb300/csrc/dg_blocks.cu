@@ -443,6 +443,98 @@ int launch_direct(Handle* h, int b, const S* A, const R* v, const R* w, R alpha,
   return DG_OK;
 }
 
+// Eight 16-bit entries (one 16-byte vector) widened to float.
+__device__ __forceinline__ void wide8(const uint4& raw, const __half*, float* o) {
+  const __half2* h2 = reinterpret_cast<const __half2*>(&raw);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 f = __half22float2(h2[j]);
+    o[2 * j] = f.x;
+    o[2 * j + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void wide8(const uint4& raw, const __nv_bfloat16*, float* o) {
+  const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 f = __bfloat1622float2(h2[j]);
+    o[2 * j] = f.x;
+    o[2 * j + 1] = f.y;
+  }
+}
+
+// y = alpha A x + beta y over rows of 7 blocks stored in 16 bits (b a multiple of 8), FP32
+// accumulation. A task is eight consecutive rows of one block: per block column it loads one
+// 16-byte vector, so a warp's load moves 512 bytes and a thread keeps eight loads (128 bytes)
+// in flight. The seven block partial sums of a row meet in shared memory and are added in
+// block order.
+template <class S>
+__global__ void __launch_bounds__(256) direct7_vec_kernel(int ne, int b, int epc, const S* __restrict__ A,
+                                                          const int* __restrict__ nbr, const float* __restrict__ v,
+                                                          float alpha, float beta, float* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char sraw_[];
+  const int ncol = 7 * b, rg = b / 8, tpe = 7 * rg;
+  float* rv = reinterpret_cast<float*>(sraw_);  // [epc][ncol] the seven slices of v
+  float* part = rv + (size_t)epc * ncol;       // [epc][7][b] block partial sums
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e0 = blockIdx.x * epc; e0 < ne; e0 += gridDim.x * epc) {
+    const int cnt = min(epc, ne - e0);
+    for (int t = tid; t < cnt * ncol; t += nt) {
+      const int el = t / ncol, q = t - el * ncol;
+      const int e = e0 + el;
+      const int sb = q / b, c = q - sb * b;
+      const int src = sb == 0 ? e : nbr[(size_t)e * 6 + sb - 1];
+      rv[t] = src >= 0 ? v[(size_t)src * b + c] : 0.0f;  // no neighbour across a wall (zero block)
+    }
+    __syncthreads();
+    if (tid < cnt * tpe) {
+      const int el = tid / tpe, r = tid - el * tpe, sb = r / rg, r8 = r - sb * rg;
+      const S* As = A + (size_t)(e0 + el) * ncol * b + (size_t)sb * b * b + 8 * r8;
+      const float* re = rv + (size_t)el * ncol + sb * b;
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+#pragma unroll 8
+      for (int c = 0; c < b; ++c) {
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(As + (size_t)c * b));
+        float a8[8];
+        wide8(raw, As, a8);
+        const float xc = re[c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fmaf(a8[u], xc, acc[u]);
+      }
+      float* ps = part + ((size_t)el * 7 + sb) * b + 8 * r8;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) ps[u] = acc[u];
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt * b; t += nt) {
+      const int el = t / b, i = t - el * b;
+      const float* pe = part + (size_t)el * 7 * b + i;
+      float acc = pe[0];
+#pragma unroll
+      for (int sb = 1; sb < 7; ++sb) acc += pe[sb * b];
+      float* ye = y + (size_t)(e0 + el) * b + i;
+      *ye = alpha * acc + (beta == 0.0f ? 0.0f : beta * *ye);
+    }
+    __syncthreads();
+  }
+}
+
+template <class S>
+int launch_direct7_vec(Handle* h, int b, const S* A, const float* v, float alpha, float beta, float* y,
+                       cudaStream_t st) {
+  const int tpe = 7 * (b / 8);
+  if (b % 8 != 0 || tpe > 256) return -1;
+  const int epc = std::max(1, 256 / tpe);
+  const int threads = 32 * ((epc * tpe + 31) / 32);
+  const size_t smem = sizeof(float) * (size_t)epc * 14 * b;  // slices of v and partial sums
+  const int grid = (h->ne + epc - 1) / epc;
+  direct7_vec_kernel<S><<<grid, threads, smem, st>>>(h->ne, b, epc, A, h->nbr, v, alpha, beta, y);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
 constexpr size_t kStageTarget = 96 * 1024;  // bytes of inverses per stage (one buffer)
 constexpr size_t kSmemLimit = 220 * 1024;    // dynamic shared memory a kernel may take
 
@@ -555,11 +647,18 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
   cudaEvent_t e0 = nullptr;
   int rc;
   if (lvl == 1 && (rc = prof_begin(h, st, &e0))) return rc;
-  if (storage == DG_PRECOND_FP32_H16)
+  if (L.b % 8 == 0) {  // 16-byte vectors of eight rows
+    if (storage == DG_PRECOND_FP32_H16)
+      rc = launch_direct7_vec<__half>(h, L.b, static_cast<const __half*>(L.Bsr16), x, alpha, beta, y, st);
+    else
+      rc = launch_direct7_vec<__nv_bfloat16>(h, L.b, static_cast<const __nv_bfloat16*>(L.Bsr16), x, alpha, beta, y,
+                                             st);
+  } else if (storage == DG_PRECOND_FP32_H16) {
     rc = launch_direct<float, 7, __half>(h, L.b, static_cast<const __half*>(L.Bsr16), x, nullptr, alpha, beta, 0, y, st);
-  else
+  } else {
     rc = launch_direct<float, 7, __nv_bfloat16>(h, L.b, static_cast<const __nv_bfloat16*>(L.Bsr16), x, nullptr, alpha,
                                                 beta, 0, y, st);
+  }
   if (rc) return rc;
   const double vec = (double)h->ne * L.b * sizeof(float);
   const double bytes = 7.0 * h->ne * L.b * L.b * 2 + vec * (2 + (beta != 0.0f ? 1 : 0));
