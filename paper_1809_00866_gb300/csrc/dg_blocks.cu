@@ -59,6 +59,127 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
   if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
 }
 
+// Four elimination steps of the panel whose pivot columns are k0..k0+3, on those columns alone,
+// held in the registers of one warp (lane l holds rows l + 32 m, m < kGjSlots): pivot search
+// over the rows not yet pivoted (ties to the lower row), row interchange by shuffles, in-place
+// elimination. The pivots go to piv[] and pq[].
+__device__ __forceinline__ void gj_factor_panel(float4 (&pv)[kGjSlots], int b, int k0, int lane, int* piv,
+                                                int (&pq)[4], unsigned* status) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = k0 + q;
+    float best = -1.0f;
+    int bi = k;
+#pragma unroll
+    for (int m = 0; m < kGjSlots; ++m) {
+      const int i = lane + 32 * m;
+      if (i >= k && i < b) {
+        const float v = fabsf(f4get(pv[m], q));
+        if (v > best) { best = v; bi = i; }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    const int p = __shfl_sync(0xffffffffu, bi, 0);
+    best = __shfl_sync(0xffffffffu, best, 0);
+    pq[q] = p;
+    if (lane == 0) {
+      piv[k] = p;
+      if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
+    }
+    // interchange rows k and p: each lane offers its slot's value, the owners exchange
+    const int sk = k >> 5, sp = p >> 5, lk = k & 31, lp = p & 31;
+    float4 rowp, rowk, o = pv[0];
+#pragma unroll
+    for (int m = 1; m < kGjSlots; ++m)
+      if (m == sp) o = pv[m];
+    rowp.x = __shfl_sync(0xffffffffu, o.x, lp);
+    rowp.y = __shfl_sync(0xffffffffu, o.y, lp);
+    rowp.z = __shfl_sync(0xffffffffu, o.z, lp);
+    rowp.w = __shfl_sync(0xffffffffu, o.w, lp);
+    o = pv[0];
+#pragma unroll
+    for (int m = 1; m < kGjSlots; ++m)
+      if (m == sk) o = pv[m];
+    rowk.x = __shfl_sync(0xffffffffu, o.x, lk);
+    rowk.y = __shfl_sync(0xffffffffu, o.y, lk);
+    rowk.z = __shfl_sync(0xffffffffu, o.z, lk);
+    rowk.w = __shfl_sync(0xffffffffu, o.w, lk);
+#pragma unroll
+    for (int m = 0; m < kGjSlots; ++m)
+      if (m == sp && lane == lp) pv[m] = rowk;
+    // the pivot row (old row p) is now row k: scale it, eliminate column k elsewhere
+    const float inv = 1.0f / f4get(rowp, q);
+    float4 r4 = make_float4(rowp.x * inv, rowp.y * inv, rowp.z * inv, rowp.w * inv);
+    f4set(r4, q, inv);
+#pragma unroll
+    for (int m = 0; m < kGjSlots; ++m) {
+      const int i = lane + 32 * m;
+      if (i == k) {
+        pv[m] = r4;
+      } else {
+        float4 v = pv[m];
+        const float c = f4get(v, q);
+        v.x = fmaf(-c, r4.x, v.x);
+        v.y = fmaf(-c, r4.y, v.y);
+        v.z = fmaf(-c, r4.z, v.z);
+        v.w = fmaf(-c, r4.w, v.w);
+        f4set(v, q, -c * inv);
+        pv[m] = v;
+      }
+    }
+  }
+}
+
+// The panel's four interchanges on every other column group (one lane per group), then its pivot
+// rows of those groups to the buffer Rp.
+__device__ __forceinline__ void gj_interchange(float* A, float* Rp, int LD, int NG, int g, const int (&pq)[4],
+                                               int lane) {
+  const int k0 = 4 * g;
+  for (int j = lane; j < NG; j += 32) {
+    if (j == g) continue;
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + q, p = pq[q];
+      if (p != k) {
+        float4* ak = reinterpret_cast<float4*>(A + (size_t)k * LD + 4 * j);
+        float4* ap = reinterpret_cast<float4*>(A + (size_t)p * LD + 4 * j);
+        const float4 t = *ak;
+        *ak = *ap;
+        *ap = t;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(Rp + q * LD + 4 * j) =
+          *reinterpret_cast<const float4*>(A + (size_t)(k0 + q) * LD + 4 * j);
+  }
+}
+
+// v + t0 r0 + t1 r1 + t2 r2 + t3 r3 on four columns
+__device__ __forceinline__ float4 gj_rank4(float4 v, const float4& t, const float4& r0, const float4& r1,
+                                           const float4& r2, const float4& r3) {
+  v.x = fmaf(t.x, r0.x, v.x);
+  v.y = fmaf(t.x, r0.y, v.y);
+  v.z = fmaf(t.x, r0.z, v.z);
+  v.w = fmaf(t.x, r0.w, v.w);
+  v.x = fmaf(t.y, r1.x, v.x);
+  v.y = fmaf(t.y, r1.y, v.y);
+  v.z = fmaf(t.y, r1.z, v.z);
+  v.w = fmaf(t.y, r1.w, v.w);
+  v.x = fmaf(t.z, r2.x, v.x);
+  v.y = fmaf(t.z, r2.y, v.y);
+  v.z = fmaf(t.z, r2.z, v.z);
+  v.w = fmaf(t.z, r2.w, v.w);
+  v.x = fmaf(t.w, r3.x, v.x);
+  v.y = fmaf(t.w, r3.y, v.y);
+  v.z = fmaf(t.w, r3.z, v.z);
+  v.w = fmaf(t.w, r3.w, v.w);
+  return v;
+}
+
 // In place D -> D^-1 (column-major FP32 blocks, b a multiple of 4) by Gauss-Jordan elimination
 // with partial (row) pivoting, one block per CTA in shared memory (row-major, leading dimension
 // gj_ld(b) so that rows are float4-aligned), in panels of four pivots. The four pivot columns K
@@ -66,17 +187,16 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
 // X = A[P,K]^-1, four elimination steps map
 //   A[:,K] -> T = [X; -A[O,K] X],   A[P,J] -> X A[P,J],   A[O,J] -> A[O,J] + T[O,:] A[P,J]
 // on every other column J (the in-place form of the inverse keeps T in the pivot columns).
-// Per panel:
-//  (1) one warp runs the four steps on the panel's columns alone, held in its registers (pivot
-//      search over the rows not yet pivoted, row interchange by shuffles, elimination), which
-//      leaves T in place; the pivots are those of the unblocked elimination, since a step
-//      reads only its own column and the pivot rows' entries in the panel;
-//  (2) the same warp, one lane per other column group, applies the four interchanges to those
-//      columns and copies the pivot rows A[P,J] to a buffer;
-//  (3) after one barrier, every row of every other column group takes the rank-4 update.
-// So four steps read and write the matrix once, and a thread applies each pivot-row float4 it
-// loads to all of its rows. b^3 multiply-adds per block; the row interchanges are undone on the
-// columns at the end, in reverse order.
+// Warp 0 factors the panels: it runs a panel's four steps on its columns alone, in registers,
+// which leaves T in place; the pivots are those of the unblocked elimination, since a step reads
+// only its own column and the pivot rows' entries in the panel. It then applies the panel's
+// interchanges to the other column groups and copies their pivot rows to a buffer. The other
+// warps apply the rank-4 update: a thread owns one column group and every RG-th row, so a
+// pivot-row float4 it loads serves all its rows, and four steps read and write the matrix once.
+// Look-ahead: while the other warps apply panel g's update, warp 0 applies it to group g + 1
+// alone and factors panel g + 1, so the factoring chain is off the critical path. Two barriers
+// per panel. b^3 multiply-adds per block; the row interchanges are undone on the columns at the
+// end, in reverse order.
 __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
   const int LD = gj_ld(b);
@@ -85,10 +205,11 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
   int* piv = reinterpret_cast<int*>(Rp + 4 * LD);
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   const int NG = b / 4;  // float4 column groups = panels
-  int RG = nt / NG;      // row groups of the update
+  int RG = (nt - 32) / NG;  // row groups of the update, on warps 1..
   if (RG > b) RG = b;
-  const int jg = tid % NG, ig = tid / NG;
-  const bool upd = tid < NG * RG;
+  const int tu = tid - 32;
+  const bool upd = tid >= 32 && tu < NG * RG;
+  const int jg = upd ? tu % NG : 0, ig = upd ? tu / NG : 0;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     float* Mb = M + (size_t)blk * b * b;
     for (int t = tid; t < b * b; t += nt) {
@@ -96,112 +217,54 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
       A[r * LD + c] = Mb[t];
     }
     __syncthreads();
+    int pq[4] = {0, 0, 0, 0};
+    if (tid < 32) {  // panel 0
+      float4 pv[kGjSlots];
+#pragma unroll
+      for (int m = 0; m < kGjSlots; ++m) {
+        const int i = lane + 32 * m;
+        pv[m] = i < b ? *reinterpret_cast<const float4*>(A + (size_t)i * LD) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      gj_factor_panel(pv, b, 0, lane, piv, pq, status);
+#pragma unroll
+      for (int m = 0; m < kGjSlots; ++m) {
+        const int i = lane + 32 * m;
+        if (i < b) *reinterpret_cast<float4*>(A + (size_t)i * LD) = pv[m];
+      }
+      gj_interchange(A, Rp, LD, NG, 0, pq, lane);
+    }
+    __syncthreads();
     for (int g = 0; g < NG; ++g) {
       const int k0 = 4 * g;
-      // (1) the panel's four elimination steps, by warp 0 with the panel in registers: lane l
-      // holds rows l + 32 m (m < kGjSlots)
+      const bool next = g + 1 < NG;
       if (tid < 32) {
-        float4 pv[kGjSlots];
-#pragma unroll
-        for (int m = 0; m < kGjSlots; ++m) {
-          const int i = lane + 32 * m;
-          pv[m] = i < b ? *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        int pq[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = k0 + q;
-          float best = -1.0f;
-          int bi = k;
+        if (next) {  // panel g's update of group g + 1, then panel g + 1's steps
+          const int j = g + 1;
+          const float4 r0 = *reinterpret_cast<const float4*>(Rp + 4 * j);
+          const float4 r1 = *reinterpret_cast<const float4*>(Rp + LD + 4 * j);
+          const float4 r2 = *reinterpret_cast<const float4*>(Rp + 2 * LD + 4 * j);
+          const float4 r3 = *reinterpret_cast<const float4*>(Rp + 3 * LD + 4 * j);
+          float4 pv[kGjSlots];
 #pragma unroll
           for (int m = 0; m < kGjSlots; ++m) {
             const int i = lane + 32 * m;
-            if (i >= k && i < b) {
-              const float v = fabsf(f4get(pv[m], q));
-              if (v > best) { best = v; bi = i; }
-            }
-          }
-          for (int off = 16; off > 0; off >>= 1) {
-            const float ov = __shfl_down_sync(0xffffffffu, best, off);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-          }
-          const int p = __shfl_sync(0xffffffffu, bi, 0);
-          best = __shfl_sync(0xffffffffu, best, 0);
-          pq[q] = p;
-          if (lane == 0) {
-            piv[k] = p;
-            if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
-          }
-          // interchange rows k and p: each lane offers its slot's value, the owners exchange
-          const int sk = k >> 5, sp = p >> 5, lk = k & 31, lp = p & 31;
-          float4 rowp, rowk, o = pv[0];
-#pragma unroll
-          for (int m = 1; m < kGjSlots; ++m)
-            if (m == sp) o = pv[m];
-          rowp.x = __shfl_sync(0xffffffffu, o.x, lp);
-          rowp.y = __shfl_sync(0xffffffffu, o.y, lp);
-          rowp.z = __shfl_sync(0xffffffffu, o.z, lp);
-          rowp.w = __shfl_sync(0xffffffffu, o.w, lp);
-          o = pv[0];
-#pragma unroll
-          for (int m = 1; m < kGjSlots; ++m)
-            if (m == sk) o = pv[m];
-          rowk.x = __shfl_sync(0xffffffffu, o.x, lk);
-          rowk.y = __shfl_sync(0xffffffffu, o.y, lk);
-          rowk.z = __shfl_sync(0xffffffffu, o.z, lk);
-          rowk.w = __shfl_sync(0xffffffffu, o.w, lk);
-#pragma unroll
-          for (int m = 0; m < kGjSlots; ++m)
-            if (m == sp && lane == lp) pv[m] = rowk;
-          // the pivot row (old row p) is now row k: scale it, eliminate column k elsewhere
-          const float inv = 1.0f / f4get(rowp, q);
-          float4 r4 = make_float4(rowp.x * inv, rowp.y * inv, rowp.z * inv, rowp.w * inv);
-          f4set(r4, q, inv);
-#pragma unroll
-          for (int m = 0; m < kGjSlots; ++m) {
-            const int i = lane + 32 * m;
-            if (i == k) {
-              pv[m] = r4;
+            if (i < b) {
+              const float4 t = *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0);
+              const float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                         : *reinterpret_cast<const float4*>(A + (size_t)i * LD + 4 * j);
+              pv[m] = gj_rank4(v, t, r0, r1, r2, r3);
             } else {
-              float4 v = pv[m];
-              const float c = f4get(v, q);
-              v.x = fmaf(-c, r4.x, v.x);
-              v.y = fmaf(-c, r4.y, v.y);
-              v.z = fmaf(-c, r4.z, v.z);
-              v.w = fmaf(-c, r4.w, v.w);
-              f4set(v, q, -c * inv);
-              pv[m] = v;
+              pv[m] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
           }
-        }
+          gj_factor_panel(pv, b, 4 * j, lane, piv, pq, status);
 #pragma unroll
-        for (int m = 0; m < kGjSlots; ++m) {
-          const int i = lane + 32 * m;
-          if (i < b) *reinterpret_cast<float4*>(A + (size_t)i * LD + k0) = pv[m];
-        }
-        // (2) the interchanges on the other column groups, and their pivot rows to the buffer
-        for (int j = lane; j < NG; j += 32) {
-          if (j == g) continue;
-          for (int q = 0; q < 4; ++q) {
-            const int k = k0 + q, p = pq[q];
-            if (p != k) {
-              float4* ak = reinterpret_cast<float4*>(A + (size_t)k * LD + 4 * j);
-              float4* ap = reinterpret_cast<float4*>(A + (size_t)p * LD + 4 * j);
-              const float4 t = *ak;
-              *ak = *ap;
-              *ap = t;
-            }
+          for (int m = 0; m < kGjSlots; ++m) {
+            const int i = lane + 32 * m;
+            if (i < b) *reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * j) = pv[m];
           }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float4*>(Rp + q * LD + 4 * j) =
-                *reinterpret_cast<const float4*>(A + (size_t)(k0 + q) * LD + 4 * j);
         }
-      }
-      __syncthreads();
-      // (3) the rank-4 update of the other column groups
-      if (upd && jg != g) {
+      } else if (upd && jg != g && jg != g + 1) {  // panel g's update of the other groups
         const float4 r0 = *reinterpret_cast<const float4*>(Rp + 4 * jg);
         const float4 r1 = *reinterpret_cast<const float4*>(Rp + LD + 4 * jg);
         const float4 r2 = *reinterpret_cast<const float4*>(Rp + 2 * LD + 4 * jg);
@@ -209,27 +272,15 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
         for (int i = ig; i < b; i += RG) {
           const float4 t = *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0);
           float4* ai = reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * jg);
-          float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f) : *ai;
-          v.x = fmaf(t.x, r0.x, v.x);
-          v.y = fmaf(t.x, r0.y, v.y);
-          v.z = fmaf(t.x, r0.z, v.z);
-          v.w = fmaf(t.x, r0.w, v.w);
-          v.x = fmaf(t.y, r1.x, v.x);
-          v.y = fmaf(t.y, r1.y, v.y);
-          v.z = fmaf(t.y, r1.z, v.z);
-          v.w = fmaf(t.y, r1.w, v.w);
-          v.x = fmaf(t.z, r2.x, v.x);
-          v.y = fmaf(t.z, r2.y, v.y);
-          v.z = fmaf(t.z, r2.z, v.z);
-          v.w = fmaf(t.z, r2.w, v.w);
-          v.x = fmaf(t.w, r3.x, v.x);
-          v.y = fmaf(t.w, r3.y, v.y);
-          v.z = fmaf(t.w, r3.z, v.z);
-          v.w = fmaf(t.w, r3.w, v.w);
-          *ai = v;
+          const float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f) : *ai;
+          *ai = gj_rank4(v, t, r0, r1, r2, r3);
         }
       }
       __syncthreads();
+      if (next) {
+        if (tid < 32) gj_interchange(A, Rp, LD, NG, g + 1, pq, lane);
+        __syncthreads();
+      }
     }
     for (int k = b - 1; k >= 0; --k) {
       const int p = piv[k];
@@ -674,9 +725,10 @@ int invert_levels_f32(Handle* h, cudaStream_t st) {
     DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
     const int grid = std::min(h->ne, h->nsm * per_sm);
-    // (column group, row group) pairs of the update: at most 512 threads, at most b row groups
-    const int ng = L.b / 4, active = ng * std::min(L.b, 512 / ng);
-    const int threads = std::min(512, 32 * ((active + 31) / 32));
+    // warp 0 factors; the (column group, row group) pairs of the update on the warps after it:
+    // at most 512 threads, at most b row groups
+    const int ng = L.b / 4, active = ng * std::min(L.b, 480 / ng);
+    const int threads = std::min(512, 32 + 32 * ((active + 31) / 32));
     gj_inverse_kernel<<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
     DG_LAUNCH_CHECK(h);
   }
