@@ -202,10 +202,10 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
     const double step = nxt - us;
     us = nxt;
     // After a Newton step of size |step| the error is about K step^2, with K = |phi''| / (2 |phi'|)
-    // at the root. The wave curves are C^2 in u, and K stays below 0.3 / c at the roots of
-    // states with |u_L|, |u_R| up to 100 c and pressure jumps up to 10^4 c^2 (evaluated in
-    // extended precision). A Newton step below 1e-9 c therefore leaves an error below 1e-18 c,
-    // and the confirming iteration is skipped.
+    // at the root. The wave curves are C^2 in u. With two rarefactions K = |u*| / (2 (u*^2 + c^2))
+    // <= 1 / (4 c); over shocks as well it stays below 0.5 / c (about 0.33 / c at most over seeded
+    // states with |u_L|, |u_R| up to 300 c, evaluated in extended precision). A Newton step below
+    // 1e-9 c therefore leaves an error below 1e-18 c, and the confirming iteration is skipped.
     if (fabs(step) <= 1e-15 * scale || (newton && fabs(step) <= 1e-9 * c)) { ok = true; break; }
   }
   if (!ok && status) atomicOr(status, (unsigned)DG_STATUS_RIEMANN);
