@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256) direct_apply_kernel(int ne, int b, int ep
 template <class R, int NBLK, class S>
 int launch_direct(Handle* h, int b, const S* A, const R* v, const R* w, R alpha, R beta, int x_zero, R* y,
                   cudaStream_t st) {
-  if (b > 256) return -1;
+  if (b > 256) return -1;  // -1, not a DG_ code: the caller falls back to bsr_kernel
   const int epc = std::max(1, 256 / b);
   const int threads = 32 * ((epc * b + 31) / 32);
   const size_t smem = sizeof(R) * (size_t)epc * NBLK * b;
@@ -576,7 +576,7 @@ template <class S>
 int launch_direct7_vec(Handle* h, int b, const S* A, const float* v, float alpha, float beta, float* y,
                        cudaStream_t st) {
   const int tpe = 7 * (b / 8);
-  if (b % 8 != 0 || tpe > 256) return -1;
+  if (b % 8 != 0 || tpe > 256) return -1;  // -1: unsuited; the caller reports it
   const int epc = std::max(1, 256 / tpe);
   const int threads = 32 * ((epc * tpe + 31) / 32);
   const size_t smem = sizeof(float) * (size_t)epc * 14 * b;  // slices of v and partial sums
@@ -601,6 +601,8 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   // as many buffers as fit (2..4): the stages in flight while one is multiplied
   const int ns = (int)std::max<size_t>(2, std::min<size_t>(kJacobiSlots, kSmemLimit / ((size_t)G * per_slot)));
   const size_t smem = (size_t)ns * G * per_slot;
+  // -1, not a DG_ code: the block does not fit the staged copies; the smoother reports it and the
+  // autotuner skips the shape
   if (smem > kSmemLimit || per % 16 != 0 || (b * sizeof(R)) % 16 != 0) return -1;
   static bool opted = false;  // per template instance; one device per process
   if (!opted) {
