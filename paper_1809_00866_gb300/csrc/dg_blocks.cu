@@ -601,8 +601,8 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   // as many buffers as fit (2..4): the stages in flight while one is multiplied
   const int ns = (int)std::max<size_t>(2, std::min<size_t>(kJacobiSlots, kSmemLimit / ((size_t)G * per_slot)));
   const size_t smem = (size_t)ns * G * per_slot;
-  // -1, not a DG_ code: the block does not fit the staged copies; the smoother reports it and the
-  // autotuner skips the shape
+  // -1, not a DG_ code: the block does not fit the staged copies; the smoother and the autotuner
+  // report it
   if (smem > kSmemLimit || per % 16 != 0 || (b * sizeof(R)) % 16 != 0) return -1;
   static bool opted = false;  // per template instance; one device per process
   if (!opted) {
