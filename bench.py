@@ -95,6 +95,24 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (the job's time is its slowest replica's); the value
+    itself on one rank. Collective: every rank must call it."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_stage(t_total, steps, world):
+    """Whole-job seconds per stage: every rank runs `steps` stages of its own replica, and the
+    job takes the slowest rank's total time t_total."""
+    return t_total / (steps * world)
+
+
 def mesh_nodes(cfg):
     n = cfg["n"]
     return S.uniform_nodes(n), S.uniform_nodes(n), S.uniform_nodes(n)
@@ -577,15 +595,12 @@ def run_ours(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
         l1, a1 = dg.dg_counters()
-        t_total = sum(times)
-        if world > 1:
-            tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_total = float(tt.item())
+        t_total = max_over_ranks(sum(times), world, "cuda")
         names = ["rhs_and_linearize", "assemble", "solve"]
         breakdown = {nm: statistics.mean(ph[i].elapsed_time(ph[i + 1]) for ph in phases) / 1e3
                      for i, nm in enumerate(names)}
-        return {"s_per_stage": t_total / (args.steps * world), "t_total": t_total, "breakdown_s": breakdown,
+        return {"s_per_stage": job_seconds_per_stage(t_total, args.steps, world), "t_total": t_total,
+                "breakdown_s": breakdown,
                 "fgmres_its": log["its"], "true_relres": log["relres"], "fallback_at": log.get("fallback_at"),
                 "operator_applications": (a1 - a0) / max(1, args.steps),
                 "gpu_launches": (l1 - l0) // max(1, args.steps)}
