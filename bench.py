@@ -76,6 +76,9 @@ HBM_FALLBACK_GBS = 6800.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of a sweep with a previous iterate: FP16:
 # 167.47 MB + 0.88 MB); None where not captured for the current kernel.
 BJ_FINE_TRAFFIC_16_P4 = {"fp32": None, "h16": 168.35e6, "bf16": None}
+# The same for the P2 block-sparse product of the FP32 cycle (first P2 product of the profiled
+# solve, 16-bit blocks: 92.53 MB + 2.75 MB).
+BSR_L1_TRAFFIC_16_P4 = {"fp32": None, "h16": 95.27e6, "bf16": None}
 
 
 def hbm_peak():
@@ -761,7 +764,8 @@ def run_ours(args):
     storage = {"fp32": "float", "h16": "half", "bf16": "bfloat16"}.get(args.form)
     names = {"bj32_fine": "staged_jacobi_kernel<float, %s> (fine level)" % storage,
              "bj64_fine": "bj_update_kernel<double> (fine level)",
-             "bsr32_l1": "direct_apply_kernel<float, 7, %s> (P2 level)" % storage,
+             "bsr32_l1": ("direct_apply_kernel<float, 7, float> (P2 level)" if args.form == "fp32" else
+                          "direct7_vec_kernel<%s> (P2 level)" % storage),
              "bsr64_l1": "direct_apply_kernel<double, 7, double> (P2 level)",
              "face_tan32": "face_kernel<%d, tangent, float>" % k, "vol_tan32": "vol_kernel<%d, tangent, float>" % k,
              "face_tan": "face_kernel<%d, tangent, double>" % k, "vol_tan": "vol_kernel<%d, tangent, double>" % k}
@@ -788,6 +792,8 @@ def run_ours(args):
         ent.update({"kernel": names[nm], "ms_per_launch": t * 1e3, "launches": cnt, "total_ms": ms_k, "traffic": None})
         if nm == "bj32_fine" and args.config == CONFIG:
             ent["traffic"] = BJ_FINE_TRAFFIC_16_P4.get(args.form)
+        if nm == "bsr32_l1" and args.config == CONFIG:
+            ent["traffic"] = BSR_L1_TRAFFIC_16_P4.get(args.form)
         by_kernel[nm] = ent
     if by_kernel:
         top = max(by_kernel, key=lambda n: by_kernel[n]["total_ms"])
