@@ -159,6 +159,22 @@ int dg_level_size(const dg_handle* h, int lvl, int* nb, long long* n);
 /* Read and clear the device status word (DG_STATUS_* bits). Synchronises `stream`. */
 int dg_get_status(dg_handle* h, unsigned* status, void* stream);
 
+/* Test settings of the failure-detection paths. The production values are the defaults;
+ * a test changes one, makes the condition happen on the host side of the GPU (no fault, no
+ * trap, no endless wait), checks the status or the error code, and restores it.
+ *  - DG_KNOB_RIEMANN_ITS (default 60, 0..1000): iteration cap of the star-state solve of the
+ *    exact Riemann flux (Sec. 2.1). A face whose iteration does not meet its stopping test
+ *    within the cap sets DG_STATUS_RIEMANN; dg_set_linearization then returns DG_ERR_RIEMANN.
+ *  - DG_KNOB_WAIT_POLLS (default 0 = 2^22, 0..2^30): polls of each bounded wait of the FP32
+ *    cycle's staged block-Jacobi apply before it gives up (DG_STATUS_WAIT).
+ *  - DG_KNOB_WITHHOLD_COPY (default 0): != 0 makes that apply leave the first stage of every
+ *    CTA uncopied, so that its first wait runs out; the CTA then waits (with the full limit)
+ *    for its other copies in flight, sets DG_STATUS_WAIT and skips its work. */
+#define DG_KNOB_RIEMANN_ITS 1
+#define DG_KNOB_WAIT_POLLS 2
+#define DG_KNOB_WITHHOLD_COPY 3
+int dg_set_test_knob(dg_handle* h, int knob, long long value);
+
 /* ------------------------------------------------------------- operators */
 
 /* w <- L2 projection (Gauss rule) of the Taylor-Green vortex
@@ -178,12 +194,16 @@ int dg_project_points(dg_handle* h, const double* vals, double* w, void* stream)
  * terms with the BR2 corrected gradient grad u - R^K(u), face terms with the
  * exact artificial-compressibility Riemann flux and the BR2 viscous flux
  * F^nu({grad u - eta r^s([u])}) (Eq. (vflux), Sec. 2.1). Fine level. w and f
- * must not alias. */
+ * must not alias. Asynchronous: a non-finite output entry sets DG_STATUS_NONFINITE and a
+ * star-state iteration that missed its stopping test sets DG_STATUS_RIEMANN (dg_get_status). */
 int dg_residual(dg_handle* h, const double* w, double* f, void* stream);
 
 /* Fix the linearisation state of G: caches w, f_h(w), ||w||_2, the velocity
  * at the volume quadrature points and the Jacobian of the Riemann flux at the
- * face points, and sets 1/(gamma dt) (>= 0). Synchronises (reads ||w||). */
+ * face points, and sets 1/(gamma dt) (>= 0). Synchronises (reads ||w||). Returns
+ * DG_ERR_NONFINITE if w or f_h(w) has a non-finite entry and DG_ERR_RIEMANN if the star-state
+ * iteration missed its stopping test on some face; the handle is then not linearised, and the
+ * condition's bit is also left in the status word. */
 int dg_set_linearization(dg_handle* h, const double* w, double inv_gamma_dt, void* stream);
 
 /* dg_set_linearization that also writes the right-hand side of the stage started from w,
@@ -359,6 +379,10 @@ int dg_recorded(const dg_handle* h, int* count);
  *    before it is read). Calls that overlap on the GPU, from any handle or
  *    stream, race on it.
  *  - Every GPU that loads the library holds the array until the process exits.
+ *  - The handle's device (current at its dg_create) must be current at the call, else
+ *    DG_ERR_ARG; the address is looked up for that device.
+ *  - The looked-up address belongs to the device's context: after cudaDeviceReset (which also
+ *    frees every handle's buffers) the entry point must not be called again in this process.
  * The handle must come from dg_create as usual; w and f as for dg_residual. */
 #define DG_NOALLOC_SCRATCH_DOUBLES (1 << 20)
 int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
@@ -443,6 +467,10 @@ typedef struct dg_tuning {
   int vol_ctas_per_sm;   /* the same for the volume pass */
   int jacobi_stage_kb;   /* FP32 cycle: KB of element inverses per bulk-copy stage of the fine-level
                             block-Jacobi apply, 8..224 (96); capped by shared memory */
+  int jacobi_max_ctas;   /* cap on the CTAs of that apply, 0..4096 (0: no cap, one wave of the GPU). A
+                            small cap makes every CTA take many stages through its ring of stage
+                            buffers (the stage size then also shrinks to keep >= 2 stages per CTA);
+                            the autotuner leaves it as set */
 } dg_tuning;
 
 int dg_get_tuning(const dg_handle* h, int which, dg_tuning* t);

@@ -55,6 +55,8 @@ def lib():
             P = ctypes.POINTER(ctypes.c_double)
             M = ctypes.POINTER(_Mesh)
             L.orc_nb.restype = ctypes.c_int
+            L.orc_threads.restype = ctypes.c_int
+            L.orc_threads.argtypes = [ctypes.c_int]
             L.orc_p_wave1.restype = ctypes.c_double
             L.orc_p_wave3.restype = ctypes.c_double
             L.orc_tang1.restype = ctypes.c_double
@@ -89,6 +91,12 @@ def _p(a):
 def nb(k):
     """Number of modes of P^k in 3D, C(k+3, 3)."""
     return lib().orc_nb(k)
+
+
+def threads(n=0):
+    """Threads of the oracle's OpenMP loops over elements (n > 0 sets them); returns the count in
+    use. Results do not depend on it."""
+    return int(lib().orc_threads(int(n)))
 
 
 def modes(k):

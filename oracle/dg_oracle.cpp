@@ -16,7 +16,7 @@
 // (dual numbers), and the Riemann star state is found by bisection. No tables,
 // no sum factorisation, no fusion.
 //
-// Readings of the paper that this file fixes (also listed in the design doc):
+// Readings of the paper that this file fixes:
 //  * basis: normalised tensor Legendre polynomials of total degree <= k on each
 //    box, ordered by total degree, then first index descending, then second
 //    index descending (Sec. 2.4.1: hierarchical orthonormal modal basis);
@@ -39,6 +39,8 @@
 //    u* = f.n, so no mass crosses a wall; the jump is [u] = u_K - f; the lifting of
 //    a wall face lives on K alone, int_K r . tau = int_s [u] tau . n (the one-sided
 //    average), and the viscous flux is F^nu(grad u_K - eta r([u])).
+
+#include <omp.h>
 
 #include <cmath>
 #include <cstdio>
@@ -331,8 +333,6 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
   const int nb = D.nb, nq = D.nq, ne = D.ne;
   const double nu = D.nu, eta = D.eta;
   for (size_t i = 0; i < (size_t)ne * 4 * nb; ++i) f[i] = T(0.0);
-  std::vector<double> phiK(nb), phiP(nb);
-  std::vector<double> dK(3 * nb), dP(3 * nb);
   auto W = [&](int e, int v, int m) -> const T& { return w[((size_t)e * 4 + v) * nb + m]; };
   auto F = [&](int e, int v, int m) -> T& { return f[((size_t)e * 4 + v) * nb + m]; };
 
@@ -345,7 +345,10 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
   // lifting of the wall face at the - side (y = yn[0]) of K, on K
   std::vector<T> liftb((size_t)ne * 3 * nb, T(0.0));
   auto LIFTB = [&](int e, int a, int m) -> T& { return liftb[((size_t)e * 3 + a) * nb + m]; };
-  for (int K = 0; K < ne; ++K)
+  // (the faces (K, d) of different K write different coefficients: K runs in parallel)
+#pragma omp parallel for schedule(static)
+  for (int K = 0; K < ne; ++K) {
+    std::vector<double> phiK(nb), phiP(nb);
     for (int d = 0; d < 3; ++d) {
       int P = D.nbr(K, d, +1);
       int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -394,9 +397,14 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
           }
     }
 
+  }
+
   // 2. volume terms: - int_K Ftilde_{p,i}(w) d_p z_i with the BR2 corrected
-  //    gradient grad u - R^K(u), R^K = sum of the liftings of the faces of K.
+  //    gradient grad u - R^K(u), R^K = sum of the liftings of the faces of K
+  //    (each K writes only its own residual: K runs in parallel).
+#pragma omp parallel for schedule(static)
   for (int K = 0; K < ne; ++K) {
+    std::vector<double> phiK(nb), dK(3 * nb);
     double vq = D.vol(K) / 8.0;
     for (int q0 = 0; q0 < nq; ++q0)
       for (int q1 = 0; q1 < nq; ++q1)
@@ -447,7 +455,16 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
   // 3. face terms: + int_s n.(Fhat^c - Fhat^nu) [z] with the exact AC Riemann
   //    flux and Fhat^nu = F^nu({grad u - eta r^s([u])}); at a wall the ghost
   //    state (f, p_K) on the missing side and the one-sided Dirichlet flux.
-  for (int K = 0; K < ne; ++K)
+  //    (a) the weighted normal flux w_q n.(Fhat^c - Fhat^nu) at every point of
+  //        every face: the faces (K, d) of different K run in parallel;
+  //    (b) the integral against the test functions of the two sides, element by
+  //        element: + on K (the face's lower side), - on K' (its upper side).
+  const size_t nqf = (size_t)nq * nq;
+  std::vector<T> fl((size_t)ne * 3 * nqf * 4, T(0.0));   // [K][d][q1 q2][i], face (K, d)
+  std::vector<T> flb(D.wall_y ? (size_t)ne * nqf * 4 : 0, T(0.0));  // [K][q1 q2][i], wall face below K
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int K = 0; K < ne; ++K) {
+    std::vector<double> phiK(nb), phiP(nb), dK(3 * nb), dP(3 * nb);
     for (int d = 0; d < 3; ++d) {
       int P = D.nbr(K, d, +1);
       int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -503,11 +520,7 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
             fn[i] = fc[i] - fv;
           }
           fn[3] = fc[3];
-          for (int i = 0; i < 4; ++i)
-            for (int m = 0; m < nb; ++m) {
-              F(K, i, m) += wq * fn[i] * phiK[m];
-              if (P >= 0) F(P, i, m) -= wq * fn[i] * phiP[m];
-            }
+          for (int i = 0; i < 4; ++i) fl[(((size_t)K * 3 + d) * nqf + q1 * nq + q2) * 4 + i] = wq * fn[i];
         }
       // the wall face below K: the ghost state on the - side, K on the + side
       if (d == 1 && D.nbr(K, 1, -1) < 0)
@@ -545,10 +558,36 @@ template <class T> static void residual(const Disc& D, const T* w, T* f) {
               fn[i] = fc[i] - fv;
             }
             fn[3] = fc[3];
-            for (int i = 0; i < 4; ++i)
-              for (int m = 0; m < nb; ++m) F(K, i, m) -= wq * fn[i] * phiK[m];
+            for (int i = 0; i < 4; ++i) flb[((size_t)K * nqf + q1 * nq + q2) * 4 + i] = wq * fn[i];
           }
     }
+  }
+#pragma omp parallel for schedule(static)
+  for (int E = 0; E < ne; ++E) {
+    std::vector<double> phi(nb);
+    for (int d = 0; d < 3; ++d) {
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      const int Km = D.nbr(E, d, -1);  // the element below E's lower face (-1: a wall)
+      for (int side = 0; side < 2; ++side) {  // 0: E is K of its face (E, d); 1: E is K' of (Km, d)
+        const T* src = side == 0 ? &fl[(size_t)E * 3 * nqf * 4 + (size_t)d * nqf * 4]
+                       : Km >= 0 ? &fl[(size_t)Km * 3 * nqf * 4 + (size_t)d * nqf * 4]
+                                 : (d == 1 ? &flb[(size_t)E * nqf * 4] : nullptr);
+        if (!src) continue;
+        const double sgn = side == 0 ? 1.0 : -1.0;
+        for (int q1 = 0; q1 < nq; ++q1)
+          for (int q2 = 0; q2 < nq; ++q2) {
+            double xi[3];
+            xi[d] = side == 0 ? 1.0 : -1.0;
+            xi[t1] = D.gx[q1];
+            xi[t2] = D.gx[q2];
+            D.eval(E, xi, phi.data(), nullptr);
+            const T* fq = src + (size_t)(q1 * nq + q2) * 4;
+            for (int i = 0; i < 4; ++i)
+              for (int m = 0; m < nb; ++m) F(E, i, m) += sgn * fq[i] * phi[m];
+          }
+      }
+    }
+  }
 }
 
 // Taylor-Green initial field on [0,2pi]^3 (U0 = L = 1).
@@ -566,6 +605,13 @@ using namespace orc;
 extern "C" {
 
 int orc_nb(int k) { return (int)modes(k).size(); }
+
+// Threads of the OpenMP loops over elements (n > 0 sets them); returns the number in use.
+// Every result is the same for any thread count: each loop iteration writes its own entries.
+int orc_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+}
 
 void orc_modes(int k, int* out) {
   auto m = modes(k);
@@ -714,10 +760,12 @@ void orc_jvp_fd(const orc_mesh* m, const double* w, const double* v, double inv_
   }
 }
 
-// Dense G (row-major, G[row * n + col]) by columns of the exact Jacobian action.
+// Dense G (row-major, G[row * n + col]) by columns of the exact Jacobian action
+// (the columns in parallel; each residual inside runs on its one thread).
 void orc_dense_G(const orc_mesh* m, const double* w, double inv_gdt, double* G) {
   Disc D(m);
   long n = (long)D.ne * 4 * D.nb;
+  omp_set_max_active_levels(1);
 #pragma omp parallel for schedule(dynamic)
   for (long col = 0; col < n; ++col) {
     std::vector<Dual> wd(n), fd(n);

@@ -37,6 +37,9 @@ DG_COARSE_GMRES = 1
 DG_COARSE_LEARNED = 2
 DG_COARSE_LEARNED_ITER = 3
 DG_STATUS_WAIT = 4
+DG_KNOB_RIEMANN_ITS = 1
+DG_KNOB_WAIT_POLLS = 2
+DG_KNOB_WITHHOLD_COPY = 3
 DG_MAX_LEVELS = 4
 DG_SMOOTH_MAX_ITS = 32
 DG_MLP_IN = 112
@@ -55,7 +58,8 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_reuse_assembly", "dg_set_linearization_rhs", "dg_set_stb_rescaling",
            "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
            "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy",
-           "dg_get_tuning", "dg_set_tuning", "dg_autotune", "dg_quad_points", "dg_project_points")
+           "dg_get_tuning", "dg_set_tuning", "dg_autotune", "dg_quad_points", "dg_project_points",
+           "dg_set_test_knob")
 DG_WALLS_NONE = 0
 DG_WALLS_Y = 1
 DG_TUNE_FP64 = 0
@@ -84,7 +88,7 @@ class DgSolveOpts(ctypes.Structure):
 
 class DgTuning(ctypes.Structure):
     _fields_ = [("face_warps", ctypes.c_int), ("vol_threads", ctypes.c_int), ("face_ctas_per_sm", ctypes.c_int),
-                ("vol_ctas_per_sm", ctypes.c_int), ("jacobi_stage_kb", ctypes.c_int)]
+                ("vol_ctas_per_sm", ctypes.c_int), ("jacobi_stage_kb", ctypes.c_int), ("jacobi_max_ctas", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -166,6 +170,7 @@ def load(path=None):
     L.dg_get_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
     L.dg_set_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
     L.dg_autotune.argtypes = [vp, i, i, ctypes.POINTER(d), vp]
+    L.dg_set_test_knob.argtypes = [vp, i, ctypes.c_longlong]
     for name in EXPORTS:
         if name not in ("dg_last_error", "dg_plan_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -359,6 +364,9 @@ class DG:
         keys = ("face_default_ms", "face_chosen_ms", "vol_default_ms", "vol_chosen_ms", "jacobi_default_ms",
                 "jacobi_chosen_ms")
         return dict(zip(keys, list(rep)))
+
+    def dg_set_test_knob(self, knob, value):
+        self._chk(self._L.dg_set_test_knob(self.h, int(knob), int(value)))
 
     def dg_get_status(self, stream=None):
         s = ctypes.c_uint()

@@ -196,6 +196,8 @@ static int build_tables(Handle* h, int k) {
   return DG_OK;
 }
 
+__global__ void or_status_kernel(unsigned* status, unsigned bits) { atomicOr(status, bits); }
+
 template <class T>
 static int dalloc(Handle* h, T** p, size_t count) {
   DG_CUDA(h, cudaMalloc((void**)p, sizeof(T) * (count ? count : 1)));
@@ -317,6 +319,7 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
   h->nlev = p->nlevels;
   int dev = 0;
   DG_CUDA(h, cudaGetDevice(&dev));
+  h->device = dev;
   DG_CUDA(h, cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
   int rc;
   if (h->nprob == 1)
@@ -399,7 +402,7 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
       (rc = dalloc(h, &h->wlin, n0)) || (rc = dalloc(h, &h->flin, n0)) || (rc = dalloc(h, &h->fd_w, n0)) ||
       (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
       (rc = dalloc(h, &h->dFlux, (size_t)(3 * ne + h->nbf) * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
-      (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 1)))
+      (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 2)))
     return rc;
   if ((rc = dalloc(h, &h->face_out_f, (size_t)ne * 6 * 4 * n2f)) ||
       (rc = dalloc(h, &h->face_lift_f, (size_t)ne * 6 * 3 * n2f)) ||
@@ -525,6 +528,25 @@ int dg_level_size(const dg_handle* hh, int lvl, int* nb, long long* n) {
   return DG_OK;
 }
 
+int dg_set_test_knob(dg_handle* hh, int knob, long long value) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  switch (knob) {
+    case DG_KNOB_RIEMANN_ITS:
+      if (value < 0 || value > 1000) return fail(h, DG_ERR_ARG, "Riemann iteration cap: 0..1000");
+      h->dbg.riemann_its = (int)value;
+      return DG_OK;
+    case DG_KNOB_WAIT_POLLS:
+      if (value < 0 || value > (1ll << 30)) return fail(h, DG_ERR_ARG, "wait polls: 0..2^30");
+      h->dbg.wait_polls = (int)value;
+      return DG_OK;
+    case DG_KNOB_WITHHOLD_COPY:
+      h->dbg.withhold_copy = value != 0;
+      return DG_OK;
+  }
+  return fail(h, DG_ERR_ARG, "unknown test knob");
+}
+
 int dg_get_status(dg_handle* hh, unsigned* status, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !status) return DG_ERR_ARG;
@@ -568,13 +590,27 @@ int dg_set_linearization(dg_handle* hh, const double* w, double inv_gamma_dt, vo
   const long long n0 = h->lev[0].n;
   DG_CUDA(h, cudaMemcpyAsync(h->wlin, w, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
   h->inv_gdt = inv_gamma_dt;
-  int rc = op_residual(h, h->wlin, h->flin, true, st);
+  h->linearized = false;
+  DG_CUDA(h, cudaMemsetAsync(h->status + 1, 0, sizeof(unsigned), st));
+  int rc = op_residual(h, h->wlin, h->flin, true, st);  // records its conditions in status[1]
   if (rc) return rc;
   if ((rc = vec_norm2(h, h->wlin, n0, h->wnorm2, st))) return rc;
+  unsigned s = 0;
+  double wn2 = 0.0;
+  DG_CUDA(h, cudaMemcpyAsync(&s, h->status + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(h, cudaMemcpyAsync(&wn2, h->wnorm2, sizeof(double), cudaMemcpyDeviceToHost, st));
   DG_CUDA(h, cudaStreamSynchronize(st));
-  h->linearized = true;
+  if (!std::isfinite(wn2)) s |= DG_STATUS_NONFINITE;
+  if (s) {  // keep the conditions for dg_get_status as well
+    or_status_kernel<<<1, 1, 0, st>>>(h->status, s);
+    DG_LAUNCH_CHECK(h);
+  }
   h->assembled = false;
   h->lin_f_ready = false;
+  if (s & DG_STATUS_NONFINITE) return fail(h, DG_ERR_NONFINITE, "non-finite state or residual at the linearisation");
+  if (s & DG_STATUS_RIEMANN)
+    return fail(h, DG_ERR_RIEMANN, "the star-state iteration of the Riemann solver did not converge on some face");
+  h->linearized = true;
   return DG_OK;
 }
 

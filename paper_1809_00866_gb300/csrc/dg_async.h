@@ -25,9 +25,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-// bounded wait for the phase with parity `parity` of the barrier; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < kBulkWaitLimit; ++it) {
+// Order this thread's earlier generic-proxy accesses of shared memory (ordinary loads and
+// stores) before later async-proxy accesses of it (a bulk copy that overwrites the same bytes).
+// Every thread that wrote a buffer executes it before the barrier after which one thread
+// issues a bulk copy into that buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bounded wait for the phase with parity `parity` of the barrier (at most `limit` polls);
+// false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = kBulkWaitLimit) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
                                                                        const S* __restrict__ A,
                                                                        const R* __restrict__ g,
                                                                        const R* __restrict__ Gx, R alpha, int x_zero,
-                                                                       R* __restrict__ x, unsigned* status) {
+                                                                       R* __restrict__ x, unsigned* status,
+                                                                       unsigned wait_polls, int withhold_first) {
   extern __shared__ __align__(128) unsigned char sraw_[];
   __shared__ uint64_t bar[kJacobiSlots];
   __shared__ R red[2 * kJacobiThreads];  // partial sums of the column slices
@@ -346,29 +347,43 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
     if (Gx) bulk_g2s(v + vec, Gx + (size_t)e0 * b, vb, &bar[slot]);
     if (!x_zero) bulk_g2s(v + 2 * vec, x + (size_t)e0 * b, vb, &bar[slot]);
   };
-  // iteration k of this CTA handles stage blockIdx.x + k * gridDim.x in slot k % ns (use k / ns)
+  // iteration k of this CTA handles stage blockIdx.x + k * gridDim.x in slot k % ns (use k / ns).
+  // Thread 0 keeps a bit per slot whose copies are in flight. withhold_first != 0 (a test of the
+  // bounded wait) leaves the first stage's copies unissued, so its barrier phase never completes.
+  unsigned inflight = 0;
   if (tid == 0)
     for (int i = 0; i < ns - 1; ++i) {
       const int st0 = blockIdx.x + i * gridDim.x;
-      if (st0 < nstages) issue(st0, i);
+      if (st0 < nstages && !(withhold_first && i == 0)) {
+        issue(st0, i);
+        inflight |= 1u << i;
+      }
     }
   int k = 0;
   for (int stg = blockIdx.x; stg < nstages; stg += gridDim.x, ++k) {
     const int slot = k % ns;
     const int ahead = stg + (ns - 1) * gridDim.x;  // into the slot released at the end of k - 1
-    if (tid == 0 && ahead < nstages) issue(ahead, (k + ns - 1) % ns);
+    if (tid == 0 && ahead < nstages) {
+      issue(ahead, (k + ns - 1) % ns);
+      inflight |= 1u << ((k + ns - 1) % ns);
+    }
     const int e0 = stg * G;
     const int cnt = min(G, ne - e0);
-    const bool got = mbar_wait(&bar[slot], (unsigned)((k / ns) & 1));
+    const bool got = mbar_wait(&bar[slot], (unsigned)((k / ns) & 1), wait_polls);
     if (!__syncthreads_and(got)) {
-      // give up: report, let the copies in flight land (bounded waits), leave
+      // give up: report, let every copy in flight land (the current slot's included; bounded
+      // waits with the full limit), then leave, so that no copy writes this CTA's shared memory
+      // after it exits
       if (tid == 0) {
         atomicOr(status, (unsigned)DG_STATUS_WAIT);
-        for (int i = 1; i < ns; ++i)
-          if (stg + i * gridDim.x < nstages) mbar_wait(&bar[(k + i) % ns], (unsigned)(((k + i) / ns) & 1));
+        for (int i = 0; i < ns; ++i) {
+          const int sl = (k + i) % ns;
+          if (inflight & (1u << sl)) mbar_wait(&bar[sl], (unsigned)(((k + i) / ns) & 1));
+        }
       }
       return;
     }
+    if (tid == 0) inflight &= ~(1u << slot);
     const S* Ab = blocks_of(slot);
     R* const rv = vecs_of(slot);  // g, turned into the residual g - Gx in place
     const R* const xo = rv + 2 * vec;
@@ -426,7 +441,10 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
         xe[1] = (x_zero ? R(0) : xs[1]) + alpha * a1;
       }
     }
-    __syncthreads();  // this slot, its residual and red are free for the copy issued next
+    // this slot, its residual and red are free for the copy issued next: the generic-proxy
+    // writes above (the residual formed in place) are ordered before that async-proxy copy
+    fence_proxy_async_smem();
+    __syncthreads();
   }
 }
 
@@ -597,7 +615,10 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   int G = (int)std::max<size_t>(1, target / per);
   const size_t per_slot = per + 3 * (size_t)b * sizeof(R);  // one buffer: block + g, Gx, x slices
   G = std::min(G, (int)std::max<size_t>(1, kSmemLimit / (2 * per_slot)));  // two buffers fit
-  G = std::max(1, std::min(G, (h->ne + 2 * h->nsm - 1) / (2 * h->nsm)));  // >= 2 stages per SM when possible
+  // at most this many CTAs (jacobi_max_ctas, 0: no cap; every CTA then walks the ring more often)
+  const int cap = h->tune[1].jacobi_max_ctas;
+  const int ctas = cap > 0 ? std::min(cap, h->nsm) : h->nsm;
+  G = std::max(1, std::min(G, (h->ne + 2 * ctas - 1) / (2 * ctas)));  // >= 2 stages per CTA when possible
   // as many buffers as fit (2..4): the stages in flight while one is multiplied
   const int ns = (int)std::max<size_t>(2, std::min<size_t>(kJacobiSlots, kSmemLimit / ((size_t)G * per_slot)));
   const size_t smem = (size_t)ns * G * per_slot;
@@ -612,9 +633,10 @@ int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, 
   }
   const int nstages = (h->ne + G - 1) / G;
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
-  const int grid = std::min(nstages, h->nsm * per_sm);
+  const int grid = std::min(nstages, cap > 0 ? ctas : h->nsm * per_sm);
+  const unsigned polls = h->dbg.wait_polls > 0 ? (unsigned)h->dbg.wait_polls : kBulkWaitLimit;
   staged_jacobi_kernel<R, S><<<grid, kJacobiThreads, smem, st>>>(h->ne, b, G, ns, A, g, Gx, alpha, x_zero, x,
-                                                                h->status);
+                                                                h->status, polls, h->dbg.withhold_copy);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }

@@ -92,11 +92,21 @@ struct OpTune {
   int face_per_sm = 0;        // cap on CTAs per SM (0: shared memory decides)
   int vol_per_sm = 0;
   int jacobi_stage_kb = 96;   // element blocks staged per bulk copy of the block-Jacobi apply (KB)
+  int jacobi_max_ctas = 0;    // cap on the CTAs of that apply (0: one wave of the GPU)
+};
+
+// Test settings of the failure-detection paths (dg_set_test_knob); the defaults are the
+// production values.
+struct DebugKnobs {
+  int riemann_its = 60;   // iteration cap of the star-state solve (Newton with bisection safeguard)
+  int wait_polls = 0;     // polls of the staged block-Jacobi apply's bounded waits (0: kBulkWaitLimit)
+  int withhold_copy = 0;  // != 0: that apply leaves each CTA's first stage uncopied (its wait gives up)
 };
 
 struct Handle {
   dg_params p{};
   OpTune tune[2];               // [0] FP64 products, [1] FP32 products (and the FP32 block-Jacobi apply)
+  DebugKnobs dbg;
   int n[3] = {0, 0, 0};
   int ne = 0;
   int nlev = 0;
@@ -128,6 +138,7 @@ struct Handle {
   TablesF tabf;                 // their FP32 copies
   Level lev[DG_MAX_LEVELS];
   int nsm = 0;
+  int device = 0;               // the CUDA device that was current at dg_create (holds every buffer)
 
   // scratch of the matrix-free operator
   double* face_out = nullptr;  // [ne][6][4][n2] face-term contributions per element face slot (2D modes)

@@ -265,7 +265,13 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_forward_kernel(const unsigned
     }
   }
   if (!mbar_wait(&bar, 0)) {
-    if (lane == 0) atomicOr(status, DG_STATUS_WAIT);
+    // give up: report, and let the weights' copy land (a second bounded wait) before leaving,
+    // so that it cannot write this CTA's shared memory after the CTA exits
+    if (lane == 0) {
+      atomicOr(status, DG_STATUS_WAIT);
+      mbar_wait(&bar, 0);
+    }
+    __syncwarp();
     return;
   }
   float acc[16][4], out[2][4];
@@ -409,7 +415,11 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_grad_kernel(const unsigned ch
   if (!ok) ok_all = 0;
   __syncthreads();
   if (!ok_all) {
-    if (threadIdx.x == 0) atomicOr(status, DG_STATUS_WAIT);
+    if (threadIdx.x == 0) {  // report; the copy in flight lands before the CTA leaves
+      atomicOr(status, DG_STATUS_WAIT);
+      mbar_wait(&bar, 0);
+    }
+    __syncthreads();
     return;
   }
   // XT (after the weights landed: the bulk copy only writes the network region)

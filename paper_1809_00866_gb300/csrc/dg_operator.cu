@@ -77,6 +77,7 @@ struct OpArgsT {
   R* dFlux;
   double nu, c, eta, inv_gdt;
   unsigned* status;
+  int riemann_its;  // iteration cap of the star-state solve
 };
 using OpArgs = OpArgsT<double>;
 
@@ -170,7 +171,7 @@ __device__ __forceinline__ void tang3(double u, double a, double uR, double aR, 
 // rounding band of zero. With J != nullptr also the Jacobian J[i][j] with respect
 // to (uL[0..2], pL, uR[0..2], pR).
 __device__ void ac_riemann(const double* uL, double pL, const double* uR, double pR, int d, double c, double* F,
-                           double (*J)[8], unsigned* status) {
+                           double (*J)[8], unsigned* status, int max_its) {
   const double ul = uL[d], ur = uR[d], c2 = c * c;
   const double al = sqrt(ul * ul + c2), ar = sqrt(ur * ur + c2);
   const double Al = asinh(ul / c), Ar = asinh(ur / c);
@@ -190,7 +191,7 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
   double lo = -1e300, hi = 1e300;
   bool ok = false;
   double p1, d1u, d1l, p3, d3u, d3r, as, As;
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < max_its; ++it) {
     at_star(us, as, As);
     wave1(us, as, As, ul, al, Al, pL, c, p1, d1u, d1l);
     wave3(us, as, As, ur, ar, Ar, pR, c, p3, d3u, d3r);
@@ -454,14 +455,14 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         }
       } else if constexpr (MODE == MODE_RES_LIN) {
         double Jm[4][8];  // residual modes run in FP64 only
-        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, Jm, a.status);
+        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, Jm, a.status, a.riemann_its);
         R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) Jq[i * 8 + j] = Jm[i][j];
       } else if constexpr (MODE == MODE_RES) {
-        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status);
+        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status, a.riemann_its);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) sF[i * NQF + q] = Fc[i] * W2[q];
@@ -625,6 +626,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   for (int pa = 0; pa < K1; ++pa)
 #pragma unroll
     for (int q = 0; q < N1; ++q) Lr[pa][q] = L1[pa * N1 + q];
+  bool nonfinite = false;
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
     const R is = R(g.is);
@@ -909,6 +911,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (MODE == MODE_TAN && i < 3) acc[i] += R(a.inv_gdt * g.sh) * sC[i * NB + m];
+          nonfinite |= !isfinite(acc[i]);
           a.out[(size_t)e * 4 * NB + i * NB + m] = acc[i];
         }
       }
@@ -940,11 +943,15 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
           acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
         }
         if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt * g.sh) * sC[t];
+        nonfinite |= !isfinite(acc);
         a.out[(size_t)e * 4 * NB + t] = acc;
       }
     }
     __syncthreads();
   }
+  // scan of the outputs: a non-finite entry (from a non-finite input or an overflow) sets the
+  // status bit, once per thread that wrote one
+  if (nonfinite && a.status) atomicOr(a.status, (unsigned)DG_STATUS_NONFINITE);
 }
 
 // ------------------------------------------------------- Taylor-Green vortex
@@ -1052,6 +1059,7 @@ static OpArgs make_args(Handle* h, const double* in, double* out) {
   a.eta = h->p.eta;
   a.inv_gdt = h->inv_gdt;
   a.status = h->status;
+  a.riemann_its = h->dbg.riemann_its;
   return a;
 }
 
@@ -1072,6 +1080,7 @@ static OpArgsT<float> make_args_f(Handle* h, const float* in, float* out) {
   a.eta = h->p.eta;
   a.inv_gdt = h->inv_gdt;
   a.status = h->status;
+  a.riemann_its = h->dbg.riemann_its;
   return a;
 }
 
@@ -1142,6 +1151,7 @@ static int dispatch(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
 
 int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStream_t st) {
   OpArgs a = make_args(h, w, f);
+  if (store_lin) a.status = h->status + 1;  // the linearisation's own word, read by dg_set_linearization
   return store_lin ? dispatch<MODE_RES_LIN>(h, a, st) : dispatch<MODE_RES>(h, a, st);
 }
 
@@ -1222,14 +1232,18 @@ int op_project_tgv(Handle* h, double* w, cudaStream_t st) {
 // loads the library holds it until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[DG_NOALLOC_SCRATCH_DOUBLES];
 
-// Device address of g_noalloc_scratch on the current device, looked up once per
-// device. In host code the array's name is only a host-side stand-in, never a
-// device address, so it must not be passed to a kernel.
+// Device address of g_noalloc_scratch on the handle's device, looked up once per device with
+// that device current (the caller's device must be the handle's). In host code the array's name
+// is only a host-side stand-in, never a device address, so it must not be passed to a kernel.
 static int noalloc_scratch(Handle* h, double** out) {
   static std::mutex mu;
   static double* addr[64] = {};
-  int dev = 0;
-  DG_CUDA(h, cudaGetDevice(&dev));
+  const int dev = h->device;
+  int cur = -1;
+  DG_CUDA(h, cudaGetDevice(&cur));
+  if (cur != dev)
+    return fail(h, DG_ERR_ARG, "dg_residual_noalloc: make the handle's device (" + std::to_string(dev) +
+                                   ") current; device " + std::to_string(cur) + " is");
   if (dev < 0 || dev >= 64) return fail(h, DG_ERR_ARG, "device index out of range for the static scratch");
   std::lock_guard<std::mutex> lock(mu);
   if (!addr[dev]) {

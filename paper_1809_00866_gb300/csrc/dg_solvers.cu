@@ -815,6 +815,7 @@ static int fgmres(Handle* h, const double* g, double* x, const dg_solve_opts& o,
   }
   double beta0;
   if ((rc = norm(r, &beta0))) return rc;
+  if (!std::isfinite(beta0)) return fail(h, DG_ERR_NONFINITE, "non-finite right-hand side or initial residual");
   int its = 0;
   const int limit = o.fixed_its > 0 ? o.fixed_its : o.maxit;
   double est = beta0;

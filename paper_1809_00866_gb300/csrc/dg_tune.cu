@@ -36,7 +36,8 @@ static int valid(const dg_tuning* t) {
   return t && (t->face_warps == 2 || t->face_warps == 4 || t->face_warps == 8) &&
          (t->vol_threads == 64 || t->vol_threads == 128 || t->vol_threads == 256) && t->face_ctas_per_sm >= 0 &&
          t->face_ctas_per_sm <= 32 && t->vol_ctas_per_sm >= 0 && t->vol_ctas_per_sm <= 32 &&
-         t->jacobi_stage_kb >= 8 && t->jacobi_stage_kb <= 224;
+         t->jacobi_stage_kb >= 8 && t->jacobi_stage_kb <= 224 && t->jacobi_max_ctas >= 0 &&
+         t->jacobi_max_ctas <= 4096;
 }
 
 static OpTune from_abi(const dg_tuning& t) {
@@ -46,6 +47,7 @@ static OpTune from_abi(const dg_tuning& t) {
   o.face_per_sm = t.face_ctas_per_sm;
   o.vol_per_sm = t.vol_ctas_per_sm;
   o.jacobi_stage_kb = t.jacobi_stage_kb;
+  o.jacobi_max_ctas = t.jacobi_max_ctas;
   return o;
 }
 
@@ -56,6 +58,7 @@ static dg_tuning to_abi(const OpTune& o) {
   t.face_ctas_per_sm = o.face_per_sm;
   t.vol_ctas_per_sm = o.vol_per_sm;
   t.jacobi_stage_kb = o.jacobi_stage_kb;
+  t.jacobi_max_ctas = o.jacobi_max_ctas;
   return t;
 }
 

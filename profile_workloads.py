@@ -1,19 +1,22 @@
 """Small, fixed workloads for profiling the library's kernels (e.g. under Nsight Compute).
 
-    python -m paper_1809_00866_gb300.profile jv [--n 16] [--reps 3]
+    python profile_workloads.py jv [--n 16] [--reps 3]
         TGV n^3 P4 handle (levels 4-2-1), linearisation at the TGV field, `reps` exact
         Jacobian actions (face_kernel + vol_kernel per action).
-    python -m paper_1809_00866_gb300.profile assemble [--n 16] [--form fp32|fp64]
+    python profile_workloads.py assemble [--n 16] [--form fp32|fp64]
         one preconditioner assembly after a warm-up one, between cudaProfilerStart/Stop.
-    python -m paper_1809_00866_gb300.profile stage [--n 16] [--form fp32|fp64|h16|bf16] [--learned]
+    python profile_workloads.py stage [--n 16] [--form fp32|fp64|h16|bf16] [--learned]
         one implicit stage to rel-res 1e-8 after two warm-up solves; only the timed FGMRES solve
         lies between cudaProfilerStart and cudaProfilerStop (ncu --profile-from-start off).
 
 Prints the wall time of the profiled region. Inputs are the synthetic Taylor-Green states.
 """
 import argparse
+import os
 import sys
 import time
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main(argv=None):
@@ -31,9 +34,9 @@ def main(argv=None):
     import torch
 
     import synthetic as S
-
-    from . import (DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP32_BF16, DG_PRECOND_FP32_H16,
-                   DG_PRECOND_FP64, DG_TUNE_FP32, DG_TUNE_FP64, build, solve_opts)
+    from paper_1809_00866_gb300 import (DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP32_BF16,
+                                        DG_PRECOND_FP32_H16, DG_PRECOND_FP64, DG_TUNE_FP32, DG_TUNE_FP64, build,
+                                        solve_opts)
     build()
     un = S.uniform_nodes(a.n)
     levels = [4, 2, 1]
@@ -76,7 +79,7 @@ def main(argv=None):
     o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.95 if low else 1.0, pre_sweeps=4 if low else 2,
                    post_sweeps=4 if low else 2, coarse_sweeps=2, precision=prec)
     if a.learned:
-        from . import learned as Lrn
+        from paper_1809_00866_gb300 import learned as Lrn
         states = [w.clone()]
         for _ in range(3):
             g = dg.empty()

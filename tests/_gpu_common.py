@@ -48,3 +48,10 @@ def meshes():
         "box233": (p(2, seed=1), p(3, seed=2), p(3, seed=3)),
         "box345": (p(3, seed=4), p(4, seed=5), p(5, seed=6)),
     }
+
+
+def maxrel(a, b):
+    """Element-wise difference relative to the largest entry: max |a - b| / max |b|."""
+    a, b = np.asarray(a).reshape(-1), np.asarray(b).reshape(-1)
+    mb = np.abs(b).max()
+    return float(np.abs(a - b).max() / (mb if mb > 0 else 1.0))

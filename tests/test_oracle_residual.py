@@ -261,3 +261,21 @@ def test_tgv_projection_and_kinetic_energy():
         phi /= math.sqrt(h ** 3 / 8)
         ref = np.einsum("q,vq,qm->vm", wr * h ** 3 / 8, tg, phi)
         np.testing.assert_allclose(w[e], ref, atol=1e-14)
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    # the OpenMP loops over elements write disjoint entries in a fixed order: the residual and the
+    # exact Jacobian action are bitwise the same on one thread and on all of them
+    xn, yn, zn = S.perturbed_nodes(3, seed=2), S.uniform_nodes(4), S.perturbed_nodes(3, seed=5)
+    m = O.Mesh(xn, yn, zn, 3, S.NU_TGV, S.AC_C, S.ETA)
+    w = O.project_tgv(m) + S.perturbation(m.ne, 3, 0.3, 4)
+    v = S.direction(m.ne, 3, 6)
+    n0 = O.threads()
+    try:
+        O.threads(1)
+        f1, j1 = O.residual(m, w), O.jvp(m, w, v, 0.7)
+        O.threads(max(2, n0))
+        f2, j2 = O.residual(m, w), O.jvp(m, w, v, 0.7)
+    finally:
+        O.threads(n0)
+    assert np.array_equal(f1, f2) and np.array_equal(j1, j2)

@@ -26,18 +26,32 @@ def _noalloc(dg, w, f):
                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
+def _free_bytes():
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
 @pytest.mark.parametrize("name,k", [("box345", 3), ("u4", 4)])
 def test_noalloc_residual_matches_dg_residual_twice(name, k):
     import paper_1809_00866_gb300 as P
     dg, m = pair(*meshes()[name], [k])
     outs = []
     for seed in (1, 2):  # two calls in a row with different states
-        w = dev(O.project_tgv(m) + S.perturbation(m.ne, k, 0.3, seed))
+        wh = O.project_tgv(m) + S.perturbation(m.ne, k, 0.3, seed)
+        w = dev(wh)
         ref = dg.empty()
-        dg.dg_residual(w, ref)
+        dg.dg_residual(w, ref)  # the existing entry point (its kernels' module is loaded by now)
         got = dg.empty().fill_(np.nan)
+        free0 = _free_bytes()
         assert _noalloc(dg, w, got) == P.DG_OK
+        # the call allocated nothing: the device's free memory is unchanged across it
+        assert _free_bytes() == free0
         assert rel(host(got), host(ref)) < 1e-12
+        # and both equal the oracle's residual, element by element as well as in norm
+        orc = O.residual(m, wh)
+        assert rel(host(got), orc) < 1e-12
+        assert np.abs(host(got) - orc).max() <= 1e-12 * np.abs(orc).max()
         outs.append(host(got))
     assert rel(outs[0], outs[1]) > 1e-6  # the second call really recomputed
     assert dg.dg_get_status() == 0
