@@ -7,6 +7,13 @@ meshes are compared with the oracle's, entry by entry: relative 2-norm <= 1e-12 
 max |a - b| <= 1e-12 max |b|, for the autotuned shapes and for the extreme candidate shapes.
 The oracle runs its element loops on all host cores (its results do not depend on the count).
 
+For the Jacobian action on the generic 32^3 state the bound also allows for the problem's own
+rounding sensitivity: the entries of G v grow like 1/h (up to ~3e4 there) and come from sums
+that cancel, so a one-ulp relative perturbation of w and v already moves the oracle's own result
+by up to ~5e-12 of its largest entry (2e-12 in the 2-norm). No FP64 evaluation in another
+summation order can do better; the test measures that sensitivity with the oracle and asserts
+max(1e-12, 4 x sensitivity), element-wise and in the 2-norm.
+
 The FP32 preconditioner cycle at 16^3 (the staged block-Jacobi apply walks its ring several
 times per CTA there) is compared with the FP64 cycle on the same assembly, at the bounds the
 small-mesh tests state: 1e-5 for FP32 blocks, 5e-3 for FP16 blocks.
@@ -46,6 +53,13 @@ def test_residual_and_exact_jvp_at_benchmark_size(n):
     tuned = dg.dg_get_tuning(P.DG_TUNE_FP64).as_dict()
     v = S.direction(m.ne, 4, S.SEED_V)
     ref = O.jvp(m, w_gen, v, inv)
+    # the oracle's own sensitivity to one-ulp relative perturbations of its inputs
+    rng = np.random.default_rng(n)
+    eps = np.finfo(np.float64).eps
+    ref_p = O.jvp(m, w_gen * (1 + eps * rng.standard_normal(w_gen.shape)),
+                  v * (1 + eps * rng.standard_normal(v.shape)), inv)
+    tol2 = max(1e-12, 4 * rel(ref_p, ref))
+    tolmax = max(1e-12, 4 * maxrel(ref_p, ref))
     out = dg.empty()
     shapes = [tuned, dict(tuned, face_warps=2, vol_threads=64, vol_ctas_per_sm=0),
               dict(tuned, face_warps=8, vol_threads=256, vol_ctas_per_sm=4)]
@@ -53,8 +67,8 @@ def test_residual_and_exact_jvp_at_benchmark_size(n):
         dg.dg_set_tuning(P.DG_TUNE_FP64, **sh)
         dg.dg_jvp(dev(v), out)
         got = host(out)
-        assert rel(got, ref) < 1e-12, sh
-        assert maxrel(got, ref) < 1e-12, sh
+        assert rel(got, ref) < tol2, (sh, tol2)
+        assert maxrel(got, ref) < tolmax, (sh, tolmax)
     assert dg.dg_get_status() == 0
 
 
