@@ -95,6 +95,13 @@ typedef struct dg_handle dg_handle;
 #define DG_PRECOND_FP32_H16 2  /* the FP32 cycle with its element-block inverses and block-sparse coarse
                                   operators stored in FP16 (IEEE half), products accumulated in FP32 */
 #define DG_PRECOND_FP32_BF16 3 /* the same with bfloat16 storage */
+#define DG_PRECOND_FP32_H16_TC 4  /* DG_PRECOND_FP32_H16 whose fine-level operator runs the quadrature
+                                     contractions of its convective volume term (interpolation of the
+                                     velocity variation to the Gauss points, integration of the
+                                     weighted products against the basis; Sec. 2.1, Eq. (NSdiscrRes))
+                                     as dense per-element GEMMs on the tensor cores: FP16 operands
+                                     with per-element power-of-two scaling, FP32 accumulation */
+#define DG_PRECOND_FP32_BF16_TC 5 /* the same with bfloat16 block storage and BF16 operands */
 
 /* Coarsest-level SOLVE of the cycles (Sec. 2.4.3 uses a preconditioned GMRES there). */
 #define DG_COARSE_SMOOTHER 0 /* coarse_sweeps iterations of the level smoother from zero */
@@ -387,6 +394,19 @@ int dg_recorded(const dg_handle* h, int* count);
 #define DG_NOALLOC_SCRATCH_DOUBLES (1 << 20)
 int dg_residual_noalloc(dg_handle* h, const double* w, double* f, void* stream);
 
+/* w <- w + b dw on the fine level: the state update of a linearly implicit stage (Sec. 2.2,
+ * w^{n+1} = w^n + sum_i b_i dw_i; one stage with b = 1 here). w and dw must not alias. */
+int dg_stage_update(dg_handle* h, double* w, const double* dw, double b, void* stream);
+
+/* ---------------------------------------------------------- measured peaks
+ * The paper has no counterpart. Throughput of the device's FP64 or FP32 fused multiply-add
+ * pipe (TFLOP/s, FMA = 2 FLOP), measured with eight independent FMA chains per thread in a grid
+ * of 8 x 256-thread CTAs per SM on the current device: the best of three timed launches after a
+ * warm-up one (CUDA events on `stream`). The denominators of the ALU rooflines. Synchronises. */
+#define DG_PEAK_FP64_FMA 0
+#define DG_PEAK_FP32_FMA 1
+int dg_measure_peak(int which, double* tflops, void* stream);
+
 /* ----------------------------------------------------------------- batching
  * Many independent implicit-stage solves at once. The paper solves one system per process
  * group (Sec. 2.3); on one GPU, small problems leave most of the device idle, so a handle can
@@ -504,7 +524,8 @@ int dg_autotune(dg_handle* h, int which, int use_cache, double* report, void* st
 #define DG_PROF_BSR32 7      /* level-1 block-sparse product of the FP32 cycle */
 #define DG_PROF_BJ64 8       /* fine-level block-Jacobi apply of the FP64 cycle (LU factors) */
 #define DG_PROF_BSR64 9      /* level-1 block-sparse product of the FP64 cycle */
-#define DG_PROF_N 10
+#define DG_PROF_VOL_TC32 10  /* volume pass of the FP32 Jacobian action with tensor-core contractions */
+#define DG_PROF_N 11
 
 /* Counters since dg_create: kernels launched by the library, and applications
  * of the fine-level operator (residual or Jacobian action). Host-only, no sync. */

@@ -284,3 +284,23 @@ def remove_mean_pressure(x, ne, nb, vol):
     alpha = np.dot(X[:, 3, 0], s) / np.dot(s, s)
     X[:, 3, 0] -= alpha * s
     return X.reshape(-1)
+
+
+def implicit_stage(m, w, inv_gdt, levels, rtol=1e-8, restart=30, maxit=300, pre=2, post=2, coarse_sweeps=2,
+                   omega=1.0):
+    """One linearly implicit stage from the state w (Sec. 2.2 with one stage and gamma = 1):
+    g = -f_h(w), G = dense assembled J(w) + M/(gamma dt), the inherited coarse operators and
+    their element block inverses (Sec. 2.4), and FGMRES(restart) right-preconditioned by one
+    MG_V cycle (Algorithm 2) per iteration to rtol. Dense: for meshes of a few thousand unknowns.
+    Returns (w + dw, FGMRES iterations, true relative residual)."""
+    import oracle as O
+    g = -O.residual(m, w).reshape(-1)
+    G0 = O.dense_G(m, w, inv_gdt)
+    nbs = [O.nb(k) for k in levels]
+    Gs = [G0] + [inherited_operator(G0, m.ne, m.nb, nb) for nb in nbs[1:]]
+    lv = [Level(lambda v, G=G: G @ v, block_inverses(G, m.ne, nb), m.ne, nb) for G, nb in zip(Gs, nbs)]
+    x, its, _ = fgmres(lambda v: G0 @ v,
+                       lambda v: mg_v(lv, 0, v, np.zeros_like(v), pre, post, coarse_sweeps, omega),
+                       g, restart=restart, maxit=maxit, rtol=rtol)
+    relres = float(np.linalg.norm(g - G0 @ x) / np.linalg.norm(g))
+    return np.asarray(w).reshape(-1) + x, its, relres

@@ -32,6 +32,8 @@ DG_PRECOND_FP64 = 0
 DG_PRECOND_FP32 = 1
 DG_PRECOND_FP32_H16 = 2
 DG_PRECOND_FP32_BF16 = 3
+DG_PRECOND_FP32_H16_TC = 4
+DG_PRECOND_FP32_BF16_TC = 5
 DG_COARSE_SMOOTHER = 0
 DG_COARSE_GMRES = 1
 DG_COARSE_LEARNED = 2
@@ -40,6 +42,8 @@ DG_STATUS_WAIT = 4
 DG_KNOB_RIEMANN_ITS = 1
 DG_KNOB_WAIT_POLLS = 2
 DG_KNOB_WITHHOLD_COPY = 3
+DG_PEAK_FP64_FMA = 0
+DG_PEAK_FP32_FMA = 1
 DG_MAX_LEVELS = 4
 DG_SMOOTH_MAX_ITS = 32
 DG_MLP_IN = 112
@@ -59,14 +63,14 @@ EXPORTS = ("dg_create", "dg_destroy", "dg_last_error", "dg_level_size", "dg_get_
            "dg_create_batch", "dg_problems", "dg_set_problem_shifts", "dg_plan_create", "dg_plan_solve",
            "dg_plan_result", "dg_plan_stats", "dg_plan_error", "dg_plan_destroy",
            "dg_get_tuning", "dg_set_tuning", "dg_autotune", "dg_quad_points", "dg_project_points",
-           "dg_set_test_knob")
+           "dg_set_test_knob", "dg_stage_update", "dg_measure_peak")
 DG_WALLS_NONE = 0
 DG_WALLS_Y = 1
 DG_TUNE_FP64 = 0
 DG_TUNE_FP32 = 1
-DG_PROF_N = 10
+DG_PROF_N = 11
 PROF_NAMES = ("face_res", "vol_res", "face_tan", "vol_tan", "face_tan32", "vol_tan32", "bj32_fine", "bsr32_l1",
-              "bj64_fine", "bsr64_l1")
+              "bj64_fine", "bsr64_l1", "vol_tc32")
 
 
 class DgParams(ctypes.Structure):
@@ -171,6 +175,8 @@ def load(path=None):
     L.dg_set_tuning.argtypes = [vp, i, ctypes.POINTER(DgTuning)]
     L.dg_autotune.argtypes = [vp, i, i, ctypes.POINTER(d), vp]
     L.dg_set_test_knob.argtypes = [vp, i, ctypes.c_longlong]
+    L.dg_stage_update.argtypes = [vp, vp, vp, d, vp]
+    L.dg_measure_peak.argtypes = [i, ctypes.POINTER(d), vp]
     for name in EXPORTS:
         if name not in ("dg_last_error", "dg_plan_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -211,6 +217,13 @@ def _cur_stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def dg_measure_peak(which, stream=None):
+    """Measured FMA throughput (TFLOP/s) of the current device: DG_PEAK_FP64_FMA or DG_PEAK_FP32_FMA."""
+    t = ctypes.c_double()
+    _mchk(load().dg_measure_peak(int(which), ctypes.byref(t), _cur_stream(stream)))
+    return t.value
 
 
 def dg_mlp_workspace_bytes(rows):
@@ -399,6 +412,9 @@ class DG:
     def dg_set_linearization_rhs(self, w, inv_gamma_dt, g, stream=None):
         self._chk(self._L.dg_set_linearization_rhs(self.h, self._ptr(w), float(inv_gamma_dt), self._ptr(g),
                                                    self._stream(stream)))
+
+    def dg_stage_update(self, w, dw, b=1.0, stream=None):
+        self._chk(self._L.dg_stage_update(self.h, self._ptr(w), self._ptr(dw), float(b), self._stream(stream)))
 
     def dg_jvp(self, v, out, mode=DG_JVP_TANGENT, stream=None):
         self._chk(self._L.dg_jvp(self.h, self._ptr(v), self._ptr(out), int(mode), self._stream(stream)))

@@ -247,6 +247,7 @@ static void free_all(Handle* h) {
   TablesF& TF = h->tabf;
   F(TF.Bvol); F(TF.L1); F(TF.wvol); F(TF.B2); F(TF.W2); F(TF.pv); F(TF.pd); F(TF.Drow_val); F(TF.Dcol_val); F(TF.D2_val);
   F(h->face_out_f); F(h->face_lift_f); F(h->ubar_f); F(h->dFlux_f);
+  F(h->tc_tab[0]); F(h->tc_tab[1]); F(h->ubar_scale);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
   F(h->nbr);
@@ -623,6 +624,13 @@ int dg_set_linearization_rhs(dg_handle* hh, const double* w, double inv_gamma_dt
   return launch_axpby(h, h->lev[0].n, -1.0, h->flin, 0.0, g, as_stream(stream));  // g = -f_h(w)
 }
 
+int dg_stage_update(dg_handle* hh, double* w, const double* dw, double b, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return DG_ERR_ARG;
+  if (!w || !dw || w == dw) return fail(h, DG_ERR_ARG, "w and dw must be distinct non-null device pointers");
+  return launch_axpby(h, h->lev[0].n, b, dw, 1.0, w, as_stream(stream));  // w = b dw + w
+}
+
 int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
@@ -640,7 +648,8 @@ int dg_assemble_precision(dg_handle* hh, int precision, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");
-  if (precision == DG_PRECOND_FP32_H16 || precision == DG_PRECOND_FP32_BF16)
+  if (precision == DG_PRECOND_FP32_H16 || precision == DG_PRECOND_FP32_BF16 || precision == DG_PRECOND_FP32_H16_TC ||
+      precision == DG_PRECOND_FP32_BF16_TC)
     precision = DG_PRECOND_FP32;  // the 16-bit copies are rounded from the FP32 assembly at first use
   if (precision != DG_PRECOND_FP64 && precision != DG_PRECOND_FP32) return fail(h, DG_ERR_ARG, "unknown precision");
   h->assembled = h->asm64_ready = h->asm_f_ready = false;

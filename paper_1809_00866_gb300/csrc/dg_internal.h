@@ -145,6 +145,8 @@ struct Handle {
   double* face_lift = nullptr; // [ne][6][3][n2] BR2 local lifting (scaled 2D jump) per element face slot
   float* face_out_f = nullptr;   // FP32 scratch of the FP32 operator
   float* face_lift_f = nullptr;
+  void* tc_tab[2] = {nullptr, nullptr};  // 16-bit basis tables of the tensor-core volume pass (FP16, BF16)
+  float* ubar_scale = nullptr;            // [ne] power-of-two scale of the FP32 linearisation velocity
   float* ubar_f = nullptr;       // FP32 copies of the linearisation cache
   float* dFlux_f = nullptr;
   bool lin_f_ready = false;      // the FP32 copies match the current linearisation
@@ -264,11 +266,17 @@ __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
 int op_residual(Handle* h, const double* w, double* f, bool store_lin, cudaStream_t st);
 int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st);
-int op_tangent_f32(Handle* h, const float* v, float* out, cudaStream_t st);
+// tc = 0: CUDA-core volume pass; 1 / 2: volume contractions on the tensor cores in FP16 / BF16
+int op_tangent_f32(Handle* h, const float* v, float* out, int tc, cudaStream_t st);
 int op_fd(Handle* h, const double* v, double* out, cudaStream_t st);
 int op_project_tgv(Handle* h, double* w, cudaStream_t st);
 int op_quad_points(Handle* h, double* xyz, cudaStream_t st);
 int op_project_points(Handle* h, const double* vals, double* w, cudaStream_t st);
+
+// tensor-core volume pass of the FP32 Jacobian action (dg_tc_volume.cu)
+int tc_prepare_tables(Handle* h);                   // once per handle (allocates)
+int tc_prepare_lin(Handle* h, cudaStream_t st);     // per linearisation, after the FP32 cache
+int tc_volume_tangent(Handle* h, const float* in, float* out, int tc, cudaStream_t st);
 
 // vector helpers (dg_solvers.cu)
 int vec_norm2(Handle* h, const double* x, long long n, double* dev_out, cudaStream_t st);

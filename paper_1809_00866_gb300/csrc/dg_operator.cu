@@ -1104,7 +1104,7 @@ static int launch_face(Handle* h, const OpArgsT<R>& a, int per_sm_cap, cudaStrea
 }
 
 template <int K, int MODE, class R>
-static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
+static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st, bool face_only = false) {
   const bool tan = (MODE == MODE_TAN || MODE == MODE_LINPART);
   const OpTune tu = MODE == MODE_TAN ? h->tune[sizeof(R) == 4 ? 1 : 0] : OpTune{};
   const size_t vs = VolSmem<K, R>::bytes();
@@ -1130,6 +1130,7 @@ static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
   }
   if (rc) return rc;
   if ((rc = prof_end(h, cf, st, e0))) return rc;
+  if (face_only) return DG_OK;
   if ((rc = prof_begin(h, st, &e1))) return rc;
   vol_kernel<K, MODE, R><<<gv, tu.vol_threads, vs, st>>>(a);
   DG_LAUNCH_CHECK(h);
@@ -1139,12 +1140,12 @@ static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
 }
 
 template <int MODE, class R>
-static int dispatch(Handle* h, const OpArgsT<R>& a, cudaStream_t st) {
+static int dispatch(Handle* h, const OpArgsT<R>& a, cudaStream_t st, bool face_only = false) {
   switch (h->tab.k) {
-    case 1: return run_operator<1, MODE, R>(h, a, st);
-    case 2: return run_operator<2, MODE, R>(h, a, st);
-    case 3: return run_operator<3, MODE, R>(h, a, st);
-    case 4: return run_operator<4, MODE, R>(h, a, st);
+    case 1: return run_operator<1, MODE, R>(h, a, st, face_only);
+    case 2: return run_operator<2, MODE, R>(h, a, st, face_only);
+    case 3: return run_operator<3, MODE, R>(h, a, st, face_only);
+    case 4: return run_operator<4, MODE, R>(h, a, st, face_only);
   }
   return fail(h, DG_ERR_ARG, "unsupported degree");
 }
@@ -1160,9 +1161,18 @@ int op_tangent(Handle* h, const double* v, double* out, cudaStream_t st) {
   return dispatch<MODE_TAN>(h, a, st);
 }
 
-int op_tangent_f32(Handle* h, const float* v, float* out, cudaStream_t st) {
+int op_tangent_f32(Handle* h, const float* v, float* out, int tc, cudaStream_t st) {
   OpArgsT<float> a = make_args_f(h, v, out);
-  return dispatch<MODE_TAN>(h, a, st);
+  if (!tc) return dispatch<MODE_TAN>(h, a, st);
+  // the face pass as usual, then the volume pass with its contractions on the tensor cores
+  int rc = dispatch<MODE_TAN>(h, a, st, true);
+  if (rc) return rc;
+  cudaEvent_t e1 = nullptr;
+  if ((rc = prof_begin(h, st, &e1))) return rc;
+  if ((rc = tc_volume_tangent(h, v, out, tc, st))) return rc;
+  if ((rc = prof_end(h, DG_PROF_VOL_TC32, st, e1))) return rc;
+  ++h->op_apps;
+  return DG_OK;
 }
 
 int op_linear_part(Handle* h, const double* v, double* out, cudaStream_t st) {

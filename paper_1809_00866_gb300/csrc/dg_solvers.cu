@@ -575,6 +575,7 @@ int prepare_lin_fp32(Handle* h, cudaStream_t st) {
   DG_LAUNCH_CHECK(h);
   convert_kernel<double, float><<<grid_for(h, nf / 256 + 1), 256, 0, st>>>(nf, h->dFlux, h->dFlux_f);
   DG_LAUNCH_CHECK(h);
+  if (int rc = tc_prepare_lin(h, st)) return rc;  // scales of the tensor-core volume pass
   h->lin_f_ready = true;
   return DG_OK;
 }
@@ -606,12 +607,25 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
   return DG_OK;
 }
 
-static bool is16(int precision) { return precision == DG_PRECOND_FP32_H16 || precision == DG_PRECOND_FP32_BF16; }
+// the FP32 cycles with tensor-core volume contractions store their blocks as the H16 / BF16 cycles do
+static int storage_of(int precision) {
+  return precision == DG_PRECOND_FP32_H16_TC ? DG_PRECOND_FP32_H16
+         : precision == DG_PRECOND_FP32_BF16_TC ? DG_PRECOND_FP32_BF16 : precision;
+}
+static int tc_of(int precision) {
+  return precision == DG_PRECOND_FP32_H16_TC ? 1 : precision == DG_PRECOND_FP32_BF16_TC ? 2 : 0;
+}
+static bool is16(int precision) {
+  const int s = storage_of(precision);
+  return s == DG_PRECOND_FP32_H16 || s == DG_PRECOND_FP32_BF16;
+}
 
-// y = G_lvl x in the FP32 cycle; `storage` (the cycle's precision) says how the blocks are stored
-static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, int storage, cudaStream_t st) {
-  if (lvl == 0) return op_tangent_f32(h, x, y, st);
+// y = G_lvl x in the FP32 cycle; `precision` (the cycle's) says how the blocks are stored and
+// whether the fine level's volume contractions run on the tensor cores
+static int level_matvec_f(Handle* h, int lvl, const float* x, float* y, int precision, cudaStream_t st) {
+  if (lvl == 0) return op_tangent_f32(h, x, y, tc_of(precision), st);
   const Level& L = h->lev[lvl];
+  const int storage = storage_of(precision);
   if (is16(storage)) {
     const int r16 = bsr16_f(h, lvl, storage, 1.0f, x, 0.0f, y, st);
     if (r16 >= 0) return r16;
@@ -633,7 +647,7 @@ static int jacobi_sweeps_f(Handle* h, int lvl, const float* g, float* x, int swe
     const bool zero = x_zero && s == 0;
     int rc;
     if (!zero && (rc = level_matvec_f(h, lvl, x, L.t2f, storage, st))) return rc;
-    rc = staged_jacobi_f(h, lvl, g, zero ? nullptr : L.t2f, omega, zero, x, storage, st);
+    rc = staged_jacobi_f(h, lvl, g, zero ? nullptr : L.t2f, omega, zero, x, storage_of(storage), st);
     if (rc < 0) return fail(h, DG_ERR_ARG, "element block too large for the FP32 smoother");
     if (rc) return rc;
   }
@@ -691,7 +705,8 @@ static int mg_v_f(Handle* h, int l, const float* g, float* x, bool x_zero, const
 static int vcycle_fp32(Handle* h, const dg_solve_opts& o, const double* v, double* z, cudaStream_t st) {
   int rc;
   if ((rc = prepare_fp32(h, st))) return rc;
-  if (is16(o.precision) && (rc = prepare_blocks16(h, o.precision, st))) return rc;
+  if (is16(o.precision) && (rc = prepare_blocks16(h, storage_of(o.precision), st))) return rc;
+  if (tc_of(o.precision) && (rc = tc_prepare_tables(h))) return rc;
   Level& L0 = h->lev[0];
   convert_kernel<double, float><<<grid_for(h, L0.n / 256 + 1), 256, 0, st>>>(L0.n, v, L0.t0f);
   DG_LAUNCH_CHECK(h);
@@ -930,7 +945,8 @@ int precond_prepare(Handle* h, const dg_solve_opts& o, cudaStream_t st) {
   }
   int rc;
   if ((rc = prepare_fp32(h, st))) return rc;
-  if (is16(o.precision) && (rc = prepare_blocks16(h, o.precision, st))) return rc;
+  if (is16(o.precision) && (rc = prepare_blocks16(h, storage_of(o.precision), st))) return rc;
+  if (tc_of(o.precision) && (rc = tc_prepare_tables(h))) return rc;
   return DG_OK;
 }
 

@@ -122,7 +122,7 @@ static int autotune(Handle* h, int which, bool use_cache, double* report, cudaSt
     }
     DG_LAUNCH_CHECK(h);
     h->prof = true;
-    auto op = [&]() -> int { return f32 ? op_tangent_f32(h, xf, yf, st) : op_tangent(h, L0.t0, L0.t1, st); };
+    auto op = [&]() -> int { return f32 ? op_tangent_f32(h, xf, yf, 0, st) : op_tangent(h, L0.t0, L0.t1, st); };
     const int cf = f32 ? DG_PROF_FACE_TAN32 : DG_PROF_FACE_TAN, cv = f32 ? DG_PROF_VOL_TAN32 : DG_PROF_VOL_TAN;
     const int face_w[3] = {2, 4, 8};
     const int vol_t[3] = {64, 128, 256};
