@@ -5,7 +5,7 @@
         Jacobian actions (face_kernel + vol_kernel per action).
     python profile_workloads.py assemble [--n 16] [--form fp32|fp64]
         one preconditioner assembly after a warm-up one, between cudaProfilerStart/Stop.
-    python profile_workloads.py stage [--n 16] [--form fp32|fp64|h16|bf16] [--learned]
+    python profile_workloads.py stage [--n 16] [--form fp32|fp64|h16|bf16|h16tc|bf16tc] [--learned]
         one implicit stage to rel-res 1e-8 after two warm-up solves; only the timed FGMRES solve
         lies between cudaProfilerStart and cudaProfilerStop (ncu --profile-from-start off).
 
@@ -24,7 +24,7 @@ def main(argv=None):
     ap.add_argument("what", choices=["jv", "stage", "assemble"])
     ap.add_argument("--n", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--form", choices=["fp32", "fp64", "h16", "bf16"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "fp64", "h16", "bf16", "h16tc", "bf16tc"], default="fp32")
     ap.add_argument("--learned", action="store_true", help="train the coarse network first and use it")
     ap.add_argument("--no-stb-rescale", dest="stb", action="store_false",
                     help="plain inherited coarse operators (the bench rescales their stabilisation part)")
@@ -35,8 +35,8 @@ def main(argv=None):
 
     import synthetic as S
     from paper_1809_00866_gb300 import (DG, DG_COARSE_LEARNED, DG_PRECOND_FP32, DG_PRECOND_FP32_BF16,
-                                        DG_PRECOND_FP32_H16, DG_PRECOND_FP64, DG_TUNE_FP32, DG_TUNE_FP64, build,
-                                        solve_opts)
+                                        DG_PRECOND_FP32_BF16_TC, DG_PRECOND_FP32_H16, DG_PRECOND_FP32_H16_TC,
+                                        DG_PRECOND_FP64, DG_TUNE_FP32, DG_TUNE_FP64, build, solve_opts)
     build()
     un = S.uniform_nodes(a.n)
     levels = [4, 2, 1]
@@ -74,7 +74,7 @@ def main(argv=None):
     # the settings of the benchmark's forms: reduced-precision cycles damped 0.95 with 4/4/2
     # sweeps, the FP64 cycle undamped with 2/2/2
     prec = {"fp32": DG_PRECOND_FP32, "fp64": DG_PRECOND_FP64, "h16": DG_PRECOND_FP32_H16,
-            "bf16": DG_PRECOND_FP32_BF16}[a.form]
+            "bf16": DG_PRECOND_FP32_BF16, "h16tc": DG_PRECOND_FP32_H16_TC, "bf16tc": DG_PRECOND_FP32_BF16_TC}[a.form]
     low = prec != DG_PRECOND_FP64
     o = solve_opts(restart=30, maxit=300, rtol=1e-8, omega=0.95 if low else 1.0, pre_sweeps=4 if low else 2,
                    post_sweeps=4 if low else 2, coarse_sweeps=2, precision=prec)
