@@ -36,19 +36,23 @@ namespace dg {
 template <int K, class R = double>
 struct AsmSmem {
   static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
-  static constexpr int B = 0;                 // [NQ][NB]
-  static constexpr int W = B + NQ * NB;       // [NQ]
-  static constexpr int UB = W + NQ;           // [3][NQ]
-  static constexpr int U = UB + 3 * NQ;       // [3][NB][NB]
-  static constexpr int E = U + 3 * NB * NB;   // [6][N2][N2]
-  static constexpr int JQ = E + 6 * N2 * N2;  // [6][NQF] Jacobian entry of the current pair at the face points
-  static constexpr int B2 = JQ + 6 * NQF;     // [NQF][N2]
-  static constexpr int W2 = B2 + NQF * N2;    // [NQF]
-  static constexpr int PV = W2 + NQF;         // [2][K+1]
-  static constexpr int DOUBLES = PV + 2 * (K + 1);
-  static constexpr int FMAP = 0;              // [3][NB]
-  static constexpr int FA = FMAP + 3 * NB;    // [3][NB]
-  static constexpr int INTS = FA + 3 * NB;
+  static constexpr int B = 0;                   // [NQ][NB]
+  static constexpr int W = B + NQ * NB;         // [NQ]
+  static constexpr int UB = W + NQ;             // [3][NQ]
+  static constexpr int U = UB + 3 * NQ;         // [3][NB][NB]
+  static constexpr int E = U + 3 * NB * NB;     // [4 j][6 slot][N2][N2] face matrices of one row variable i
+  static constexpr int N2C = K * (K + 1) / 2;  // 2D modes of a coarser level (degree <= K - 1)
+  static constexpr int EO = E + 24 * N2 * N2;   // [6 slot][4 j][N2c][N2c] the same with the other side's columns
+  static constexpr int JQ = EO + 24 * N2C * N2C;  // [2 buffers][2 own/other][6 slot][NQF][4 j] weighted Jacobian entries
+  static constexpr int B2 = JQ + 2 * 2 * 6 * NQF * 4;  // [NQF][N2]
+  static constexpr int W2 = B2 + NQF * N2;      // [NQF]
+  static constexpr int PV = W2 + NQF;           // [2][K+1]
+  static constexpr int SLOT = PV + 2 * (K + 1); // [6] scale of the slot's off-diagonal block
+  static constexpr int DOUBLES = SLOT + 6;
+  static constexpr int FMAP = 0;                // [3][NB]
+  static constexpr int FA = FMAP + 3 * NB;      // [3][NB]
+  static constexpr int SINFO = FA + 3 * NB;     // [6][3] face index, neighbour, target slot
+  static constexpr int INTS = SINFO + 18;
   static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
 
@@ -83,14 +87,22 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   R* sUb = sm + L::UB;
   R* sU = sm + L::U;
   R* sE = sm + L::E;
+  R* sEo = sm + L::EO;
   R* sJ = sm + L::JQ;
   R* sB2 = sm + L::B2;
   R* sW2 = sm + L::W2;
   R* sPV = sm + L::PV;
+  R* sScl = sm + L::SLOT;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
   int* FMAP = ism + L::FMAP;
   int* FA = ism + L::FA;
+  int* SI = ism + L::SINFO;  // per slot: face index, neighbour (-1 at a wall), target block slot
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int nb1 = a.nb1, b1 = 4 * nb1;
+  // coarse 2D modes: the graded 2D ordering lists the modes of degree <= k_1 first
+  int k1 = 0;
+  while (nb1 > 0 && nb_of(k1) < nb1) ++k1;
+  const int N2c = nb1 > 0 ? (k1 + 1) * (k1 + 2) / 2 : 0;  // <= L::N2C: the coarse degree is below K
   for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.Bvol[t];
   for (int t = tid; t < NQ; t += nt) sW[t] = a.wvol[t];
   for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.B2[t];
@@ -101,7 +113,48 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
     const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
+    // the weighted Jacobian entries (i, j) of the six face slots at the face points: the own
+    // side's columns (diagonal block) and the other side's (off-diagonal block); buffer i & 1
+    auto load_jac = [&](int i) {
+      R* dst = sJ + (i & 1) * 2 * 6 * NQF * 4;
+      for (int t = tid; t < 2 * 6 * NQF * 4; t += nt) {
+        const int oth = t / (6 * NQF * 4), r = t - oth * 6 * NQF * 4, sl = r / (NQF * 4), r2 = r - sl * NQF * 4;
+        const int q = r2 >> 2, j = r2 & 3, d = sl >> 1, side = (sl & 1) ? 0 : 1;
+        const int nb_ = a.M.nbr[e * 6 + sl];
+        R v = R(0);
+        if (!oth) {
+          const int f = side == 0 ? 3 * e + d : (nb_ >= 0 ? 3 * nb_ + d : 3 * a.M.ne + a.M.bslot[e]);
+          const R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32 + i * 8;
+          v = Jq[(side == 0 ? 0 : 4) + j];
+          // at a wall the ghost state (-u_K, p_K) is the element's own: its columns add with
+          // sign -1 (velocity) and +1 (pressure)
+          if (nb_ < 0) v += (j == 3 ? R(1) : -R(1)) * Jq[(side == 0 ? 4 : 0) + j];
+        } else if (nb_ >= 0 && nb1 > 0) {
+          const int f = side == 0 ? 3 * e + d : 3 * nb_ + d;
+          v = a.dFlux[((size_t)f * NQF + q) * 32 + i * 8 + (side == 0 ? 4 : 0) + j];
+        }
+        dst[t] = v * sW2[q];
+      }
+    };
     for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
+    if (tid < 6) {
+      const int sl = tid, d = sl >> 1, side = (sl & 1) ? 0 : 1;
+      const int p = a.M.nbr[e * 6 + sl];
+      int tgt = sl;
+      for (int s2 = 0; s2 < sl; ++s2)
+        if (a.M.nbr[e * 6 + s2] == p) { tgt = s2; break; }
+      SI[3 * sl + 0] = side == 0 ? 3 * e + d : (p >= 0 ? 3 * p + d : -1);
+      SI[3 * sl + 1] = p;
+      SI[3 * sl + 2] = tgt;
+      R sc = R(0);
+      if (p >= 0) {
+        const ElemGeom gp = elem_geom(a.M, p);
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        sc = R((side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is);
+      }
+      sScl[sl] = sc;
+    }
+    load_jac(0);
     __syncthreads();
     // weighted mass matrices U_c (symmetric): one thread per mode pair n1 <= n computes all three
     // c, so the two basis values of a point are loaded once
@@ -111,9 +164,9 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       const int n = n1 + r;
       R acc[3] = {R(0), R(0), R(0)};
       for (int q = 0; q < NQ; ++q) {
-        const R b1 = sB[q * NB + n1], b2 = sB[q * NB + n], wq = sW[q];
+        const R b1v = sB[q * NB + n1], b2v = sB[q * NB + n], wq = sW[q];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += wq * sUb[c * NQ + q] * b1 * b2;
+        for (int c = 0; c < 3; ++c) acc[c] += wq * sUb[c * NQ + q] * b1v * b2v;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -121,124 +174,96 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
         sU[(c * NB + n) * NB + n1] = acc[c];
       }
     }
-    __syncthreads();
-    // face geometry of the six slots: face index, own side, Jacobian column offset, scale
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        // Jacobian entry (i, own j) at the points of the six faces
-        for (int t = tid; t < 6 * NQF; t += nt) {
-          const int sl = t / NQF, q = t - sl * NQF, d = sl >> 1, side = (sl & 1) ? 0 : 1;
-          const int nb_ = a.M.nbr[e * 6 + sl];
-          const int f = side == 0 ? 3 * e + d : (nb_ >= 0 ? 3 * nb_ + d : 3 * a.M.ne + a.M.bslot[e]);
-          const R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32 + i * 8;
-          R v = Jq[(side == 0 ? 0 : 4) + j];
-          // at a wall the ghost state (-u_K, p_K) is the element's own: its columns add with
-          // sign -1 (velocity) and +1 (pressure)
-          if (nb_ < 0) v += (j == 3 ? R(1) : -R(1)) * Jq[(side == 0 ? 4 : 0) + j];
-          sJ[t] = v * sW2[q];
+    for (int i = 0; i < 4; ++i) {
+      // face matrices of row variable i: E[j][sl] = sum_q w_q dF_ij(q) B2[q][j1] B2[q][j2] (one
+      // thread per (j, 2D mode pair), six slots), and the other side's for the coarse 2D modes
+      const R* Jo = sJ + (i & 1) * 2 * 6 * NQF * 4;  // own columns [6][NQF][4]
+      const R* Jx = Jo + 6 * NQF * 4;                 // other side's columns
+      for (int t = tid; t < 4 * N2 * N2; t += nt) {
+        const int j = t / (N2 * N2), pr = t - j * N2 * N2, j1 = pr / N2, j2 = pr - j1 * N2;
+        R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+        for (int q = 0; q < NQF; ++q) {
+          const R bb = sB2[q * N2 + j1] * sB2[q * N2 + j2];
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) acc[sl] += Jo[(sl * NQF + q) * 4 + j] * bb;
         }
-        __syncthreads();
-        // one thread per 2D mode pair computes the six face slots from one load of its basis values
-        for (int t = tid; t < N2 * N2; t += nt) {
-          const int j1 = t / N2, j2 = t - j1 * N2;
-          R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
-          for (int q = 0; q < NQF; ++q) {
-            const R b1 = sB2[q * N2 + j1], b2 = sB2[q * N2 + j2];
+        for (int sl = 0; sl < 6; ++sl) sE[(j * 6 + sl) * N2 * N2 + pr] = acc[sl];
+      }
+      for (int t = tid; t < 6 * 4 * N2c * N2c; t += nt) {
+        const int sl = t / (4 * N2c * N2c), r = t - sl * 4 * N2c * N2c, j = r / (N2c * N2c), pr = r - j * N2c * N2c;
+        const int j1 = pr / N2c, j2 = pr - j1 * N2c;
+        R acc = R(0);
 #pragma unroll
-            for (int sl = 0; sl < 6; ++sl) acc[sl] += sJ[sl * NQF + q] * b1 * b2;
+        for (int q = 0; q < NQF; ++q) acc += Jx[(sl * NQF + q) * 4 + j] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
+        sEo[((sl * 4 + j) * N2c + j1) * N2c + j2] = acc;
+      }
+      __syncthreads();
+      if (i < 3) load_jac(i + 1);  // the other buffer, read after the next barrier
+      // the diagonal block's rows of variable i: one thread per (j, n, m), column-major within
+      // the pair (consecutive threads, consecutive rows)
+      R* Dout = a.D + (size_t)e * BS * BS;
+      const double* Dl = a.Dlin + (size_t)e * BS * BS;
+      for (int t = tid; t < 4 * NB * NB; t += nt) {
+        const int j = t / (NB * NB), r = t - j * NB * NB, n = r / NB, m = r - n * NB;
+        R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
+        if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
+        if (i < 3 && j < 3) {
+          // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
+          R cv = R(0);
+#pragma unroll
+          for (int q = 0; q < DW; ++q) {
+            const int o = (j * NB + m) * DW + q;
+            cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
           }
+          v -= Jd[j] * cv;
+          if (i == j) {
 #pragma unroll
-          for (int sl = 0; sl < 6; ++sl) sE[sl * N2 * N2 + t] = acc[sl];
-        }
-        __syncthreads();
-        R* Dout = a.D + (size_t)e * BS * BS;
-        const double* Dl = a.Dlin + (size_t)e * BS * BS;
-        for (int t = tid; t < NB * NB; t += nt) {
-          const int n = t / NB, m = t - n * NB;  // column-major within the pair: consecutive threads, consecutive rows
-          R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
-          if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
-          if (i < 3 && j < 3) {
-            // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
-            R cv = R(0);
+            for (int pp = 0; pp < 3; ++pp) {
+              R c2 = R(0);
 #pragma unroll
-            for (int q = 0; q < DW; ++q) {
-              const int o = (j * NB + m) * DW + q;
-              cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
-            }
-            v -= Jd[j] * cv;
-            if (i == j) {
-#pragma unroll
-              for (int pp = 0; pp < 3; ++pp) {
-                R c2 = R(0);
-#pragma unroll
-                for (int q = 0; q < DW; ++q) {
-                  const int o = (pp * NB + m) * DW + q;
-                  c2 += a.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
-                }
-                v -= Jd[pp] * c2;
+              for (int q = 0; q < DW; ++q) {
+                const int o = (pp * NB + m) * DW + q;
+                c2 += a.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
               }
+              v -= Jd[pp] * c2;
             }
           }
+        }
 #pragma unroll
-          for (int sl = 0; sl < 6; ++sl) {
-            const int d = sl >> 1, side = (sl & 1) ? 0 : 1;
-            const R scale = (side == 0 ? R(1) : -R(1)) * Jd[d];  // A4 / s^2 = 2 / h_d
-            v += scale * sPV[side * K1 + FA[d * NB + m]] * sPV[side * K1 + FA[d * NB + n]] *
-                 sE[(sl * N2 + FMAP[d * NB + m]) * N2 + FMAP[d * NB + n]];
-          }
-          Dout[(size_t)(j * NB + n) * BS + i * NB + m] = v;
+        for (int sl = 0; sl < 6; ++sl) {
+          const int d = sl >> 1, side = (sl & 1) ? 0 : 1;
+          const R scale = (side == 0 ? R(1) : -R(1)) * Jd[d];  // A4 / s^2 = 2 / h_d
+          v += scale * sPV[side * K1 + FA[d * NB + m]] * sPV[side * K1 + FA[d * NB + n]] *
+               sE[((j * 6 + sl) * N2 + FMAP[d * NB + m]) * N2 + FMAP[d * NB + n]];
         }
-        __syncthreads();
+        Dout[(size_t)(j * NB + n) * BS + i * NB + m] = v;
       }
-    // level-1 off-diagonal blocks: the other side's Jacobian columns, coarse modes only
-    if (a.nb1 > 0) {
-      const int nb1 = a.nb1, b1 = 4 * nb1;
-      for (int sl = 0; sl < 6; ++sl) {
-        const int d = sl >> 1, side = (sl & 1) ? 0 : 1, other = 1 - side;
-        const int p = a.M.nbr[e * 6 + sl];
-        if (p < 0) {  // a wall: no neighbour block (the ghost's dependence is in the diagonal)
-          R* wb = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
-          for (int t = tid; t < b1 * b1; t += nt) wb[t] = R(0);
-          continue;
-        }
-        const int f = side == 0 ? 3 * e + d : 3 * p + d;
-        int tgt = sl;
-        for (int s2 = 0; s2 < sl; ++s2)
-          if (a.M.nbr[e * 6 + s2] == p) { tgt = s2; break; }
-        const ElemGeom gp = elem_geom(a.M, p);
-        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        const R scale = R((side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is);
-        R* blk = a.Bsr + ((size_t)e * 7 + 1 + tgt) * b1 * b1;
-        const double* lin = a.Blin + ((size_t)e * 7 + 1 + sl) * b1 * b1;
-        for (int i = 0; i < 4; ++i)
-          for (int j = 0; j < 4; ++j) {
-            for (int t = tid; t < NQF; t += nt)
-              sJ[t] = a.dFlux[((size_t)f * NQF + t) * 32 + i * 8 + (other == 0 ? 0 : 4) + j] * sW2[t];
-            __syncthreads();
-            for (int t = tid; t < N2 * N2; t += nt) {
-              const int j1 = t / N2, j2 = t - j1 * N2;
-              R acc = R(0);
-#pragma unroll
-              for (int q = 0; q < NQF; ++q) acc += sJ[q] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
-              sE[t] = acc;
-            }
-            __syncthreads();
-            for (int t = tid; t < nb1 * nb1; t += nt) {
-              const int n = t / nb1, m = t - n * nb1;
-              const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
-              const R base = (tgt == sl) ? R(lin[o]) : blk[o];
-              blk[o] = base + scale * sPV[side * K1 + FA[d * NB + m]] * sPV[other * K1 + FA[d * NB + n]] *
-                                  sE[FMAP[d * NB + m] * N2 + FMAP[d * NB + n]];
-            }
-            __syncthreads();
+      // level-1 off-diagonal blocks, rows of variable i, coarse modes only: the linear part of
+      // the slot plus the Riemann terms of every slot facing the same neighbour, in slot order
+      // (a neighbour met on two faces keeps its block at the first slot; the other is zero; a
+      // wall slot is zero)
+      if (nb1 > 0)
+        for (int t = tid; t < 6 * 4 * nb1 * nb1; t += nt) {
+          const int so = t / (4 * nb1 * nb1), r = t - so * 4 * nb1 * nb1, j = r / (nb1 * nb1), r2 = r - j * nb1 * nb1;
+          const int n = r2 / nb1, m = r2 - n * nb1;
+          const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
+          R* blk = a.Bsr + ((size_t)e * 7 + 1 + so) * b1 * b1;
+          if (SI[3 * so + 1] < 0 || SI[3 * so + 2] != so) {
+            blk[o] = R(0);
+            continue;
           }
-        if (tgt != sl) {
-          R* z = a.Bsr + ((size_t)e * 7 + 1 + sl) * b1 * b1;
-          for (int t = tid; t < b1 * b1; t += nt) z[t] = R(0);
+          R v = R(a.Blin[((size_t)e * 7 + 1 + so) * b1 * b1 + o]);
+          for (int sl = so; sl < 6; ++sl) {
+            if (SI[3 * sl + 1] < 0 || SI[3 * sl + 2] != so) continue;
+            const int d = sl >> 1, side = (sl & 1) ? 0 : 1, other = 1 - side;
+            v += sScl[sl] * sPV[side * K1 + FA[d * NB + m]] * sPV[other * K1 + FA[d * NB + n]] *
+                 sEo[((sl * 4 + j) * N2c + FMAP[d * NB + m]) * N2c + FMAP[d * NB + n]];
+          }
+          blk[o] = v;
         }
-        __syncthreads();
-      }
+      __syncthreads();
     }
   }
 }
