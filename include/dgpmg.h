@@ -402,9 +402,12 @@ int dg_stage_update(dg_handle* h, double* w, const double* dw, double b, void* s
  * The paper has no counterpart. Throughput of the device's FP64 or FP32 fused multiply-add
  * pipe (TFLOP/s, FMA = 2 FLOP), measured with eight independent FMA chains per thread in a grid
  * of 8 x 256-thread CTAs per SM on the current device: the best of three timed launches after a
- * warm-up one (CUDA events on `stream`). The denominators of the ALU rooflines. Synchronises. */
+ * warm-up one (CUDA events on `stream`). The denominators of the ALU rooflines.
+ * DG_PEAK_HBM_READ: the bandwidth (GB/s, written to *tflops) of a read-only stream of 16-byte
+ * loads over a 2 GiB buffer (allocated and freed by the call). Synchronises. */
 #define DG_PEAK_FP64_FMA 0
 #define DG_PEAK_FP32_FMA 1
+#define DG_PEAK_HBM_READ 2
 int dg_measure_peak(int which, double* tflops, void* stream);
 
 /* ----------------------------------------------------------------- batching

@@ -44,6 +44,7 @@ DG_KNOB_WAIT_POLLS = 2
 DG_KNOB_WITHHOLD_COPY = 3
 DG_PEAK_FP64_FMA = 0
 DG_PEAK_FP32_FMA = 1
+DG_PEAK_HBM_READ = 2
 DG_MAX_LEVELS = 4
 DG_SMOOTH_MAX_ITS = 32
 DG_MLP_IN = 112
@@ -220,7 +221,8 @@ def _cur_stream(stream):
 
 
 def dg_measure_peak(which, stream=None):
-    """Measured FMA throughput (TFLOP/s) of the current device: DG_PEAK_FP64_FMA or DG_PEAK_FP32_FMA."""
+    """Measured FMA throughput (TFLOP/s) of the current device (DG_PEAK_FP64_FMA, DG_PEAK_FP32_FMA) or its
+    read-only HBM streaming bandwidth in GB/s (DG_PEAK_HBM_READ)."""
     t = ctypes.c_double()
     _mchk(load().dg_measure_peak(int(which), ctypes.byref(t), _cur_stream(stream)))
     return t.value

@@ -36,22 +36,21 @@ namespace dg {
 template <int K, class R = double>
 struct AsmSmem {
   static constexpr int NB = nb_of(K), N1 = K + 1, NQ = N1 * N1 * N1, NQF = N1 * N1, N2 = (K + 1) * (K + 2) / 2;
+  static constexpr int N2C = K * (K + 1) / 2;   // 2D modes of a coarser level (degree <= K - 1)
   static constexpr int B = 0;                   // [NQ][NB]
-  static constexpr int W = B + NQ * NB;         // [NQ]
-  static constexpr int UB = W + NQ;             // [3][NQ]
+  static constexpr int UB = B + NQ * NB;        // [3][NQ] w_q ubar_c(q)
   static constexpr int U = UB + 3 * NQ;         // [3][NB][NB]
   static constexpr int E = U + 3 * NB * NB;     // [4 j][6 slot][N2][N2] face matrices of one row variable i
-  static constexpr int N2C = K * (K + 1) / 2;  // 2D modes of a coarser level (degree <= K - 1)
   static constexpr int EO = E + 24 * N2 * N2;   // [6 slot][4 j][N2c][N2c] the same with the other side's columns
   static constexpr int JQ = EO + 24 * N2C * N2C;  // [2 buffers][2 own/other][6 slot][NQF][4 j] weighted Jacobian entries
   static constexpr int B2 = JQ + 2 * 2 * 6 * NQF * 4;  // [NQF][N2]
   static constexpr int W2 = B2 + NQF * N2;      // [NQF]
-  static constexpr int PV = W2 + NQF;           // [2][K+1]
-  static constexpr int SLOT = PV + 2 * (K + 1); // [6] scale of the slot's off-diagonal block
+  static constexpr int PVN = W2 + NQF;          // [6 slot][NB] P_hat_a(side) of mode n's exponent along the slot's axis
+  static constexpr int SLOT = PVN + 6 * NB;     // [6] scale of the slot's off-diagonal block
   static constexpr int DOUBLES = SLOT + 6;
-  static constexpr int FMAP = 0;                // [3][NB]
-  static constexpr int FA = FMAP + 3 * NB;      // [3][NB]
-  static constexpr int SINFO = FA + 3 * NB;     // [6][3] face index, neighbour, target slot
+  static constexpr int FMN = 0;                 // [6 slot][NB] 2D mode of mode n on the slot's face
+  static constexpr int PVO = FMN + 6 * NB;      // [6 slot][NB] index of P_hat_a(other side) of mode n (into pv)
+  static constexpr int SINFO = PVO + 6 * NB;    // [6][3] face index, neighbour, target slot
   static constexpr int INTS = SINFO + 18;
   static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
 };
@@ -80,10 +79,10 @@ template <int K, class R>
 __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   using L = AsmSmem<K, R>;
   constexpr int NB = L::NB, NQ = L::NQ, NQF = L::NQF, N2 = L::N2, K1 = K + 1, BS = 4 * NB, DW = Tables::kDw;
+  constexpr int NDT = 4 * NB;  // diagonal-block tasks (j, m) of one row variable
   extern __shared__ __align__(16) unsigned char smraw_[];
   R* sm = reinterpret_cast<R*>(smraw_);
   R* sB = sm + L::B;
-  R* sW = sm + L::W;
   R* sUb = sm + L::UB;
   R* sU = sm + L::U;
   R* sE = sm + L::E;
@@ -91,11 +90,11 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   R* sJ = sm + L::JQ;
   R* sB2 = sm + L::B2;
   R* sW2 = sm + L::W2;
-  R* sPV = sm + L::PV;
+  R* PVN = sm + L::PVN;
   R* sScl = sm + L::SLOT;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
-  int* FMAP = ism + L::FMAP;
-  int* FA = ism + L::FA;
+  int* FMN = ism + L::FMN;
+  int* PVO = ism + L::PVO;
   int* SI = ism + L::SINFO;  // per slot: face index, neighbour (-1 at a wall), target block slot
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nb1 = a.nb1, b1 = 4 * nb1;
@@ -104,11 +103,17 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   while (nb1 > 0 && nb_of(k1) < nb1) ++k1;
   const int N2c = nb1 > 0 ? (k1 + 1) * (k1 + 2) / 2 : 0;  // <= L::N2C: the coarse degree is below K
   for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.Bvol[t];
-  for (int t = tid; t < NQ; t += nt) sW[t] = a.wvol[t];
   for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.B2[t];
   for (int t = tid; t < NQF; t += nt) sW2[t] = a.W2[t];
-  for (int t = tid; t < 2 * K1; t += nt) sPV[t] = a.pv[t];
-  for (int t = tid; t < 3 * NB; t += nt) { FMAP[t] = a.T.fmap[t]; FA[t] = a.T.fa[t]; }
+  // per slot sl (face normal d = sl / 2, the element on side 1 of slot 2d and side 0 of slot 2d+1)
+  // and mode n: P_hat of n's exponent along d on the element's side, its 2D face mode, and the
+  // index of P_hat on the other side
+  for (int t = tid; t < 6 * NB; t += nt) {
+    const int sl = t / NB, n = t - sl * NB, d = sl >> 1, side = (sl & 1) ? 0 : 1;
+    PVN[t] = a.pv[side * K1 + a.T.fa[d * NB + n]];
+    PVO[t] = (1 - side) * K1 + a.T.fa[d * NB + n];
+    FMN[t] = a.T.fmap[d * NB + n];
+  }
   __syncthreads();
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
@@ -136,7 +141,10 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
         dst[t] = v * sW2[q];
       }
     };
-    for (int t = tid; t < 3 * NQ; t += nt) sUb[t] = a.ubar[(size_t)e * 3 * NQ + t];
+    for (int t = tid; t < 3 * NQ; t += nt) {
+      const int q = t % NQ;
+      sUb[t] = a.wvol[q] * a.ubar[(size_t)e * 3 * NQ + t];
+    }
     if (tid < 6) {
       const int sl = tid, d = sl >> 1, side = (sl & 1) ? 0 : 1;
       const int p = a.M.nbr[e * 6 + sl];
@@ -164,9 +172,9 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       const int n = n1 + r;
       R acc[3] = {R(0), R(0), R(0)};
       for (int q = 0; q < NQ; ++q) {
-        const R b1v = sB[q * NB + n1], b2v = sB[q * NB + n], wq = sW[q];
+        const R bb = sB[q * NB + n1] * sB[q * NB + n];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += wq * sUb[c * NQ + q] * b1v * b2v;
+        for (int c = 0; c < 3; ++c) acc[c] += sUb[c * NQ + q] * bb;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -175,77 +183,159 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       }
     }
     for (int i = 0; i < 4; ++i) {
-      // face matrices of row variable i: E[j][sl] = sum_q w_q dF_ij(q) B2[q][j1] B2[q][j2] (one
-      // thread per (j, 2D mode pair), six slots), and the other side's for the coarse 2D modes
+      // face matrices of row variable i: E[j][sl] = sum_q w_q dF_ij(q) B2[q][j1] B2[q][j2]: one
+      // thread per 2D mode pair, all 4 j and 6 slots (the four j of a point are one vector);
+      // the threads after them form the other side's matrices for the coarse 2D modes
       const R* Jo = sJ + (i & 1) * 2 * 6 * NQF * 4;  // own columns [6][NQF][4]
       const R* Jx = Jo + 6 * NQF * 4;                 // other side's columns
-      for (int t = tid; t < 4 * N2 * N2; t += nt) {
-        const int j = t / (N2 * N2), pr = t - j * N2 * N2, j1 = pr / N2, j2 = pr - j1 * N2;
-        R acc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+      for (int t = tid; t < N2 * N2; t += nt) {
+        const int j1 = t / N2, j2 = t - j1 * N2;
+        R acc[4][6];
 #pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) acc[j][sl] = R(0);
+#pragma unroll 5
         for (int q = 0; q < NQF; ++q) {
           const R bb = sB2[q * N2 + j1] * sB2[q * N2 + j2];
 #pragma unroll
-          for (int sl = 0; sl < 6; ++sl) acc[sl] += Jo[(sl * NQF + q) * 4 + j] * bb;
+          for (int sl = 0; sl < 6; ++sl) {
+            const R* jv = Jo + (sl * NQF + q) * 4;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j][sl] += jv[j] * bb;
+          }
         }
 #pragma unroll
-        for (int sl = 0; sl < 6; ++sl) sE[(j * 6 + sl) * N2 * N2 + pr] = acc[sl];
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) sE[(j * 6 + sl) * N2 * N2 + t] = acc[j][sl];
       }
       for (int t = tid; t < 6 * 4 * N2c * N2c; t += nt) {
         const int sl = t / (4 * N2c * N2c), r = t - sl * 4 * N2c * N2c, j = r / (N2c * N2c), pr = r - j * N2c * N2c;
         const int j1 = pr / N2c, j2 = pr - j1 * N2c;
         R acc = R(0);
-#pragma unroll
-        for (int q = 0; q < NQF; ++q) acc += Jx[(sl * NQF + q) * 4 + j] * sB2[q * N2 + j1] * sB2[q * N2 + j2];
+#pragma unroll 5
+        for (int q = 0; q < NQF; ++q) acc += Jx[(sl * NQF + q) * 4 + j] * (sB2[q * N2 + j1] * sB2[q * N2 + j2]);
         sEo[((sl * 4 + j) * N2c + j1) * N2c + j2] = acc;
       }
       __syncthreads();
       if (i < 3) load_jac(i + 1);  // the other buffer, read after the next barrier
-      // the diagonal block's rows of variable i: one thread per (j, n, m), column-major within
-      // the pair (consecutive threads, consecutive rows)
-      R* Dout = a.D + (size_t)e * BS * BS;
-      const double* Dl = a.Dlin + (size_t)e * BS * BS;
-      for (int t = tid; t < 4 * NB * NB; t += nt) {
-        const int j = t / (NB * NB), r = t - j * NB * NB, n = r / NB, m = r - n * NB;
-        R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
-        if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
-        if (i < 3 && j < 3) {
-          // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
-          R cv = R(0);
+      if constexpr (sizeof(R) == 4) {
+        // FP32: one thread per (j, n, m) over the whole CTA, so that many loads of the probed
+        // linear part are in flight (the FP32 assembly waits on memory, not on its arithmetic)
+        R* Dout = a.D + (size_t)e * BS * BS;
+        const double* Dl = a.Dlin + (size_t)e * BS * BS;
+        for (int t = tid; t < 4 * NB * NB; t += nt) {
+          const int j = t / (NB * NB), r = t - j * NB * NB, n = r / NB, m = r - n * NB;
+          R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
+          if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
+          if (i < 3 && j < 3) {
+            // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
+            R cv = R(0);
 #pragma unroll
-          for (int q = 0; q < DW; ++q) {
-            const int o = (j * NB + m) * DW + q;
-            cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
-          }
-          v -= Jd[j] * cv;
-          if (i == j) {
+            for (int q = 0; q < DW; ++q) {
+              const int o = (j * NB + m) * DW + q;
+              cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
+            }
+            v -= Jd[j] * cv;
+            if (i == j) {
 #pragma unroll
-            for (int pp = 0; pp < 3; ++pp) {
-              R c2 = R(0);
+              for (int pp = 0; pp < 3; ++pp) {
+                R c2 = R(0);
 #pragma unroll
-              for (int q = 0; q < DW; ++q) {
-                const int o = (pp * NB + m) * DW + q;
-                c2 += a.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
+                for (int q = 0; q < DW; ++q) {
+                  const int o = (pp * NB + m) * DW + q;
+                  c2 += a.Dcol_val[o] * sU[(pp * NB + a.T.Dcol_idx[o]) * NB + n];
+                }
+                v -= Jd[pp] * c2;
               }
-              v -= Jd[pp] * c2;
             }
           }
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) {
+            const int d = sl >> 1;
+            const R scale = ((sl & 1) ? R(1) : -R(1)) * Jd[d];  // A4 / s^2 = 2 / h_d, sign of the side
+            v += scale * PVN[sl * NB + m] * PVN[sl * NB + n] *
+                 sE[((j * 6 + sl) * N2 + FMN[sl * NB + m]) * N2 + FMN[sl * NB + n]];
+          }
+          Dout[(size_t)(j * NB + n) * BS + i * NB + m] = v;
         }
+        if (nb1 > 0)
+          for (int t = tid; t < 6 * 4 * nb1 * nb1; t += nt) {
+            const int so = t / (4 * nb1 * nb1), r = t - so * 4 * nb1 * nb1, j = r / (nb1 * nb1), r2 = r - j * nb1 * nb1;
+            const int n = r2 / nb1, m = r2 - n * nb1;
+            const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
+            R* blk = a.Bsr + ((size_t)e * 7 + 1 + so) * b1 * b1;
+            if (SI[3 * so + 1] < 0 || SI[3 * so + 2] != so) {
+              blk[o] = R(0);
+              continue;
+            }
+            R v = R(a.Blin[((size_t)e * 7 + 1 + so) * b1 * b1 + o]);
+            for (int sl = so; sl < 6; ++sl) {
+              if (SI[3 * sl + 1] < 0 || SI[3 * sl + 2] != so) continue;
+              v += sScl[sl] * PVN[sl * NB + m] * a.pv[PVO[sl * NB + n]] *
+                   sEo[((sl * 4 + j) * N2c + FMN[sl * NB + m]) * N2c + FMN[sl * NB + n]];
+            }
+            blk[o] = v;
+          }
+      } else if (tid < NDT) {
+        // the diagonal block's rows of variable i: one thread per (j, m), all columns n
+        const int j = tid / NB, m = tid - j * NB;
+        R* Dout = a.D + (size_t)e * BS * BS + i * NB + m;
+        const double* Dl = a.Dlin + (size_t)e * BS * BS + i * NB + m;
+        R pm[6];
+        int fm[6];
 #pragma unroll
         for (int sl = 0; sl < 6; ++sl) {
           const int d = sl >> 1, side = (sl & 1) ? 0 : 1;
-          const R scale = (side == 0 ? R(1) : -R(1)) * Jd[d];  // A4 / s^2 = 2 / h_d
-          v += scale * sPV[side * K1 + FA[d * NB + m]] * sPV[side * K1 + FA[d * NB + n]] *
-               sE[((j * 6 + sl) * N2 + FMAP[d * NB + m]) * N2 + FMAP[d * NB + n]];
+          pm[sl] = (side == 0 ? R(1) : -R(1)) * Jd[d] * PVN[sl * NB + m];  // A4 / s^2 = 2 / h_d
+          fm[sl] = ((j * 6 + sl) * N2 + FMN[sl * NB + m]) * N2;
         }
-        Dout[(size_t)(j * NB + n) * BS + i * NB + m] = v;
-      }
-      // level-1 off-diagonal blocks, rows of variable i, coarse modes only: the linear part of
-      // the slot plus the Riemann terms of every slot facing the same neighbour, in slot order
-      // (a neighbour met on two faces keeps its block at the first slot; the other is zero; a
-      // wall slot is zero)
-      if (nb1 > 0)
-        for (int t = tid; t < 6 * 4 * nb1 * nb1; t += nt) {
+        // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]: rows of U the sparse
+        // derivative picks for (j, m) and, on the diagonal pair, for every p
+        const bool vol = i < 3 && j < 3;
+        int ui[4][DW];
+        R uv[4][DW];
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+          for (int q = 0; q < DW; ++q) {
+            const int dj = pp < 3 ? pp : j;  // slot 3: the off-diagonal term -J_j (D_j^T U_i)
+            const int ci = pp < 3 ? pp : i;
+            const int o = (dj * NB + m) * DW + q;
+            const bool use = vol && (pp == 3 || i == j);
+            ui[pp][q] = use ? (ci * NB + a.T.Dcol_idx[o]) * NB : 0;
+            uv[pp][q] = use ? -a.Dcol_val[o] * (pp < 3 ? Jd[pp] : Jd[j]) : R(0);
+          }
+        const R shift = R(a.inv_gdt * g.sh);
+        for (int n = 0; n < NB; ++n) {
+          R v = R(Dl[(size_t)(j * NB + n) * BS]);
+          if (i == j && i < 3 && m == n) v += shift;
+          if (vol) {
+            R cv = R(0);
+#pragma unroll
+            for (int q = 0; q < DW; ++q) cv += uv[3][q] * sU[ui[3][q] + n];
+            v += cv;
+            if (i == j) {
+#pragma unroll
+              for (int pp = 0; pp < 3; ++pp) {
+                R c2 = R(0);
+#pragma unroll
+                for (int q = 0; q < DW; ++q) c2 += uv[pp][q] * sU[ui[pp][q] + n];
+                v += c2;
+              }
+            }
+          }
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl) v += pm[sl] * PVN[sl * NB + n] * sE[fm[sl] + FMN[sl * NB + n]];
+          Dout[(size_t)(j * NB + n) * BS] = v;
+        }
+      } else if (nb1 > 0) {
+        // level-1 off-diagonal blocks, rows of variable i, coarse modes only: the linear part of
+        // the slot plus the Riemann terms of every slot facing the same neighbour, in slot order
+        // (a neighbour met on two faces keeps its block at the first slot; the other is zero; a
+        // wall slot is zero)
+        for (int t = tid - NDT; t < 6 * 4 * nb1 * nb1; t += nt - NDT) {
           const int so = t / (4 * nb1 * nb1), r = t - so * 4 * nb1 * nb1, j = r / (nb1 * nb1), r2 = r - j * nb1 * nb1;
           const int n = r2 / nb1, m = r2 - n * nb1;
           const size_t o = (size_t)(j * nb1 + n) * b1 + i * nb1 + m;
@@ -257,12 +347,12 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
           R v = R(a.Blin[((size_t)e * 7 + 1 + so) * b1 * b1 + o]);
           for (int sl = so; sl < 6; ++sl) {
             if (SI[3 * sl + 1] < 0 || SI[3 * sl + 2] != so) continue;
-            const int d = sl >> 1, side = (sl & 1) ? 0 : 1, other = 1 - side;
-            v += sScl[sl] * sPV[side * K1 + FA[d * NB + m]] * sPV[other * K1 + FA[d * NB + n]] *
-                 sEo[((sl * 4 + j) * N2c + FMAP[d * NB + m]) * N2c + FMAP[d * NB + n]];
+            v += sScl[sl] * PVN[sl * NB + m] * a.pv[PVO[sl * NB + n]] *
+                 sEo[((sl * 4 + j) * N2c + FMN[sl * NB + m]) * N2c + FMN[sl * NB + n]];
           }
           blk[o] = v;
         }
+      }
       __syncthreads();
     }
   }
