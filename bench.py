@@ -427,7 +427,8 @@ def run_batch(args, P, make_opts, prec, stream, flush, world):
         "workload": "64 independent Taylor-Green boxes [0,2pi]^3, n^3 periodic hexahedra with n ~ U{4..12} and "
                     "k ~ U{2,3,4} (seed 64), p-levels k-2-1 (2-1 for k=2), own acoustic dt (CFL 50) each; one "
                     "linearly implicit stage each from the Taylor-Green field to rel-res 1e-8 with the chosen "
-                    "form's cycle (step = right-hand side, linearisation, assembly and solve of all 64)",
+                    "form's precision, block-Jacobi omega %.2f and sweeps %s (step = right-hand side, "
+                    "linearisation, assembly and solve of all 64)" % (args.batch_omega, args.batch_sweeps),
         "problems_per_degree": {str(k): len(groups[k]) for k in sorted(groups)},
         "elements": sum(d.ne for d in hs), "dofs": ndof,
         "s_per_stage": {"graph": t_graph, "eager": t_eager, "sequential_one_handle_per_problem": t_single},
@@ -995,8 +996,8 @@ def run_ours(args):
     elif "learned_form" in line:
         line["learned_form"].pop("_opts", None)
     if args.batch:
-        line["batch_form"] = run_batch(args, P, lambda: case.opts(chosen_prec, args.omega, args.sweeps), chosen_prec,
-                                       st, flush, world)
+        line["batch_form"] = run_batch(args, P, lambda: case.opts(chosen_prec, args.batch_omega, args.batch_sweeps),
+                                       chosen_prec, st, flush, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, ORACLE_APPS_PER_STAGE[args.config])
         line["cpu_baseline"]["gpu_plain_fp64_operator_applications_per_stage"] = plain["operator_applications"]
@@ -1089,6 +1090,10 @@ def main():
                     help="precision of the chosen form's cycle (h16 / bf16: FP32 cycle with 16-bit block storage; "
                          "h16tc / bf16tc: the same with the volume contractions on the tensor cores)")
     ap.add_argument("--omega", type=float, default=0.95, help="block-Jacobi damping of the chosen form")
+    ap.add_argument("--batch-sweeps", default="3,3,2",
+                    help="pre,post,coarse smoothing iterations of the batch of uneven solves (its small meshes "
+                         "converge best with fewer sweeps)")
+    ap.add_argument("--batch-omega", type=float, default=0.9, help="block-Jacobi damping of the batch")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned coarse correction (trained and timed on the 24^3 mesh)")
     ap.add_argument("--learn-steps", type=int, default=2000)
