@@ -25,6 +25,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Hint: start bringing the 16-byte aligned part of [lo, hi) from global memory into L2 (no data
+// is returned; the later loads of that range hit L2 instead of HBM). [lo, hi) must lie inside
+// one allocation; the range is shrunk to 16-byte boundaries, so it never reaches outside it.
+__device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
+  const unsigned long long a = (reinterpret_cast<unsigned long long>(lo) + 15ull) & ~15ull;
+  const unsigned long long b = reinterpret_cast<unsigned long long>(hi) & ~15ull;
+  if (b > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(b - a)) : "memory");
+}
 // Order this thread's earlier generic-proxy accesses of shared memory (ordinary loads and
 // stores) before later async-proxy accesses of it (a bulk copy that overwrites the same bytes).
 // Every thread that wrote a buffer executes it before the barrier after which one thread

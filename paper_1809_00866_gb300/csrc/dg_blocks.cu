@@ -196,13 +196,14 @@ __device__ __forceinline__ float4 gj_rank4(float4 v, const float4& t, const floa
 // Look-ahead: while the other warps apply panel g's update, warp 0 applies it to group g + 1
 // alone and factors panel g + 1, so the factoring chain is off the critical path. Two barriers
 // per panel. b^3 multiply-adds per block; the row interchanges are undone on the columns at the
-// end, in reverse order.
+// end, as one column permutation applied while the inverse is written out.
 __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
   const int LD = gj_ld(b);
   float* A = reinterpret_cast<float*>(sraw_);  // [b][LD]
   float* Rp = A + (size_t)b * LD;             // [4][LD] the panel's pivot rows before the update
   int* piv = reinterpret_cast<int*>(Rp + 4 * LD);
+  int* colsrc = piv + b;  // [b]
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   const int NG = b / 4;  // float4 column groups = panels
   int RG = (nt - 32) / NG;  // row groups of the update, on warps 1..
@@ -282,19 +283,23 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
         __syncthreads();
       }
     }
-    for (int k = b - 1; k >= 0; --k) {
-      const int p = piv[k];
-      if (p != k)
-        for (int i = tid; i < b; i += nt) {
-          const float t = A[i * LD + k];
-          A[i * LD + k] = A[i * LD + p];
-          A[i * LD + p] = t;
+    // the row interchanges, undone on the columns in reverse order, composed into one column
+    // permutation (column c of the inverse is column colsrc[c] of A) and applied while writing out
+    if (tid == 0) {
+      for (int c = 0; c < b; ++c) colsrc[c] = c;
+      for (int k = b - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k) {
+          const int t = colsrc[k];
+          colsrc[k] = colsrc[p];
+          colsrc[p] = t;
         }
-      __syncthreads();
+      }
     }
+    __syncthreads();
     for (int t = tid; t < b * b; t += nt) {
       const int c = t / b, r = t - c * b;
-      Mb[t] = A[r * LD + c];
+      Mb[t] = A[r * LD + colsrc[c]];
     }
     __syncthreads();
   }
@@ -743,7 +748,7 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
-    const size_t smem = sizeof(float) * ((size_t)(L.b + 4) * gj_ld(L.b)) + sizeof(int) * L.b;
+    const size_t smem = sizeof(float) * ((size_t)(L.b + 4) * gj_ld(L.b)) + sizeof(int) * 2 * L.b;
     if (smem > kSmemLimit || L.b % 4 != 0 || L.b > 32 * kGjSlots)
       return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
     DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));

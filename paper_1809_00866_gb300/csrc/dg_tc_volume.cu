@@ -276,6 +276,14 @@ __global__ void __launch_bounds__(kTcThreads) tc_vol_kernel(TcVolArgs a) {
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * kTcE;
     const int cnt = min(kTcE, ne - e0);
+    if (tid == 0 && tile + (int)gridDim.x < ntiles) {
+      // the next tile's contiguous inputs into L2 while this tile is computed
+      const int n0 = (tile + gridDim.x) * kTcE, n1 = min(ne, n0 + kTcE);
+      prefetch_l2(a.in + (size_t)n0 * 4 * NB, a.in + (size_t)n1 * 4 * NB);
+      prefetch_l2(a.face_lift + (size_t)n0 * 6 * 3 * N2, a.face_lift + (size_t)n1 * 6 * 3 * N2);
+      prefetch_l2(a.ubar + (size_t)n0 * 3 * NQ, a.ubar + (size_t)n1 * 3 * NQ);
+      prefetch_l2(a.face_out + (size_t)n0 * 6 * 4 * N2, a.face_out + (size_t)n1 * 6 * 4 * N2);
+    }
     // 1. input coefficients (FP32, contiguous), element geometry
     for (int t = tid; t < kTcE * 4 * NB; t += nt)
       sC[t] = t < cnt * 4 * NB ? a.in[(size_t)e0 * 4 * NB + t] : 0.0f;
