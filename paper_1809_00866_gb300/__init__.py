@@ -528,11 +528,15 @@ class DG:
         self._chk(self._L.dg_recorded(self.h, ctypes.byref(c)))
         return c.value
 
-    def fgmres_solve(self, g, x, opts=None, stream=None, check=True):
+    def fgmres_solve(self, g, x, opts=None, stream=None, check=True, log=None, **log_fields):
+        """``log``: a path; one JSON line per solve (iterations, residuals, rho, status) is appended."""
         o = opts or solve_opts()
         info = DgSolveInfo()
         rc = self._L.fgmres_solve(self.h, self._ptr(g), self._ptr(x), ctypes.byref(o), ctypes.byref(info),
                                   self._stream(stream))
+        if log is not None:
+            from .checkpoint import log_solve
+            log_solve(log, info, rc, precision=int(o.precision), **log_fields)
         if check and rc not in (DG_OK, DG_ERR_NOT_CONVERGED):
             self._chk(rc)
         return info, rc

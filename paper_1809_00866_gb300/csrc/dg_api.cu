@@ -577,6 +577,7 @@ int dg_project_points(dg_handle* hh, const double* vals, double* w, void* stream
 }
 
 int dg_residual(dg_handle* hh, const double* w, double* f, void* stream) {
+  const dg::NvtxRange nvtx_range_("dg_residual");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!w || !f || w == f) return fail(h, DG_ERR_ARG, "w and f must be distinct non-null device pointers");
@@ -584,6 +585,7 @@ int dg_residual(dg_handle* hh, const double* w, double* f, void* stream) {
 }
 
 int dg_set_linearization(dg_handle* hh, const double* w, double inv_gamma_dt, void* stream) {
+  const dg::NvtxRange nvtx_range_("dg_set_linearization");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!w || !(inv_gamma_dt >= 0.0)) return fail(h, DG_ERR_ARG, "null state or negative 1/(gamma dt)");
@@ -632,6 +634,7 @@ int dg_stage_update(dg_handle* hh, double* w, const double* dw, double b, void* 
 }
 
 int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) {
+  const dg::NvtxRange nvtx_range_("dg_jvp");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!v || !out || v == out) return fail(h, DG_ERR_ARG, "v and out must be distinct non-null device pointers");
@@ -645,6 +648,7 @@ int dg_jvp(dg_handle* hh, const double* v, double* out, int mode, void* stream) 
 }
 
 int dg_assemble_precision(dg_handle* hh, int precision, void* stream) {
+  const dg::NvtxRange nvtx_range_("dg_assemble");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   if (!h->linearized) return fail(h, DG_ERR_STATE, "dg_assemble needs dg_set_linearization first");

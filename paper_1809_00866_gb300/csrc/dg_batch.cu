@@ -663,6 +663,7 @@ const char* dg_plan_error(const dg_plan* pp) {
 }
 
 int dg_plan_solve(dg_plan* pp, void* stream) {
+  const dg::NvtxRange nvtx_range_("dg_plan_solve");
   Plan* P = reinterpret_cast<Plan*>(pp);
   if (!P) return DG_ERR_ARG;
   P->err.clear();

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -202,6 +203,15 @@ struct Handle {
   double prof_ms[DG_PROF_N] = {};
   long long prof_cnt[DG_PROF_N] = {};
   double prof_bytes[DG_PROF_N] = {};
+};
+
+// A named NVTX range for the span of one C-ABI call (visible in Nsight timelines; a no-op when no
+// tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // error helpers

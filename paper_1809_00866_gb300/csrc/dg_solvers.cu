@@ -1013,6 +1013,7 @@ int dg_coarse_apply(dg_handle* hh, const double* d, double* x, int accumulate, v
 }
 
 int pmg_vcycle(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, void* stream) {
+  const dg::NvtxRange nvtx_range_("pmg_vcycle");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   int rc = check_opts(h, opts);
@@ -1094,6 +1095,7 @@ int pmg_level_solve(dg_handle* hh, int lvl, const double* g, double* x, double r
 
 int fgmres_solve(dg_handle* hh, const double* g, double* x, const dg_solve_opts* opts, dg_solve_info* info,
                  void* stream) {
+  const dg::NvtxRange nvtx_range_("fgmres_solve");
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return DG_ERR_ARG;
   int rc = check_opts(h, opts);
