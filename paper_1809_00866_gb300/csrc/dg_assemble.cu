@@ -225,9 +225,10 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
         // linear part are in flight (the FP32 assembly waits on memory, not on its arithmetic)
         R* Dout = a.D + (size_t)e * BS * BS;
         const double* Dl = a.Dlin + (size_t)e * BS * BS;
+#pragma unroll 4
         for (int t = tid; t < 4 * NB * NB; t += nt) {
           const int j = t / (NB * NB), r = t - j * NB * NB, n = r / NB, m = r - n * NB;
-          R v = R(Dl[(size_t)(j * NB + n) * BS + i * NB + m]);
+          R v = R(__ldg(Dl + (size_t)(j * NB + n) * BS + i * NB + m));
           if (i == j && i < 3 && m == n) v += R(a.inv_gdt * g.sh);
           if (i < 3 && j < 3) {
             // -J_j (D_j^T U_i)[m][n] - delta_ij sum_p J_p (D_p^T U_p)[m][n]
@@ -308,8 +309,9 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
             uv[pp][q] = use ? -a.Dcol_val[o] * (pp < 3 ? Jd[pp] : Jd[j]) : R(0);
           }
         const R shift = R(a.inv_gdt * g.sh);
+#pragma unroll 5
         for (int n = 0; n < NB; ++n) {
-          R v = R(Dl[(size_t)(j * NB + n) * BS]);
+          R v = R(__ldg(Dl + (size_t)(j * NB + n) * BS));
           if (i == j && i < 3 && m == n) v += shift;
           if (vol) {
             R cv = R(0);
