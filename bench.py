@@ -77,11 +77,8 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch from Nsight Compute captures of the current kernels, by
 # (profiler class, mesh n, block storage); a kernel changed since its capture has no entry.
 # From one one-pass capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^3 P4 stage
-# with FP16 blocks and 5/5/2 sweeps: the fine-level block-Jacobi sweep moves 1.320 GB when it
-# starts from zero and 1.357 GB when it applies G x first; a cycle's ten fine-level sweeps hold
-# one of the first kind and nine of the second, 1.353 GB per launch on average. The tensor-core
-# volume pass moves 173.6 MB per launch.
-NCU_TRAFFIC = {("bj32_fine", 32, "half"): 1.353e9, ("vol_tc32", 32, "half"): 1.736e8}
+# with FP16 blocks and 5/5/2 sweeps: the tensor-core volume pass moves 173.6 MB per launch.
+NCU_TRAFFIC = {("vol_tc32", 32, "half"): 1.736e8}
 
 
 def measured_peaks():

@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "dg_async.h"
 #include "dg_internal.h"
@@ -453,6 +455,153 @@ __global__ void __launch_bounds__(kJacobiThreads) staged_jacobi_kernel(int ne, i
   }
 }
 
+// The 16-bit block-Jacobi apply for large blocks (b = 140 at P4: a 39.2 KB inverse per element),
+// one element per stage and a ring of up to kPairSlots stages, so that four elements stream in
+// while one is multiplied. Same update as staged_jacobi_kernel. A column pair of the
+// column-major inverse (2 B entries) is B / 4 chunks of 16 bytes, and thread tid reads chunks
+// tid, tid + T, tid + 2 T, ... (T = CS * B / 4): all of them hold the same eight rows (rows of
+// column 2m, of column 2m + 1, or four of each where a chunk straddles the two), so the thread
+// keeps eight row sums in registers, and consecutive threads read consecutive chunks (no bank
+// conflicts). The sums over the even and the odd columns of the CS column slices meet in shared
+// memory. The residual g - Gx is formed where it
+// is used. Per element: one barrier after the stage's wait (it also frees the previous stage's
+// buffer, refilled right after it) and one before the slice reduction.
+constexpr int kPairSlots = 5;
+
+template <class S> __device__ __forceinline__ float2 widen_word(unsigned w);
+template <> __device__ __forceinline__ float2 widen_word<__half>(unsigned w) {
+  __half2 h;
+  memcpy(&h, &w, sizeof(h));
+  return __half22float2(h);
+}
+template <> __device__ __forceinline__ float2 widen_word<__nv_bfloat16>(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));  // exact
+}
+
+template <int B, int NT, class S>
+__global__ void __launch_bounds__(NT) pair_jacobi_kernel(int ne, int ns, const S* __restrict__ A,
+                                                         const float* __restrict__ g, const float* __restrict__ Gx,
+                                                         float alpha, int x_zero, float* __restrict__ x,
+                                                         unsigned* status, unsigned wait_polls, int withhold_first) {
+  static_assert(B % 4 == 0 && sizeof(S) == 2, "16-bit blocks of 4 n rows");
+  constexpr int CP = B / 4;                  // 16-byte chunks per column pair
+  constexpr int NP = B / 2;                  // column pairs
+  constexpr int CS = NT / CP;                // column slices
+  constexpr int PPS = (NP + CS - 1) / CS;    // column pairs per slice (the last ones ragged)
+  constexpr size_t kBlk = (size_t)B * B * 2;
+  constexpr size_t kSlot = kBlk + 3 * B * sizeof(float);  // inverse, then g, Gx, old x
+  static_assert(CS >= 1 && kBlk % 16 == 0 && kSlot % 16 == 0, "stage layout");
+  extern __shared__ __align__(128) unsigned char sraw_[];
+  __shared__ uint64_t bar[kPairSlots];
+  float* red = reinterpret_cast<float*>(sraw_ + (size_t)ns * kSlot);  // [CS][2][B] slice sums
+  const int tid = threadIdx.x;
+  const bool has_gx = Gx != nullptr;
+  if (tid == 0)
+    for (int i = 0; i < ns; ++i) mbar_init(&bar[i], 1);
+  __syncthreads();
+  auto issue = [&](int e, int slot) {
+    unsigned char* sb = sraw_ + (size_t)slot * kSlot;
+    float* v = reinterpret_cast<float*>(sb + kBlk);
+    const unsigned vb = B * sizeof(float);
+    mbar_expect_tx(&bar[slot], (unsigned)kBlk + vb * (1 + (has_gx ? 1 : 0) + (x_zero ? 0 : 1)));
+    bulk_g2s(sb, A + (size_t)e * B * B, (unsigned)kBlk, &bar[slot]);
+    bulk_g2s(v, g + (size_t)e * B, vb, &bar[slot]);
+    if (has_gx) bulk_g2s(v + B, Gx + (size_t)e * B, vb, &bar[slot]);
+    if (!x_zero) bulk_g2s(v + 2 * B, x + (size_t)e * B, vb, &bar[slot]);
+  };
+  // iteration k of this CTA takes element blockIdx.x + k * gridDim.x in slot k % ns (phase k / ns);
+  // thread 0 keeps a bit per slot whose copies are in flight; withhold_first (a test of the
+  // bounded wait) leaves the first element's copies unissued
+  unsigned inflight = 0;
+  if (tid == 0)
+    for (int i = 0; i < ns - 1; ++i) {
+      const int e = blockIdx.x + i * gridDim.x;
+      if (e < ne && !(withhold_first && i == 0)) {
+        issue(e, i);
+        inflight |= 1u << i;
+      }
+    }
+  // the thread's chunk within a column pair, its first column pair, and the rows of its chunk:
+  // entries 0-3 at rows lo_r.. of column 2m + lo_c, entries 4-7 at rows up_r.. of column 2m + up_c
+  const int t = tid % CP, s0 = tid / CP;
+  const bool active = tid < CS * CP;
+  const int lo_c = 8 * t < B ? 0 : 1, lo_r = 8 * t - lo_c * B;
+  const int up_c = 8 * t + 4 < B ? 0 : 1, up_r = 8 * t + 4 - up_c * B;
+  int k = 0;
+  for (int e = blockIdx.x; e < ne; e += gridDim.x, ++k) {
+    const int slot = k % ns;
+    const bool got = mbar_wait(&bar[slot], (unsigned)((k / ns) & 1), wait_polls);
+    if (!__syncthreads_and(got)) {
+      // give up: report, let every copy in flight land (bounded waits with the full limit), then
+      // leave, so that no copy writes this CTA's shared memory after it exits
+      if (tid == 0) {
+        atomicOr(status, (unsigned)DG_STATUS_WAIT);
+        for (int i = 0; i < ns; ++i) {
+          const int sl = (k + i) % ns;
+          if (inflight & (1u << sl)) mbar_wait(&bar[sl], (unsigned)(((k + i) / ns) & 1));
+        }
+      }
+      return;
+    }
+    if (tid == 0) {
+      // every thread is past the previous element (its reads of that slot were fenced against
+      // the async proxy): refill that slot with the element ns - 1 ahead
+      inflight &= ~(1u << slot);
+      const int ahead = e + (ns - 1) * gridDim.x;
+      if (ahead < ne) {
+        const int sl = (k + ns - 1) % ns;
+        issue(ahead, sl);
+        inflight |= 1u << sl;
+      }
+    }
+    const unsigned char* sb = sraw_ + (size_t)slot * kSlot;
+    const uint4* Ab = reinterpret_cast<const uint4*>(sb);
+    const float* gv = reinterpret_cast<const float*>(sb + kBlk);
+    if (active) {
+      float acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < PPS; ++i) {
+        const int m = s0 + i * CS;
+        if (NP % CS == 0 || m < NP) {
+          const uint4 w = Ab[m * CP + t];
+          float2 r = *reinterpret_cast<const float2*>(gv + 2 * m);
+          if (has_gx) {
+            const float2 q = *reinterpret_cast<const float2*>(gv + B + 2 * m);
+            r.x -= q.x;
+            r.y -= q.y;
+          }
+          const float rl = lo_c ? r.y : r.x, ru = up_c ? r.y : r.x;
+          const float2 a0 = widen_word<S>(w.x), a1 = widen_word<S>(w.y);
+          const float2 a2 = widen_word<S>(w.z), a3 = widen_word<S>(w.w);
+          acc[0] = fmaf(a0.x, rl, acc[0]);
+          acc[1] = fmaf(a0.y, rl, acc[1]);
+          acc[2] = fmaf(a1.x, rl, acc[2]);
+          acc[3] = fmaf(a1.y, rl, acc[3]);
+          acc[4] = fmaf(a2.x, ru, acc[4]);
+          acc[5] = fmaf(a2.y, ru, acc[5]);
+          acc[6] = fmaf(a3.x, ru, acc[6]);
+          acc[7] = fmaf(a3.y, ru, acc[7]);
+        }
+      }
+      // every row has one sum over the slice's even columns and one over its odd columns
+      *reinterpret_cast<float4*>(red + (2 * s0 + lo_c) * B + lo_r) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      *reinterpret_cast<float4*>(red + (2 * s0 + up_c) * B + up_r) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+    __syncthreads();
+    const float* xo = gv + 2 * B;
+    for (int r = tid; r < B; r += NT) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int s = 0; s < 2 * CS; ++s) sum += red[s * B + r];
+      x[(size_t)e * B + r] = (x_zero ? 0.0f : xo[r]) + alpha * sum;
+    }
+    // this slot's reads (generic proxy) before the bulk copy that refills it (async proxy)
+    fence_proxy_async_smem();
+  }
+}
+
 // The same row products read straight from global memory: one thread per output row, `epc`
 // elements per CTA (b rows each), the input vectors in shared memory. Loads of one warp cover
 // 32 consecutive rows of a column (coalesced); eight independent accumulators keep eight loads
@@ -612,9 +761,37 @@ int launch_direct7_vec(Handle* h, int b, const S* A, const float* v, float alpha
 constexpr size_t kStageTarget = 96 * 1024;  // bytes of inverses per stage (one buffer)
 constexpr size_t kSmemLimit = 220 * 1024;    // dynamic shared memory a kernel may take
 
+// the 16-bit apply of large blocks, one element per stage (pair_jacobi_kernel); -1: unsuited
+template <int B, class S>
+int launch_pair_jacobi(Handle* h, const S* A, const float* g, const float* Gx, float alpha, int x_zero, float* x,
+                       cudaStream_t st) {
+  constexpr int NT = kJacobiThreads, CS = NT / (B / 4);
+  constexpr size_t slot = (size_t)B * B * 2 + 3 * (size_t)B * sizeof(float);
+  const size_t red = sizeof(float) * 2 * CS * B;
+  const int ns = (int)std::min<size_t>(kPairSlots, (kSmemLimit - red) / slot);
+  if (ns < 2) return -1;
+  const size_t smem = (size_t)ns * slot + red;
+  static bool opted = false;  // per template instance; one device per process
+  if (!opted) {
+    DG_CUDA(h, cudaFuncSetAttribute(pair_jacobi_kernel<B, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemLimit));
+    opted = true;
+  }
+  const int cap = h->tune[1].jacobi_max_ctas;  // 0: one CTA per SM
+  const int grid = std::min(h->ne, cap > 0 ? std::min(cap, h->nsm) : h->nsm);
+  const unsigned polls = h->dbg.wait_polls > 0 ? (unsigned)h->dbg.wait_polls : kBulkWaitLimit;
+  pair_jacobi_kernel<B, NT, S><<<grid, NT, smem, st>>>(h->ne, ns, A, g, Gx, alpha, x_zero, x, h->status, polls,
+                                                      h->dbg.withhold_copy);
+  DG_LAUNCH_CHECK(h);
+  return DG_OK;
+}
+
 template <class R, class S>
 int launch_staged_jacobi(Handle* h, int b, const S* A, const R* g, const R* Gx, R alpha, int x_zero, R* x,
                          cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value && sizeof(S) == 2) {
+    if (b == 140) return launch_pair_jacobi<140, S>(h, A, g, Gx, alpha, x_zero, x, st);
+  }
   const size_t per = (size_t)b * b * sizeof(S);
   const size_t target = h->tune[1].jacobi_stage_kb > 0 ? (size_t)h->tune[1].jacobi_stage_kb * 1024 : kStageTarget;
   int G = (int)std::max<size_t>(1, target / per);

@@ -84,12 +84,14 @@ def test_nonfinite_state_is_reported():
     assert dg.dg_get_status() == 0
 
 
-@pytest.mark.parametrize("storage", ["FP32_H16", "FP32"])
-def test_staged_jacobi_wait_gives_up_and_recovers(storage):
+@pytest.mark.parametrize("levels,storage", [([2, 1], "FP32_H16"), ([2, 1], "FP32"), ([4, 2, 1], "FP32_H16"),
+                                            ([4, 2, 1], "FP32_BF16")])
+def test_staged_jacobi_wait_gives_up_and_recovers(levels, storage):
     # the FP32 cycle's fine-level block-Jacobi apply inside one V-cycle: with the first stage of
-    # every CTA withheld, each CTA's first wait runs out after 2000 polls
+    # every CTA withheld, each CTA's first wait runs out after 2000 polls (at P4 with 16-bit
+    # blocks, the one-element-per-stage apply of 140 x 140 inverses)
     import paper_1809_00866_gb300 as P
-    dg, m = pair(*meshes()["u4"], [2, 1])
+    dg, m = pair(*meshes()["u4"], levels)
     w = O.project_tgv(m)
     inv = 1.0 / S.acoustic_dt(m.nx, m.k)
     g = dg.empty()

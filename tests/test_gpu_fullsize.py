@@ -72,7 +72,7 @@ def test_residual_and_exact_jvp_at_benchmark_size(n):
     assert dg.dg_get_status() == 0
 
 
-@pytest.mark.parametrize("storage,bound", [("FP32", 1e-5), ("FP32_H16", 5e-3)])
+@pytest.mark.parametrize("storage,bound", [("FP32", 1e-5), ("FP32_H16", 5e-3), ("FP32_BF16", 4e-2)])
 def test_fp32_cycle_at_benchmark_size(storage, bound):
     import paper_1809_00866_gb300 as P
     dg, m = _mesh(16)

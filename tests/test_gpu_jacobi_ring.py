@@ -7,7 +7,9 @@ more stages than the ring has buffers, which on the benchmark's 16^3 mesh happen
 times per CTA, but never on small meshes at the default launch shape. A cap on the CTAs
 (dg_tuning.jacobi_max_ctas) makes one or a few CTAs take every stage here, with several stage
 sizes (jacobi_stage_kb): G = 1, 2, 15, 16 and 30 elements, ragged last stages, and the
-column-slice reduction (stages of few rows) as well as the direct path.
+column-slice reduction (stages of few rows) as well as the direct path. With 16-bit blocks of
+140 rows (the P4 fine level of box233) the apply takes one element per stage in a ring of five
+buffers, whatever the stage size asked for; the cap still applies.
 
 Reference: the oracle's V-cycle (Algorithm 2) on its dense operators. The cycle runs its
 fine-level and coarse-level smoothing through this apply. Bounds per block storage, as for the
