@@ -369,11 +369,13 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
     }
     const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    // the geometry along the face's axes, read with selects (no run-time indexing of g0, g1)
-    auto sel3 = [](const double* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
-    const double J0d = sel3(g0.J, d), J1d = sel3(g1.J, d);
-    const double J0t1 = sel3(g0.J, t1), J0t2 = sel3(g0.J, t2);
-    const R A4 = R(0.25 * sel3(g0.h, t1) * sel3(g0.h, t2));
+    // the geometry along the face's axes, read with selects (no run-time indexing of g0, g1), in
+    // the kernel's precision: the FP32 pass does no FP64 arithmetic (GB300's FP64 pipe is 1/64 of
+    // the FP32 rate), the FP64 pass is unchanged
+    auto sel3 = [](const double* v, int i) { return R(i == 0 ? v[0] : (i == 1 ? v[1] : v[2])); };
+    const R J0d = sel3(g0.J, d), J1d = sel3(g1.J, d);
+    const R J0t1 = sel3(g0.J, t1), J0t2 = sel3(g0.J, t2);
+    const R A4 = R(0.25) * sel3(g0.h, t1) * sel3(g0.h, t2);
     const R is0 = R(g0.is), is1 = R(g1.is);
     for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         }
       }
       const R is = side ? is1 : is0;
-      const R js = is * R(side ? J1d : J0d);
+      const R js = is * (side ? J1d : J0d);
       R* tt = sT + j * 8 + side * 4;
 #pragma unroll
       for (int v = 0; v < 4; ++v) tt[v] = val[v] * is;
@@ -486,8 +488,8 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       const int bj = DEG[j];
       // at a wall the lifting lives on the real element alone, with the full jump:
       // (k - bj + 1)^2 / 2 * (2/h_K) * [u]
-      const R lr = wall ? R(0.5 * (double)((K - bj + 1) * (K - bj + 1)) * J0d)
-                        : R(0.125 * (double)((K - bj + 1) * (K - bj + 1)) * (J0d + J1d));
+      const R lr = wall ? R(0.5) * R((K - bj + 1) * (K - bj + 1)) * J0d
+                        : R(0.125) * R((K - bj + 1) * (K - bj + 1)) * (J0d + J1d);
       R jump[3], Gd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         }
         return acc;
       };
-      const R it1 = R(J0t1), it2 = R(J0t2);
+      const R it1 = J0t1, it2 = J0t2;
       // tangential derivatives: the average of both sides, or the real side's at a wall
       const int A0 = wall == 2 ? 1 : 0;
       const int A1 = wall == 1 ? 0 : 1;
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       auto pick = [&](int c) { return c == 0 ? Gd[0] : (c == 1 ? Gd[1] : Gd[2]); };
       const R Gdd = pick(d), Gt1d = pick(t1), Gt2d = pick(t2);
       const R trG = Gdd + Gt1 + Gt2;
-      const R Fvd = R(a.nu) * (2.0 * Gdd - R(2.0 / 3.0) * trG);
+      const R Fvd = R(a.nu) * (R(2) * Gdd - R(2.0 / 3.0) * trG);
       const R Fvt1 = R(a.nu) * (Gt1d + Gdt1);
       const R Fvt2 = R(a.nu) * (Gt2d + Gdt2);
       R Fn[4];
