@@ -250,6 +250,7 @@ static void free_all(Handle* h) {
   F(h->tc_tab[0]); F(h->tc_tab[1]); F(h->ubar_scale);
   for (int d = 0; d < 3; ++d) F(h->dnode[d]);
   F(h->geo);
+  F(h->geof);
   F(h->nbr);
   F(h->elem_prob); F(h->dshift); F(h->chunk); F(h->chunk_prob); F(h->pchunk0); F(h->bface); F(h->bslot);
   F(h->colour);
@@ -268,13 +269,15 @@ static void free_all(Handle* h) {
   F(h->net);
 }
 
-__global__ void write_shifts_kernel(int ne, const int* elem_prob, const double* shift, double* geo) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+__global__ void write_shifts_kernel(int ne, const int* elem_prob, const double* shift, double* geo, float* geof) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
     geo[(size_t)e * kGeo + 11] = shift[elem_prob[e]];
+    geof[(size_t)e * kGeo + 11] = (float)shift[elem_prob[e]];
+  }
 }
 
 static int write_shifts(Handle* h, cudaStream_t st) {
-  write_shifts_kernel<<<(h->ne + 255) / 256, 256, 0, st>>>(h->ne, h->elem_prob, h->dshift, h->geo);
+  write_shifts_kernel<<<(h->ne + 255) / 256, 256, 0, st>>>(h->ne, h->elem_prob, h->dshift, h->geo, h->geof);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -388,6 +391,10 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
       return rc;
   }
   if ((rc = upload(h, &h->geo, geo))) return rc;
+  {
+    const std::vector<float> geof(geo.begin(), geo.end());
+    if ((rc = upload(h, &h->geof, geof))) return rc;
+  }
   if ((rc = build_tables(h, p->k[0]))) return rc;
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->lev[l];

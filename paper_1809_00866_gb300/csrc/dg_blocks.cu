@@ -50,7 +50,7 @@ template <class R> __device__ __forceinline__ void wide2(const __nv_bfloat16* p,
 // The leading dimension of a block in shared memory: a multiple of 4 (float4 rows) that is 4 mod 8,
 // so that a column (stride LD) spreads over 8 banks instead of 2 (LD = b + 4 would be 0 mod 8 at
 // b = 140).
-__host__ __device__ inline int gj_ld(int b) { return (b + 4) % 8 == 4 ? b + 4 : b + 8; }
+__host__ __device__ constexpr int gj_ld(int b) { return (b + 4) % 8 == 4 ? b + 4 : b + 8; }
 
 constexpr int kGjSlots = 5;  // panel rows per lane of the factoring warp: b <= 160
 
@@ -137,7 +137,8 @@ __device__ __forceinline__ void gj_factor_panel(float4 (&pv)[kGjSlots], int b, i
 }
 
 // The panel's four interchanges on every other column group (one lane per group), then its pivot
-// rows of those groups to the buffer Rp.
+// rows of those groups to the buffer Rp, zeroed in A: the panel's update then writes
+// A[P,J] = X A[P,J] into them with the same multiply-adds as every other row.
 __device__ __forceinline__ void gj_interchange(float* A, float* Rp, int LD, int NG, int g, const int (&pq)[4],
                                                int lane) {
   const int k0 = 4 * g;
@@ -154,9 +155,11 @@ __device__ __forceinline__ void gj_interchange(float* A, float* Rp, int LD, int 
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      *reinterpret_cast<float4*>(Rp + q * LD + 4 * j) =
-          *reinterpret_cast<const float4*>(A + (size_t)(k0 + q) * LD + 4 * j);
+    for (int q = 0; q < 4; ++q) {
+      float4* ak = reinterpret_cast<float4*>(A + (size_t)(k0 + q) * LD + 4 * j);
+      *reinterpret_cast<float4*>(Rp + q * LD + 4 * j) = *ak;
+      *ak = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 }
 
@@ -198,18 +201,22 @@ __device__ __forceinline__ float4 gj_rank4(float4 v, const float4& t, const floa
 // Look-ahead: while the other warps apply panel g's update, warp 0 applies it to group g + 1
 // alone and factors panel g + 1, so the factoring chain is off the critical path. Two barriers
 // per panel. b^3 multiply-adds per block; the row interchanges are undone on the columns at the
-// end, as one column permutation applied while the inverse is written out.
-__global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, float* __restrict__ M, unsigned* status) {
+// end, as one column permutation applied while the inverse is written out. BT > 0 fixes b = BT
+// and 512 threads at compile time (the P4 fine level, b = 140): the update's rows are then an
+// unrolled loop with constant shared-memory offsets.
+template <int BT>
+__global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b_arg, float* __restrict__ M,
+                                                            unsigned* status) {
   extern __shared__ __align__(16) unsigned char sraw_[];
+  const int b = BT > 0 ? BT : b_arg;
   const int LD = gj_ld(b);
   float* A = reinterpret_cast<float*>(sraw_);  // [b][LD]
   float* Rp = A + (size_t)b * LD;             // [4][LD] the panel's pivot rows before the update
   int* piv = reinterpret_cast<int*>(Rp + 4 * LD);
   int* colsrc = piv + b;  // [b]
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int tid = threadIdx.x, nt = BT > 0 ? 512 : (int)blockDim.x, lane = tid & 31;
   const int NG = b / 4;  // float4 column groups = panels
-  int RG = (nt - 32) / NG;  // row groups of the update, on warps 1..
-  if (RG > b) RG = b;
+  const int RG = (nt - 32) / NG < b ? (nt - 32) / NG : b;  // row groups of the update, on warps 1..
   const int tu = tid - 32;
   const bool upd = tid >= 32 && tu < NG * RG;
   const int jg = upd ? tu % NG : 0, ig = upd ? tu / NG : 0;
@@ -253,8 +260,7 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
             const int i = lane + 32 * m;
             if (i < b) {
               const float4 t = *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0);
-              const float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                                         : *reinterpret_cast<const float4*>(A + (size_t)i * LD + 4 * j);
+              const float4 v = *reinterpret_cast<const float4*>(A + (size_t)i * LD + 4 * j);
               pv[m] = gj_rank4(v, t, r0, r1, r2, r3);
             } else {
               pv[m] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -272,11 +278,25 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b, flo
         const float4 r1 = *reinterpret_cast<const float4*>(Rp + LD + 4 * jg);
         const float4 r2 = *reinterpret_cast<const float4*>(Rp + 2 * LD + 4 * jg);
         const float4 r3 = *reinterpret_cast<const float4*>(Rp + 3 * LD + 4 * jg);
-        for (int i = ig; i < b; i += RG) {
-          const float4 t = *reinterpret_cast<const float4*>(A + (size_t)i * LD + k0);
-          float4* ai = reinterpret_cast<float4*>(A + (size_t)i * LD + 4 * jg);
-          const float4 v = (i >= k0 && i < k0 + 4) ? make_float4(0.f, 0.f, 0.f, 0.f) : *ai;
-          *ai = gj_rank4(v, t, r0, r1, r2, r3);
+        const float* At = A + ig * LD + k0;
+        float* Av = A + ig * LD + 4 * jg;
+        if constexpr (BT > 0) {
+          constexpr int RGc = (512 - 32) / (BT / 4) < BT ? (512 - 32) / (BT / 4) : BT;
+          constexpr int LDc = gj_ld(BT);
+#pragma unroll
+          for (int u = 0; u < (BT + RGc - 1) / RGc; ++u) {
+            if (BT % RGc == 0 || ig + u * RGc < BT) {
+              const float4 t = *reinterpret_cast<const float4*>(At + u * RGc * LDc);
+              float4* ai = reinterpret_cast<float4*>(Av + u * RGc * LDc);
+              *ai = gj_rank4(*ai, t, r0, r1, r2, r3);
+            }
+          }
+        } else {
+          for (int i = ig; i < b; i += RG, At += RG * LD, Av += RG * LD) {
+            const float4 t = *reinterpret_cast<const float4*>(At);
+            float4* ai = reinterpret_cast<float4*>(Av);
+            *ai = gj_rank4(*ai, t, r0, r1, r2, r3);
+          }
         }
       }
       __syncthreads();
@@ -928,14 +948,20 @@ int invert_levels_f32(Handle* h, cudaStream_t st) {
     const size_t smem = sizeof(float) * ((size_t)(L.b + 4) * gj_ld(L.b)) + sizeof(int) * 2 * L.b;
     if (smem > kSmemLimit || L.b % 4 != 0 || L.b > 32 * kGjSlots)
       return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
-    DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemLimit));
+    DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_kernel<140>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemLimit));
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
     const int grid = std::min(h->ne, h->nsm * per_sm);
     // warp 0 factors; the (column group, row group) pairs of the update on the warps after it:
     // at most 512 threads, at most b row groups
     const int ng = L.b / 4, active = ng * std::min(L.b, 480 / ng);
     const int threads = std::min(512, 32 + 32 * ((active + 31) / 32));
-    gj_inverse_kernel<<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
+    if (L.b == 140 && threads == 512)
+      gj_inverse_kernel<140><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
+    else
+      gj_inverse_kernel<0><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
     DG_LAUNCH_CHECK(h);
   }
   return DG_OK;

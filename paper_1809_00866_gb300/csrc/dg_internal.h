@@ -114,6 +114,7 @@ struct Handle {
   std::vector<double> node[3];  // host node coordinates
   double* dnode[3] = {nullptr, nullptr, nullptr};
   double* geo = nullptr;        // [ne][kGeo] per-element geometry
+  float* geof = nullptr;        // the same in FP32 (read by the FP32 passes)
   int* nbr = nullptr;           // [ne][6] face neighbours -x,+x,-y,+y,-z,+z; -1 across a wall
   std::vector<int> nbr_host;    // host copy of nbr
   // faces: 3 per element (its +x, +y, +z faces; a +y face on a wall has no neighbour), then the
@@ -243,13 +244,14 @@ constexpr int kGeo = 12;
 struct MeshDev {
   int nx, ny, nz, ne;
   const double* geo;  // [ne][kGeo]
+  const float* geof;  // the same in FP32
   const int* nbr;
   int nbf;            // wall faces below the first row (faces 3 ne .. 3 ne + nbf - 1)
   const int* bface;   // [nbf] element above each of them
   const int* bslot;   // [ne] index of the wall face below the element, or -1
 };
 inline MeshDev mesh_dev(const Handle* h) {
-  return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->geo, h->nbr, h->nbf, h->bface, h->bslot};
+  return MeshDev{h->n[0], h->n[1], h->n[2], h->ne, h->geo, h->geof, h->nbr, h->nbf, h->bface, h->bslot};
 }
 
 struct ElemGeom {
@@ -260,6 +262,16 @@ struct ElemGeom {
   double J[3];   // 2/h
   double sh;     // multiplier of the mass shift
 };
+// the geometry row of element e in the arithmetic type R (FP32 passes read the FP32 copy, so
+// that they convert nothing on GB300's narrow FP64 pipe): h[0..2] at 0, s at 3, 1/s at 4,
+// 2/h[0..2] at 5, lower corner at 8, mass-shift multiplier at 11
+template <class R> __device__ __forceinline__ const R* geo_row(const MeshDev& M, int e);
+template <> __device__ __forceinline__ const double* geo_row<double>(const MeshDev& M, int e) {
+  return M.geo + (size_t)e * kGeo;
+}
+template <> __device__ __forceinline__ const float* geo_row<float>(const MeshDev& M, int e) {
+  return M.geof + (size_t)e * kGeo;
+}
 __device__ __forceinline__ ElemGeom elem_geom(const MeshDev& M, int e) {
   ElemGeom g;
   const double* G = M.geo + (size_t)e * kGeo;

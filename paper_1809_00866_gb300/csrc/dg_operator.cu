@@ -31,6 +31,7 @@
 // gradient (Sec. 2.1).
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "dg_internal.h"
 
@@ -344,6 +345,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
   for (int t = tid; t < 3 * N2 * K1; t += blockDim.x) M3[t] = a.T.M3[t];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
+  const R nu = R(a.nu), eta = R(a.eta);
   R* W = sm + warp * L::WARP;
   R* sC = W + L::C;
   R* sT = W + L::T;
@@ -367,16 +369,17 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       d = 1;
       wall = 2;
     }
-    const ElemGeom g0 = elem_geom(a.M, e0), g1 = elem_geom(a.M, e1);
+    const R* g0 = geo_row<R>(a.M, e0);
+    const R* g1 = geo_row<R>(a.M, e1);
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    // the geometry along the face's axes, read with selects (no run-time indexing of g0, g1), in
-    // the kernel's precision: the FP32 pass does no FP64 arithmetic (GB300's FP64 pipe is 1/64 of
-    // the FP32 rate), the FP64 pass is unchanged
-    auto sel3 = [](const double* v, int i) { return R(i == 0 ? v[0] : (i == 1 ? v[1] : v[2])); };
-    const R J0d = sel3(g0.J, d), J1d = sel3(g1.J, d);
-    const R J0t1 = sel3(g0.J, t1), J0t2 = sel3(g0.J, t2);
-    const R A4 = R(0.25) * sel3(g0.h, t1) * sel3(g0.h, t2);
-    const R is0 = R(g0.is), is1 = R(g1.is);
+    // the geometry along the face's axes, read with selects (no run-time indexing), in the
+    // kernel's precision: the FP32 pass does no FP64 arithmetic or conversion (GB300's FP64 pipe
+    // is 1/64 of the FP32 rate); the FP64 pass reads the same values as before
+    auto sel3 = [](const R* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
+    const R J0d = sel3(g0 + 5, d), J1d = sel3(g1 + 5, d);
+    const R J0t1 = sel3(g0 + 5, t1), J0t2 = sel3(g0 + 5, t2);
+    const R A4 = R(0.25) * sel3(g0, t1) * sel3(g0, t2);
+    const R is0 = g0[4], is1 = g1[4];
     for (int t = lane; t < 8 * NB; t += 32) {
       const int side = t / (4 * NB), r = t - side * 4 * NB;
       sC[t] = a.in[(size_t)(side ? e1 : e0) * 4 * NB + r];
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         // [u] = u_K - u_K' inside; at a wall u_K - f (upper) or f - u_K (lower), half the
         // difference of the real and the mirrored ghost traces
         jump[c] = (wall ? R(0.5) : R(1)) * (tr(0, c, j) - tr(1, c, j));
-        Gd[c] = R(0.5) * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - R(a.eta) * lr * jump[c];  // Ghat[c][d]
+        Gd[c] = R(0.5) * (sN[c * N2 + j] + sN[3 * N2 + c * N2 + j]) - eta * lr * jump[c];  // Ghat[c][d]
       }
       // tangential derivatives (2D modal) of the normal component and of the tangential ones
       auto tder = [&](int s2, int v, int dir) {
@@ -520,9 +523,9 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       auto pick = [&](int c) { return c == 0 ? Gd[0] : (c == 1 ? Gd[1] : Gd[2]); };
       const R Gdd = pick(d), Gt1d = pick(t1), Gt2d = pick(t2);
       const R trG = Gdd + Gt1 + Gt2;
-      const R Fvd = R(a.nu) * (R(2) * Gdd - R(2.0 / 3.0) * trG);
-      const R Fvt1 = R(a.nu) * (Gt1d + Gdt1);
-      const R Fvt2 = R(a.nu) * (Gt2d + Gdt2);
+      const R Fvd = nu * (R(2) * Gdd - R(2.0 / 3.0) * trG);
+      const R Fvt1 = nu * (Gt1d + Gdt1);
+      const R Fvt2 = nu * (Gt2d + Gdt2);
       R Fn[4];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -1086,6 +1089,32 @@ static OpArgsT<float> make_args_f(Handle* h, const float* in, float* out) {
   return a;
 }
 
+// CTAs of `kernel` that one SM holds at once (registers, shared memory and threads), cached per
+// (kernel, block size): the grids below are one wave of the GPU, so that no SM runs a second,
+// thinner wave of a grid-stride loop
+template <class Kern>
+static int resident_ctas(Kern kernel, int threads, size_t smem) {
+  struct Entry {
+    const void* fn;
+    int threads;
+    size_t smem;
+    int n;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lk(mu);
+  for (const Entry& c : cache)
+    if (c.fn == fn && c.threads == threads && c.smem == smem) return c.n;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 0;  // unknown: the caller keeps its own bound
+  }
+  cache.push_back(Entry{fn, threads, smem, n});
+  return n;
+}
+
 // Launch shapes of the tangent passes (the hot products of the solver): faces per CTA of the face
 // pass, threads per CTA of the volume pass, CTAs per SM of each (0: as many as shared memory
 // allows, at most 8 / 12). Every output entry is computed by the same arithmetic in the same order
@@ -1096,6 +1125,8 @@ static int launch_face(Handle* h, const OpArgsT<R>& a, int per_sm_cap, cudaStrea
   DG_CUDA(h, cudaFuncSetAttribute(face_kernel<K, MODE, R, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
   int per_sm = (int)((200 * 1024) / fs);
   per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+  const int res = resident_ctas(face_kernel<K, MODE, R, FW>, 32 * FW, fs);
+  if (res > 0 && per_sm > res) per_sm = res;
   if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
   const int fblocks = (3 * h->ne + h->nbf + FW - 1) / FW;
   int gf = h->nsm * per_sm;
@@ -1113,6 +1144,8 @@ static int run_operator(Handle* h, const OpArgsT<R>& a, cudaStream_t st, bool fa
   DG_CUDA(h, cudaFuncSetAttribute(vol_kernel<K, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs));
   int per_sm_v = (int)((200 * 1024) / vs);
   per_sm_v = per_sm_v < 1 ? 1 : (per_sm_v > 12 ? 12 : per_sm_v);
+  const int res_v = resident_ctas(vol_kernel<K, MODE, R>, tu.vol_threads, vs);
+  if (res_v > 0 && per_sm_v > res_v) per_sm_v = res_v;
   if (tu.vol_per_sm > 0 && per_sm_v > tu.vol_per_sm) per_sm_v = tu.vol_per_sm;
   int gv = h->nsm * per_sm_v;
   if (gv > h->ne) gv = h->ne;
