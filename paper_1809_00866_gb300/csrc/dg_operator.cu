@@ -293,25 +293,37 @@ __device__ __forceinline__ void load8g(const double* p, double* o) {
   }
 }
 
+__device__ __forceinline__ void store8(float* p, const float* v) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store8(double* p, const double* v) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
 constexpr int kFaceWarps = 4;  // default faces per CTA, one warp each (the tangent pass's is tunable)
 
 template <int K, class R = double, int FW = kFaceWarps>
 struct FaceSmem {
   using S = Sz2<K>;
   // per warp
-  static constexpr int C = 0;                           // [2][4][NB] coefficients of K and K'
+  static constexpr int C = 0;                           // [2][4][NB] coefficients of K and K'; later the
+                                                        // partial sums of the two sum-factorised steps
   static constexpr int T = C + 8 * S::NB;               // [N2][2][4] value traces (a 2D mode's 8 together)
   static constexpr int N = T + 8 * S::N2;               // [2][3][N2] normal-derivative traces of velocity
   static constexpr int F = N + 6 * S::N2;               // [4][NQF] weighted Riemann flux
   static constexpr int P = F + 4 * S::NQF;              // [4][N2] its projection
   static constexpr int WARP = (P + 4 * S::N2 + 3) / 4 * 4;  // 16-byte multiple (vector loads of T)
   // per CTA tables (after the warps)
-  static constexpr int B2 = FW * WARP;                  // [NQF][N2]
-  static constexpr int W2 = B2 + S::NQF * S::N2;        // [NQF]
+  static constexpr int B2 = FW * WARP;                  // [NQF][N2] (the FP32 pass's dense 2D tables)
+  static constexpr int W2 = B2 + (sizeof(R) == 4 ? S::NQF * S::N2 : 0);  // [NQF]
   static constexpr int PV = W2 + S::NQF;                // [2][K+1]
   static constexpr int PD = PV + 2 * (K + 1);           // [2][K+1]
   static constexpr int D2V = PD + 2 * (K + 1);          // [2][N2][kDw]
-  static constexpr int DOUBLES = D2V + 2 * S::N2 * Tables::kDw;
+  static constexpr int L1 = D2V + 2 * S::N2 * Tables::kDw;  // [K+1][N1] P_hat_a at the 1D Gauss points
+  static constexpr int DOUBLES = L1 + (K + 1) * S::N1;
+  static_assert(8 * (K + 1) * S::N1 <= 8 * S::NB && 4 * (K + 1) * S::N1 <= 8 * S::NB, "partial sums fit in C");
   // ints after the doubles
   static constexpr int M3 = 0;                          // [3][N2][K+1]
   static constexpr int D2I = M3 + 3 * S::N2 * (K + 1);  // [2][N2][kDw]
@@ -327,22 +339,28 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
   constexpr int NB = S::NB, NQF = S::NQF, N2 = S::N2, K1 = K + 1, DW = Tables::kDw;
   extern __shared__ __align__(16) unsigned char smraw_[];
   R* sm = reinterpret_cast<R*>(smraw_);
-  R* B2 = sm + L::B2;
   R* W2 = sm + L::W2;
   R* PV = sm + L::PV;
   R* PD = sm + L::PD;
   R* D2V = sm + L::D2V;
+  R* sL1 = sm + L::L1;
+  R* B2 = sm + L::B2;
+  // the FP64 pass (bound by GB300's FP64 pipe) takes the face points by sum factorisation, 40 %
+  // fewer multiply-adds; the FP32 pass, bound by issue and latency, keeps the dense 2D tables
+  constexpr bool kSumFact = sizeof(R) == 8;
   int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
   int* M3 = ism + L::M3;
   int* D2I = ism + L::D2I;
   int* DEG = ism + L::DEG;
   const int tid = threadIdx.x;
   for (int t = tid; t < N2; t += blockDim.x) DEG[t] = a.T.pab[2 * t] + a.T.pab[2 * t + 1];
-  for (int t = tid; t < NQF * N2; t += blockDim.x) B2[t] = a.rt.B2[t];
   for (int t = tid; t < NQF; t += blockDim.x) W2[t] = a.rt.W2[t];
   for (int t = tid; t < 2 * K1; t += blockDim.x) { PV[t] = a.rt.pv[t]; PD[t] = a.rt.pd[t]; }
   for (int t = tid; t < 2 * N2 * DW; t += blockDim.x) { D2V[t] = a.rt.D2_val[t]; D2I[t] = a.T.D2_idx[t]; }
   for (int t = tid; t < 3 * N2 * K1; t += blockDim.x) M3[t] = a.T.M3[t];
+  for (int t = tid; t < K1 * K1; t += blockDim.x) sL1[t] = a.rt.L1[t];
+  if constexpr (!kSumFact)
+    for (int t = tid; t < NQF * N2; t += blockDim.x) B2[t] = a.rt.B2[t];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
   const R nu = R(a.nu), eta = R(a.eta);
@@ -426,21 +444,55 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       for (int c = 0; c < 3; ++c) sN[gs * 3 * N2 + c * N2 + j] = sN[rs * 3 * N2 + c * N2 + j];
     }
     __syncwarp();
-    // one lane per face point: the point values of both sides (kept in registers) and the
-    // Riemann flux, or its linearisation, at that point
+    // point values by sum factorisation over the face's two axes (the 2D basis at point
+    // q = (q1, q2) is P_hat_a(x_q1) P_hat_b(x_q2)): first U[a][q2] = sum_b P_hat_b(x_q2) T[(a, b)], one lane per
+    // (a, q2), for the 8 traces of a mode together; the coefficients in C are dead by now
+    R* sU = W + L::C;  // [K+1][N1][8]
+    if (kSumFact && lane < NQF) {
+      const int a0 = lane / K1, q2 = lane - a0 * K1;
+      R u[8];
+#pragma unroll
+      for (int s8 = 0; s8 < 8; ++s8) u[s8] = R(0);
+#pragma unroll
+      for (int b = 0; b <= K; ++b) {
+        if (a0 + b <= K) {
+          const int j = (a0 + b) * (a0 + b + 1) / 2 + b;  // graded 2D order: degree, then b
+          const R l = sL1[b * K1 + q2];
+          R tt[8];
+          load8(sT + j * 8, tt);
+#pragma unroll
+          for (int s8 = 0; s8 < 8; ++s8) u[s8] += l * tt[s8];
+        }
+      }
+      store8(sU + lane * 8, u);
+    }
+    if constexpr (kSumFact) __syncwarp();
+    // one lane per face point q = (q1, q2): the point values of both sides (kept in registers),
+    // sum_a P_hat_a(x_q1) U[a][q2], and the Riemann flux, or its linearisation, at that point
     if (lane < NQF) {
-      const int q = lane;
+      const int q = lane, q1 = q / K1, q2 = q - q1 * K1;
       R pvq[8];
 #pragma unroll
       for (int s8 = 0; s8 < 8; ++s8) pvq[s8] = R(0);
-      const R* b = B2 + q * N2;
+      if constexpr (kSumFact) {
 #pragma unroll
-      for (int j = 0; j < N2; ++j) {
-        const R bj = b[j];
-        R tt[8];
-        load8(sT + j * 8, tt);
+        for (int a0 = 0; a0 <= K; ++a0) {
+          const R l = sL1[a0 * K1 + q1];
+          R tt[8];
+          load8(sU + (a0 * K1 + q2) * 8, tt);
 #pragma unroll
-        for (int s8 = 0; s8 < 8; ++s8) pvq[s8] += bj * tt[s8];
+          for (int s8 = 0; s8 < 8; ++s8) pvq[s8] += l * tt[s8];
+        }
+      } else {
+        const R* b = B2 + q * N2;  // dense: sum over the 2D modes
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const R bj = b[j];
+          R tt[8];
+          load8(sT + j * 8, tt);
+#pragma unroll
+          for (int s8 = 0; s8 < 8; ++s8) pvq[s8] += bj * tt[s8];
+        }
       }
       R uL[3] = {pvq[0], pvq[1], pvq[2]};
       R uR[3] = {pvq[4], pvq[5], pvq[6]};
@@ -473,12 +525,31 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       for (int i = 0; i < 4; ++i) sF[i * NQF + q] = Fc[i] * W2[q];
     }
     __syncwarp();
-    for (int t = lane; t < 4 * N2; t += 32) {
-      const int i = t / N2, j = t - i * N2;
-      const R* Fi = sF + i * NQF;
+    // projection onto the 2D modes, sum factorised the other way round: S[i][a][q2] =
+    // sum_q1 P_hat_a(x_q1) F_i(q1, q2), then P[i][(a, b)] = sum_q2 P_hat_b(x_q2) S[i][a][q2]
+    R* sS = W + L::C;  // [4][K+1][N1]; the point-value partial sums are dead by now
+    for (int t = lane; kSumFact && t < 4 * NQF; t += 32) {
+      const int i = t / NQF, r = t - i * NQF, a0 = r / K1, q2 = r - a0 * K1;
+      const R* Fi = sF + i * NQF + q2;
       R acc = R(0);
 #pragma unroll
-      for (int q = 0; q < NQF; ++q) acc += B2[q * N2 + j] * Fi[q];
+      for (int q1 = 0; q1 < K1; ++q1) acc += sL1[a0 * K1 + q1] * Fi[q1 * K1];
+      sS[t] = acc;
+    }
+    if constexpr (kSumFact) __syncwarp();
+    for (int t = lane; t < 4 * N2; t += 32) {
+      const int i = t / N2, j = t - i * N2;
+      R acc = R(0);
+      if constexpr (kSumFact) {
+        const int deg = DEG[j], b = j - deg * (deg + 1) / 2, a0 = deg - b;
+        const R* Si = sS + (i * K1 + a0) * K1;
+#pragma unroll
+        for (int q2 = 0; q2 < K1; ++q2) acc += sL1[b * K1 + q2] * Si[q2];
+      } else {
+        const R* Fi = sF + i * NQF;
+#pragma unroll
+        for (int q = 0; q < NQF; ++q) acc += B2[q * N2 + j] * Fi[q];
+      }
       sP[t] = acc;
     }
     __syncwarp();
