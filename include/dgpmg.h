@@ -485,7 +485,8 @@ int dg_plan_destroy(dg_plan* plan);
 #define DG_TUNE_FP32 1  /* the FP32 Jacobian action and block-Jacobi apply of the FP32 cycle */
 typedef struct dg_tuning {
   int face_warps;        /* faces per CTA of the face pass (one warp each): 2, 4 or 8 (default 4) */
-  int vol_threads;       /* threads per CTA of the volume pass (one element per CTA): 64, 128 or 256 (128) */
+  int vol_threads;       /* threads per CTA of the volume pass (one element per CTA): 64, 128, 160, 192
+                            or 256 (128) */
   int face_ctas_per_sm;  /* cap on resident CTAs per SM of the face pass, 0..32 (0: shared memory decides) */
   int vol_ctas_per_sm;   /* the same for the volume pass */
   int jacobi_stage_kb;   /* FP32 cycle: KB of element inverses per bulk-copy stage of the fine-level
@@ -504,7 +505,7 @@ int dg_set_tuning(dg_handle* h, int which, const dg_tuning* t);
 
 /* Measure the candidate shapes on h (CUDA events around the real kernels at h's current
  * linearisation; for DG_TUNE_FP32 the block-Jacobi stages too when an FP32 assembly exists) and
- * keep the fastest per kernel. The candidates: face_warps 2/4/8; vol_threads 64/128/256 with no
+ * keep the fastest per kernel. The candidates: face_warps 2/4/8; vol_threads 64/128/160/192/256 with no
  * CTA cap and with 4 CTAs per SM; jacobi_stage_kb 48/96/144/200. use_cache != 0: reuse the result
  * of an earlier call in this process on the same (which, k, N_q, SM count, log2 N_e, block
  * storage). report: NULL or HOST [6] = device ms per launch of the default and of the chosen face

@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
         // R^K_b(u_av): liftings of the faces normal to b, K on side 1 (slot 2b) and side 0 (slot 2b+1)
         const int j2 = FMAP[b * NB + m], ex = FA[b * NB + m];
         const R r = PV[K1 + ex] * Lf[(2 * b) * 3 * N2 + av * N2 + j2] + PV[ex] * Lf[(2 * b + 1) * 3 * N2 + av * N2 + j2];
-        sG[t] = acc * Jd[b] - r;
+        sG[t] = acc * (b == 0 ? Jd[0] : (b == 1 ? Jd[1] : Jd[2])) - r;  // selects: no local memory
       }
     }
     if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output

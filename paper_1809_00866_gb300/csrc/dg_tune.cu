@@ -34,7 +34,8 @@ static int ilog2(long long v) {
 
 static int valid(const dg_tuning* t) {
   return t && (t->face_warps == 2 || t->face_warps == 4 || t->face_warps == 8) &&
-         (t->vol_threads == 64 || t->vol_threads == 128 || t->vol_threads == 256) && t->face_ctas_per_sm >= 0 &&
+         (t->vol_threads == 64 || t->vol_threads == 128 || t->vol_threads == 160 || t->vol_threads == 192 ||
+          t->vol_threads == 256) && t->face_ctas_per_sm >= 0 &&
          t->face_ctas_per_sm <= 32 && t->vol_ctas_per_sm >= 0 && t->vol_ctas_per_sm <= 32 &&
          t->jacobi_stage_kb >= 8 && t->jacobi_stage_kb <= 224 && t->jacobi_max_ctas >= 0 &&
          t->jacobi_max_ctas <= 4096;
@@ -125,16 +126,17 @@ static int autotune(Handle* h, int which, bool use_cache, double* report, cudaSt
     auto op = [&]() -> int { return f32 ? op_tangent_f32(h, xf, yf, 0, st) : op_tangent(h, L0.t0, L0.t1, st); };
     const int cf = f32 ? DG_PROF_FACE_TAN32 : DG_PROF_FACE_TAN, cv = f32 ? DG_PROF_VOL_TAN32 : DG_PROF_VOL_TAN;
     const int face_w[3] = {2, 4, 8};
-    const int vol_t[3] = {64, 128, 256};
+    // 160 threads: one pass over the 4 N_b outputs of the last volume phase at P4 (140)
+    const int vol_t[5] = {64, 128, 160, 192, 256};
     const int vol_cap[2] = {0, 4};
     double ms[DG_PROF_N];
-    // six operator configurations: face shape i % 3 (timed for i < 3), volume shape i
-    for (int i = 0; i < 6; ++i) {
+    // ten operator configurations: face shape i % 3 (timed for i < 3), volume shape i
+    for (int i = 0; i < 10; ++i) {
       OpTune t = base;
       t.face_warps = face_w[i % 3];
       t.face_per_sm = 0;
-      t.vol_threads = vol_t[i % 3];
-      t.vol_per_sm = vol_cap[i / 3];
+      t.vol_threads = vol_t[i % 5];
+      t.vol_per_sm = vol_cap[i / 5];
       h->tune[which] = t;
       if ((r = time_classes(h, op, 5, ms, st))) return r;
       if (i < 3 && ms[cf] < best_f) { best_f = ms[cf]; best.face_warps = t.face_warps; best.face_per_sm = 0; }

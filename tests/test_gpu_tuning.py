@@ -28,7 +28,8 @@ def setup(name, levels, precision):
 
 
 SHAPES = [dict(face_warps=fw, vol_threads=vt, face_ctas_per_sm=fc, vol_ctas_per_sm=vc, jacobi_stage_kb=kb)
-          for (fw, vt), (fc, vc), kb in itertools.product([(2, 64), (4, 128), (8, 256)], [(0, 0), (1, 3)],
+          for (fw, vt), (fc, vc), kb in itertools.product([(2, 64), (4, 128), (8, 256), (4, 160), (2, 192)],
+                                                          [(0, 0), (1, 3)],
                                                           [16, 96, 200])]
 
 
@@ -79,7 +80,7 @@ def test_autotune_keeps_results_and_caches():
         if which == P.DG_TUNE_FP32:
             assert 0 < rep["jacobi_chosen_ms"] <= rep["jacobi_default_ms"]
         t = dg.dg_get_tuning(which).as_dict()
-        assert t["face_warps"] in (2, 4, 8) and t["vol_threads"] in (64, 128, 256)
+        assert t["face_warps"] in (2, 4, 8) and t["vol_threads"] in (64, 128, 160, 192, 256)
     out = dg.empty()
     dg.pmg_vcycle(g, out, opts)
     assert np.array_equal(host(out), host(ref))
