@@ -706,6 +706,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
     const R is = R(g.is);
+    const R shift = R(a.inv_gdt * g.sh);  // the mass shift's multiplier (tangent mode)
     const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
     for (int t = tid; t < 4 * NB; t += nt) sC[t] = a.in[(size_t)e * 4 * NB + t];
     __syncthreads();
@@ -938,7 +939,8 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
             R acc = R(0);
   #pragma unroll
             for (int q2 = 0; q2 < N1; ++q2) acc += Lr[pc][q2] * v[q2];
-            sCv[sp * NB + row[pc]] = acc * R(g.s);
+            const int m = row[pc];
+            sCv[sp * NB + m] = (sp < 3 ? sFv[sp * NB + m] - sC[3 * NB + m] : sFv[sp * NB + m]) - acc * R(g.s);
           }
       }
     } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
@@ -949,7 +951,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
         R acc = R(0);
   #pragma unroll
         for (int q2 = 0; q2 < N1; ++q2) acc += L1[pc * N1 + q2] * s2[q2];
-        sCv[t] = acc * R(g.s);
+        sCv[t] = (sp < 3 ? sFv[t] - sC[3 * NB + m] : sFv[t]) - acc * R(g.s);
       }
     }
     __syncthreads();
@@ -969,7 +971,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
               const int sp = sym_index(pp, i);
-              s2[i] += dv * (sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0)));
+              s2[i] += dv * sCv[sp * NB + n];
             }
             s2[3] += dv * (-sC[pp * NB + n]);
           }
@@ -986,7 +988,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          if (MODE == MODE_TAN && i < 3) acc[i] += R(a.inv_gdt * g.sh) * sC[i * NB + m];
+          if (MODE == MODE_TAN && i < 3) acc[i] += shift * sC[i * NB + m];
           nonfinite |= !isfinite(acc[i]);
           a.out[(size_t)e * 4 * NB + i * NB + m] = acc[i];
         }
@@ -1002,13 +1004,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
           for (int j = 0; j < DW; ++j) {
             const int o = (pp * NB + m) * DW + j;
             const int n = a.T.Dcol_idx[o];
-            R fld;
-            if (i < 3) {
-              const int sp = sym_index(pp, i);
-              fld = sFv[sp * NB + n] - sCv[sp * NB + n] - (pp == i ? sC[3 * NB + n] : R(0));
-            } else {
-              fld = -sC[pp * NB + n];
-            }
+            const R fld = i < 3 ? sCv[sym_index(pp, i) * NB + n] : -sC[pp * NB + n];
             s2 += a.rt.Dcol_val[o] * fld;
           }
           acc += Jd[pp] * s2;
@@ -1018,7 +1014,7 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
           const int dd = sl >> 1, side = (sl & 1) ? 0 : 1;
           acc += PV[side * K1 + FA[dd * NB + m]] * FO[sl * 4 * N2 + i * N2 + FMAP[dd * NB + m]];
         }
-        if (MODE == MODE_TAN && i < 3) acc += R(a.inv_gdt * g.sh) * sC[t];
+        if (MODE == MODE_TAN && i < 3) acc += shift * sC[t];
         nonfinite |= !isfinite(acc);
         a.out[(size_t)e * 4 * NB + t] = acc;
       }

@@ -2,7 +2,8 @@
 
     python profile_workloads.py jv [--n 16] [--reps 3]
         TGV n^3 P4 handle (levels 4-2-1), linearisation at the TGV field, `reps` exact
-        Jacobian actions (face_kernel + vol_kernel per action).
+        Jacobian actions (face_kernel + vol_kernel per action) after a warm-up one, between
+        cudaProfilerStart/Stop.
     python profile_workloads.py assemble [--n 16] [--form fp32|fp64]
         one preconditioner assembly after a warm-up one, between cudaProfilerStart/Stop.
     python profile_workloads.py stage [--n 16] [--form fp32|fp64|h16|bf16|h16tc|bf16tc] [--learned]
@@ -50,12 +51,16 @@ def main(argv=None):
         dg.dg_set_linearization(w, inv)
         v = torch.from_numpy(S.direction(dg.ne, levels[0], S.SEED_V)).cuda()
         out = dg.empty()
+        dg.dg_jvp(v, out)  # warm-up, outside the profiled window
         torch.cuda.synchronize()
+        torch.cuda.profiler.start()
         t0 = time.perf_counter()
         for _ in range(a.reps):
             dg.dg_jvp(v, out)
         torch.cuda.synchronize()
-        print("jv: %d actions, %.3f ms each" % (a.reps, 1e3 * (time.perf_counter() - t0) / a.reps))
+        t = time.perf_counter() - t0
+        torch.cuda.profiler.stop()
+        print("jv: %d actions, %.3f ms each" % (a.reps, 1e3 * t / a.reps))
         return 0
     if a.what == "assemble":
         prec = DG_PRECOND_FP64 if a.form == "fp64" else DG_PRECOND_FP32
