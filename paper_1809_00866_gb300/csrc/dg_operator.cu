@@ -785,12 +785,17 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
     }
     __syncthreads();
     // (B) viscous flux coefficients; interpolation step 2
-    for (int t = tid; t < 6 * NB; t += nt) {
-      const int sp = t / NB, m = t - sp * NB;
-      int p, i;
-      if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
-      const R trG = sG[0 * NB + m] + sG[4 * NB + m] + sG[8 * NB + m];
-      sFv[t] = R(a.nu) * (sG[(i * 3 + p) * NB + m] + sG[(p * 3 + i) * NB + m] - (p == i ? R(2.0 / 3.0) * trG : R(0)));
+    // one thread per mode for the six symmetric pairs (p, i): nu (G_ip + G_pi - 2/3 delta_pi tr G)
+    for (int m = tid; m < NB; m += nt) {
+      const R nu = R(a.nu);
+      const R g00 = sG[0 * NB + m], g11 = sG[4 * NB + m], g22 = sG[8 * NB + m];
+      const R c23 = R(2.0 / 3.0) * (g00 + g11 + g22);
+      sFv[0 * NB + m] = nu * (g00 + g00 - c23);
+      sFv[1 * NB + m] = nu * (g11 + g11 - c23);
+      sFv[2 * NB + m] = nu * (g22 + g22 - c23);
+      sFv[3 * NB + m] = nu * (sG[(1 * 3 + 0) * NB + m] + sG[(0 * 3 + 1) * NB + m]);  // (p, i) = (0, 1)
+      sFv[4 * NB + m] = nu * (sG[(2 * 3 + 0) * NB + m] + sG[(0 * 3 + 2) * NB + m]);  // (0, 2)
+      sFv[5 * NB + m] = nu * (sG[(2 * 3 + 1) * NB + m] + sG[(1 * 3 + 2) * NB + m]);  // (1, 2)
     }
     if constexpr (sizeof(R) == 4) {  // FP32: pencils, fewer instructions per output
       for (int t = tid; t < 3 * K1 * N1; t += nt) {  // pencil (field, a, q2): all q1
@@ -861,14 +866,25 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) a.ubar[((size_t)e * 3 + c) * NQ + q] = u[c];
       }
+      // the weight goes on the velocity (or its variation) first: u_w = w_q u
       const R wq = W3[q];
+      const R uw[3] = {u[0] * wq, u[1] * wq, u[2] * wq};
 #pragma unroll
       for (int sp = 0; sp < 6; ++sp) {
         int p, i;
         if (sp < 3) { p = sp; i = sp; } else if (sp == 3) { p = 0; i = 1; } else if (sp == 4) { p = 0; i = 2; } else { p = 1; i = 2; }
-        const R v = (MODE == MODE_TAN) ? (u[p] * ub[i] + ub[p] * u[i])
-                         : (MODE == MODE_LINPART) ? R(0) : u[p] * u[i];
-        sPr[sp * NQ + q] = v * wq;
+        R v;
+        if (MODE == MODE_TAN) {
+          if (sp < 3) {
+            const R h = uw[p] * ub[p];
+            v = h + h;
+          } else {
+            v = uw[p] * ub[i] + ub[p] * uw[i];
+          }
+        } else {
+          v = (MODE == MODE_LINPART) ? R(0) : uw[p] * u[i];
+        }
+        sPr[sp * NQ + q] = v;
       }
     }
     __syncthreads();
