@@ -327,6 +327,83 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b_arg,
   }
 }
 
+// In place D -> D^-1 for small blocks (b <= 64; the coarse levels at P4, b = 40 and 16), one
+// warp per block in its own shared memory, column-major like the blocks in HBM. Gauss-Jordan
+// with partial pivoting by row choice instead of row interchanges: step k takes as pivot row p_k
+// the not yet pivoted row with the largest |A[i][k]| (ties to the lower row), the same pivots as
+// with interchanges, and updates every entry in place (pivot row scaled, column k replaced by
+// -A[i][k] / pivot). That is the in-place inversion of the row-permuted block P A, stored with
+// row k at row p_k, so D^-1[r][c] = X[p_r][j] with p_j = c, read so while writing out. The
+// b^2 entries of a step are dealt to the lanes in order (conflict-free), b^3 multiply-adds in
+// all; eight blocks per CTA.
+constexpr int kGjwWarps = 8;
+
+template <int B>
+__global__ void __launch_bounds__(32 * kGjwWarps) gj_inverse_warp_kernel(int nblk, float* __restrict__ M,
+                                                                         unsigned* status) {
+  static_assert(B >= 1 && B <= 64, "one warp per block of at most 64 rows");
+  constexpr int W = B * B + 2 * B + 2 * B;  // floats per warp: block, column k, pivot row, order (ints)
+  extern __shared__ __align__(16) unsigned char sraw_[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* A = reinterpret_cast<float*>(sraw_) + (size_t)warp * W;
+  float* colk = A + B * B;
+  float* prow = colk + B;
+  int* ord = reinterpret_cast<int*>(prow + B);  // [B] p_k
+  int* inv_ord = ord + B;                        // [B] j with p_j = c
+  for (int blk = blockIdx.x * kGjwWarps + warp; blk < nblk; blk += gridDim.x * kGjwWarps) {
+    float* Mb = M + (size_t)blk * B * B;
+    for (int t = lane; t < B * B; t += 32) A[t] = Mb[t];
+    __syncwarp();
+    unsigned long long used = 0ull;
+    for (int k = 0; k < B; ++k) {
+      float best = -1.0f;
+      int bi = B;
+      for (int i = lane; i < B; i += 32)
+        if (!((used >> i) & 1ull)) {
+          const float v = fabsf(A[k * B + i]);
+          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      const int p = bi;
+      used |= 1ull << p;
+      if (lane == 0) {
+        ord[k] = p;
+        inv_ord[p] = k;
+        if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
+      }
+      const float inv = 1.0f / A[k * B + p];
+      for (int i = lane; i < B; i += 32) colk[i] = A[k * B + i];
+      for (int j = lane; j < B; j += 32) prow[j] = j == k ? inv : A[j * B + p] * inv;
+      __syncwarp();
+      // entry e = j B + i (column-major): i the row, j the column
+      int i = lane % B, j = lane / B;
+#pragma unroll 4
+      for (int e = lane; e < B * B; e += 32) {
+        float nv;
+        if (i == p) nv = prow[j];
+        else if (j == k) nv = -colk[i] * inv;
+        else nv = fmaf(-colk[i], prow[j], A[e]);
+        A[e] = nv;
+        i += 32;
+        j += i / B;
+        i %= B;
+      }
+      __syncwarp();
+    }
+    // D^-1[r][c] = X[p_r][inv_ord[c]]: column-major output entry t = c B + r
+    for (int t = lane; t < B * B; t += 32) {
+      const int c = t / B, r = t - c * B;
+      Mb[t] = A[inv_ord[c] * B + ord[r]];
+    }
+    __syncwarp();
+  }
+}
+
 // Block Jacobi with explicit inverses, x <- (x_zero ? 0 : x) + alpha D_e^-1 (g - Gx)_e (Gx may
 // be null): stages of G consecutive elements, whose inverses (contiguous) arrive by one bulk
 // asynchronous copy into one of two shared-memory buffers while the previous stage is
@@ -945,6 +1022,19 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
 int invert_levels_f32(Handle* h, cudaStream_t st) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
+    if (L.b == 40 || L.b == 16) {  // one warp per block
+      const size_t smem = sizeof(float) * kGjwWarps * (size_t)(L.b * L.b + 4 * L.b);
+      const int grid = std::min((h->ne + kGjwWarps - 1) / kGjwWarps, h->nsm * 4);
+      if (L.b == 40) {
+        DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_warp_kernel<40>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+        gj_inverse_warp_kernel<40><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, h->status);
+      } else {
+        gj_inverse_warp_kernel<16><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, h->status);
+      }
+      DG_LAUNCH_CHECK(h);
+      continue;
+    }
     const size_t smem = sizeof(float) * ((size_t)(L.b + 4) * gj_ld(L.b)) + sizeof(int) * 2 * L.b;
     if (smem > kSmemLimit || L.b % 4 != 0 || L.b > 32 * kGjSlots)
       return fail(h, DG_ERR_ARG, "element block unsuited to the FP32 inverse");
