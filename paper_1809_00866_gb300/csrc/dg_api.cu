@@ -266,6 +266,7 @@ static void free_all(Handle* h) {
   for (int l = 0; l < DG_MAX_LEVELS; ++l) F(h->smV[l]);
   F(h->smSmall);
   F(h->stb1);
+  F(h->stb1f);
   F(h->net);
 }
 

@@ -467,33 +467,30 @@ __global__ void scatter_rows_kernel(int ne, int nb0, int nb1, const int* nbr, co
   }
 }
 
-// dst block (level-l size, nbl modes) += coef * leading sub-block of the level-1 stabilisation
-// block of the same slot (nb1 modes): the rescaled-inherited correction of Appendix A.
+// Inherited coarse blocks (Eq. (GalProj) with a hierarchical orthonormal basis: the leading
+// sub-block of every variable pair), with the rescaling of Appendix A: for the slots
+// s = blockIdx.y of every element block, dst = sub(src) [+ coef * sub(stb)], where stb holds the
+// level-1 stabilisation blocks (nb1 modes per variable) and src the finer blocks (nbs modes);
+// dst2, if given, receives a second copy. src and dst may be the same blocks (an in-place add).
+// One CTA row per slot, 32-bit index arithmetic within a block, arithmetic in R.
 template <class R>
-__global__ void stb_add_kernel(long long nblocks, int nb1, int nbl, const double* stb, long long stb_stride,
-                               double coef, R* dst, long long dst_stride) {
-  const int b1 = 4 * nb1, bl = 4 * nbl;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblocks * bl * bl;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long blk = i / ((long long)bl * bl);
-    const int t = (int)(i - blk * bl * bl), jc = t / bl, rc = t - jc * bl;
-    const int sj = (jc / nbl) * nb1 + jc % nbl, sr = (rc / nbl) * nb1 + rc % nbl;
-    R& d = dst[blk * dst_stride + t];
-    d = R((double)d + coef * stb[blk * stb_stride + (long long)sj * b1 + sr]);
-  }
-}
-
-// dst block (size bd, nbd modes/variable) = leading sub-block of src block (bs, nbs).
-template <class R>
-__global__ void subblock_kernel(long long nblocks, int nbs, int nbd, const R* src, long long src_stride,
-                                R* dst, long long dst_stride) {
-  const int bs = 4 * nbs, bd = 4 * nbd;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblocks * bd * bd;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long blk = i / ((long long)bd * bd);
-    const int rem = (int)(i - blk * bd * bd), c = rem / bd, r = rem - c * bd;
-    const int cs = (c / nbd) * nbs + c % nbd, rs = (r / nbd) * nbs + r % nbd;
-    dst[blk * dst_stride + (long long)c * bd + r] = src[blk * src_stride + (long long)cs * bs + rs];
+__global__ void inherit_kernel(int nblocks, int nbs, const R* src, long long src_blk, long long src_slot, int nbd,
+                               R* dst, long long dst_blk, long long dst_slot, R* dst2, long long dst2_blk,
+                               const R* __restrict__ stb, long long stb_blk, long long stb_slot, int nb1, R coef) {
+  const int bs = 4 * nbs, bd = 4 * nbd, b1 = 4 * nb1, sl = blockIdx.y;
+  for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    const R* sb = src + blk * src_blk + sl * src_slot;
+    const R* tb = stb ? stb + blk * stb_blk + sl * stb_slot : nullptr;
+    R* db = dst + blk * dst_blk + sl * dst_slot;
+    R* d2 = dst2 ? dst2 + blk * dst2_blk : nullptr;
+    for (int t = threadIdx.x; t < bd * bd; t += blockDim.x) {
+      const int c = t / bd, r = t - c * bd;
+      const int cv = c / nbd, cm = c - cv * nbd, rv = r / nbd, rm = r - rv * nbd;
+      R v = sb[(cv * nbs + cm) * bs + rv * nbs + rm];
+      if (tb) v += coef * tb[(cv * nb1 + cm) * b1 + rv * nb1 + rm];
+      db[t] = v;
+      if (d2) d2[t] = v;
+    }
   }
 }
 
@@ -688,7 +685,8 @@ static int alloc_fp32_levels(Handle* h) {
 }
 
 template <class R>
-static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* const* Bsrlev, cudaStream_t st) {
+static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* const* Bsrlev, const R* stb,
+                           cudaStream_t st) {
   const int ne = h->ne;
   const int grid = h->nsm * 8;
   int rc;
@@ -705,38 +703,36 @@ static int assemble_levels(Handle* h, const AsmArgs<R>& a, R* const* Dlev, R* co
   // coarse levels: inherited sub-blocks (taken before the fine blocks are factored in place);
   // with the rescaling of Appendix A, the stabilisation part of level l is weighted by S_0^l
   const int k0 = L0.k, nb1 = h->nlev > 1 ? h->lev[1].nb : 0, b1 = 4 * nb1;
+  const R* sb = h->stb_rescale ? stb : nullptr;
+  const long long s1 = (long long)b1 * b1;
   double s_prev = 1.0;
   for (int l = 1; l < h->nlev; ++l) {
     Level& L = h->lev[l];
-    const size_t bb = (size_t)L.b * L.b;
+    const long long bb = (long long)L.b * L.b;
     const double S = (double)(L.k * (L.k + 3)) / (double)(k0 * (k0 + 3));
-    subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L0.nb, L.nb, Dlev[0], (long long)b0 * b0, Dlev[l], (long long)bb);
+    // diagonal: sub(D_0) [+ (S - 1) sub(stabilisation slot 0)], also slot 0 of the block row
+    inherit_kernel<R><<<dim3(grid, 1), 256, 0, st>>>(ne, L0.nb, Dlev[0], (long long)b0 * b0, 0, L.nb, Dlev[l], bb, 0,
+                                                   Bsrlev[l], bb * 7, sb, s1 * 7, s1, nb1, R(S - 1.0));
     DG_LAUNCH_CHECK(h);
-    if (h->stb_rescale) {
-      stb_add_kernel<R><<<grid, 256, 0, st>>>(ne, nb1, L.nb, h->stb1, (long long)b1 * b1 * 7, S - 1.0, Dlev[l],
-                                              (long long)bb);
+    // off-diagonal slots: level 1's come from the state assembly (the add is in place), level
+    // l >= 2 inherits level l - 1's; level 1 carries S - 1, level l >= 2 adds S - s_prev
+    if (l >= 2 || sb) {
+      const Level& P = h->lev[l == 1 ? 1 : l - 1];
+      const long long pbb = (long long)P.b * P.b;
+      inherit_kernel<R><<<dim3(grid, 6), 256, 0, st>>>(ne, P.nb, Bsrlev[l == 1 ? 1 : l - 1] + pbb, pbb * 7, pbb,
+                                                     L.nb, Bsrlev[l] + bb, bb * 7, bb, nullptr, 0,
+                                                     sb ? sb + s1 : nullptr, s1 * 7, s1, nb1,
+                                                     R(l == 1 ? S - 1.0 : S - s_prev));
       DG_LAUNCH_CHECK(h);
     }
-    subblock_kernel<R><<<grid, 256, 0, st>>>(ne, L.nb, L.nb, Dlev[l], (long long)bb, Bsrlev[l], (long long)bb * 7);
-    DG_LAUNCH_CHECK(h);
-    if (l >= 2) {
-      const Level& P = h->lev[l - 1];
-      for (int s = 1; s < 7; ++s) {
-        subblock_kernel<R><<<grid, 256, 0, st>>>(ne, P.nb, L.nb, Bsrlev[l - 1] + (size_t)s * P.b * P.b,
-                                                 (long long)P.b * P.b * 7, Bsrlev[l] + (size_t)s * bb, (long long)bb * 7);
-        DG_LAUNCH_CHECK(h);
-      }
-    }
-    if (h->stb_rescale)  // off-diagonal slots: level 1 carries S - 1, level l >= 2 inherits s_prev - 1
-      for (int s = 1; s < 7; ++s) {
-        stb_add_kernel<R><<<grid, 256, 0, st>>>(ne, nb1, L.nb, h->stb1 + (size_t)s * b1 * b1, (long long)b1 * b1 * 7,
-                                                l == 1 ? S - 1.0 : S - s_prev, Bsrlev[l] + (size_t)s * bb,
-                                                (long long)bb * 7);
-        DG_LAUNCH_CHECK(h);
-      }
     s_prev = S;
   }
   return DG_OK;
+}
+
+__global__ void narrow_f32_kernel(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 int assemble_all(Handle* h, int precision, cudaStream_t st) {
@@ -783,7 +779,7 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
     double* Dl[DG_MAX_LEVELS];
     double* Bl[DG_MAX_LEVELS];
     for (int l = 0; l < h->nlev; ++l) { Dl[l] = h->lev[l].Dblk; Bl[l] = h->lev[l].Bsr; }
-    if ((rc = assemble_levels<double>(h, a, Dl, Bl, st))) return rc;
+    if ((rc = assemble_levels<double>(h, a, Dl, Bl, h->stb1, st))) return rc;
     for (int l = 0; l < h->nlev; ++l) {
       Level& L = h->lev[l];
       if ((rc = factor_blocks<double>(h, ne, L.b, L.Dblk, L.Dinv, L.perm, st))) return rc;
@@ -807,7 +803,13 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
     float* Dl[DG_MAX_LEVELS];
     float* Bl[DG_MAX_LEVELS];
     for (int l = 0; l < h->nlev; ++l) { Dl[l] = h->lev[l].LUf; Bl[l] = h->lev[l].Bsrf; }
-    if ((rc = assemble_levels<float>(h, a, Dl, Bl, st))) return rc;
+    if (h->stb_rescale && !h->stb1f) {  // an FP32 copy of the stabilisation blocks (fixed per handle)
+      const long long n = 7ll * h->lev[1].b * h->lev[1].b * ne;
+      DG_CUDA(h, cudaMalloc((void**)&h->stb1f, sizeof(float) * n));
+      narrow_f32_kernel<<<h->nsm * 8, 256, 0, st>>>(n, h->stb1, h->stb1f);
+      DG_LAUNCH_CHECK(h);
+    }
+    if ((rc = assemble_levels<float>(h, a, Dl, Bl, h->stb1f, st))) return rc;
     if ((rc = invert_levels_f32(h, st))) return rc;  // the FP32 smoother applies explicit inverses
   }
   DG_CUDA(h, cudaStreamSynchronize(st));

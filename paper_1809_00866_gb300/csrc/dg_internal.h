@@ -164,6 +164,7 @@ struct Handle {
   bool stb_rescale = false;
   bool stb_ready = false;
   double* stb1 = nullptr;
+  float* stb1f = nullptr;       // the same in FP32, for the FP32 assembly
   double inv_gdt = 0.0;
   double* wlin = nullptr;   // [n0]
   double* flin = nullptr;   // [n0] f_h(wlin)
