@@ -41,18 +41,20 @@ struct AsmSmem {
   static constexpr int UB = B + NQ * NB;        // [3][NQ] w_q ubar_c(q)
   static constexpr int U = UB + 3 * NQ;         // [3][NB][NB]
   static constexpr int E = U + 3 * NB * NB;     // [4 j][6 slot][N2][N2] face matrices of one row variable i
-  static constexpr int EO = E + 24 * N2 * N2;   // [6 slot][4 j][N2c][N2c] the same with the other side's columns
-  static constexpr int JQ = EO + 24 * N2C * N2C;  // [2 buffers][2 own/other][6 slot][NQF][4 j] weighted Jacobian entries
+  static constexpr int JQ = E + 24 * N2 * N2;   // [2 buffers][2 own/other][6 slot][NQF][4 j] weighted Jacobian entries
   static constexpr int B2 = JQ + 2 * 2 * 6 * NQF * 4;  // [NQF][N2]
   static constexpr int W2 = B2 + NQF * N2;      // [NQF]
   static constexpr int PVN = W2 + NQF;          // [6 slot][NB] P_hat_a(side) of mode n's exponent along the slot's axis
   static constexpr int SLOT = PVN + 6 * NB;     // [6] scale of the slot's off-diagonal block
-  static constexpr int DOUBLES = SLOT + 6;
+  // last, sized for the coarse degree of the handle (n2c 2D modes): [6 slot][4 j][n2c][n2c] the
+  // face matrices with the other side's columns; the ints follow it
+  static constexpr int EO = SLOT + 6;
+  __host__ __device__ static constexpr int doubles(int n2c) { return EO + 24 * n2c * n2c; }
   static constexpr int FMN = 0;                 // [6 slot][NB] 2D mode of mode n on the slot's face
   static constexpr int PVO = FMN + 6 * NB;      // [6 slot][NB] index of P_hat_a(other side) of mode n (into pv)
   static constexpr int SINFO = PVO + 6 * NB;    // [6][3] face index, neighbour, target slot
   static constexpr int INTS = SINFO + 18;
-  static constexpr size_t bytes() { return sizeof(R) * DOUBLES + sizeof(int) * INTS; }
+  __host__ __device__ static constexpr size_t bytes(int n2c) { return sizeof(R) * doubles(n2c) + sizeof(int) * INTS; }
 };
 
 template <class R>
@@ -92,16 +94,16 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   R* sW2 = sm + L::W2;
   R* PVN = sm + L::PVN;
   R* sScl = sm + L::SLOT;
-  int* ism = reinterpret_cast<int*>(sm + L::DOUBLES);
-  int* FMN = ism + L::FMN;
-  int* PVO = ism + L::PVO;
-  int* SI = ism + L::SINFO;  // per slot: face index, neighbour (-1 at a wall), target block slot
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nb1 = a.nb1, b1 = 4 * nb1;
   // coarse 2D modes: the graded 2D ordering lists the modes of degree <= k_1 first
   int k1 = 0;
   while (nb1 > 0 && nb_of(k1) < nb1) ++k1;
   const int N2c = nb1 > 0 ? (k1 + 1) * (k1 + 2) / 2 : 0;  // <= L::N2C: the coarse degree is below K
+  int* ism = reinterpret_cast<int*>(sm + L::doubles(N2c));
+  int* FMN = ism + L::FMN;
+  int* PVO = ism + L::PVO;
+  int* SI = ism + L::SINFO;  // per slot: face index, neighbour (-1 at a wall), target block slot
   for (int t = tid; t < NQ * NB; t += nt) sB[t] = a.Bvol[t];
   for (int t = tid; t < NQF * N2; t += nt) sB2[t] = a.B2[t];
   for (int t = tid; t < NQF; t += nt) sW2[t] = a.W2[t];
@@ -118,6 +120,8 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
   for (int e = blockIdx.x; e < a.M.ne; e += gridDim.x) {
     const ElemGeom g = elem_geom(a.M, e);
     const R Jd[3] = {R(g.J[0]), R(g.J[1]), R(g.J[2])};
+    // Jd at a run-time index through selects (no local-memory copy of the array)
+    auto jd = [&](int c) { return c == 0 ? Jd[0] : (c == 1 ? Jd[1] : Jd[2]); };
     // the weighted Jacobian entries (i, j) of the six face slots at the face points: the own
     // side's columns (diagonal block) and the other side's (off-diagonal block); buffer i & 1
     auto load_jac = [&](int i) {
@@ -158,7 +162,8 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       if (p >= 0) {
         const ElemGeom gp = elem_geom(a.M, p);
         const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        sc = R((side == 0 ? 1.0 : -1.0) * 0.25 * g.h[t1] * g.h[t2] * g.is * gp.is);
+        auto h3 = [&](int c) { return c == 0 ? g.h[0] : (c == 1 ? g.h[1] : g.h[2]); };  // no local memory
+        sc = R((side == 0 ? 1.0 : -1.0) * 0.25 * h3(t1) * h3(t2) * g.is * gp.is);
       }
       sScl[sl] = sc;
     }
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
               const int o = (j * NB + m) * DW + q;
               cv += a.Dcol_val[o] * sU[(i * NB + a.T.Dcol_idx[o]) * NB + n];
             }
-            v -= Jd[j] * cv;
+            v -= jd(j) * cv;
             if (i == j) {
 #pragma unroll
               for (int pp = 0; pp < 3; ++pp) {
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
             const int o = (dj * NB + m) * DW + q;
             const bool use = vol && (pp == 3 || i == j);
             ui[pp][q] = use ? (ci * NB + a.T.Dcol_idx[o]) * NB : 0;
-            uv[pp][q] = use ? -a.Dcol_val[o] * (pp < 3 ? Jd[pp] : Jd[j]) : R(0);
+            uv[pp][q] = use ? -a.Dcol_val[o] * (pp < 3 ? jd(pp) : jd(j)) : R(0);
           }
         const R shift = R(a.inv_gdt * g.sh);
 #pragma unroll 5
@@ -362,9 +367,15 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
 
 template <int K, class R>
 static int launch_assemble_state(Handle* h, const AsmArgs<R>& a, cudaStream_t st) {
-  const size_t smem = AsmSmem<K, R>::bytes();
+  // the coarse face matrices are sized for the handle's level-1 degree
+  const int n2c = a.nb1 > 0 ? (h->lev[1].k + 1) * (h->lev[1].k + 2) / 2 : 0;
+  const size_t smem = AsmSmem<K, R>::bytes(n2c);
   DG_CUDA(h, cudaFuncSetAttribute(assemble_state_kernel<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = (int)((200 * 1024) / smem);
+  int per_sm = (int)((227 * 1024) / (smem + 1024));  // 1 KB of each CTA's shared memory is reserved
+  int res = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, assemble_state_kernel<K, R>, 256, smem) == cudaSuccess &&
+      res > 0 && res < per_sm)
+    per_sm = res;
   per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
   int grid = h->nsm * per_sm;
   if (grid > h->ne) grid = h->ne;
