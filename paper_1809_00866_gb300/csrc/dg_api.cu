@@ -411,7 +411,7 @@ static int create(const dg_params* p, const std::vector<Box>& boxes, Handle* h) 
       (rc = dalloc(h, &h->wlin, n0)) || (rc = dalloc(h, &h->flin, n0)) || (rc = dalloc(h, &h->fd_w, n0)) ||
       (rc = dalloc(h, &h->fd_f, n0)) || (rc = dalloc(h, &h->ubar, (size_t)ne * 3 * h->tab.nq)) ||
       (rc = dalloc(h, &h->dFlux, (size_t)(3 * ne + h->nbf) * h->tab.nqf * 32)) || (rc = dalloc(h, &h->wnorm2, 1)) ||
-      (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 2)))
+      (rc = dalloc(h, &h->red, 4096)) || (rc = dalloc(h, &h->red_out, 8)) || (rc = dalloc(h, &h->status, 3)))
     return rc;
   if ((rc = dalloc(h, &h->face_out_f, (size_t)ne * 6 * 4 * n2f)) ||
       (rc = dalloc(h, &h->face_lift_f, (size_t)ne * 6 * 3 * n2f)) ||

@@ -596,7 +596,7 @@ static int factor_blocks(Handle* h, int nblk, int b, const R* in, R* out, int* p
   if (per_sm > 8) per_sm = 8;
   int grid = h->nsm * per_sm;
   if (grid > nblk) grid = nblk;
-  lu_factor_kernel<R><<<grid, 256, smem, st>>>(nblk, b, in, out, perm, h->status);
+  lu_factor_kernel<R><<<grid, 256, smem, st>>>(nblk, b, in, out, perm, h->status + 2);
   DG_LAUNCH_CHECK(h);
   return DG_OK;
 }
@@ -746,10 +746,13 @@ __global__ void narrow_f32_kernel(long long n, const double* __restrict__ x, flo
     y[i] = (float)x[i];
 }
 
+__global__ void or_bits_kernel(unsigned* status, unsigned bits) { atomicOr(status, bits); }
+
 int assemble_all(Handle* h, int precision, cudaStream_t st) {
   const int ne = h->ne;
   Level& L0 = h->lev[0];
   int rc;
+  DG_CUDA(h, cudaMemsetAsync(h->status + 2, 0, sizeof(unsigned), st));  // this assembly's own status word
   // the linear part (FP64, mesh only) and the FP64 fine diagonal-block buffer it lives next to
   if (!L0.Dlin) DG_CUDA(h, cudaMalloc((void**)&L0.Dlin, sizeof(double) * (size_t)L0.b * L0.b * ne));
   if (h->nlev > 1 && !h->lev[1].Blin) {
@@ -821,11 +824,17 @@ int assemble_all(Handle* h, int precision, cudaStream_t st) {
       DG_LAUNCH_CHECK(h);
     }
     if ((rc = assemble_levels<float>(h, a, Dl, Bl, h->stb1f, st))) return rc;
-    if ((rc = invert_levels_f32(h, st))) return rc;  // the FP32 smoother applies explicit inverses
+    if ((rc = invert_levels_f32(h, st, h->status + 2))) return rc;  // the FP32 smoother applies explicit inverses
   }
+  // the verdict on this assembly's own status word (flags of earlier calls do not count); its
+  // bits also go to the handle's word, which dg_get_status reads
   DG_CUDA(h, cudaStreamSynchronize(st));
   unsigned s = 0;
-  DG_CUDA(h, cudaMemcpy(&s, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  DG_CUDA(h, cudaMemcpy(&s, h->status + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (s) {
+    or_bits_kernel<<<1, 1, 0, st>>>(h->status, s);
+    DG_LAUNCH_CHECK(h);
+  }
   if (s & DG_STATUS_NONFINITE) return fail(h, DG_ERR_NONFINITE, "singular or non-finite element block");
   return DG_OK;
 }

@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(32 * kGjwWarps) gj_inverse_warp_kernel(int nbl
         const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
-      const int p = bi;
+      // no comparable candidate (a column of NaNs): the lowest unpivoted row, flagged below
+      const int p = bi < B ? bi : __ffsll((long long)~used) - 1;
       used |= 1ull << p;
       if (lane == 0) {
         ord[k] = p;
@@ -1019,7 +1020,7 @@ int bsr16_f(Handle* h, int lvl, int storage, float alpha, const float* x, float 
   return lvl == 1 ? prof_end(h, DG_PROF_BSR32, st, e0, bytes) : DG_OK;
 }
 
-int invert_levels_f32(Handle* h, cudaStream_t st) {
+int invert_levels_f32(Handle* h, cudaStream_t st, unsigned* status) {
   for (int l = 0; l < h->nlev; ++l) {
     const Level& L = h->lev[l];
     if (L.b == 40 || L.b == 16) {  // one warp per block
@@ -1028,9 +1029,9 @@ int invert_levels_f32(Handle* h, cudaStream_t st) {
       if (L.b == 40) {
         DG_CUDA(h, cudaFuncSetAttribute(gj_inverse_warp_kernel<40>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
-        gj_inverse_warp_kernel<40><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, h->status);
+        gj_inverse_warp_kernel<40><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, status);
       } else {
-        gj_inverse_warp_kernel<16><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, h->status);
+        gj_inverse_warp_kernel<16><<<grid, 32 * kGjwWarps, smem, st>>>(h->ne, L.LUf, status);
       }
       DG_LAUNCH_CHECK(h);
       continue;
@@ -1049,9 +1050,9 @@ int invert_levels_f32(Handle* h, cudaStream_t st) {
     const int ng = L.b / 4, active = ng * std::min(L.b, 480 / ng);
     const int threads = std::min(512, 32 + 32 * ((active + 31) / 32));
     if (L.b == 140 && threads == 512)
-      gj_inverse_kernel<140><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
+      gj_inverse_kernel<140><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, status);
     else
-      gj_inverse_kernel<0><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, h->status);
+      gj_inverse_kernel<0><<<grid, threads, smem, st>>>(h->ne, L.b, L.LUf, status);
     DG_LAUNCH_CHECK(h);
   }
   return DG_OK;

@@ -176,7 +176,8 @@ struct Handle {
   double* fd_f = nullptr;
   double* red = nullptr;    // reduction partials
   double* red_out = nullptr;
-  unsigned* status = nullptr;  // device status word
+  unsigned* status = nullptr;  // device status words: [0] the handle's (dg_get_status), [1] the
+                               // linearisation's, [2] the current assembly's
   // Krylov workspace
   int kry_m = 0;
   double* V = nullptr;  // [(m+1)][n0]
@@ -312,7 +313,8 @@ int level_matvec(Handle* h, int lvl, const double* x, double* y, cudaStream_t st
 
 // element-block products streamed through shared memory (dg_blocks.cu). The FP32 cycle keeps
 // explicit inverses in Level::LUf (invert_levels_f32 turns the FP32 blocks held there into them).
-int invert_levels_f32(Handle* h, cudaStream_t st);
+// status: the word the singular-block flags go to (the assembly's own word, or the handle's)
+int invert_levels_f32(Handle* h, cudaStream_t st, unsigned* status);
 int staged_jacobi_f(Handle* h, int lvl, const float* g, const float* Gx, float omega, bool x_zero, float* x,
                     int storage, cudaStream_t st);  // x <- (x_zero ? 0 : x) + omega D^-1 (g - Gx); Gx may be null
 int prepare_blocks16(Handle* h, int storage, cudaStream_t st);  // LUf, Bsrf -> 16-bit copies

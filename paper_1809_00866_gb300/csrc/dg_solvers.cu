@@ -601,7 +601,7 @@ static int prepare_fp32(Handle* h, cudaStream_t st) {
         DG_LAUNCH_CHECK(h);
       }
     }
-    if (int rc2 = invert_levels_f32(h, st)) return rc2;  // the blocks (rounded) -> explicit inverses
+    if (int rc2 = invert_levels_f32(h, st, h->status)) return rc2;  // the blocks (rounded) -> explicit inverses
     h->asm_f_ready = true;
   }
   return DG_OK;
