@@ -83,9 +83,13 @@ BF16_FALLBACK_TFLOPS = 1900.0
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch from Nsight Compute captures of the current kernels, by
 # (profiler class, mesh n, block storage); a kernel changed since its capture has no entry.
-# From one one-pass capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^3 P4 stage
-# with FP16 blocks and 5/5/2 sweeps: the tensor-core volume pass moves 173.6 MB per launch.
-NCU_TRAFFIC = {("vol_tc32", 32, "half"): 1.736e8}
+# One-pass captures (dram__bytes_read.sum + dram__bytes_write.sum) at 32^3 P4: of the chosen
+# stage (FP16 blocks, 5/5/2 sweeps), the fine-level block-Jacobi apply moves 1.320 GB per sweep
+# from zero and 1.357 GB per sweep with G x, one and nine of a cycle's ten fine-level sweeps,
+# 1.353 GB per launch on average; the tensor-core volume pass 173.6 MB; of the exact FP64
+# Jacobian action, the face pass 852.8 MB and the volume pass 330.4 MB.
+NCU_TRAFFIC = {("bj32_fine", 32, "half"): 1.353e9, ("vol_tc32", 32, "half"): 1.736e8,
+               ("face_tan", 32, "half"): 8.528e8, ("vol_tan", 32, "half"): 3.304e8}
 
 
 def measured_peaks():
@@ -839,8 +843,10 @@ def run_ours(args):
     else:
         kname, kms, kflop = "vol_kernel<%d,tangent,double>" % k, vol_ms, fv * dg.ne
     achieved = kflop / (kms / 1e3) / 1e12
+    storage_jv = {"fp32": "float", "h16": "half", "bf16": "bfloat16", "h16tc": "half", "bf16tc": "bfloat16"}.get(args.form)
+    traffic_jv = NCU_TRAFFIC.get(("face_tan" if kname.startswith("face") else "vol_tan", case.cfg["n"], storage_jv))
     roofline_jv = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp64_peak,
-                   "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None, "peak_source": fp64_src,
+                   "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic_jv, "peak_source": fp64_src,
                    "frac_of": "of measured" if fp64_src.startswith("measured") else "of nominal",
                    "flop_per_element": {"face": ff, "vol": fv},
                    "kernel_ms": {"face_tan": face_ms, "vol_tan": vol_ms},
