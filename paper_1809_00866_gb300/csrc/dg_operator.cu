@@ -164,16 +164,19 @@ __device__ __forceinline__ void tang3(double u, double a, double uR, double aR, 
   }
 }
 
-// Exact interface flux of the artificial-compressibility Riemann problem along
-// e_d: F[i] = n.(u(x)u + pI) at the interface state for i < 3, F[3] = u_n*.
-// The two acoustic waves always travel in opposite directions, so the interface
-// state is the star state; the tangential velocity is taken from the side the
-// contact (speed u*) comes from, the two sides averaged when |u*| is within a
-// rounding band of zero. With J != nullptr also the Jacobian J[i][j] with respect
-// to (uL[0..2], pL, uR[0..2], pR).
-__device__ void ac_riemann(const double* uL, double pL, const double* uR, double pR, int d, double c, double* F,
-                           double (*J)[8], unsigned* status, int max_its) {
-  const double ul = uL[d], ur = uR[d], c2 = c * c;
+// Exact interface flux of the artificial-compressibility Riemann problem along the face
+// normal, in the face's frame (n, t1, t2): inputs the normal and the two tangential velocity
+// components and the pressure of each side, outputs F = (n.(u(x)u + pI) along n, t1, t2; u_n*)
+// at the interface state, which is the star state, since the two acoustic waves always travel
+// in opposite directions. The tangential velocity is taken from the side the contact (speed
+// u*) comes from, the two sides averaged when |u*| is within a rounding band of zero. With
+// J != nullptr also the Jacobian J[r][c] of F with respect to (un, t1, t2, p) of the left side
+// (c = 0..3) and of the right side (c = 4..7). Every index is fixed at compile time, so after
+// inlining F and J stay in registers.
+__device__ __forceinline__ void ac_riemann(double ul, double t1l, double t2l, double pL, double ur, double t1r,
+                                           double t2r, double pR, double c, double (&F)[4], double (*J)[8],
+                                           unsigned* status, int max_its) {
+  const double c2 = c * c;
   const double al = sqrt(ul * ul + c2), ar = sqrt(ur * ur + c2);
   const double Al = asinh(ul / c), Ar = asinh(ur / c);
   const double scale = fabs(ul) + fabs(ur) + c;
@@ -215,11 +218,6 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
   wave1(us, as, As, ul, al, Al, pL, c, p1, d1u, d1l);
   wave3(us, as, As, ur, ar, Ar, pR, c, p3, d3u, d3r);
   const double ps = p1;
-  // implicit-function derivatives of u* and p* with respect to (ul, pL, ur, pR)
-  const double iphi = 1.0 / (d1u - d3u);
-  const double dus_ul = -d1l * iphi, dus_pl = -iphi, dus_ur = d3r * iphi, dus_pr = iphi;
-  const double dps_ul = d1u * dus_ul + d1l, dps_pl = d1u * dus_pl + 1.0;
-  const double dps_ur = d1u * dus_ur, dps_pr = d1u * dus_pr;
   // tangential ratios
   double tl, tlu, tll, tr, tru, trr;
   tang1(us, as, ul, al, c, tl, tlu, tll);
@@ -229,38 +227,37 @@ __device__ void ac_riemann(const double* uL, double pL, const double* uR, double
   if (us > band) { wl = 1.0; wr = 0.0; }
   else if (us < -band) { wl = 0.0; wr = 1.0; }
   else { wl = 0.5; wr = 0.5; }
-  F[d] = us * us + ps;
+  const double tL[2] = {t1l, t2l}, tR[2] = {t1r, t2r};
+  F[0] = us * us + ps;
   F[3] = us;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) F[1 + t] = (wl * tL[t] * tl + wr * tR[t] * tr) * us;
   if (J) {
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 8; ++j) J[i][j] = 0.0;
-    // d(u*) row and the normal momentum row
-    const double gus[8] = {0, 0, 0, dus_pl, 0, 0, 0, dus_pr};
-    double du[8], dp[8];
-    for (int j = 0; j < 8; ++j) { du[j] = gus[j]; dp[j] = 0.0; }
-    du[d] = dus_ul; du[4 + d] = dus_ur;
-    dp[d] = dps_ul; dp[3] = dps_pl; dp[4 + d] = dps_ur; dp[7] = dps_pr;
+    // implicit-function derivatives of u* and p* with respect to (ul, pL, ur, pR)
+    const double iphi = 1.0 / (d1u - d3u);
+    const double dus_ul = -d1l * iphi, dus_pl = -iphi, dus_ur = d3r * iphi, dus_pr = iphi;
+    const double dps_ul = d1u * dus_ul + d1l, dps_pl = d1u * dus_pl + 1.0;
+    const double dps_ur = d1u * dus_ur, dps_pr = d1u * dus_pr;
+    const double du[8] = {dus_ul, 0.0, 0.0, dus_pl, dus_ur, 0.0, 0.0, dus_pr};
+    const double dp[8] = {dps_ul, 0.0, 0.0, dps_pl, dps_ur, 0.0, 0.0, dps_pr};
+#pragma unroll
     for (int j = 0; j < 8; ++j) {
       J[3][j] = du[j];
-      J[d][j] = 2.0 * us * du[j] + dp[j];
+      J[0][j] = 2.0 * us * du[j] + dp[j];
     }
-    for (int t = 1; t < 3; ++t) {
-      const int i = (d + t) % 3;
-      const double ut = wl * uL[i] * tl + wr * uR[i] * tr;
-      F[i] = ut * us;
-      // d(ut) = wl (tl duL_i + uL_i (tlu du* + tll dul)) + wr (tr duR_i + uR_i (tru du* + trr dur))
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const double ut = wl * tL[t] * tl + wr * tR[t] * tr;
+      // d(ut) = wl (tl dtL + tL (tlu du* + tll dul)) + wr (tr dtR + tR (tru du* + trr dur))
       double dut[8];
-      for (int j = 0; j < 8; ++j) dut[j] = (wl * uL[i] * tlu + wr * uR[i] * tru) * du[j];
-      dut[d] += wl * uL[i] * tll;
-      dut[4 + d] += wr * uR[i] * trr;
-      dut[i] += wl * tl;
-      dut[4 + i] += wr * tr;
-      for (int j = 0; j < 8; ++j) J[i][j] = us * dut[j] + ut * du[j];
-    }
-  } else {
-    for (int t = 1; t < 3; ++t) {
-      const int i = (d + t) % 3;
-      F[i] = (wl * uL[i] * tl + wr * uR[i] * tr) * us;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) dut[j] = (wl * tL[t] * tlu + wr * tR[t] * tru) * du[j];
+      dut[0] += wl * tL[t] * tll;
+      dut[4] += wr * tR[t] * trr;
+      dut[1 + t] += wl * tl;
+      dut[5 + t] += wr * tr;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) J[1 + t][j] = us * dut[j] + ut * du[j];
     }
   }
 }
@@ -510,16 +507,25 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
           for (int j = 0; j < 8; ++j) acc += Jr[i * 8 + j] * pvq[j];
           Fc[i] = acc;
         }
-      } else if constexpr (MODE == MODE_RES_LIN) {
-        double Jm[4][8];  // residual modes run in FP64 only
-        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, Jm, a.status, a.riemann_its);
-        R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
+      } else if constexpr (MODE == MODE_RES_LIN || MODE == MODE_RES) {
+        // residual modes run in FP64 only. The solve works in the face's frame (n, t1, t2):
+        // components d, t1, t2 of the velocities in, the flux and its Jacobian back to x, y, z
+        auto comp = [&](const R* u, int i) { return i == 0 ? u[0] : (i == 1 ? u[1] : u[2]); };
+        double Fr[4], Jr[4][8];
+        ac_riemann(comp(uL, d), comp(uL, t1), comp(uL, t2), pL, comp(uR, d), comp(uR, t1), comp(uR, t2), pR, a.c,
+                   Fr, MODE == MODE_RES_LIN ? Jr : nullptr, a.status, a.riemann_its);
+        // original component i of a frame row / column r: d, t1, t2, then the pressure (3)
+        auto orig = [&](int r) { return r == 0 ? d : (r == 1 ? t1 : (r == 2 ? t2 : 3)); };
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 3; ++i) Fc[i] = i == d ? Fr[0] : (i == t1 ? Fr[1] : Fr[2]);
+        Fc[3] = Fr[3];
+        if constexpr (MODE == MODE_RES_LIN) {
+          R* Jq = a.dFlux + ((size_t)f * NQF + q) * 32;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) Jq[i * 8 + j] = Jm[i][j];
-      } else if constexpr (MODE == MODE_RES) {
-        ac_riemann(uL, pL, uR, pR, d, a.c, Fc, nullptr, a.status, a.riemann_its);
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) Jq[orig(r) * 8 + (cc >> 2) * 4 + orig(cc & 3)] = Jr[r][cc];
+        }
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) sF[i * NQF + q] = Fc[i] * W2[q];
