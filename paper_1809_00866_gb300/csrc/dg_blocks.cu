@@ -62,34 +62,33 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
 }
 
 // Four elimination steps of the panel whose pivot columns are k0..k0+3, on those columns alone,
-// held in the registers of one warp (lane l holds rows l + 32 m, m < kGjSlots): pivot search
-// over the rows not yet pivoted (ties to the lower row), row interchange by shuffles, in-place
-// elimination. The pivots go to piv[] and pq[].
+// held in the registers of one warp (lane l holds rows l + 32 m, m < kGjSlots, b <= 160): pivot
+// search over the rows not yet pivoted by one warp-wide maximum (ties to the lower row), row
+// interchange by shuffles, in-place elimination. The pivots go to piv[] and pq[].
 __device__ __forceinline__ void gj_factor_panel(float4 (&pv)[kGjSlots], int b, int k0, int lane, int* piv,
                                                 int (&pq)[4], unsigned* status) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int k = k0 + q;
-    float best = -1.0f;
-    int bi = k;
+    // one warp-wide integer maximum over keys |v| (bit pattern, the low 8 mantissa bits
+    // replaced by 255 - row): the largest |v|, ties and values within 2^-15 relative to the
+    // lower row; rows not eligible have key 0
+    unsigned key = 0u;
 #pragma unroll
     for (int m = 0; m < kGjSlots; ++m) {
       const int i = lane + 32 * m;
       if (i >= k && i < b) {
-        const float v = fabsf(f4get(pv[m], q));
-        if (v > best) { best = v; bi = i; }
+        const unsigned kv = (__float_as_uint(fabsf(f4get(pv[m], q))) & 0xffffff00u) | (unsigned)(255 - i);
+        key = kv > key ? kv : key;
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ov = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    const int p = __shfl_sync(0xffffffffu, bi, 0);
-    best = __shfl_sync(0xffffffffu, best, 0);
+    key = __reduce_max_sync(0xffffffffu, key);
+    const int p = 255 - (int)(key & 0xffu);
     pq[q] = p;
     if (lane == 0) {
       piv[k] = p;
+      // a zero (or NaN, whose key exceeds every finite one) pivot
+      const float best = __uint_as_float(key & 0xffffff00u);
       if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
     }
     // interchange rows k and p: each lane offers its slot's value, the owners exchange
@@ -330,8 +329,8 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b_arg,
 // In place D -> D^-1 for small blocks (b <= 64; the coarse levels at P4, b = 40 and 16), one
 // warp per block in its own shared memory, column-major like the blocks in HBM. Gauss-Jordan
 // with partial pivoting by row choice instead of row interchanges: step k takes as pivot row p_k
-// the not yet pivoted row with the largest |A[i][k]| (ties to the lower row), the same pivots as
-// with interchanges, and updates every entry in place (pivot row scaled, column k replaced by
+// the not yet pivoted row with the largest |A[i][k]| (ties, and values within 2^-15 relative,
+// to the lower row), and updates every entry in place (pivot row scaled, column k replaced by
 // -A[i][k] / pivot). That is the in-place inversion of the row-permuted block P A, stored with
 // row k at row p_k, so D^-1[r][c] = X[p_r][j] with p_j = c, read so while writing out. The
 // b^2 entries of a step are dealt to the lanes in order (conflict-free), b^3 multiply-adds in
@@ -356,25 +355,22 @@ __global__ void __launch_bounds__(32 * kGjwWarps) gj_inverse_warp_kernel(int nbl
     __syncwarp();
     unsigned long long used = 0ull;
     for (int k = 0; k < B; ++k) {
-      float best = -1.0f;
-      int bi = B;
+      // one warp-wide integer maximum over keys |A[i][k]| (bit pattern, the low 8 mantissa bits
+      // replaced by 255 - i) of the rows not yet pivoted: the largest, ties and values within
+      // 2^-15 relative to the lower row; a NaN's key exceeds every finite one
+      unsigned key = 0u;
       for (int i = lane; i < B; i += 32)
         if (!((used >> i) & 1ull)) {
-          const float v = fabsf(A[k * B + i]);
-          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+          const unsigned kv = (__float_as_uint(fabsf(A[k * B + i])) & 0xffffff00u) | (unsigned)(255 - i);
+          key = kv > key ? kv : key;
         }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      // no comparable candidate (a column of NaNs): the lowest unpivoted row, flagged below
-      const int p = bi < B ? bi : __ffsll((long long)~used) - 1;
+      key = __reduce_max_sync(0xffffffffu, key);
+      const int p = key ? 255 - (int)(key & 0xffu) : __ffsll((long long)~used) - 1;
       used |= 1ull << p;
       if (lane == 0) {
         ord[k] = p;
         inv_ord[p] = k;
+        const float best = __uint_as_float(key & 0xffffff00u);
         if (!(best > 0.0f) && status) atomicOr(status, (unsigned)DG_STATUS_NONFINITE);
       }
       const float inv = 1.0f / A[k * B + p];
