@@ -188,40 +188,57 @@ __global__ void __launch_bounds__(256) assemble_state_kernel(AsmArgs<R> a) {
       }
     }
     for (int i = 0; i < 4; ++i) {
-      // face matrices of row variable i: E[j][sl] = sum_q w_q dF_ij(q) B2[q][j1] B2[q][j2]: one
-      // thread per 2D mode pair, all 4 j and 6 slots (the four j of a point are one vector);
-      // the threads after them form the other side's matrices for the coarse 2D modes
+      // face matrices of row variable i: E[j][sl] = sum_q w_q dF_ij(q) B2[q][j1] B2[q][j2], symmetric
+      // in (j1, j2): threads [0, ntE) take one 2D mode pair j1 <= j2 each (all 4 j and 6 slots;
+      // the four j of a point are one vector) and write both halves; the threads after them
+      // form the other side's matrices for the coarse 2D modes, symmetric as well
       const R* Jo = sJ + (i & 1) * 2 * 6 * NQF * 4;  // own columns [6][NQF][4]
       const R* Jx = Jo + 6 * NQF * 4;                 // other side's columns
-      for (int t = tid; t < N2 * N2; t += nt) {
-        const int j1 = t / N2, j2 = t - j1 * N2;
-        R acc[4][6];
+      constexpr int NPE = N2 * (N2 + 1) / 2;
+      const int ntE = NPE < nt - 32 ? NPE : nt - 32;
+      const int NPc = N2c * (N2c + 1) / 2;
+      if (tid < ntE) {
+        for (int t = tid; t < NPE; t += ntE) {
+          int j1 = 0, r = t;
+          while (r >= N2 - j1) { r -= N2 - j1; ++j1; }
+          const int j2 = j1 + r;
+          R acc[4][6];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+          for (int j = 0; j < 4; ++j)
 #pragma unroll
-          for (int sl = 0; sl < 6; ++sl) acc[j][sl] = R(0);
+            for (int sl = 0; sl < 6; ++sl) acc[j][sl] = R(0);
 #pragma unroll 5
-        for (int q = 0; q < NQF; ++q) {
-          const R bb = sB2[q * N2 + j1] * sB2[q * N2 + j2];
+          for (int q = 0; q < NQF; ++q) {
+            const R bb = sB2[q * N2 + j1] * sB2[q * N2 + j2];
 #pragma unroll
-          for (int sl = 0; sl < 6; ++sl) {
-            const R* jv = Jo + (sl * NQF + q) * 4;
+            for (int sl = 0; sl < 6; ++sl) {
+              const R* jv = Jo + (sl * NQF + q) * 4;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j][sl] += jv[j] * bb;
+              for (int j = 0; j < 4; ++j) acc[j][sl] += jv[j] * bb;
+            }
           }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int sl = 0; sl < 6; ++sl) {
+              R* Ejs = sE + (j * 6 + sl) * N2 * N2;
+              Ejs[j1 * N2 + j2] = acc[j][sl];
+              Ejs[j2 * N2 + j1] = acc[j][sl];
+            }
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int sl = 0; sl < 6; ++sl) sE[(j * 6 + sl) * N2 * N2 + t] = acc[j][sl];
-      }
-      for (int t = tid; t < 6 * 4 * N2c * N2c; t += nt) {
-        const int sl = t / (4 * N2c * N2c), r = t - sl * 4 * N2c * N2c, j = r / (N2c * N2c), pr = r - j * N2c * N2c;
-        const int j1 = pr / N2c, j2 = pr - j1 * N2c;
-        R acc = R(0);
+      } else {
+        for (int t = tid - ntE; t < 6 * 4 * NPc; t += nt - ntE) {
+          const int sl = t / (4 * NPc), r0 = t - sl * 4 * NPc, j = r0 / NPc;
+          int j1 = 0, r = r0 - j * NPc;
+          while (r >= N2c - j1) { r -= N2c - j1; ++j1; }
+          const int j2 = j1 + r;
+          R acc = R(0);
 #pragma unroll 5
-        for (int q = 0; q < NQF; ++q) acc += Jx[(sl * NQF + q) * 4 + j] * (sB2[q * N2 + j1] * sB2[q * N2 + j2]);
-        sEo[((sl * 4 + j) * N2c + j1) * N2c + j2] = acc;
+          for (int q = 0; q < NQF; ++q) acc += Jx[(sl * NQF + q) * 4 + j] * (sB2[q * N2 + j1] * sB2[q * N2 + j2]);
+          R* Eo = sEo + (sl * 4 + j) * N2c * N2c;
+          Eo[j1 * N2c + j2] = acc;
+          Eo[j2 * N2c + j1] = acc;
+        }
       }
       __syncthreads();
       if (i < 3) load_jac(i + 1);  // the other buffer, read after the next barrier
