@@ -162,6 +162,30 @@ __device__ __forceinline__ void gj_interchange(float* A, float* Rp, int LD, int 
   }
 }
 
+// The same for panel g with one thread per column (t < 4 NG, column t of group t / 4), the
+// panel's pivots read from piv[]: the interchanges of a column in panel order, then its pivot
+// rows to Rp and zero.
+__device__ __forceinline__ void gj_interchange_cols(float* A, float* Rp, int LD, int NG, int g, const int* piv,
+                                                    int t) {
+  const int j = t >> 2, k0 = 4 * g;
+  if (t >= 4 * NG || j == g) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = k0 + q, p = piv[k];
+    if (p != k) {
+      const float a = A[(size_t)k * LD + t], b2 = A[(size_t)p * LD + t];
+      A[(size_t)k * LD + t] = b2;
+      A[(size_t)p * LD + t] = a;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float* ak = A + (size_t)(k0 + q) * LD + t;
+    Rp[q * LD + t] = *ak;
+    *ak = 0.0f;
+  }
+}
+
 // v + t0 r0 + t1 r1 + t2 r2 + t3 r3 on four columns
 __device__ __forceinline__ float4 gj_rank4(float4 v, const float4& t, const float4& r0, const float4& r1,
                                            const float4& r2, const float4& r3) {
@@ -299,8 +323,8 @@ __global__ void __launch_bounds__(512, 2) gj_inverse_kernel(int nblk, int b_arg,
         }
       }
       __syncthreads();
-      if (next) {
-        if (tid < 32) gj_interchange(A, Rp, LD, NG, g + 1, pq, lane);
+      if (next) {  // the next panel's interchanges on the other groups, one thread per column
+        gj_interchange_cols(A, Rp, LD, NG, g + 1, piv, tid);
         __syncthreads();
       }
     }
