@@ -559,8 +559,16 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       sP[t] = acc;
     }
     __syncwarp();
-    // viscous face flux in 2D modal space, total flux, lifting; one lane per 2D mode
-    for (int j = lane; j < N2; j += 32) {
+    // viscous face flux in 2D modal space, total flux, lifting: two lanes per 2D mode j (lane j
+    // and lane j + 16). The first forms the tangential derivatives of the normal component and
+    // writes the - side's (element e0's) slot, the second those of the tangential components
+    // and writes the + side's; they swap their derivatives by one shuffle. Every lane of the
+    // warp takes part in the shuffle; lanes past the last mode compute on mode 0 and store nothing.
+    static_assert(N2 <= 16, "two lanes per 2D mode");
+    {
+      const int half = lane >> 4, j0 = lane & 15;
+      const bool act = j0 < N2;
+      const int j = act ? j0 : 0;
       // trace of variable v on side s at 2D mode jj
       auto tr = [&](int s2, int v, int jj) { return sT[jj * 8 + s2 * 4 + v]; };
       // {r^s} of the normal gradient component, 2D mode j of total degree bj:
@@ -589,13 +597,16 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
         return acc;
       };
       const R it1 = J0t1, it2 = J0t2;
-      // tangential derivatives: the average of both sides, or the real side's at a wall
+      // tangential derivatives: the average of both sides, or the real side's at a wall; the
+      // first lane of a mode: Ghat[d][t1], Ghat[d][t2]; the second: Ghat[t1][t1], Ghat[t2][t2]
       const int A0 = wall == 2 ? 1 : 0;
       const int A1 = wall == 1 ? 0 : 1;
-      const R Gdt1 = R(0.5) * (tder(A0, d, 0) + tder(A1, d, 0)) * it1;    // Ghat[d][t1]
-      const R Gdt2 = R(0.5) * (tder(A0, d, 1) + tder(A1, d, 1)) * it2;    // Ghat[d][t2]
-      const R Gt1 = R(0.5) * (tder(A0, t1, 0) + tder(A1, t1, 0)) * it1;   // Ghat[t1][t1]
-      const R Gt2 = R(0.5) * (tder(A0, t2, 1) + tder(A1, t2, 1)) * it2;   // Ghat[t2][t2]
+      const int va = half ? t1 : d, vb = half ? t2 : d;
+      const R x0 = R(0.5) * (tder(A0, va, 0) + tder(A1, va, 0)) * it1;
+      const R x1 = R(0.5) * (tder(A0, vb, 1) + tder(A1, vb, 1)) * it2;
+      const R y0 = __shfl_xor_sync(0xffffffffu, x0, 16), y1 = __shfl_xor_sync(0xffffffffu, x1, 16);
+      const R Gdt1 = half ? y0 : x0, Gdt2 = half ? y1 : x1;  // Ghat[d][t1], Ghat[d][t2]
+      const R Gt1 = half ? x0 : y0, Gt2 = half ? x1 : y1;    // Ghat[t1][t1], Ghat[t2][t2]
       // Ghat[c][d] of the components along d, t1, t2 (selects: no run-time array indexing)
       auto pick = [&](int c) { return c == 0 ? Gd[0] : (c == 1 ? Gd[1] : Gd[2]); };
       const R Gdd = pick(d), Gt1d = pick(t1), Gt2d = pick(t2);
@@ -611,7 +622,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
       }
       Fn[3] = A4 * sP[3 * N2 + j];
       const R lw = wall ? R(1) : R(0.5);  // share of the lifting on each real side
-      if (wall != 2) {
+      if (act && half == 0 && wall != 2) {
         R* o0 = a.face_out + ((size_t)e0 * 6 + 2 * d + 1) * 4 * N2;
         R* l0 = a.face_lift + ((size_t)e0 * 6 + 2 * d + 1) * 3 * N2;
 #pragma unroll
@@ -619,7 +630,7 @@ __global__ void __launch_bounds__(32 * FW) face_kernel(OpArgsT<R> a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) l0[c * N2 + j] = lw * A4 * is0 * jump[c];
       }
-      if (wall != 1) {
+      if (act && half == 1 && wall != 1) {
         R* o1 = a.face_out + ((size_t)e1 * 6 + 2 * d) * 4 * N2;
         R* l1 = a.face_lift + ((size_t)e1 * 6 + 2 * d) * 3 * N2;
 #pragma unroll
