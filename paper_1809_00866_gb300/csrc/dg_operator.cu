@@ -789,15 +789,16 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   #pragma unroll
         for (int q = 0; q < N1; ++q) sT1[(fl * N2 + pi) * N1 + q] = o[q];
       }
-    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy; the field is the
+              // fastest index, so a warp's items share the pair (a, b) and the sum's length
       for (int t = tid; t < 3 * N2 * N1; t += nt) {
-        const int fl = t / (N2 * N1), r = t - fl * N2 * N1, pi = r / N1, q2 = r - pi * N1;
+        const int fl = t % 3, r = t / 3, pi = r / N1, q2 = r - pi * N1;
         const int pa = PAB[2 * pi], pb = PAB[2 * pi + 1];
         const R* c = sC + fl * NB;
         R acc = R(0);
         const int* row = IDX3 + (pa * K1 + pb) * K1;
         for (int cc = 0; cc <= K - pa - pb; ++cc) acc += c[row[cc]] * L1[cc * N1 + q2];
-        sT1[t] = acc;
+        sT1[(fl * N2 + pi) * N1 + q2] = acc;
       }
     }
     __syncthreads();
@@ -830,13 +831,14 @@ __global__ void __launch_bounds__(256) vol_kernel(OpArgsT<R> a) {
   #pragma unroll
         for (int q1 = 0; q1 < N1; ++q1) sT2[((fl * K1 + pa) * N1 + q1) * N1 + q2] = o[q1];
       }
-    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy
+    } else {  // FP64 (pipe-bound): one output per item keeps more threads busy; the field is the
+              // fastest index, so a warp's items share a and the sum's length
       for (int t = tid; t < 3 * K1 * N1 * N1; t += nt) {
-        const int fl = t / (K1 * N1 * N1), r = t - fl * K1 * N1 * N1, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
+        const int fl = t % 3, r = t / 3, pa = r / (N1 * N1), r2 = r - pa * N1 * N1;
         const int q1 = r2 / N1, q2 = r2 - q1 * N1;
         R acc = R(0);
         for (int pb = 0; pb <= K - pa; ++pb) acc += sT1[fl * N2 * N1 + PIDX[pa * K1 + pb] * N1 + q2] * L1[pb * N1 + q1];
-        sT2[t] = acc;
+        sT2[fl * K1 * N1 * N1 + r] = acc;
       }
     }
     __syncthreads();
