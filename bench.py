@@ -83,13 +83,12 @@ BF16_FALLBACK_TFLOPS = 1900.0
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch from Nsight Compute captures of the current kernels, by
 # (profiler class, mesh n, block storage); a kernel changed since its capture has no entry.
-# One-pass captures (dram__bytes_read.sum + dram__bytes_write.sum) at 32^3 P4: of the chosen
-# stage (FP16 blocks, 5/5/2 sweeps), the fine-level block-Jacobi apply moves 1.320 GB per sweep
-# from zero and 1.357 GB per sweep with G x, one and nine of a cycle's ten fine-level sweeps,
-# 1.353 GB per launch on average; the tensor-core volume pass 173.6 MB; of the exact FP64
-# Jacobian action, the face pass 852.8 MB and the volume pass 330.4 MB.
-NCU_TRAFFIC = {("bj32_fine", 32, "half"): 1.353e9, ("vol_tc32", 32, "half"): 1.736e8,
-               ("face_tan", 32, "half"): 8.528e8, ("vol_tan", 32, "half"): 3.304e8}
+# One-pass captures (dram__bytes_read.sum + dram__bytes_write.sum) of the chosen stage at 32^3 P4
+# (FP16 blocks, 5/5/2 sweeps): the fine-level block-Jacobi apply moves 1.320 GB per sweep from
+# zero and 1.357 GB per sweep with G x, one and nine of a cycle's ten fine-level sweeps, 1.353 GB
+# per launch on average; the tensor-core volume pass 173.6 MB. (The FP64 face and volume passes
+# changed after their capture.)
+NCU_TRAFFIC = {("bj32_fine", 32, "half"): 1.353e9, ("vol_tc32", 32, "half"): 1.736e8}
 
 
 def measured_peaks():
