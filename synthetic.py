@@ -179,6 +179,34 @@ def _channel_curl(md, x, y, z):
     return np.stack([d[2, 1] - d[1, 2], d[0, 2] - d[2, 0], d[1, 0] - d[0, 1]])
 
 
+def box_noise_field(x, y, z, seed, amp=0.05, modes=8):
+    """Seeded smooth perturbation of the periodic box [0, 2 pi]^3 at points (arrays of equal
+    shape): amp times a unit-rms divergence-free velocity, the curl of a vector potential with
+    `modes` seeded Fourier modes per component (integer wavenumbers 1..3 per axis, seeded
+    phases and amplitudes); zero pressure. Returns (u, v, w, p)."""
+    rng = np.random.default_rng(seed)
+    kk = rng.integers(1, 4, size=(3, modes, 3)).astype(float)
+    ph = rng.uniform(0.0, TWO_PI, size=(3, modes))
+    aa = rng.standard_normal((3, modes))
+
+    def curl(X, Y, Z):
+        d = np.zeros((3, 3) + np.shape(X))  # d[i, j] = d psi_i / d x_j
+        for i in range(3):
+            for m in range(modes):
+                kx, ky, kz = kk[i, m]
+                sn = np.sin(kx * X + ky * Y + kz * Z + ph[i, m]) * aa[i, m]
+                d[i, 0] += kx * sn
+                d[i, 1] += ky * sn
+                d[i, 2] += kz * sn
+        return np.stack([d[2, 1] - d[1, 2], d[0, 2] - d[2, 0], d[1, 0] - d[0, 1]])
+
+    g = np.linspace(0.0, TWO_PI, 17)[:-1]
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    rms = math.sqrt(np.mean(np.sum(curl(X, Y, Z) ** 2, axis=0)))
+    up = curl(x, y, z) * (amp / rms)
+    return up[0], up[1], up[2], 0.0 * np.asarray(x)
+
+
 def channel_nu(re_tau=180.0, u_center=1.0):
     """Viscosity for which the laminar profile u_c (1 - y^2) has friction Reynolds number re_tau
     (half-height 1): u_tau^2 = nu |du/dy|_wall = 2 nu u_c, re_tau = u_tau / nu."""

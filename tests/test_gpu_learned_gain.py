@@ -11,8 +11,9 @@ CFL 50), then judged on later states it has not seen.
    decides the outer count, and the network's cycle is within a few iterations either way).
 2. 32^3 P4, levels 4-2-1, the benchmark's chosen cycle (FP32 with FP16 block storage and
    tensor-core volume contractions, omega 0.95, 4/4/2 sweeps), network trained on the first
-   stages of the Taylor-Green run and judged on the two states after them, which training never
-   saw: the network leaves less of the coarse residual than the two
+   stages of the Taylor-Green run and judged on states from seeds training never saw (the field
+   plus a seeded smooth divergence-free perturbation): the network leaves less of the coarse
+   residual than the two
    block-Jacobi sweeps it replaces, and the outer solves converge without falling back. The
    outer FGMRES iterations and wall times with and without it are printed, not asserted: with
    this cycle the fine-level smoothing decides the outer count, and no wall-time gain exists
@@ -128,15 +129,18 @@ def test_learned_coarse_correction_held_out_32():
     dg.dg_assemble()
     theta, rep = Lrn.train_residual(dg, D, steps=2000, lr=1e-3, seed=0)
     dg.dg_set_coarse_network(theta)
-    # held out: the next two states of the run, which training never saw (seeded modal noise on
-    # the field is no stand-in at this mesh: with amplitude 0.005 or more no form of the solver
-    # reaches 1e-8 in 100 iterations, the plain FP64 one included)
-    held, prev = [], states[-1]
-    for _ in range(2):
-        x, info, rc, _ = stage(prev, opts())
-        assert rc == P.DG_OK
-        prev = (prev + x).contiguous()
-        held.append(prev)
+    # held out: the field plus a seeded smooth divergence-free perturbation (seeds 11 and 12,
+    # 5 % of the field's peak speed), projected on the handle's Gauss points. (Seeded noise on
+    # every modal coefficient is no stand-in at this mesh: with amplitude 0.005 or more no form
+    # of the solver reaches 1e-8 in 100 iterations, the plain FP64 one included.)
+    xyz = dg.dg_quad_points().cpu().numpy()
+    held = []
+    for seed in (11, 12):
+        vals = np.ascontiguousarray(np.stack(S.box_noise_field(xyz[..., 0], xyz[..., 1], xyz[..., 2], seed),
+                                             axis=1))
+        dw = dg.empty()
+        dg.dg_project_points(torch.from_numpy(vals).cuda(), dw)
+        held.append((w + dw).contiguous())
     # coarse level: the network against the two block-Jacobi sweeps it replaces, on held-out data
     Dv = Lrn.collect_rhs(dg, held, inv, opts(), per_state=8)
     dg.dg_set_coarse_network(theta)
@@ -156,7 +160,7 @@ def test_learned_coarse_correction_held_out_32():
         _, i1, rc1, t1 = stage(wh, opts(coarse_solver=P.DG_COARSE_LEARNED, fallback_its=5, fallback_rho=0.8))
         assert rc0 == P.DG_OK and rc1 == P.DG_OK and i1.fallback_at == -1
         its[k], secs[k] = (i0.its, i1.its), (round(t0, 4), round(t1, 4))
-    print("32^3 P4, held-out states 4 and 5: coarse residual ratio network %.3f vs 2 block-Jacobi sweeps %.3f; "
+    print("32^3 P4, held-out seeded states: coarse residual ratio network %.3f vs 2 block-Jacobi sweeps %.3f; "
           "FGMRES its (without, with) %s; solve seconds (without, with) %s; training %.2f s"
           % (r_net, r_jac, its, secs, rep["train_s"]))
     assert r_net < 0.9 * r_jac
